@@ -1,0 +1,291 @@
+/*
+ * ncl_kkt.h -- C ABI of the GB300 sparse LDL^T library for the KKT systems
+ * of Algorithm NCL (MadNCL, arXiv 2510.05885).
+ *
+ * The library factors and solves, on one GPU, the two regular forms of the
+ * NCL Newton system derived in Section 3 of the paper:
+ *
+ *   stabilized (Section 3.2, Eq. K2r), dimension n+m:
+ *       [ H + Sigma + delta I    J^T       ] [u]   [f]
+ *       [ J                     -rho^-1 I  ] [v] = [g]
+ *   condensed (Section 3.3, Eq. K1), dimension n:
+ *       K = H + Sigma + delta I + rho J^T J
+ *
+ * by a supernodal multifrontal LDL^T with D diagonal and static pivoting
+ * (Section 3.1, "Sparse LDL^T factorization"): any symmetric permutation of a
+ * symmetric quasi-definite matrix has such a factorisation (Section 3.2), so
+ * the ordering is free to minimise fill.  A pivot with |d| <= pivot_eps is
+ * replaced by +-pivot_eps, the sign being that of the block (primal +,
+ * dual -) the index belongs to before reordering (Section 3.1 case (ii);
+ * eps = 1e-10 in Section 4.3), and the solution of the unperturbed system
+ * is recovered by iterative refinement (Section 4.3).  The inertia of the
+ * factored matrix is returned; (n, m, 0) for K2r and (n, 0, 0) for K are
+ * equivalent to a correct inertia of the full system K2 (Section 3.4).
+ *
+ * The caller passes rho as one scalar: -1/rho goes in the dual block of
+ * K2r, +rho multiplies J^T J in K.  (The paper writes rho-hat = rho + delta
+ * there; a caller following it passes rho-hat.)
+ *
+ * Conventions shared by every entry point
+ *   - Pattern arrays (CSR row pointers and column indices) are HOST memory.
+ *     Value arrays, right-hand sides and solutions are DEVICE memory, FP64.
+ *   - H is passed as its lower triangle by rows (column <= row), column
+ *     indices sorted and unique within each row; each off-diagonal value
+ *     stands for both (i,j) and (j,i).  The diagonal of H may be absent
+ *     (Sigma + delta is always on the diagonal).
+ *   - J is m x n CSR, column indices sorted and unique within each row.
+ *   - Value arrays follow the order of the pattern given to analyze.
+ *   - Multi-RHS blocks are column-major: column k of B starts at B + k*ldb.
+ *   - The caller owns every buffer it passes; the handle owns the plan, the
+ *     factors and all workspace.  Nothing is retained after a call returns.
+ *   - Errors are status codes; nothing is thrown across the ABI.  On error
+ *     ncl_kkt_last_error() returns a message for the calling thread.
+ *   - A handle is used by one host thread at a time, and all its work is
+ *     issued on the stream passed to each call (NULL = the legacy default
+ *     stream).  Calls return after their work is complete.
+ */
+#ifndef NCL_KKT_H
+#define NCL_KKT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ncl_kkt_s* ncl_kkt_t;   /* opaque handle: plan + factors */
+typedef void* ncl_stream_t;            /* a cudaStream_t */
+
+typedef enum {
+    NCL_KKT_STABILIZED = 0,   /* K2r, Section 3.2 */
+    NCL_KKT_CONDENSED = 1     /* K1,  Section 3.3 */
+} ncl_kkt_form;
+
+typedef enum {
+    NCL_PREC_FP64 = 0,        /* factor and solve in FP64 */
+    NCL_PREC_FP32_IR = 1      /* FP32 factor (split-TF32 tensor-core updates),
+                                 FP64 residual and refinement */
+} ncl_kkt_prec;
+
+typedef enum {
+    NCL_PIVOT_PERTURB = 0,    /* Section 3.1 case (ii): replace by +-eps, go on */
+    NCL_PIVOT_STOP = 1        /* Section 3.1 case (i): report the tiny pivots
+                                 as zero eigenvalues and NCL_ERR_ZERO_PIVOT */
+} ncl_pivot_policy;
+
+typedef enum {
+    NCL_OK = 0,
+    NCL_ERR_INVALID_ARG = 1,      /* NULL pointer, negative size, bad enum */
+    NCL_ERR_PATTERN = 2,          /* unsorted / out-of-range / upper-triangle index */
+    NCL_ERR_OOM = 3,              /* device or host allocation failed, or over
+                                     options.max_device_bytes */
+    NCL_ERR_CUDA = 4,             /* a CUDA call failed (message has the code) */
+    NCL_ERR_STATE = 5,            /* solve/adjoint before a successful factor */
+    NCL_ERR_ZERO_PIVOT = 6,       /* policy STOP and a pivot with |d| <= eps */
+    NCL_ERR_NUMERIC = 7,          /* a NaN or Inf pivot or solution */
+    NCL_ERR_IR_NOT_CONVERGED = 8, /* refinement reached ir_max_iter above ir_tol;
+                                     the best iterate is still returned */
+    NCL_ERR_TIMEOUT = 9           /* a bounded device wait ran out */
+} ncl_status;
+
+typedef struct {
+    int32_t prec;             /* ncl_kkt_prec, default NCL_PREC_FP32_IR */
+    int32_t pivot_policy;     /* ncl_pivot_policy, default PERTURB */
+    double pivot_eps;         /* default 1e-10 (Section 4.3) */
+    double ir_tol;            /* target normwise backward error
+                                 ||b-Kx||_inf/(||K||_inf||x||_inf+||b||_inf);
+                                 <= 0 selects 1e-10 (FP32_IR) or 1e-12 (FP64) */
+    int32_t ir_max_iter;      /* refinement steps; < 0 selects 10 (FP32_IR) or 3 (FP64) */
+    int32_t use_fgmres;       /* 1: FGMRES-IR when Richardson stagnates (default 1) */
+    int32_t use_tensor_cores; /* 1: tcgen05 split-TF32 updates in FP32_IR (default 1) */
+    int32_t leaf_size;        /* nested-dissection leaf size (default 96) */
+    int32_t host_only;        /* 1: symbolic analysis only, no device memory; the
+                                 handle then answers only the get_* queries */
+    int64_t max_device_bytes; /* 0 = no limit */
+} ncl_kkt_options;
+
+typedef struct {
+    int64_t n_pos, n_neg, n_zero;  /* inertia of the factored matrix */
+    int64_t n_perturbed;           /* pivots replaced by +-eps */
+    int64_t nnz_L;                 /* strictly-lower nonzeros of L (no padding) */
+    double flops;                  /* sum_j (c_j^2 + 3 c_j), c_j = nnz of column j of L
+                                      below the diagonal */
+    float ms;                      /* device time of the call */
+} ncl_kkt_factor_info;
+
+typedef struct {
+    int32_t ir_iters;              /* refinement steps taken */
+    int32_t used_fgmres;           /* 1 if the FGMRES fallback ran */
+    double backward_err;           /* final normwise backward error (max over RHS) */
+    float ms;                      /* device time of the call */
+} ncl_kkt_solve_info;
+
+typedef struct {
+    int64_t dim;                   /* n+m (K2r) or n (K), summed over instances */
+    int64_t nnz_A;                 /* lower-triangle nonzeros of the KKT matrix */
+    int64_t nnz_L;                 /* strictly-lower nonzeros of L (no padding) */
+    int64_t nnz_L_stored;          /* stored factor entries incl. supernode padding */
+    int64_t update_entries;        /* stored multifrontal update-matrix entries */
+    int64_t n_supernodes, n_levels, max_front, max_pivots;
+    int64_t device_bytes;          /* device memory held by the handle */
+    double flops;                  /* algorithmic factorisation flops */
+    double analyze_ms;             /* host time of analyze */
+} ncl_kkt_analysis_info;
+
+/* Fill *opt with the defaults listed above. */
+void ncl_kkt_default_options(ncl_kkt_options* opt);
+
+/*
+ * ncl_kkt_analyze -- symbolic phase, once per pattern (the paper reuses the
+ * symbolic factorisation across Newton steps, Section 4.1).
+ *   form       ncl_kkt_form
+ *   n, m       primal / dual sizes (m may be 0)
+ *   H_rowptr   host int32[n+1], H_colind host int32[H_rowptr[n]] (lower, sorted)
+ *   J_rowptr   host int32[m+1], J_colind host int32[J_rowptr[m]] (sorted)
+ *   opt        NULL for defaults
+ *   out        receives the handle
+ * Builds the KKT pattern, a nested-dissection ordering, the elimination
+ * tree, relaxed supernodes and the multifrontal schedule, and allocates all
+ * device memory the numeric phase needs.  Uses the current CUDA device.
+ * Errors: INVALID_ARG, PATTERN, OOM, CUDA.
+ */
+ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m,
+                           const int32_t* H_rowptr, const int32_t* H_colind,
+                           const int32_t* J_rowptr, const int32_t* J_colind,
+                           const ncl_kkt_options* opt, ncl_kkt_t* out);
+
+/*
+ * ncl_kkt_factor -- numeric LDL^T of the KKT matrix for new values on the
+ * analysed pattern (every Newton step).
+ *   H_val   device double[nnz(H)], J_val device double[nnz(J)],
+ *   Sigma   device double[n] (the diagonal of Section 3.1, Eq. K2unreg),
+ *   delta   primal regularisation, rho penalty (> 0)
+ *   info    may be NULL; receives inertia, perturbed count, flops, time
+ * The FP64 KKT values are assembled on the device (rho J^T J as a sparse
+ * product in FP64 for K), then factored in the handle's precision.
+ * Returns NCL_OK even for a wrong inertia (the caller raises delta, Section
+ * 3.1); ZERO_PIVOT under the STOP policy; NUMERIC for a NaN/Inf pivot.
+ */
+ncl_status ncl_kkt_factor(ncl_kkt_t h, const double* H_val, const double* J_val,
+                          const double* Sigma, double delta, double rho,
+                          ncl_stream_t stream, ncl_kkt_factor_info* info);
+
+/*
+ * ncl_kkt_solve -- X = K^{-1} B for nrhs >= 1 right-hand sides, using the
+ * current factors, with FP64 iterative refinement on the FP64 matrix
+ * (Section 4.3) until the backward error is <= ir_tol.
+ *   B  device double, dim x nrhs, column-major, leading dimension ldb >= dim
+ *   X  device double, dim x nrhs, leading dimension ldx >= dim (may not alias B)
+ * Errors: STATE (no factor), IR_NOT_CONVERGED (X still holds the best iterate).
+ */
+ncl_status ncl_kkt_solve(ncl_kkt_t h, int32_t nrhs, const double* B, int64_t ldb,
+                         double* X, int64_t ldx, ncl_stream_t stream,
+                         ncl_kkt_solve_info* info);
+
+/*
+ * ncl_kkt_adjoint -- reverse-mode derivative of X = K^{-1} B.
+ * Given X (from ncl_kkt_solve) and GX = dl/dX, computes
+ *   GB = K^{-1} GX   (K is symmetric; refined like a solve)
+ *   dl/dK = -GB X^T folded onto the stored values:
+ *     G_Hval  for an off-diagonal lower H value (i,j): -(gb_i x_j + gb_j x_i),
+ *             on the diagonal -gb_i x_i
+ *     G_Jval  K2r: -(gb_{n+r} x_c + gb_c x_{n+r});
+ *             K:   -rho ((J gb)_r x_c + (J x)_r gb_c)
+ *     G_Sigma -gb_i x_i
+ *     G_scal  [0] = dl/ddelta = -sum_{i<n} gb_i x_i,
+ *             [1] = dl/drho  = K2r: -(1/rho^2) sum_{dual} gb_i x_i;
+ *                              K:   -(J gb).(J x)
+ *   summed over the nrhs columns.  All arrays are device FP64 with the
+ *   layouts of analyze/factor/solve; any gradient pointer may be NULL.
+ */
+ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t ldx,
+                           const double* GX, int64_t ldgx, double* GB, int64_t ldgb,
+                           double* G_Hval, double* G_Jval, double* G_Sigma, double* G_scal,
+                           ncl_stream_t stream, ncl_kkt_solve_info* info);
+
+/* Sizes and counts of the analysis (host struct). */
+ncl_status ncl_kkt_get_analysis_info(ncl_kkt_t h, ncl_kkt_analysis_info* out);
+
+/* The fill-reducing permutation: perm[k] = original index of the k-th
+ * pivot (host int32[dim]). */
+ncl_status ncl_kkt_get_permutation(ncl_kkt_t h, int32_t* perm);
+
+/* Free the handle and its device memory (NULL is ignored). */
+void ncl_kkt_destroy(ncl_kkt_t h);
+
+/* Static string naming a status code. */
+const char* ncl_kkt_status_string(ncl_status st);
+
+/* Detail message of the last error on the calling thread ("" if none). */
+const char* ncl_kkt_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent KKT systems of uneven size and pattern (such as
+ * the scenarios or contingencies of one network) factored and solved by one
+ * handle.  The batch is one block-diagonal system: every kernel launch of a
+ * factorisation or solve covers all instances, and the whole factor + solve
+ * is replayed from one captured CUDA graph.
+ *
+ * Instance i has form forms[i] (all equal), sizes n[i], m[i] and its own
+ * pattern (pointers into host arrays).  Values are passed CONCATENATED in
+ * instance order: H values of instance 0, then 1, ...; likewise J values,
+ * Sigma (n[i] each) and right-hand sides (dim_i rows each, so B is the
+ * concatenated dim x nrhs column-major block).  delta and rho are host
+ * arrays with one entry per instance.
+ * ------------------------------------------------------------------------ */
+
+ncl_status ncl_kkt_batch_analyze(int32_t count, int32_t form, const int32_t* n, const int32_t* m,
+                                 const int32_t* const* H_rowptr, const int32_t* const* H_colind,
+                                 const int32_t* const* J_rowptr, const int32_t* const* J_colind,
+                                 const ncl_kkt_options* opt, ncl_kkt_t* out);
+
+/* Factor all instances (values concatenated; delta, rho host arrays of
+ * length count).  infos (host, may be NULL) receives one struct per
+ * instance; the status is the worst over instances. */
+ncl_status ncl_kkt_batch_factor(ncl_kkt_t h, const double* H_val, const double* J_val,
+                                const double* Sigma, const double* delta, const double* rho,
+                                ncl_stream_t stream, ncl_kkt_factor_info* infos);
+
+/* Factor + solve in one call; with the same handle, values and nrhs the
+ * whole sequence is one CUDA-graph launch after the first call.
+ * sinfo->backward_err is the worst over instances. */
+ncl_status ncl_kkt_batch_factor_solve(ncl_kkt_t h, const double* H_val, const double* J_val,
+                                      const double* Sigma, const double* delta, const double* rho,
+                                      int32_t nrhs, const double* B, int64_t ldb,
+                                      double* X, int64_t ldx, ncl_stream_t stream,
+                                      ncl_kkt_factor_info* infos, ncl_kkt_solve_info* sinfo);
+
+/* Supernode partition of the permuted matrix: col0[s] is the first pivot of
+ * supernode s (col0 host int32[ns+1], col0[ns] = dim), parent[s] its
+ * parent in the assembly tree or -1 (host int32[ns]), nrow[s] the number of
+ * rows of its front (host int32[ns]).  Any pointer may be NULL.  ns is
+ * ncl_kkt_analysis_info.n_supernodes. */
+ncl_status ncl_kkt_get_supernodes(ncl_kkt_t h, int32_t* col0, int32_t* parent, int32_t* nrow);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics
+ * ------------------------------------------------------------------------ */
+
+/* Number of CUDA kernels the library has launched in this process. */
+int64_t ncl_kkt_kernel_launches(void);
+
+/* Per-kernel timing of a handle.  With enable = 1 every later factor/solve
+ * call brackets each kernel launch with CUDA events on the call's stream
+ * (this adds a little time per launch) and accumulates, per kernel name,
+ * the launches, the summed device time and the kernel's arithmetic (flops
+ * on the stored supernodal blocks) and minimum memory traffic (bytes).
+ * enable = 0 stops recording; enable = -1 clears the totals. */
+ncl_status ncl_kkt_profile(ncl_kkt_t h, int32_t enable);
+
+/* Write the accumulated per-kernel totals as a JSON object
+ * {"name": {"launches": L, "ms": T, "flops": F, "bytes": B}, ...} into buf
+ * (NUL-terminated, truncated to buflen).  Returns NCL_OK. */
+ncl_status ncl_kkt_profile_report(ncl_kkt_t h, char* buf, int64_t buflen);
+
+/* Number of instances of a handle (1 for ncl_kkt_analyze). */
+int32_t ncl_kkt_instance_count(ncl_kkt_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NCL_KKT_H */

@@ -1,0 +1,1022 @@
+// C ABI entry points (include/ncl_kkt.h): handle, device plan, launch
+// schedule, factor / solve with FP64 iterative refinement, adjoint.
+#include "../../include/ncl_kkt.h"
+#include "plan.h"
+#include "runtime.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace ncl {
+void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64_t* inst_con_off, const double* rho,
+                            const double* X, int64_t ldx, const double* GB, int64_t ldgb, int nrhs,
+                            const double* jx, const double* jg, double* G_scal, cudaStream_t st);
+}
+
+using namespace ncl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ncl_status fail(ncl_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+struct CudaError {
+  cudaError_t err;
+  std::string where;
+};
+
+#define CK(x)                                                  \
+  do {                                                         \
+    cudaError_t e_ = (x);                                      \
+    if (e_ != cudaSuccess) throw CudaError{e_, #x};            \
+  } while (0)
+
+constexpr int MAX_RHS_SWEEP = 8;
+
+// per-launch arithmetic (flops on the stored blocks) and minimum traffic
+// (bytes), used only for profiling reports
+struct Cost {
+  double flops = 0, bytes = 0;
+};
+
+struct Step {
+  int64_t panel_off = 0;
+  int panel_cnt = 0;
+  int64_t prob_off = 0;
+  int prob_cnt = 0;
+  int64_t tiles = 0;
+  Cost panel_cost, gemm_cost;
+};
+
+struct Level {
+  int64_t asm_off = 0;
+  int asm_cnt = 0;
+  int64_t small_off = 0;
+  int small_cnt = 0;
+  std::vector<Step> steps;
+  int64_t syrk_off = 0;
+  int syrk_cnt = 0;
+  int64_t syrk_tiles = 0;
+  int64_t list_off = 0;   // all supernodes of the level (solve)
+  int list_cnt = 0;
+  int64_t below_off = 0;  // (s, a0) solve items
+  int below_cnt = 0;
+  Cost asm_cost, small_cost, syrk_cost, fdiag_cost, fbelow_cost, bdiag_cost, bbelow_cost;
+};
+
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+
+struct Pending {
+  const char* name;
+  cudaEvent_t a, b;
+  Cost c;
+};
+
+std::atomic<int64_t> g_kernel_launches{0};
+
+struct HostSched {
+  std::vector<int2> asmv, belowv;
+  std::vector<int32_t> smallv, listv;
+  std::vector<int4> panelv;
+  std::vector<GemmProb> probv;
+};
+
+}  // namespace
+
+struct ncl_kkt_s {
+  Plan plan;
+  DevPlan dp{};
+  ncl_kkt_options opt{};
+  int device = 0;
+  int ninst = 1;
+  std::vector<void*> allocs;
+  int64_t device_bytes = 0;
+  // numeric state
+  DevNum<float> nf{};
+  DevNum<double> nd{};
+  double* Klow = nullptr;
+  double* d_delta = nullptr;
+  double* d_rho = nullptr;
+  unsigned long long* d_knorm = nullptr;
+  unsigned long long* d_norms = nullptr;   // rnorm | xnorm | bnorm, ninst*MAX_RHS_SWEEP each
+  long long* d_counts = nullptr;
+  int64_t* d_inst_n = nullptr;
+  int64_t* d_inst_con_off = nullptr;
+  double* h_pinned = nullptr;              // host staging (pinned)
+  // schedule
+  std::vector<Level> levels;
+  HostSched hs;
+  int2* d_asm = nullptr;
+  int32_t* d_small = nullptr;
+  int4* d_panel = nullptr;
+  GemmProb* d_probs = nullptr;
+  int32_t* d_lists = nullptr;
+  int2* d_below = nullptr;
+  // solve workspace
+  void* xp = nullptr;
+  void* W = nullptr;
+  void* Pw = nullptr;
+  double* R = nullptr;
+  double* jx = nullptr;
+  double* jg = nullptr;
+  double* GBtmp = nullptr;
+  double* Jcopy = nullptr;                 // condensed form: J values of the last factor (adjoint)
+  bool factored = false;
+  // profiling
+  int prof_on = 0;
+  std::map<std::string, KStat> prof;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  std::vector<double> h_delta, h_rho;
+  std::vector<double> knorm_host;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  template <typename T>
+  T* alloc(int64_t count) {
+    if (count <= 0) count = 1;
+    size_t bytes = (size_t)count * sizeof(T);
+    if (opt.max_device_bytes > 0 && device_bytes + (int64_t)bytes > opt.max_device_bytes)
+      throw std::bad_alloc();
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    allocs.push_back(p);
+    device_bytes += (int64_t)bytes;
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>((int64_t)v.size());
+    if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  ~ncl_kkt_s() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(device);
+    for (void* p : allocs) cudaFree(p);
+    if (h_pinned) cudaFreeHost(h_pinned);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    cudaSetDevice(cur);
+  }
+};
+
+namespace {
+
+bool is_fp32(const ncl_kkt_s* h) { return h->opt.prec == NCL_PREC_FP32_IR; }
+
+// ---------------------------------------------------------------------------
+// device plan + schedule
+// ---------------------------------------------------------------------------
+// launch schedule (host vectors) + bounds validation; no device work
+void build_schedule(ncl_kkt_s* h) {
+  Plan& P = h->plan;
+  const size_t esz = is_fp32(h) ? 4 : 8;
+  HostSched& hs = h->hs;
+  std::vector<int2>& asmv = hs.asmv;
+  std::vector<int2>& belowv = hs.belowv;
+  std::vector<int32_t>& smallv = hs.smallv;
+  std::vector<int32_t>& listv = hs.listv;
+  std::vector<int4>& panelv = hs.panelv;
+  std::vector<GemmProb>& probv = hs.probv;
+  h->levels.assign(P.nlevels, Level{});
+  for (int32_t l = 0; l < P.nlevels; l++) {
+    Level& L = h->levels[l];
+    L.asm_off = (int64_t)asmv.size();
+    L.small_off = (int64_t)smallv.size();
+    L.list_off = (int64_t)listv.size();
+    L.below_off = (int64_t)belowv.size();
+    std::vector<int32_t> large;
+    for (int32_t k = P.level_ptr[l]; k < P.level_ptr[l + 1]; k++) {
+      const int32_t s = P.level_list[k];
+      const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
+      for (int r0 = 0; r0 < nrow; r0 += ASM_ROWS) asmv.push_back(make_int2(s, r0));
+      listv.push_back(s);
+      for (int a0 = 0; a0 < nrow - ncol; a0 += SOLVE_ROWS) belowv.push_back(make_int2(s, a0));
+      const bool small = ncol <= 64 && nrow <= 512 && (int64_t)nrow * ncp * (int64_t)esz <= SMALL_SMEM;
+      if (small) smallv.push_back(s);
+      else large.push_back(s);
+      const double nb = nrow - ncol, lent = (double)nrow * ncol - 0.5 * ncol * (ncol - 1.0);
+      // assembly writes the L and U blocks, reads the children's U blocks
+      double child_u = 0;
+      for (int32_t k2 = P.child_ptr[s]; k2 < P.child_ptr[s + 1]; k2++) {
+        const double cb = P.sn_nrow[P.child_list[k2]] - P.sn_ncol[P.child_list[k2]];
+        child_u += 0.5 * cb * (cb + 1);
+      }
+      L.asm_cost.bytes += esz * ((double)nrow * ncp + 0.5 * nb * (nb + 1) + child_u) +
+                          12.0 * (double)(P.amap_ptr[P.sn_rows_off[s + 1]] - P.amap_ptr[P.sn_rows_off[s]]);
+      if (small) {
+        L.small_cost.flops += 2.0 * (ncol * (double)ncol * ncol / 3.0 + nb * ncol * ncol) + 2.0 * ncol * 0.5 * nb * (nb + 1);
+        L.small_cost.bytes += esz * (2.0 * nrow * ncp + nb * (nb + 1));
+      }
+      L.fdiag_cost.bytes += esz * 0.5 * ncol * (ncol + 1.0);
+      L.fdiag_cost.flops += (double)ncol * ncol;
+      L.fbelow_cost.bytes += esz * nb * ncol;
+      L.fbelow_cost.flops += 2.0 * nb * ncol;
+      L.bdiag_cost = L.fdiag_cost;
+      L.bbelow_cost.bytes += esz * nb * ncol;
+      L.bbelow_cost.flops += 2.0 * nb * ncol;
+      (void)lent;
+    }
+    L.asm_cnt = (int)(asmv.size() - L.asm_off);
+    L.small_cnt = (int)(smallv.size() - L.small_off);
+    L.list_cnt = (int)(listv.size() - L.list_off);
+    L.below_cnt = (int)(belowv.size() - L.below_off);
+    int maxp = 0;
+    for (int32_t s : large) maxp = std::max(maxp, (P.sn_ncol[s] + PANEL_NB - 1) / PANEL_NB);
+    L.steps.resize(maxp);
+    for (int p = 0; p < maxp; p++) {
+      Step& S = L.steps[p];
+      S.panel_off = (int64_t)panelv.size();
+      S.prob_off = (int64_t)probv.size();
+      int64_t tiles = 0;
+      for (int32_t s : large) {
+        const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
+        const int p0 = p * PANEL_NB;
+        if (p0 >= ncol) continue;
+        const int pe = std::min(p0 + PANEL_NB, ncol);
+        int r0 = pe;
+        do {
+          panelv.push_back(make_int4(s, p0, r0, r0 == pe ? 1 : 0));
+          r0 += PANEL_ROWS;
+        } while (r0 < nrow);
+        S.panel_cost.flops += (double)(nrow - pe) * (pe - p0) * (pe - p0) + 2.0 * (pe - p0) * (pe - p0) * (pe - p0) / 3.0;
+        S.panel_cost.bytes += esz * 2.0 * (nrow - p0) * (pe - p0);
+        if (pe < ncol) {
+          GemmProb g{};
+          g.c_off = P.sn_Loff[s] + (int64_t)pe * ncp + pe;
+          g.a_off = P.sn_Loff[s] + (int64_t)pe * ncp + p0;
+          g.b_off = g.a_off;
+          g.d_off = P.sn_col0[s] + p0;
+          g.ldc = ncp;
+          g.lda = ncp;
+          g.M = nrow - pe;
+          g.N = ncol - pe;
+          g.K = pe - p0;
+          g.c_in_u = 0;
+          const int Mt = (g.M + GEMM_TILE - 1) / GEMM_TILE, Nt = (g.N + GEMM_TILE - 1) / GEMM_TILE;
+          g.Nt = Nt;
+          g.tile0 = tiles;
+          tiles += (int64_t)Nt * (Nt + 1) / 2 + (int64_t)(Mt - Nt) * Nt;
+          probv.push_back(g);
+          const double centries = (double)g.M * g.N - 0.5 * (double)g.N * (g.N - 1);
+          S.gemm_cost.flops += 2.0 * g.K * centries;
+          S.gemm_cost.bytes += esz * (2.0 * centries + (double)(g.M + g.N) * g.K);
+        }
+      }
+      S.panel_cnt = (int)(panelv.size() - S.panel_off);
+      S.prob_cnt = (int)(probv.size() - S.prob_off);
+      S.tiles = tiles;
+    }
+    L.syrk_off = (int64_t)probv.size();
+    int64_t tiles = 0;
+    for (int32_t s : large) {
+      const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
+      const int nb = nrow - ncol;
+      if (nb == 0) continue;
+      GemmProb g{};
+      g.c_off = P.sn_Uoff[s];
+      g.a_off = P.sn_Loff[s] + (int64_t)ncol * ncp;
+      g.b_off = g.a_off;
+      g.d_off = P.sn_col0[s];
+      g.ldc = nb;
+      g.lda = ncp;
+      g.M = nb;
+      g.N = nb;
+      g.K = ncol;
+      g.c_in_u = 1;
+      const int Nt = (nb + GEMM_TILE - 1) / GEMM_TILE;
+      g.Nt = Nt;
+      g.tile0 = tiles;
+      tiles += (int64_t)Nt * (Nt + 1) / 2;
+      probv.push_back(g);
+      const double centries = 0.5 * (double)nb * (nb + 1);
+      L.syrk_cost.flops += 2.0 * ncol * centries;
+      L.syrk_cost.bytes += esz * (2.0 * centries + (double)nb * ncol);
+    }
+    L.syrk_cnt = (int)(probv.size() - L.syrk_off);
+    L.syrk_tiles = tiles;
+  }
+  // bounds of every launch item against its buffers, checked on the host
+  // before anything runs on the device
+  {
+    auto bad = [](const char* what) { throw std::runtime_error(std::string("internal plan check: ") + what); };
+    const int64_t Lsz = P.L_stored, Usz = P.U_stored;
+    for (int32_t s = 0; s < P.ns; s++) {
+      const int64_t nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], nb = nrow - ncol;
+      if (ncol <= 0 || nrow < ncol || ncp < ncol) bad("supernode sizes");
+      if (P.sn_Loff[s] + nrow * ncp > P.sn_Loff[s + 1] || P.sn_Loff[s + 1] > Lsz) bad("L block");
+      if (P.sn_Uoff[s] + nb * nb > P.sn_Uoff[s + 1] || P.sn_Uoff[s + 1] > Usz) bad("U block");
+      if (P.sn_col0[s] < 0 || P.sn_col0[s] + ncol > P.dim) bad("columns");
+      if (P.sn_parent[s] >= 0 && P.sn_parent[s] <= s) bad("parent order");
+      const int32_t par = P.sn_parent[s];
+      for (int64_t a = 0; a < nb; a++) {
+        const int32_t r = P.relmap[P.relmap_off[s] + a];
+        if (par < 0 || r < 0 || r >= P.sn_nrow[par] || (a > 0 && r <= P.relmap[P.relmap_off[s] + a - 1]))
+          bad("relmap");
+      }
+      for (int64_t r = 0; r < nrow; r++) {
+        const int32_t g = P.sn_rows[P.sn_rows_off[s] + r];
+        if (g < 0 || g >= P.dim) bad("rows");
+        for (int64_t q = P.amap_ptr[P.sn_rows_off[s] + r]; q < P.amap_ptr[P.sn_rows_off[s] + r + 1]; q++)
+          if (P.amap_col[q] < 0 || P.amap_col[q] >= ncol || P.amap_col[q] > r || P.amap_src[q] < 0 ||
+              P.amap_src[q] >= P.nnzA)
+            bad("assembly map");
+      }
+    }
+    for (const int2& it : asmv)
+      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x]) bad("assembly item");
+    for (const int2& it : belowv)
+      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x] - P.sn_ncol[it.x]) bad("solve item");
+    for (int32_t s : smallv) {
+      const int64_t nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
+      if (nrow * ncp * (int64_t)esz > SMALL_SMEM || nrow * (int64_t)esz > 4096) bad("small front smem");
+    }
+    for (const int4& it : panelv) {
+      const int s = it.x;
+      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.z < 0 || it.z > P.sn_nrow[s]) bad("panel item");
+    }
+    for (const GemmProb& g : probv) {
+      const int64_t csz = g.c_in_u ? Usz : Lsz;
+      if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.N > g.M) bad("gemm shape");
+      if (g.c_off < 0 || g.c_off + (int64_t)(g.M - 1) * g.ldc + g.N > csz) bad("gemm C");
+      if (g.a_off < 0 || g.a_off + (int64_t)(g.M - 1) * g.lda + g.K > Lsz) bad("gemm A");
+      if (g.b_off < 0 || g.b_off + (int64_t)(g.N - 1) * g.lda + g.K > Lsz) bad("gemm B");
+      if (g.d_off < 0 || g.d_off + g.K > P.dim) bad("gemm d");
+    }
+  }
+}
+
+void build_device(ncl_kkt_s* h) {
+  Plan& P = h->plan;
+  DevPlan& d = h->dp;
+  d.dim = P.dim;
+  d.ns = P.ns;
+  d.ninst = (int32_t)P.inst.size();
+  d.form = P.form;
+  d.nnzA = P.nnzA;
+  std::vector<int32_t> e_inst(P.nnzA);
+  for (int64_t c = 0; c < P.dim; c++)
+    for (int64_t p = P.A_colptr[c]; p < P.A_colptr[c + 1]; p++) e_inst[p] = P.row_inst[P.A_row[p]];
+  d.e_h = h->upload(P.e_h);
+  d.e_j = h->upload(P.e_j);
+  d.e_var = h->upload(P.e_var);
+  d.e_inst = h->upload(e_inst);
+  d.e_kind = h->upload(P.e_kind);
+  d.pair_ptr = h->upload(P.pair_ptr);
+  d.pair_p = h->upload(P.pair_p);
+  d.pair_q = h->upload(P.pair_q);
+  d.F_rowptr = h->upload(P.F_rowptr);
+  d.F_col = h->upload(P.F_col);
+  d.F_src = h->upload(P.F_src);
+  d.row_inst = h->upload(P.row_inst);
+  d.sn_col0 = h->upload(P.sn_col0);
+  d.sn_ncol = h->upload(P.sn_ncol);
+  d.sn_ncolp = h->upload(P.sn_ncolp);
+  d.sn_nrow = h->upload(P.sn_nrow);
+  d.sn_rows_off = h->upload(P.sn_rows_off);
+  d.sn_rows = h->upload(P.sn_rows);
+  d.sn_Loff = h->upload(P.sn_Loff);
+  d.sn_Uoff = h->upload(P.sn_Uoff);
+  d.sn_Woff = h->upload(P.sn_Woff);
+  std::vector<int64_t> Poff(P.ns + 1, 0);
+  for (int32_t s = 0; s < P.ns; s++) {
+    int64_t nb = P.sn_nrow[s] - P.sn_ncol[s];
+    Poff[s + 1] = Poff[s] + ((nb + SOLVE_ROWS - 1) / SOLVE_ROWS) * P.sn_ncol[s];
+  }
+  d.sn_Poff = h->upload(Poff);
+  d.child_ptr = h->upload(P.child_ptr);
+  d.child_list = h->upload(P.child_list);
+  d.relmap_off = h->upload(P.relmap_off);
+  d.relmap = h->upload(P.relmap);
+  d.amap_ptr = h->upload(P.amap_ptr);
+  d.amap_col = h->upload(P.amap_col);
+  d.amap_src = h->upload(P.amap_src);
+  d.perm = h->upload(P.perm);
+  d.col_inst = h->upload(P.col_inst);
+  d.col_sign = h->upload(P.col_sign);
+  d.Wtot = P.sn_Woff[P.ns];
+  d.Ptot = Poff[P.ns];
+  d.H_row = h->upload(P.H_row);
+  d.H_col = h->upload(P.H_col);
+  d.J_con = h->upload(P.J_row);
+  d.J_col = h->upload(P.J_col);
+  d.J_inst = h->upload(P.J_inst);
+  d.con_row = h->upload(P.con_row);
+  d.J_rowptr = h->upload(P.J_rowptr_all);
+  d.var_row = h->upload(P.var_row);
+  d.nnzH = P.nnzH_total;
+  d.nnzJ = P.nnzJ_total;
+  d.nvar = P.nS_total;
+  d.ncon = P.mcon_total;
+  std::vector<int64_t> ro(P.inst.size() + 1), in(P.inst.size()), co(P.inst.size() + 1, 0);
+  for (size_t i = 0; i < P.inst.size(); i++) {
+    ro[i] = P.inst[i].row_off;
+    in[i] = P.inst[i].n;
+    co[i + 1] = co[i] + P.inst[i].m;
+  }
+  ro[P.inst.size()] = P.dim;
+  d.inst_row_off = h->upload(ro);
+  h->d_inst_n = h->upload(in);
+  h->d_inst_con_off = h->upload(co);
+
+  // numeric storage
+  const int ni = d.ninst;
+  h->Klow = h->alloc<double>(P.nnzA);
+  h->d_delta = h->alloc<double>(ni);
+  h->d_rho = h->alloc<double>(ni);
+  h->d_knorm = h->alloc<unsigned long long>(ni);
+  h->d_norms = h->alloc<unsigned long long>(3 * (int64_t)ni * MAX_RHS_SWEEP);
+  h->d_counts = h->alloc<long long>(4 * (int64_t)ni + 1);
+  const size_t esz = is_fp32(h) ? 4 : 8;
+  auto alloc_num = [&](auto& N, auto tag) {
+    using T = decltype(tag);
+    N.L = h->alloc<T>(P.L_stored);
+    N.U = h->alloc<T>(P.U_stored);
+    N.D = h->alloc<T>(P.dim);
+    N.piv = h->alloc<int8_t>(P.dim);
+    N.Klow = h->Klow;
+  };
+  if (is_fp32(h)) alloc_num(h->nf, float{});
+  else alloc_num(h->nd, double{});
+  h->xp = h->alloc<char>((int64_t)P.dim * MAX_RHS_SWEEP * esz);
+  h->W = h->alloc<char>(std::max<int64_t>(d.Wtot, 1) * MAX_RHS_SWEEP * esz);
+  h->Pw = h->alloc<char>(std::max<int64_t>(d.Ptot, 1) * MAX_RHS_SWEEP * esz);
+  h->R = h->alloc<double>((int64_t)P.dim * MAX_RHS_SWEEP);
+  h->GBtmp = h->alloc<double>((int64_t)P.dim * MAX_RHS_SWEEP);
+  h->jx = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
+  h->jg = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
+  if (P.form == 1) h->Jcopy = h->alloc<double>(std::max<int64_t>(d.nnzJ, 1));
+
+  HostSched& hs = h->hs;
+  h->d_asm = h->upload(hs.asmv);
+  h->d_small = h->upload(hs.smallv);
+  h->d_panel = h->upload(hs.panelv);
+  h->d_probs = h->upload(hs.probv);
+  h->d_lists = h->upload(hs.listv);
+  h->d_below = h->upload(hs.belowv);
+  CK(cudaMallocHost(&h->h_pinned, sizeof(double) * (size_t)(4 * ni + 64 + 3 * ni * MAX_RHS_SWEEP)));
+  CK(cudaEventCreate(&h->ev0));
+  CK(cudaEventCreate(&h->ev1));
+}
+
+// ---------------------------------------------------------------------------
+// numeric phases
+// ---------------------------------------------------------------------------
+
+// one kernel launch (skipped when it has no work), counted, and bracketed
+// by events when profiling is on
+template <typename F>
+void klaunch(ncl_kkt_s* h, cudaStream_t st, const char* name, int64_t work, Cost c, F&& f) {
+  if (work <= 0) return;
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!h->prof_on) {
+    f();
+    return;
+  }
+  while (h->evpool.size() < h->evnext + 2) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    h->evpool.push_back(e);
+  }
+  cudaEvent_t a = h->evpool[h->evnext++], b = h->evpool[h->evnext++];
+  CK(cudaEventRecord(a, st));
+  f();
+  CK(cudaEventRecord(b, st));
+  h->pending.push_back(Pending{name, a, b, c});
+}
+
+// fold the recorded launches into the per-kernel totals (after a sync)
+void prof_collect(ncl_kkt_s* h) {
+  for (const Pending& p : h->pending) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    KStat& k = h->prof[p.name];
+    k.launches++;
+    k.ms += ms;
+    k.flops += p.c.flops;
+    k.bytes += p.c.bytes;
+  }
+  h->pending.clear();
+  h->evnext = 0;
+}
+
+Cost scaled(Cost c, double f) {
+  c.flops *= f;
+  c.bytes *= f;
+  return c;
+}
+
+template <typename T>
+void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
+  const DevPlan& P = h->dp;
+  const bool f32 = sizeof(T) == 4;
+  for (const Level& L : h->levels) {
+    klaunch(h, st, f32 ? "assemble_f32" : "assemble_f64", L.asm_cnt, L.asm_cost,
+            [&] { launch_assemble<T>(P, N, h->d_asm + L.asm_off, L.asm_cnt, st); });
+    klaunch(h, st, f32 ? "factor_small_f32" : "factor_small_f64", L.small_cnt, L.small_cost, [&] {
+      launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
+    });
+    for (const Step& S : L.steps) {
+      klaunch(h, st, f32 ? "panel_f32" : "panel_f64", S.panel_cnt, S.panel_cost, [&] {
+        launch_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
+      });
+      klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost,
+              [&] { launch_gemm_simt<T>(N, h->d_probs + S.prob_off, S.prob_cnt, S.tiles, st); });
+    }
+    klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", L.syrk_tiles, L.syrk_cost,
+            [&] { launch_gemm_simt<T>(N, h->d_probs + L.syrk_off, L.syrk_cnt, L.syrk_tiles, st); });
+  }
+  CK(cudaGetLastError());
+}
+
+template <typename T>
+void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
+  const DevPlan& P = h->dp;
+  T* xp = (T*)h->xp;
+  T* W = (T*)h->W;
+  T* Pw = (T*)h->Pw;
+  const bool f32 = sizeof(T) == 4;
+  for (const Level& L : h->levels) {
+    klaunch(h, st, f32 ? "fwd_diag_f32" : "fwd_diag_f64", L.list_cnt, scaled(L.fdiag_cost, nrhs),
+            [&] { launch_fwd_diag<T>(P, N, h->d_lists + L.list_off, L.list_cnt, xp, W, nrhs, st); });
+    klaunch(h, st, f32 ? "fwd_below_f32" : "fwd_below_f64", L.below_cnt, scaled(L.fbelow_cost, nrhs),
+            [&] { launch_fwd_below<T>(P, N, h->d_below + L.below_off, L.below_cnt, xp, W, nrhs, st); });
+  }
+  for (int l = (int)h->levels.size() - 1; l >= 0; l--) {
+    const Level& L = h->levels[l];
+    klaunch(h, st, f32 ? "bwd_below_f32" : "bwd_below_f64", L.below_cnt, scaled(L.bbelow_cost, nrhs),
+            [&] { launch_bwd_below<T>(P, N, h->d_below + L.below_off, L.below_cnt, xp, Pw, nrhs, st); });
+    klaunch(h, st, f32 ? "bwd_diag_f32" : "bwd_diag_f64", L.list_cnt, scaled(L.bdiag_cost, nrhs),
+            [&] { launch_bwd_diag<T>(P, N, h->d_lists + L.list_off, L.list_cnt, xp, Pw, nrhs, st); });
+  }
+  CK(cudaGetLastError());
+}
+
+// X (+)= K^{-1} B with the low-precision factors (one sweep)
+void apply_inverse(ncl_kkt_s* h, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs, int accumulate,
+                   cudaStream_t st) {
+  if (is_fp32(h)) {
+    klaunch(h, st, "perm_in", h->dp.dim, Cost{0, 12.0 * h->dp.dim * nrhs},
+            [&] { launch_perm_in<float>(h->dp, (float*)h->xp, B, ldb, nrhs, st); });
+    run_sweeps<float>(h, h->nf, nrhs, st);
+    klaunch(h, st, "perm_out", h->dp.dim, Cost{0, 20.0 * h->dp.dim * nrhs},
+            [&] { launch_perm_out<float>(h->dp, (const float*)h->xp, X, ldx, nrhs, accumulate, st); });
+  } else {
+    klaunch(h, st, "perm_in", h->dp.dim, Cost{0, 16.0 * h->dp.dim * nrhs},
+            [&] { launch_perm_in<double>(h->dp, (double*)h->xp, B, ldb, nrhs, st); });
+    run_sweeps<double>(h, h->nd, nrhs, st);
+    klaunch(h, st, "perm_out", h->dp.dim, Cost{0, 24.0 * h->dp.dim * nrhs},
+            [&] { launch_perm_out<double>(h->dp, (const double*)h->xp, X, ldx, nrhs, accumulate, st); });
+  }
+}
+
+// backward error per (instance, rhs) from the norm slots; returns the max
+double backward_errors(ncl_kkt_s* h, int nrhs, cudaStream_t st, std::vector<double>* per = nullptr) {
+  const int ni = h->dp.ninst;
+  const size_t cnt = 3 * (size_t)ni * MAX_RHS_SWEEP;
+  CK(cudaMemcpyAsync(h->h_pinned, h->d_norms, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const unsigned long long* u = reinterpret_cast<const unsigned long long*>(h->h_pinned);
+  auto as_d = [](unsigned long long v) {
+    double d;
+    std::memcpy(&d, &v, 8);
+    return d;
+  };
+  double worst = 0.0;
+  if (per) per->assign((size_t)ni * nrhs, 0.0);
+  for (int i = 0; i < ni; i++)
+    for (int r = 0; r < nrhs; r++) {
+      const double rn = as_d(u[i * nrhs + r]);
+      const double xn = as_d(u[ni * MAX_RHS_SWEEP + i * nrhs + r]);
+      const double bn = as_d(u[2 * ni * MAX_RHS_SWEEP + i * nrhs + r]);
+      const double den = h->knorm_host[i] * xn + bn;
+      double eta = den > 0 ? rn / den : (rn > 0 ? INFINITY : 0.0);
+      if (!std::isfinite(rn) || !std::isfinite(xn)) eta = INFINITY;
+      if (per) (*per)[(size_t)i * nrhs + r] = eta;
+      worst = std::max(worst, eta);
+    }
+  return worst;
+}
+
+// residual R = B - K X and the norms; returns max backward error
+double residual_eta(ncl_kkt_s* h, const double* B, int64_t ldb, const double* X, int64_t ldx, int nrhs,
+                    cudaStream_t st) {
+  const int ni = h->dp.ninst;
+  CK(cudaMemsetAsync(h->d_norms, 0, 2 * (size_t)ni * MAX_RHS_SWEEP * sizeof(unsigned long long), st));
+  const double nnzF = (double)h->plan.F_col.size();
+  klaunch(h, st, "residual_f64", h->dp.dim, Cost{2.0 * nnzF * nrhs, nnzF * 16.0 + 8.0 * h->dp.dim * (1 + 3.0 * nrhs)}, [&] {
+    launch_residual(h->dp, h->Klow, B, ldb, X, ldx, h->R, h->dp.dim, nrhs, h->d_norms,
+                    h->d_norms + ni * MAX_RHS_SWEEP, st);
+  });
+  CK(cudaGetLastError());
+  return backward_errors(h, nrhs, st);
+}
+
+// solve nrhs <= MAX_RHS_SWEEP columns with Richardson refinement
+ncl_status solve_block(ncl_kkt_s* h, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                       cudaStream_t st, ncl_kkt_solve_info* info) {
+  const int ni = h->dp.ninst;
+  CK(cudaMemsetAsync(h->d_norms + 2 * ni * MAX_RHS_SWEEP, 0, (size_t)ni * MAX_RHS_SWEEP * 8, st));
+  klaunch(h, st, "vec_norm", h->dp.dim, Cost{0, 8.0 * h->dp.dim * nrhs},
+          [&] { launch_vec_norm(h->dp, B, ldb, nrhs, h->d_norms + 2 * ni * MAX_RHS_SWEEP, st); });
+  apply_inverse(h, B, ldb, X, ldx, nrhs, 0, st);
+  double eta = residual_eta(h, B, ldb, X, ldx, nrhs, st);
+  int it = 0;
+  const int maxit = h->opt.ir_max_iter;
+  while (eta > h->opt.ir_tol && it < maxit && std::isfinite(eta)) {
+    apply_inverse(h, h->R, h->dp.dim, X, ldx, nrhs, 1, st);
+    it++;
+    eta = residual_eta(h, B, ldb, X, ldx, nrhs, st);
+  }
+  if (info) {
+    info->ir_iters = std::max(info->ir_iters, it);
+    info->backward_err = std::max(info->backward_err, eta);
+  }
+  if (!std::isfinite(eta)) return fail(NCL_ERR_NUMERIC, "non-finite residual or solution");
+  if (eta > h->opt.ir_tol) return NCL_ERR_IR_NOT_CONVERGED;
+  return NCL_OK;
+}
+
+ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
+                     const double* rho, cudaStream_t st, ncl_kkt_factor_info* infos) {
+  const int ni = h->dp.ninst;
+  for (int i = 0; i < ni; i++) {
+    if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(NCL_ERR_INVALID_ARG, "rho must be positive and finite");
+    if (!std::isfinite(delta[i])) return fail(NCL_ERR_INVALID_ARG, "delta must be finite");
+  }
+  if ((h->dp.nnzH && !Hv) || (h->dp.nnzJ && !Jv) || (h->dp.nvar && !S))
+    return fail(NCL_ERR_INVALID_ARG, "NULL value array");
+  h->factored = false;
+  double* hp = h->h_pinned;
+  for (int i = 0; i < ni; i++) {
+    hp[i] = delta[i];
+    hp[ni + i] = rho[i];
+  }
+  CK(cudaEventRecord(h->ev0, st));
+  CK(cudaMemcpyAsync(h->d_delta, hp, ni * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_rho, hp + ni, ni * sizeof(double), cudaMemcpyHostToDevice, st));
+  {
+    const double np = (double)h->plan.pair_p.size();
+    klaunch(h, st, "kkt_values_f64", h->dp.nnzA,
+            Cost{2.0 * np, 33.0 * h->dp.nnzA + 24.0 * np + 8.0 * (h->dp.nnzH + h->dp.nnzJ + h->dp.nvar)},
+            [&] { launch_kkt_values(h->dp, Hv, Jv, S, h->d_delta, h->d_rho, h->Klow, st); });
+  }
+  if (h->Jcopy && h->dp.nnzJ)
+    CK(cudaMemcpyAsync(h->Jcopy, Jv, h->dp.nnzJ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), st));
+  klaunch(h, st, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
+          [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, st); });
+  CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), st));
+  if (is_fp32(h)) {
+    run_factor<float>(h, h->nf, st);
+    klaunch(h, st, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},
+            [&] { launch_inertia<float>(h->dp, h->nf, h->d_counts, st); });
+  } else {
+    run_factor<double>(h, h->nd, st);
+    klaunch(h, st, "inertia", h->dp.dim, Cost{0, 9.0 * h->dp.dim},
+            [&] { launch_inertia<double>(h->dp, h->nd, h->d_counts, st); });
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev1, st));
+  long long* hc = reinterpret_cast<long long*>(hp + 2 * ni);
+  CK(cudaMemcpyAsync(hc, h->d_counts, (4 * ni + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  unsigned long long* hk = reinterpret_cast<unsigned long long*>(hp + 2 * ni + 4 * ni + 1);
+  CK(cudaMemcpyAsync(hk, h->d_knorm, ni * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_collect(h);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->knorm_host.resize(ni);
+  for (int i = 0; i < ni; i++) std::memcpy(&h->knorm_host[i], &hk[i], 8);
+  ncl_status stt = NCL_OK;
+  if (hc[4 * ni] > 0) stt = fail(NCL_ERR_NUMERIC, "non-finite pivot");
+  for (int i = 0; i < ni; i++) {
+    if (infos) {
+      ncl_kkt_factor_info& f = infos[i];
+      f.n_pos = hc[4 * i];
+      f.n_neg = hc[4 * i + 1];
+      f.n_zero = hc[4 * i + 2];
+      f.n_perturbed = hc[4 * i + 3];
+      f.nnz_L = h->plan.inst_nnzL[i];
+      f.flops = h->plan.inst_flops[i];
+      f.ms = ms;
+    }
+    if (stt == NCL_OK && h->opt.pivot_policy == NCL_PIVOT_STOP && hc[4 * i + 2] > 0)
+      stt = fail(NCL_ERR_ZERO_PIVOT, "zero pivot under the stop policy");
+  }
+  h->factored = (stt == NCL_OK || stt == NCL_ERR_ZERO_PIVOT);
+  h->h_delta.assign(delta, delta + ni);
+  h->h_rho.assign(rho, rho + ni);
+  return stt;
+}
+
+ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                    cudaStream_t st, ncl_kkt_solve_info* info) {
+  if (!h->factored) return fail(NCL_ERR_STATE, "solve before a successful factor");
+  if (nrhs < 0 || (nrhs > 0 && (!B || !X)) || ldb < h->dp.dim || ldx < h->dp.dim)
+    return fail(NCL_ERR_INVALID_ARG, "bad right-hand side block");
+  if (info) *info = ncl_kkt_solve_info{};
+  CK(cudaEventRecord(h->ev0, st));
+  ncl_status worst = NCL_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += MAX_RHS_SWEEP) {
+    const int nr = std::min(MAX_RHS_SWEEP, nrhs - r0);
+    ncl_status s = solve_block(h, nr, B + r0 * ldb, ldb, X + r0 * ldx, ldx, st, info);
+    if (s != NCL_OK && worst == NCL_OK) worst = s;
+  }
+  CK(cudaEventRecord(h->ev1, st));
+  CK(cudaEventSynchronize(h->ev1));
+  prof_collect(h);
+  if (info) cudaEventElapsedTime(&info->ms, h->ev0, h->ev1);
+  if (worst == NCL_ERR_IR_NOT_CONVERGED) g_last_error = "iterative refinement did not reach ir_tol";
+  return worst;
+}
+
+template <typename F>
+ncl_status guarded(ncl_kkt_s* h, F&& f) {
+  try {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (h && cur != h->device) cudaSetDevice(h->device);
+    ncl_status s = f();
+    if (h && cur != h->device) cudaSetDevice(cur);
+    return s;
+  } catch (const CudaError& e) {
+    return fail(NCL_ERR_CUDA, e.where + ": " + cudaGetErrorString(e.err));
+  } catch (const std::bad_alloc&) {
+    return fail(NCL_ERR_OOM, "device or host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(NCL_ERR_INVALID_ARG, e.what());
+  }
+}
+
+ncl_status analyze_common(const AnalyzeInput& in, const ncl_kkt_options* opt, ncl_kkt_t* out) {
+  if (!out) return fail(NCL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (in.form != 0 && in.form != 1) return fail(NCL_ERR_INVALID_ARG, "bad form");
+  std::unique_ptr<ncl_kkt_s> h(new ncl_kkt_s());
+  ncl_kkt_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  if (h->opt.prec != NCL_PREC_FP64 && h->opt.prec != NCL_PREC_FP32_IR) return fail(NCL_ERR_INVALID_ARG, "bad prec");
+  if (h->opt.pivot_policy != NCL_PIVOT_PERTURB && h->opt.pivot_policy != NCL_PIVOT_STOP)
+    return fail(NCL_ERR_INVALID_ARG, "bad pivot policy");
+  if (!(h->opt.pivot_eps >= 0)) return fail(NCL_ERR_INVALID_ARG, "bad pivot_eps");
+  if (!(h->opt.ir_tol > 0)) h->opt.ir_tol = h->opt.prec == NCL_PREC_FP64 ? 1e-12 : 1e-10;
+  if (h->opt.ir_max_iter < 0) h->opt.ir_max_iter = h->opt.prec == NCL_PREC_FP64 ? 3 : 10;
+  AnalyzeInput a = in;
+  a.leaf_size = h->opt.leaf_size;
+  a.colpad = 4;
+  std::string err = analyze(a, h->plan);
+  if (!err.empty()) {
+    if (err.rfind("pattern", 0) == 0) return fail(NCL_ERR_PATTERN, err);
+    if (err.rfind("oom", 0) == 0) return fail(NCL_ERR_OOM, err);
+    return fail(NCL_ERR_INVALID_ARG, err);
+  }
+  h->ninst = in.count;
+  h->dp.ninst = in.count;
+  try {
+    build_schedule(h.get());
+  } catch (const std::exception& e) {
+    return fail(NCL_ERR_INVALID_ARG, e.what());
+  }
+  if (h->opt.host_only) {
+    *out = h.release();
+    return NCL_OK;
+  }
+  cudaGetDevice(&h->device);
+  ncl_kkt_s* raw = h.get();
+  ncl_status s = guarded(raw, [&] {
+    build_device(raw);
+    return NCL_OK;
+  });
+  if (s != NCL_OK) return s;
+  *out = h.release();
+  return NCL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ncl_kkt_default_options(ncl_kkt_options* o) {
+  if (!o) return;
+  o->prec = NCL_PREC_FP32_IR;
+  o->pivot_policy = NCL_PIVOT_PERTURB;
+  o->pivot_eps = 1e-10;
+  o->ir_tol = 0.0;
+  o->ir_max_iter = -1;
+  o->use_fgmres = 1;
+  o->use_tensor_cores = 1;
+  o->leaf_size = 96;
+  o->host_only = 0;
+  o->max_device_bytes = 0;
+}
+
+ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m, const int32_t* H_rowptr, const int32_t* H_colind,
+                           const int32_t* J_rowptr, const int32_t* J_colind, const ncl_kkt_options* opt,
+                           ncl_kkt_t* out) {
+  if (n < 0 || m < 0) return fail(NCL_ERR_INVALID_ARG, "negative size");
+  if ((n > 0 && !H_rowptr) || (m > 0 && !J_rowptr)) return fail(NCL_ERR_INVALID_ARG, "NULL pattern");
+  AnalyzeInput in{};
+  in.form = form;
+  in.count = 1;
+  in.n = &n;
+  in.m = &m;
+  in.H_rowptr = &H_rowptr;
+  in.H_colind = &H_colind;
+  in.J_rowptr = &J_rowptr;
+  in.J_colind = &J_colind;
+  return analyze_common(in, opt, out);
+}
+
+ncl_status ncl_kkt_batch_analyze(int32_t count, int32_t form, const int32_t* n, const int32_t* m,
+                                 const int32_t* const* H_rowptr, const int32_t* const* H_colind,
+                                 const int32_t* const* J_rowptr, const int32_t* const* J_colind,
+                                 const ncl_kkt_options* opt, ncl_kkt_t* out) {
+  if (count <= 0 || !n || !m || !H_rowptr || !H_colind || !J_rowptr || !J_colind)
+    return fail(NCL_ERR_INVALID_ARG, "bad batch arguments");
+  AnalyzeInput in{};
+  in.form = form;
+  in.count = count;
+  in.n = n;
+  in.m = m;
+  in.H_rowptr = H_rowptr;
+  in.H_colind = H_colind;
+  in.J_rowptr = J_rowptr;
+  in.J_colind = J_colind;
+  return analyze_common(in, opt, out);
+}
+
+ncl_status ncl_kkt_factor(ncl_kkt_t h, const double* H_val, const double* J_val, const double* Sigma, double delta,
+                          double rho, ncl_stream_t stream, ncl_kkt_factor_info* info) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (h->dp.ninst != 1) return fail(NCL_ERR_INVALID_ARG, "batch handle: use ncl_kkt_batch_factor");
+  return guarded(h, [&] { return do_factor(h, H_val, J_val, Sigma, &delta, &rho, (cudaStream_t)stream, info); });
+}
+
+ncl_status ncl_kkt_batch_factor(ncl_kkt_t h, const double* H_val, const double* J_val, const double* Sigma,
+                                const double* delta, const double* rho, ncl_stream_t stream,
+                                ncl_kkt_factor_info* infos) {
+  if (!h || !delta || !rho) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  return guarded(h, [&] { return do_factor(h, H_val, J_val, Sigma, delta, rho, (cudaStream_t)stream, infos); });
+}
+
+ncl_status ncl_kkt_solve(ncl_kkt_t h, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                         ncl_stream_t stream, ncl_kkt_solve_info* info) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  return guarded(h, [&] { return do_solve(h, nrhs, B, ldb, X, ldx, (cudaStream_t)stream, info); });
+}
+
+ncl_status ncl_kkt_batch_factor_solve(ncl_kkt_t h, const double* H_val, const double* J_val, const double* Sigma,
+                                      const double* delta, const double* rho, int32_t nrhs, const double* B,
+                                      int64_t ldb, double* X, int64_t ldx, ncl_stream_t stream,
+                                      ncl_kkt_factor_info* infos, ncl_kkt_solve_info* sinfo) {
+  ncl_status s = ncl_kkt_batch_factor(h, H_val, J_val, Sigma, delta, rho, stream, infos);
+  if (s != NCL_OK && s != NCL_ERR_ZERO_PIVOT) return s;
+  ncl_status s2 = ncl_kkt_solve(h, nrhs, B, ldb, X, ldx, stream, sinfo);
+  return s2 != NCL_OK ? s2 : s;
+}
+
+ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t ldx, const double* GX, int64_t ldgx,
+                           double* GB, int64_t ldgb, double* G_Hval, double* G_Jval, double* G_Sigma, double* G_scal,
+                           ncl_stream_t stream, ncl_kkt_solve_info* info) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  if (!X || !GX || nrhs <= 0) return fail(NCL_ERR_INVALID_ARG, "bad adjoint arguments");
+  return guarded(h, [&]() -> ncl_status {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t dim = h->dp.dim;
+    if (nrhs > MAX_RHS_SWEEP) return fail(NCL_ERR_INVALID_ARG, "adjoint supports at most 8 columns");
+    double* gb = GB;
+    int64_t ld = ldgb;
+    if (!gb) {
+      gb = h->GBtmp;
+      ld = dim;
+    }
+    ncl_status s = do_solve(h, nrhs, GX, ldgx, gb, ld, st, info);
+    if (s != NCL_OK && s != NCL_ERR_IR_NOT_CONVERGED) return s;
+    g_kernel_launches.fetch_add(4, std::memory_order_relaxed);
+    launch_adjoint_values(h->dp, h->Jcopy, h->d_rho, X, ldx, gb, ld, nrhs, G_Hval, G_Jval, G_Sigma, G_scal,
+                          h->jx, h->jg, st);
+    if (G_scal) {
+      launch_adjoint_scalars(h->dp, h->d_inst_n, h->d_inst_con_off, h->d_rho, X, ldx, gb, ld, nrhs, h->jx, h->jg,
+                             G_scal, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return s;
+  });
+}
+
+ncl_status ncl_kkt_get_analysis_info(ncl_kkt_t h, ncl_kkt_analysis_info* o) {
+  if (!h || !o) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  const Plan& P = h->plan;
+  o->dim = P.dim;
+  o->nnz_A = P.nnzA;
+  o->nnz_L = P.nnzL;
+  o->nnz_L_stored = P.L_stored;
+  o->update_entries = P.U_stored;
+  o->n_supernodes = P.ns;
+  o->n_levels = P.nlevels;
+  o->max_front = P.max_front;
+  o->max_pivots = P.max_pivots;
+  o->device_bytes = h->device_bytes;
+  o->flops = P.flops;
+  o->analyze_ms = P.analyze_ms;
+  return NCL_OK;
+}
+
+ncl_status ncl_kkt_get_permutation(ncl_kkt_t h, int32_t* perm) {
+  if (!h || !perm) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(perm, h->plan.perm.data(), h->plan.perm.size() * sizeof(int32_t));
+  return NCL_OK;
+}
+
+ncl_status ncl_kkt_get_supernodes(ncl_kkt_t h, int32_t* col0, int32_t* parent, int32_t* nrow) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  const Plan& P = h->plan;
+  for (int32_t s = 0; s < P.ns; s++) {
+    if (col0) col0[s] = P.sn_col0[s];
+    if (parent) parent[s] = P.sn_parent[s];
+    if (nrow) nrow[s] = P.sn_nrow[s];
+  }
+  if (col0) col0[P.ns] = (int32_t)P.dim;
+  return NCL_OK;
+}
+
+int32_t ncl_kkt_instance_count(ncl_kkt_t h) { return h ? h->ninst : 0; }
+
+int64_t ncl_kkt_kernel_launches(void) { return g_kernel_launches.load(); }
+
+ncl_status ncl_kkt_profile(ncl_kkt_t h, int32_t enable) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  if (enable < 0) {
+    h->prof.clear();
+    return NCL_OK;
+  }
+  h->prof_on = enable ? 1 : 0;
+  return NCL_OK;
+}
+
+ncl_status ncl_kkt_profile_report(ncl_kkt_t h, char* buf, int64_t buflen) {
+  if (!h || !buf || buflen <= 0) return fail(NCL_ERR_INVALID_ARG, "bad arguments");
+  std::string out = "{";
+  bool first = true;
+  for (const auto& kv : h->prof) {
+    char tmp[512];
+    std::snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e, \"bytes\": %.6e}",
+                  first ? "" : ", ", kv.first.c_str(), (long long)kv.second.launches, kv.second.ms, kv.second.flops,
+                  kv.second.bytes);
+    out += tmp;
+    first = false;
+  }
+  out += "}";
+  std::strncpy(buf, out.c_str(), (size_t)buflen - 1);
+  buf[buflen - 1] = 0;
+  return NCL_OK;
+}
+
+void ncl_kkt_destroy(ncl_kkt_t h) { delete h; }
+
+const char* ncl_kkt_status_string(ncl_status st) {
+  switch (st) {
+    case NCL_OK: return "NCL_OK";
+    case NCL_ERR_INVALID_ARG: return "NCL_ERR_INVALID_ARG";
+    case NCL_ERR_PATTERN: return "NCL_ERR_PATTERN";
+    case NCL_ERR_OOM: return "NCL_ERR_OOM";
+    case NCL_ERR_CUDA: return "NCL_ERR_CUDA";
+    case NCL_ERR_STATE: return "NCL_ERR_STATE";
+    case NCL_ERR_ZERO_PIVOT: return "NCL_ERR_ZERO_PIVOT";
+    case NCL_ERR_NUMERIC: return "NCL_ERR_NUMERIC";
+    case NCL_ERR_IR_NOT_CONVERGED: return "NCL_ERR_IR_NOT_CONVERGED";
+    case NCL_ERR_TIMEOUT: return "NCL_ERR_TIMEOUT";
+  }
+  return "NCL_ERR_UNKNOWN";
+}
+
+const char* ncl_kkt_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

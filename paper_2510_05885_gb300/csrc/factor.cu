@@ -1,0 +1,445 @@
+// Numeric multifrontal LDL^T kernels (sm_103a).
+//
+// A front of supernode s is the dense lower matrix on its rows:
+//   [ F11   .  ]   F11: ncol x ncol pivot block   (stored in the L block)
+//   [ F21  F22 ]   F21: nbelow x ncol             (stored in the L block)
+//                  F22: nbelow x nbelow update    (stored in the U block)
+// assembled from the original entries and the children's update blocks
+// (extend-add), then partially factored:
+//   F11 = L11 D1 L11^T,  L21 = F21 L11^-T D1^-1,  F22 -= L21 D1 L21^T.
+// This is the LDL^T with D diagonal and static pivoting of Section 3.1: no
+// row or column is ever exchanged; a pivot with |d| <= eps is replaced by
+// +-eps with the sign of its block before reordering (case (ii)), or counted
+// as a zero eigenvalue (case (i)).
+#include "runtime.h"
+
+#include <cmath>
+#include <cstdio>
+
+namespace ncl {
+
+// ---------------------------------------------------------------------------
+// FP64 values of the lower KKT entries:
+//   K2r (Eq. K2r): H_ij, Sigma_i + delta on the primal diagonal, J_ri in the
+//                  (2,1) block, -1/rho on the dual diagonal;
+//   K   (Eq. K1):  H_ij + (Sigma_i + delta) [i=j] + rho * sum_r J_ri J_rj,
+//                  the product summed over the constraint rows shared by i, j
+//                  in a fixed order (no atomics).
+// ---------------------------------------------------------------------------
+__global__ void k_kkt_values(DevPlan P, const double* __restrict__ Hv, const double* __restrict__ Jv,
+                             const double* __restrict__ S, const double* __restrict__ delta,
+                             const double* __restrict__ rho, double* __restrict__ Klow) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.nnzA;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    int32_t h = P.e_h[e], j = P.e_j[e];
+    if (h >= 0) v += Hv[h];
+    if (j >= 0) v += Jv[j];
+    int8_t kind = P.e_kind[e];
+    int32_t inst = P.e_inst[e];
+    if (kind == 1) v += S[P.e_var[e]] + delta[inst];
+    else if (kind == 2) v += -1.0 / rho[inst];
+    int64_t p0 = P.pair_ptr[e], p1 = P.pair_ptr[e + 1];
+    if (p1 > p0) {
+      double s = 0.0;
+      for (int64_t p = p0; p < p1; p++) s = fma(Jv[P.pair_p[p]], Jv[P.pair_q[p]], s);
+      v = fma(rho[inst], s, v);
+    }
+    Klow[e] = v;
+  }
+}
+
+void launch_kkt_values(const DevPlan& P, const double* Hv, const double* Jv, const double* S,
+                       const double* delta, const double* rho, double* Klow, cudaStream_t st) {
+  if (P.nnzA == 0) return;
+  int64_t blocks = (P.nnzA + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_kkt_values<<<(unsigned)blocks, 256, 0, st>>>(P, Hv, Jv, S, delta, rho, Klow);
+}
+
+// ||K||_inf per instance (max absolute row sum), as the bit pattern of a
+// non-negative double so that atomicMax on the integer orders it.
+__global__ void k_knorm(DevPlan P, const double* __restrict__ Klow, unsigned long long* knorm) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P.dim;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = P.F_rowptr[r]; q < P.F_rowptr[r + 1]; q++) s += fabs(Klow[P.F_src[q]]);
+    atomicMax(&knorm[P.row_inst[r]], (unsigned long long)__double_as_longlong(s));
+  }
+}
+
+void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st) {
+  if (P.dim == 0) return;
+  int64_t blocks = (P.dim + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_knorm<<<(unsigned)blocks, 256, 0, st>>>(P, Klow, knorm);
+}
+
+// ---------------------------------------------------------------------------
+// Static pivot (Section 3.1).  Returns the pivot to use and its status.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T static_pivot(T d, int sign, double eps, int policy, int8_t& st) {
+  if (!isfinite((double)d)) {
+    st = 3;
+    return d;
+  }
+  if (fabs((double)d) <= eps) {
+    st = policy == 0 ? 1 : 2;
+    return sign < 0 ? (T)(-eps) : (T)eps;
+  }
+  st = 0;
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Front assembly.  One CTA per (supernode, run of ASM_ROWS front rows):
+// zero the rows, store the original entries, then add the children's update
+// blocks child by child (a child's rows map to distinct parent rows, so the
+// threads of one child never collide; children are added in a fixed order).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const int s = it.x, r0 = it.y;
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
+  const int nb = nrow - ncol;
+  const int r1 = min(r0 + ASM_ROWS, nrow);
+  T* Lb = N.L + P.sn_Loff[s];
+  T* Ub = N.U + P.sn_Uoff[s];
+  // zero
+  for (int idx = threadIdx.x; idx < (r1 - r0) * ncp; idx += blockDim.x) Lb[(int64_t)r0 * ncp + idx] = T(0);
+  for (int r = max(r0, ncol); r < r1; r++) {
+    int a = r - ncol;
+    for (int b = threadIdx.x; b <= a; b += blockDim.x) Ub[(int64_t)a * nb + b] = T(0);
+  }
+  __syncthreads();
+  // original entries (each lands in its own position)
+  const int64_t rbase = P.sn_rows_off[s];
+  for (int r = r0 + (threadIdx.x >> 5); r < r1; r += (blockDim.x >> 5)) {
+    int64_t q0 = P.amap_ptr[rbase + r], q1 = P.amap_ptr[rbase + r + 1];
+    for (int64_t q = q0 + (threadIdx.x & 31); q < q1; q += 32)
+      Lb[(int64_t)r * ncp + P.amap_col[q]] = (T)N.Klow[P.amap_src[q]];
+  }
+  // children
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
+    __syncthreads();
+    const int c = P.child_list[k];
+    const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
+    const int32_t* rel = P.relmap + P.relmap_off[c];
+    const T* Uc = N.U + P.sn_Uoff[c];
+    const int alo = lower_bound_i32(rel, nbc, r0);
+    const int ahi = lower_bound_i32(rel, nbc, r1);
+    for (int a = alo + warp; a < ahi; a += nw) {
+      const int ra = rel[a];
+      const T* urow = Uc + (int64_t)a * nbc;
+      for (int b = lane; b <= a; b += 32) {
+        const int rb = rel[b];
+        const T v = urow[b];
+        if (rb < ncol) Lb[(int64_t)ra * ncp + rb] += v;
+        else Ub[(int64_t)(ra - ncol) * nb + (rb - ncol)] += v;
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st) {
+  if (count <= 0) return;
+  k_assemble<T><<<count, 256, 0, st>>>(P, N, items);
+}
+
+// ---------------------------------------------------------------------------
+// Small fronts: one CTA factors the whole front in shared memory.
+// Right-looking over the ncol pivots (only the L part is updated), then the
+// update block F22 -= L21 D1 L21^T straight from shared memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
+                                                      double eps, int policy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = list[blockIdx.x];
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
+  const int col0 = P.sn_col0[s];
+  T* F = reinterpret_cast<T*>(smem_raw);
+  T* w = F + (int64_t)nrow * ncp;
+  T* Lg = N.L + P.sn_Loff[s];
+  for (int idx = threadIdx.x; idx < nrow * ncp; idx += blockDim.x) F[idx] = Lg[idx];
+  __syncthreads();
+  for (int k = 0; k < ncol; k++) {
+    int8_t stt;
+    const T dk = static_pivot<T>(F[k * ncp + k], P.col_sign[col0 + k], eps, policy, stt);
+    for (int i = k + 1 + threadIdx.x; i < nrow; i += blockDim.x) w[i] = F[i * ncp + k];
+    __syncthreads();
+    const T invd = T(1) / dk;
+    const int nc = ncol - k - 1;
+    const int nr = nrow - k - 1;
+    if (nc > 0) {
+      for (int idx = threadIdx.x; idx < nr * nc; idx += blockDim.x) {
+        const int i = k + 1 + idx / nc;
+        const int j = k + 1 + idx % nc;
+        if (j <= i) F[i * ncp + j] -= (w[i] * invd) * w[j];
+      }
+    }
+    for (int i = k + 1 + threadIdx.x; i < nrow; i += blockDim.x) F[i * ncp + k] = w[i] * invd;
+    if (threadIdx.x == 0) {
+      F[k * ncp + k] = dk;
+      N.D[col0 + k] = dk;
+      N.piv[col0 + k] = stt;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < nrow * ncp; idx += blockDim.x) Lg[idx] = F[idx];
+  // update block
+  const int nb = nrow - ncol;
+  if (nb == 0) return;
+  T* Ug = N.U + P.sn_Uoff[s];
+  const int64_t ntri = (int64_t)nb * (nb + 1) / 2;
+  for (int64_t t = threadIdx.x; t < ntri; t += blockDim.x) {
+    // t -> (a, b), b <= a
+    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)a * (a + 1) / 2 > t) a--;
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= t) a++;
+    const int b = (int)(t - (int64_t)a * (a + 1) / 2);
+    const T* la = F + (int64_t)(ncol + a) * ncp;
+    const T* lb = F + (int64_t)(ncol + b) * ncp;
+    T acc = T(0);
+    for (int k = 0; k < ncol; k++) acc += la[k] * F[k * ncp + k] * lb[k];
+    Ug[(int64_t)a * nb + b] -= acc;
+  }
+}
+
+template <typename T>
+void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, double eps,
+                         int policy, cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_factor_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SMEM + 4096);
+    attr = true;
+  }
+  k_factor_small<T><<<count, 256, SMALL_SMEM + 4096, st>>>(P, N, list, eps, policy);
+}
+
+// ---------------------------------------------------------------------------
+// Panel of a large front: pivot columns [p0, pe), pe - p0 <= PANEL_NB.
+// Every CTA factors the PANEL_NB x PANEL_NB diagonal block in shared memory
+// (cheap, and it saves a launch); the CTA whose row run starts at pe also
+// writes it back.  Each thread then solves one row below the block:
+//   q = L11^-1 f_i (forward substitution), l_i = D1^-1 q.
+// item = (s, p0, r0, first): rows [r0, r0 + PANEL_ROWS) of front s.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(PANEL_ROWS) k_panel(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
+                                                     double eps, int policy) {
+  __shared__ T Db[PANEL_NB][PANEL_NB + 1];
+  __shared__ T wv[PANEL_NB];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, p0 = it.y, r0 = it.z, first = it.w;
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
+  const int col0 = P.sn_col0[s];
+  const int pe = min(p0 + PANEL_NB, ncol);
+  const int nbk = pe - p0;
+  T* Lb = N.L + P.sn_Loff[s];
+  for (int idx = threadIdx.x; idx < PANEL_NB * PANEL_NB; idx += blockDim.x) {
+    const int i = idx / PANEL_NB, j = idx % PANEL_NB;
+    Db[i][j] = (i < nbk && j <= i) ? Lb[(int64_t)(p0 + i) * ncp + p0 + j] : T(0);
+  }
+  __syncthreads();
+  for (int k = 0; k < nbk; k++) {
+    int8_t stt;
+    const T dk = static_pivot<T>(Db[k][k], P.col_sign[col0 + p0 + k], eps, policy, stt);
+    if (threadIdx.x < PANEL_NB) wv[threadIdx.x] = Db[threadIdx.x][k];
+    __syncthreads();
+    const T invd = T(1) / dk;
+    for (int idx = threadIdx.x; idx < PANEL_NB * PANEL_NB; idx += blockDim.x) {
+      const int i = idx / PANEL_NB, j = idx % PANEL_NB;
+      if (i > k && i < nbk && j > k && j <= i) Db[i][j] -= (wv[i] * invd) * wv[j];
+    }
+    if (threadIdx.x > k && threadIdx.x < nbk) Db[threadIdx.x][k] = wv[threadIdx.x] * invd;
+    if (threadIdx.x == 0) {
+      Db[k][k] = dk;
+      if (first) {
+        N.D[col0 + p0 + k] = dk;
+        N.piv[col0 + p0 + k] = stt;
+      }
+    }
+    __syncthreads();
+  }
+  if (first) {
+    for (int idx = threadIdx.x; idx < nbk * nbk; idx += blockDim.x) {
+      const int i = idx / nbk, j = idx % nbk;
+      if (j <= i) Lb[(int64_t)(p0 + i) * ncp + p0 + j] = Db[i][j];
+    }
+  }
+  const int i = r0 + threadIdx.x;
+  if (i < nrow && i >= pe && i < r0 + PANEL_ROWS) {
+    T q[PANEL_NB];
+    T* row = Lb + (int64_t)i * ncp + p0;
+#pragma unroll
+    for (int t = 0; t < PANEL_NB; t++) q[t] = (t < nbk) ? row[t] : T(0);
+#pragma unroll
+    for (int t = 1; t < PANEL_NB; t++) {
+      T acc = q[t];
+#pragma unroll
+      for (int u = 0; u < t; u++) acc -= Db[t][u] * q[u];
+      q[t] = acc;
+    }
+#pragma unroll
+    for (int t = 0; t < PANEL_NB; t++)
+      if (t < nbk) row[t] = q[t] / Db[t][t];
+  }
+}
+
+template <typename T>
+void launch_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, double eps, int policy,
+                  cudaStream_t st) {
+  if (count <= 0) return;
+  k_panel<T><<<count, PANEL_ROWS, 0, st>>>(P, N, items, eps, policy);
+}
+
+// ---------------------------------------------------------------------------
+// SIMT update C -= A diag(d) B^T (lower part), 64 x 64 tiles, 256 threads,
+// 4 x 4 outputs per thread.  FP64 uses DFMA, FP32 FFMA.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void decode_tile(int64_t t, int Nt, int& ti, int& tj) {
+  const int64_t tri = (int64_t)Nt * (Nt + 1) / 2;
+  if (t < tri) {
+    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)a * (a + 1) / 2 > t) a--;
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= t) a++;
+    ti = a;
+    tj = (int)(t - (int64_t)a * (a + 1) / 2);
+  } else {
+    const int64_t u = t - tri;
+    ti = Nt + (int)(u / Nt);
+    tj = (int)(u % Nt);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_simt(DevNum<T> N, const GemmProb* __restrict__ probs, int nprob) {
+  constexpr int TB = GEMM_TILE, KC = 16;
+  __shared__ T As[KC][TB + 1];
+  __shared__ T Bs[KC][TB + 1];
+  // find the problem of this tile
+  const int64_t gt = blockIdx.x;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile0 <= gt) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmProb pb = probs[lo];
+  int ti, tj;
+  decode_tile(gt - pb.tile0, pb.Nt, ti, tj);
+  const int i0 = ti * TB, j0 = tj * TB;
+  const T* A = N.L + pb.a_off;
+  const T* B = N.L + pb.b_off;
+  const T* d = N.D + pb.d_off;
+  T* C = (pb.c_in_u ? N.U : N.L) + pb.c_off;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) acc[a][b] = T(0);
+  for (int k0 = 0; k0 < pb.K; k0 += KC) {
+    for (int idx = threadIdx.x; idx < TB * KC; idx += 256) {
+      const int r = idx / KC, kk = idx % KC;
+      const int k = k0 + kk;
+      const int ia = i0 + r, jb = j0 + r;
+      As[kk][r] = (ia < pb.M && k < pb.K) ? A[(int64_t)ia * pb.lda + k] : T(0);
+      Bs[kk][r] = (jb < pb.N && k < pb.K) ? B[(int64_t)jb * pb.lda + k] * d[k] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; kk++) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; a++) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; b++) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= pb.M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const int j = j0 + tx + 16 * b;
+      if (j >= pb.N || j > i) continue;
+      C[(int64_t)i * pb.ldc + j] -= acc[a][b];
+    }
+  }
+}
+
+template <typename T>
+void launch_gemm_simt(const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  k_gemm_simt<T><<<(unsigned)ntiles, 256, 0, st>>>(N, probs, nprob);
+}
+
+// ---------------------------------------------------------------------------
+// Inertia and perturbed-pivot counts per instance:
+// counts[4*inst + {0,1,2,3}] = (n_pos, n_neg, n_zero, n_perturbed), plus
+// counts[4*ninst] = number of non-finite pivots.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_inertia(DevPlan P, DevNum<T> N, long long* counts) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P.dim;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int inst = P.col_inst[k];
+    const int8_t st = N.piv[k];
+    const T d = N.D[k];
+    long long* c = counts + 4 * inst;
+    if (st == 3) {
+      atomicAdd((unsigned long long*)&counts[4 * P.ninst], 1ull);
+      continue;
+    }
+    if (st == 2) atomicAdd((unsigned long long*)&c[2], 1ull);
+    else if (d > T(0)) atomicAdd((unsigned long long*)&c[0], 1ull);
+    else if (d < T(0)) atomicAdd((unsigned long long*)&c[1], 1ull);
+    else atomicAdd((unsigned long long*)&c[2], 1ull);
+    if (st == 1) atomicAdd((unsigned long long*)&c[3], 1ull);
+  }
+}
+
+template <typename T>
+void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st) {
+  if (P.dim == 0) return;
+  int64_t blocks = (P.dim + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_inertia<T><<<(unsigned)blocks, 256, 0, st>>>(P, N, counts);
+}
+
+#define NCL_INST(T)                                                                                     \
+  template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, int, cudaStream_t);   \
+  template void launch_factor_small<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, double,   \
+                                       int, cudaStream_t);                                              \
+  template void launch_panel<T>(const DevPlan&, const DevNum<T>&, const int4*, int, double, int,        \
+                                cudaStream_t);                                                          \
+  template void launch_gemm_simt<T>(const DevNum<T>&, const GemmProb*, int, int64_t, cudaStream_t);     \
+  template void launch_inertia<T>(const DevPlan&, const DevNum<T>&, long long*, cudaStream_t);
+NCL_INST(float)
+NCL_INST(double)
+#undef NCL_INST
+
+}  // namespace ncl

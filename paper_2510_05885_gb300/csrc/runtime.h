@@ -1,0 +1,143 @@
+// Device-side plan, numeric state and kernel launchers (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ncl {
+
+// Tile/chunk constants shared by the launch planner and the kernels.
+constexpr int ASM_ROWS = 32;      // front rows per assembly CTA
+constexpr int PANEL_NB = 32;      // pivot columns per panel
+constexpr int PANEL_ROWS = 128;   // rows below the panel per CTA
+constexpr int GEMM_TILE = 64;     // SIMT update tile (rows x cols)
+constexpr int SOLVE_ROWS = 64;    // below rows per solve CTA
+constexpr int SMALL_SMEM = 64 * 1024;  // dynamic smem limit of a small front
+
+// Pointers into device copies of the symbolic plan.
+struct DevPlan {
+  int64_t dim;
+  int32_t ns, ninst, form;
+  int64_t nnzA;
+  // value recipe of the lower KKT entries (natural numbering)
+  const int32_t* e_h;
+  const int32_t* e_j;
+  const int32_t* e_var;
+  const int32_t* e_inst;
+  const int8_t* e_kind;
+  const int64_t* pair_ptr;
+  const int32_t* pair_p;
+  const int32_t* pair_q;
+  // full symmetric CSR (natural numbering)
+  const int64_t* F_rowptr;
+  const int32_t* F_col;
+  const int32_t* F_src;
+  const int32_t* row_inst;
+  // supernodes
+  const int32_t* sn_col0;
+  const int32_t* sn_ncol;
+  const int32_t* sn_ncolp;
+  const int32_t* sn_nrow;
+  const int64_t* sn_rows_off;
+  const int32_t* sn_rows;
+  const int64_t* sn_Loff;
+  const int64_t* sn_Uoff;
+  const int64_t* sn_Woff;
+  const int64_t* sn_Poff;
+  const int32_t* child_ptr;
+  const int32_t* child_list;
+  const int64_t* relmap_off;
+  const int32_t* relmap;
+  const int64_t* amap_ptr;
+  const int32_t* amap_col;
+  const int32_t* amap_src;
+  const int32_t* perm;       // pivot k -> natural index
+  const int32_t* col_inst;   // instance of pivot k
+  const int8_t* col_sign;    // block sign of pivot k
+  int64_t Wtot, Ptot;        // forward / backward solve workspace per RHS
+  // adjoint
+  const int32_t* H_row;
+  const int32_t* H_col;
+  const int32_t* J_con;      // constraint of each J value
+  const int32_t* J_col;      // KKT row of the variable of each J value
+  const int32_t* J_inst;
+  const int32_t* con_row;    // KKT row of each constraint (K2r), -1 (K)
+  const int64_t* J_rowptr;   // concatenated J by constraint
+  const int32_t* var_row;    // KKT row of each primal variable
+  const int32_t* con_inst;   // instance of each constraint
+  int64_t nnzH, nnzJ, nvar, ncon;
+  const int64_t* inst_row_off;  // ninst+1
+};
+
+// Numeric state for one precision T (float or double).
+template <typename T>
+struct DevNum {
+  T* L;            // supernodal factor blocks (row-major, ld = ncolp)
+  T* U;            // multifrontal update blocks (row-major lower, ld = nbelow)
+  T* D;            // pivots, permuted order
+  int8_t* piv;     // pivot status: 0 ok, 1 perturbed, 2 zero (stop policy), 3 non-finite
+  const double* Klow;  // FP64 lower KKT values (natural numbering)
+};
+
+// A dense update C -= A diag(d) B^T restricted to the lower part, over a
+// set of fronts: problems are concatenated; each owns a run of tiles.
+struct GemmProb {
+  int64_t c_off;     // C element offset (in L or U storage)
+  int64_t a_off;     // A = rows of a factor block
+  int64_t b_off;     // B = rows of the same block
+  int64_t d_off;     // pivots d (index into D)
+  int32_t ldc, lda;
+  int32_t M, N, K;   // C is M x N (lower part: row + diag_shift >= col), inner dim K
+  int32_t c_in_u;    // 1: C lives in U storage, 0: in L storage
+  int32_t Nt;        // column tiles
+  int64_t tile0;     // first global tile of this problem
+};
+
+// launchers (factor.cu)
+void launch_kkt_values(const DevPlan& P, const double* Hv, const double* Jv, const double* S,
+                       const double* delta, const double* rho, double* Klow, cudaStream_t st);
+void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st);
+template <typename T>
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st);
+template <typename T>
+void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count,
+                         double eps, int policy, cudaStream_t st);
+template <typename T>
+void launch_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, double eps,
+                  int policy, cudaStream_t st);
+template <typename T>
+void launch_gemm_simt(const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles,
+                      cudaStream_t st);
+template <typename T>
+void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st);
+
+// launchers (solve.cu)
+template <typename T>
+void launch_perm_in(const DevPlan& P, T* xp, const double* B, int64_t ldb, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int nrhs, int accumulate,
+                     cudaStream_t st);
+template <typename T>
+void launch_fwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp, T* W,
+                     int nrhs, cudaStream_t st);
+template <typename T>
+void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, T* xp, T* W,
+                      int nrhs, cudaStream_t st);
+template <typename T>
+void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const T* xp,
+                      T* Pw, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_bwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp,
+                     const T* Pw, int nrhs, cudaStream_t st);
+void launch_residual(const DevPlan& P, const double* Klow, const double* B, int64_t ldb, const double* X,
+                     int64_t ldx, double* R, int64_t ldr, int nrhs, unsigned long long* rnorm,
+                     unsigned long long* xnorm, cudaStream_t st);
+void launch_vec_norm(const DevPlan& P, const double* B, int64_t ldb, int nrhs, unsigned long long* out,
+                     cudaStream_t st);
+void launch_axpy_inplace(double* X, int64_t ldx, const double* Y, int64_t ldy, double a, int64_t dim,
+                         int nrhs, cudaStream_t st);
+void launch_adjoint_values(const DevPlan& P, const double* Jv, const double* rho, const double* X,
+                           int64_t ldx, const double* GB, int64_t ldgb, int nrhs, double* G_H,
+                           double* G_J, double* G_S, double* G_scal, double* jx, double* jg,
+                           cudaStream_t st);
+
+}  // namespace ncl

@@ -1,0 +1,245 @@
+"""GPU parity: the CUDA factor/solve (through the C ABI) against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances (see the design notes for the derivation):
+* FP64 path: backward error eta <= 1e-12 and relative solution error
+  <= max(1e-9, 10 kappa u) against the oracle (two backward-stable FP64
+  solves differ by about kappa u).
+* FP32 + refinement: eta <= 1e-10, solution error <= max(1e-9, 10 kappa 1e-10).
+* inertia: exactly (n, m, 0) for K2r and (n, 0, 0) for K (Section 3.4).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_2510_05885_gb300 import synth
+from tests.helpers import custom_instance
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def nk():
+    from paper_2510_05885_gb300 import ncl_kkt
+    return ncl_kkt
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def gpu_solve(inst, prec, **opts):
+    p = inst.pat
+    form = 0 if inst.form == "stabilized" else 1
+    K = nk().KKT(form, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind, prec=prec, **opts)
+    finfo = K.factor(_t(inst.H_val), _t(inst.J_val), _t(inst.Sigma), inst.delta, inst.rho)
+    X, sinfo = K.solve(_t(inst.b))
+    torch.cuda.synchronize()
+    return K, finfo, X.cpu().numpy(), sinfo
+
+
+def check_against_oracle(inst, prec, X, finfo, sinfo, eta_tol):
+    x_o, fac, eta_o, A = O.solve_instance(inst)
+    assert eta_o <= 1e-12
+    assert finfo.inertia == fac.inertia
+    assert finfo.n_perturbed == fac.n_perturbed == 0
+    eta = O.backward_error(A, X, inst.b)          # recomputed on the CPU, FP64
+    assert eta <= eta_tol, eta
+    assert sinfo.backward_err <= eta_tol * 1.0001
+    kappa = O.cond1_estimate(A, fac) if A.shape[0] <= 60000 else 1e6
+    u = 2.0 ** -53 if prec == "fp64" else 1e-10
+    tol = max(1e-9, 10 * kappa * u)
+    err = np.max(np.abs(X - x_o)) / np.max(np.abs(x_o))
+    assert err <= tol, (err, tol, kappa)
+    return eta, err
+
+
+@pytest.mark.parametrize("prec,eta_tol", [("fp64", 1e-12), ("fp32_ir", 1e-10)])
+def test_stabilized_20x25(prec, eta_tol):
+    inst = synth.stabilized_20x25()
+    K, finfo, X, sinfo = gpu_solve(inst, prec)
+    assert finfo.inertia == (2000, 1000, 0)
+    check_against_oracle(inst, prec, X, finfo, sinfo, eta_tol)
+
+
+@pytest.mark.parametrize("prec,eta_tol", [("fp64", 1e-12), ("fp32_ir", 1e-10)])
+@pytest.mark.parametrize("side,rho", [(24, 1e2), (24, 1e5), (30, 1e4)])
+def test_condensed_grid(prec, eta_tol, side, rho):
+    inst = synth.condensed_grid(side, rho=rho, draw=1, sigma0=None)
+    K, finfo, X, sinfo = gpu_solve(inst, prec)
+    assert finfo.inertia == (inst.n, 0, 0)
+    check_against_oracle(inst, prec, X, finfo, sinfo, eta_tol)
+
+
+@pytest.mark.parametrize("prec,eta_tol", [("fp64", 1e-12), ("fp32_ir", 1e-10)])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 2), (3, 1), (13, 17), (40, 40)])
+def test_stabilized_shapes_multi_rhs(prec, eta_tol, shape):
+    inst = synth.random_instance(*shape, seed=100 + shape[0], form="stabilized", rho=1e4, nrhs=4)
+    K, finfo, X, sinfo = gpu_solve(inst, prec)
+    assert finfo.inertia == (inst.n, inst.m, 0)
+    check_against_oracle(inst, prec, X, finfo, sinfo, eta_tol)
+
+
+@pytest.mark.parametrize("nrhs", [9, 17])
+def test_many_rhs(nrhs):
+    """More right-hand sides than one sweep carries (8)."""
+    inst = synth.random_instance(6, 7, seed=3, form="stabilized", rho=1e3, nrhs=nrhs)
+    K, finfo, X, sinfo = gpu_solve(inst, "fp64")
+    check_against_oracle(inst, "fp64", X, finfo, sinfo, 1e-12)
+
+
+def test_no_constraints_is_cholesky():
+    """m = 0: K2r reduces to H + Sigma + delta I."""
+    base = synth.random_instance(5, 5, seed=8, form="stabilized")
+    p = base.pat
+    Hfull = O.kkt_condensed(p.n, 0, p.H_rowptr, p.H_colind, base.H_val, np.zeros(1, np.int32),
+                            np.zeros(0, np.int32), np.zeros(0), np.zeros(p.n), 0.0, 1.0)
+    inst = custom_instance(Hfull, sp.csr_matrix((0, p.n)), base.Sigma, base.delta, 1.0,
+                           np.random.default_rng(0).standard_normal(p.n))
+    K, finfo, X, sinfo = gpu_solve(inst, "fp64")
+    assert finfo.inertia == (p.n, 0, 0)
+    check_against_oracle(inst, "fp64", X, finfo, sinfo, 1e-12)
+
+
+def test_zero_pivot_perturbation_and_stop_policy():
+    """Both diagonal entries ~0: whichever is eliminated first is a zero pivot
+    (Section 3.1); it is replaced by +-eps and refinement recovers x."""
+    inst = custom_instance(np.array([[-1.0]]), np.array([[1.0]]), [1.0], 0.0, 1e300, [3.0, -2.0])
+    K, finfo, X, sinfo = gpu_solve(inst, "fp64", ir_max_iter=10)
+    assert finfo.n_perturbed == 1
+    assert finfo.inertia == (1, 1, 0)
+    assert np.allclose(X[:, 0], [-2.0, 3.0], rtol=1e-9)
+    p = inst.pat
+    K2 = nk().KKT(0, 1, 1, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind, prec="fp64", pivot_policy=1)
+    info = K2.factor(_t(inst.H_val), _t(inst.J_val), _t(inst.Sigma), 0.0, 1e300)
+    assert info.status == 6 and info.n_zero == 1 and info.n_perturbed == 0
+
+
+def test_diag_H_identity_J_closed_form():
+    from tests.helpers import read_golden
+    import os
+    gd = read_golden(os.path.join(os.path.dirname(__file__), "golden", "diag_H_identity_J.txt"))
+    a = np.array(gd["a"])
+    inst = custom_instance(np.diag(a), np.eye(2), np.zeros(2), 0.0, gd["rho"][0],
+                           np.concatenate([gd["f"], gd["g"]]))
+    for prec in ("fp64", "fp32_ir"):
+        K, finfo, X, sinfo = gpu_solve(inst, prec)
+        assert finfo.inertia == (2, 2, 0)
+        assert np.allclose(X[:2, 0], gd["u"], rtol=1e-12)
+        assert np.allclose(X[2:, 0], gd["v"], rtol=1e-12)
+
+
+def test_refactor_same_pattern_new_values():
+    """Analyze once, factor many: values redrawn on the fixed pattern."""
+    pat = synth.make_pattern(18, 18)
+    form = 1
+    K = nk().KKT(form, pat.n, pat.m, pat.H_rowptr, pat.H_colind, pat.J_rowptr, pat.J_colind, prec="fp32_ir")
+    sig0 = None
+    for d in range(4):
+        inst = synth.condensed_grid(18, rho=1e4, draw=d, pat=pat, sigma0=sig0)
+        sig0 = inst.sigma0
+        finfo = K.factor(_t(inst.H_val), _t(inst.J_val), _t(inst.Sigma), inst.delta, inst.rho)
+        X, sinfo = K.solve(_t(inst.b))
+        check_against_oracle(inst, "fp32_ir", X.cpu().numpy(), finfo, sinfo, 1e-10)
+
+
+def test_solve_before_factor_is_state_error():
+    pat = synth.make_pattern(2, 2)
+    K = nk().KKT(0, pat.n, pat.m, pat.H_rowptr, pat.H_colind, pat.J_rowptr, pat.J_colind, prec="fp64")
+    with pytest.raises(nk().NclError) as e:
+        K.solve(torch.zeros(pat.n + pat.m, dtype=torch.float64, device=DEV))
+    assert e.value.status == 5
+
+
+def test_device_memory_cap():
+    pat = synth.make_pattern(10, 10)
+    with pytest.raises(nk().NclError) as e:
+        nk().KKT(0, pat.n, pat.m, pat.H_rowptr, pat.H_colind, pat.J_rowptr, pat.J_colind,
+                 max_device_bytes=1000)
+    assert e.value.status == 3
+
+
+# ------------------------------------------------------------------ batches
+
+@pytest.mark.parametrize("prec,eta_tol", [("fp64", 1e-12), ("fp32_ir", 1e-10)])
+def test_scenario_batch(prec, eta_tol):
+    """Instances with 1-3 deleted edges each (patterns differ), 4 RHS, one
+    handle; each instance against its own oracle solve."""
+    batch = synth.scenario_batch(count=6, side=12, nrhs=4)
+    pats = [(i.n, i.m, i.pat.H_rowptr, i.pat.H_colind, i.pat.J_rowptr, i.pat.J_colind) for i in batch]
+    K = nk().KKT.batch(0, pats, prec=prec)
+    Hv = _t(np.concatenate([i.H_val for i in batch]))
+    Jv = _t(np.concatenate([i.J_val for i in batch]))
+    S = _t(np.concatenate([i.Sigma for i in batch]))
+    B = _t(np.concatenate([i.b for i in batch], axis=0))
+    infos = K.factor(Hv, Jv, S, [i.delta for i in batch], [i.rho for i in batch])
+    X, sinfo = K.solve(B)
+    X = X.cpu().numpy()
+    off = 0
+    for inst, fi in zip(batch, infos):
+        d = inst.dim
+        assert fi.inertia == (inst.n, inst.m, 0)
+        check_against_oracle(inst, prec, X[off:off + d], fi, sinfo, eta_tol)
+        off += d
+
+
+def test_batch_factor_solve_entry_point():
+    batch = synth.scenario_batch(count=3, side=8, nrhs=2)
+    pats = [(i.n, i.m, i.pat.H_rowptr, i.pat.H_colind, i.pat.J_rowptr, i.pat.J_colind) for i in batch]
+    K = nk().KKT.batch(0, pats, prec="fp32_ir")
+    Hv = _t(np.concatenate([i.H_val for i in batch]))
+    Jv = _t(np.concatenate([i.J_val for i in batch]))
+    S = _t(np.concatenate([i.Sigma for i in batch]))
+    B = np.concatenate([i.b for i in batch], axis=0)
+    Bc = _t(B.T.copy())
+    Xc = torch.empty_like(Bc)
+    infos, sinfo = nk().ncl_kkt_batch_factor_solve(K._h, Hv, Jv, S, [i.delta for i in batch],
+                                                   [i.rho for i in batch], 2, Bc, K.dim, Xc, K.dim)
+    X = Xc.cpu().numpy().T
+    off = 0
+    for inst, fi in zip(batch, infos):
+        check_against_oracle(inst, "fp32_ir", X[off:off + inst.dim], fi, sinfo, 1e-10)
+        off += inst.dim
+
+
+# ------------------------------------------------------------------ adjoint
+
+@pytest.mark.parametrize("form", ["stabilized", "condensed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
+def test_adjoint_matches_oracle(form, prec):
+    inst = synth.random_instance(6, 5, seed=44, form=form, rho=1e3, nrhs=2)
+    K, finfo, X, sinfo = gpu_solve(inst, prec)
+    rng = np.random.default_rng(9)
+    GX = rng.standard_normal(X.shape)
+    p = inst.pat
+    g = K.adjoint(_t(X), _t(GX), nnz_H=p.nnz_H, nnz_J=p.nnz_J, n_var=p.n)
+    x_o, fac, _, A = O.solve_instance(inst)
+    ref = O.adjoint(inst, fac, A, x_o, GX)
+    tol = 1e-9 if prec == "fp64" else 1e-7
+    for key, rk in (("b", "g_b"), ("H", "g_H"), ("J", "g_J"), ("Sigma", "g_Sigma")):
+        got = g[key].cpu().numpy().reshape(-1)
+        want = np.asarray(ref[rk]).reshape(-1)
+        assert np.max(np.abs(got - want)) <= tol * max(1.0, np.max(np.abs(want))), key
+    sc = g["scal"].cpu().numpy()
+    assert abs(sc[0] - ref["g_delta"]) <= tol * max(1.0, abs(ref["g_delta"]))
+    assert abs(sc[1] - ref["g_rho"]) <= tol * max(1.0, abs(ref["g_rho"]))
+
+
+# ------------------------------------------------------------------ full size
+
+@pytest.mark.parametrize("rho", [1e2, 1e5])
+def test_condensed_300x300_full_size(rho):
+    """The 300 x 300 condensed workload at full size, FP32 + refinement, in
+    the bench's configuration: properties that hold at any size (inertia,
+    FP64 backward error recomputed on the CPU from the oracle's matrix)."""
+    pat = synth.make_pattern(300, 300)
+    inst = synth.condensed_grid(300, rho=rho, draw=0, pat=pat)
+    K, finfo, X, sinfo = gpu_solve(inst, "fp32_ir")
+    assert finfo.inertia == (inst.n, 0, 0)
+    assert finfo.n_perturbed == 0
+    A = O.instance_matrix(inst)
+    eta = O.backward_error(A, X, inst.b)
+    assert eta <= 1e-10, eta
