@@ -53,6 +53,8 @@ struct Cost {
 };
 
 struct Step {
+  int64_t pdiag_off = 0;
+  int pdiag_cnt = 0;
   int64_t panel_off = 0;
   int panel_cnt = 0;
   int64_t prob_off = 0;
@@ -94,6 +96,7 @@ struct HostSched {
   std::vector<int2> asmv, belowv;
   std::vector<int32_t> smallv, listv;
   std::vector<int4> panelv;
+  std::vector<int2> pdiagv;
   std::vector<GemmProb> probv;
 };
 
@@ -125,6 +128,7 @@ struct ncl_kkt_s {
   int2* d_asm = nullptr;
   int32_t* d_small = nullptr;
   int4* d_panel = nullptr;
+  int2* d_pdiag = nullptr;
   GemmProb* d_probs = nullptr;
   int32_t* d_lists = nullptr;
   int2* d_below = nullptr;
@@ -200,6 +204,7 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<int32_t>& smallv = hs.smallv;
   std::vector<int32_t>& listv = hs.listv;
   std::vector<int4>& panelv = hs.panelv;
+  std::vector<int2>& pdiagv = hs.pdiagv;
   std::vector<GemmProb>& probv = hs.probv;
   h->levels.assign(P.nlevels, Level{});
   for (int32_t l = 0; l < P.nlevels; l++) {
@@ -250,6 +255,7 @@ void build_schedule(ncl_kkt_s* h) {
     for (int p = 0; p < maxp; p++) {
       Step& S = L.steps[p];
       S.panel_off = (int64_t)panelv.size();
+      S.pdiag_off = (int64_t)pdiagv.size();
       S.prob_off = (int64_t)probv.size();
       int64_t tiles = 0;
       for (int32_t s : large) {
@@ -257,11 +263,8 @@ void build_schedule(ncl_kkt_s* h) {
         const int p0 = p * PANEL_NB;
         if (p0 >= ncol) continue;
         const int pe = std::min(p0 + PANEL_NB, ncol);
-        int r0 = pe;
-        do {
-          panelv.push_back(make_int4(s, p0, r0, r0 == pe ? 1 : 0));
-          r0 += PANEL_ROWS;
-        } while (r0 < nrow);
+        pdiagv.push_back(make_int2(s, p0));
+        for (int r0 = pe; r0 < nrow; r0 += PANEL_ROWS) panelv.push_back(make_int4(s, p0, r0, 0));
         S.panel_cost.flops += (double)(nrow - pe) * (pe - p0) * (pe - p0) + 2.0 * (pe - p0) * (pe - p0) * (pe - p0) / 3.0;
         S.panel_cost.bytes += esz * 2.0 * (nrow - p0) * (pe - p0);
         if (pe < ncol) {
@@ -287,6 +290,7 @@ void build_schedule(ncl_kkt_s* h) {
         }
       }
       S.panel_cnt = (int)(panelv.size() - S.panel_off);
+      S.pdiag_cnt = (int)(pdiagv.size() - S.pdiag_off);
       S.prob_cnt = (int)(probv.size() - S.prob_off);
       S.tiles = tiles;
     }
@@ -356,8 +360,10 @@ void build_schedule(ncl_kkt_s* h) {
     }
     for (const int4& it : panelv) {
       const int s = it.x;
-      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.z < 0 || it.z > P.sn_nrow[s]) bad("panel item");
+      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.z < 0 || it.z >= P.sn_nrow[s]) bad("panel item");
     }
+    for (const int2& it : pdiagv)
+      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_ncol[it.x]) bad("panel diag item");
     for (const GemmProb& g : probv) {
       const int64_t csz = g.c_in_u ? Usz : Lsz;
       if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.N > g.M) bad("gemm shape");
@@ -474,6 +480,7 @@ void build_device(ncl_kkt_s* h) {
   h->d_asm = h->upload(hs.asmv);
   h->d_small = h->upload(hs.smallv);
   h->d_panel = h->upload(hs.panelv);
+  h->d_pdiag = h->upload(hs.pdiagv);
   h->d_probs = h->upload(hs.probv);
   h->d_lists = h->upload(hs.listv);
   h->d_below = h->upload(hs.belowv);
@@ -540,9 +547,11 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
       launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
     });
     for (const Step& S : L.steps) {
-      klaunch(h, st, f32 ? "panel_f32" : "panel_f64", S.panel_cnt, S.panel_cost, [&] {
-        launch_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
+      klaunch(h, st, f32 ? "panel_diag_f32" : "panel_diag_f64", S.pdiag_cnt, Cost{}, [&] {
+        launch_panel_diag<T>(P, N, h->d_pdiag + S.pdiag_off, S.pdiag_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
       });
+      klaunch(h, st, f32 ? "panel_rows_f32" : "panel_rows_f64", S.panel_cnt, S.panel_cost,
+              [&] { launch_panel_rows<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, st); });
       klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost,
               [&] { launch_gemm_simt<T>(N, h->d_probs + S.prob_off, S.prob_cnt, S.tiles, st); });
     }

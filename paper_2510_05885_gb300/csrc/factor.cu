@@ -234,20 +234,21 @@ void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* li
 
 // ---------------------------------------------------------------------------
 // Panel of a large front: pivot columns [p0, pe), pe - p0 <= PANEL_NB.
-// Every CTA factors the PANEL_NB x PANEL_NB diagonal block in shared memory
-// (cheap, and it saves a launch); the CTA whose row run starts at pe also
-// writes it back.  Each thread then solves one row below the block:
+// k_panel_diag (one CTA per front) factors the diagonal block in shared
+// memory and writes L11 and D1 back; then k_panel_rows solves the rows
+// below it, PANEL_ROWS rows per CTA, one row per thread:
 //   q = L11^-1 f_i (forward substitution), l_i = D1^-1 q.
-// item = (s, p0, r0, first): rows [r0, r0 + PANEL_ROWS) of front s.
+// (Two launches: the row CTAs must read the factored block, which no CTA
+// of the same launch may be rewriting.)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(PANEL_ROWS) k_panel(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
-                                                     double eps, int policy) {
+__global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+                                                   double eps, int policy) {
   __shared__ T Db[PANEL_NB][PANEL_NB + 1];
   __shared__ T wv[PANEL_NB];
-  const int4 it = items[blockIdx.x];
-  const int s = it.x, p0 = it.y, r0 = it.z, first = it.w;
-  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
+  const int2 it = items[blockIdx.x];
+  const int s = it.x, p0 = it.y;
+  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
   const int col0 = P.sn_col0[s];
   const int pe = min(p0 + PANEL_NB, ncol);
   const int nbk = pe - p0;
@@ -270,23 +271,35 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(DevPlan P, DevNum<T> N, co
     if (threadIdx.x > k && threadIdx.x < nbk) Db[threadIdx.x][k] = wv[threadIdx.x] * invd;
     if (threadIdx.x == 0) {
       Db[k][k] = dk;
-      if (first) {
-        N.D[col0 + p0 + k] = dk;
-        N.piv[col0 + p0 + k] = stt;
-      }
+      N.D[col0 + p0 + k] = dk;
+      N.piv[col0 + p0 + k] = stt;
     }
     __syncthreads();
   }
-  if (first) {
-    for (int idx = threadIdx.x; idx < nbk * nbk; idx += blockDim.x) {
-      const int i = idx / nbk, j = idx % nbk;
-      if (j <= i) Lb[(int64_t)(p0 + i) * ncp + p0 + j] = Db[i][j];
-    }
+  for (int idx = threadIdx.x; idx < nbk * nbk; idx += blockDim.x) {
+    const int i = idx / nbk, j = idx % nbk;
+    if (j <= i) Lb[(int64_t)(p0 + i) * ncp + p0 + j] = Db[i][j];
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PANEL_ROWS) k_panel_rows(DevPlan P, DevNum<T> N, const int4* __restrict__ items) {
+  __shared__ T Db[PANEL_NB][PANEL_NB + 1];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, p0 = it.y, r0 = it.z;
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
+  const int pe = min(p0 + PANEL_NB, ncol);
+  const int nbk = pe - p0;
+  const T* Lc = N.L + P.sn_Loff[s];
+  for (int idx = threadIdx.x; idx < PANEL_NB * PANEL_NB; idx += blockDim.x) {
+    const int i = idx / PANEL_NB, j = idx % PANEL_NB;
+    Db[i][j] = (i < nbk && j <= i) ? Lc[(int64_t)(p0 + i) * ncp + p0 + j] : T(1);
+  }
+  __syncthreads();
   const int i = r0 + threadIdx.x;
   if (i < nrow && i >= pe && i < r0 + PANEL_ROWS) {
     T q[PANEL_NB];
-    T* row = Lb + (int64_t)i * ncp + p0;
+    T* row = N.L + P.sn_Loff[s] + (int64_t)i * ncp + p0;
 #pragma unroll
     for (int t = 0; t < PANEL_NB; t++) q[t] = (t < nbk) ? row[t] : T(0);
 #pragma unroll
@@ -303,10 +316,16 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel(DevPlan P, DevNum<T> N, co
 }
 
 template <typename T>
-void launch_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, double eps, int policy,
-                  cudaStream_t st) {
+void launch_panel_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
+                       cudaStream_t st) {
   if (count <= 0) return;
-  k_panel<T><<<count, PANEL_ROWS, 0, st>>>(P, N, items, eps, policy);
+  k_panel_diag<T><<<count, 128, 0, st>>>(P, N, items, eps, policy);
+}
+
+template <typename T>
+void launch_panel_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st) {
+  if (count <= 0) return;
+  k_panel_rows<T><<<count, PANEL_ROWS, 0, st>>>(P, N, items);
 }
 
 // ---------------------------------------------------------------------------
@@ -434,8 +453,9 @@ void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cud
   template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, int, cudaStream_t);   \
   template void launch_factor_small<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, double,   \
                                        int, cudaStream_t);                                              \
-  template void launch_panel<T>(const DevPlan&, const DevNum<T>&, const int4*, int, double, int,        \
-                                cudaStream_t);                                                          \
+  template void launch_panel_diag<T>(const DevPlan&, const DevNum<T>&, const int2*, int, double, int,   \
+                                     cudaStream_t);                                                     \
+  template void launch_panel_rows<T>(const DevPlan&, const DevNum<T>&, const int4*, int, cudaStream_t); \
   template void launch_gemm_simt<T>(const DevNum<T>&, const GemmProb*, int, int64_t, cudaStream_t);     \
   template void launch_inertia<T>(const DevPlan&, const DevNum<T>&, long long*, cudaStream_t);
 NCL_INST(float)

@@ -102,8 +102,10 @@ template <typename T>
 void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count,
                          double eps, int policy, cudaStream_t st);
 template <typename T>
-void launch_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, double eps,
-                  int policy, cudaStream_t st);
+void launch_panel_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps,
+                       int policy, cudaStream_t st);
+template <typename T>
+void launch_panel_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st);
 template <typename T>
 void launch_gemm_simt(const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles,
                       cudaStream_t st);

@@ -230,16 +230,22 @@ def test_adjoint_matches_oracle(form, prec):
 
 # ------------------------------------------------------------------ full size
 
-@pytest.mark.parametrize("rho", [1e2, 1e5])
-def test_condensed_300x300_full_size(rho):
-    """The 300 x 300 condensed workload at full size, FP32 + refinement, in
-    the bench's configuration: properties that hold at any size (inertia,
-    FP64 backward error recomputed on the CPU from the oracle's matrix)."""
+@pytest.mark.parametrize("prec,rho,eta_tol", [("fp32_ir", 1e2, 1e-10), ("fp32_ir", 1e5, 1e-10),
+                                              ("fp64", 1e5, 1e-12)])
+def test_condensed_300x300_full_size(prec, rho, eta_tol):
+    """The 300 x 300 condensed workload at full size, in the bench's
+    configuration: properties that hold at any size (inertia, FP64 backward
+    error recomputed on the CPU from the oracle's matrix), plus sampled
+    entries of K x against b computed row by row from the oracle's matrix."""
     pat = synth.make_pattern(300, 300)
     inst = synth.condensed_grid(300, rho=rho, draw=0, pat=pat)
-    K, finfo, X, sinfo = gpu_solve(inst, "fp32_ir")
+    K, finfo, X, sinfo = gpu_solve(inst, prec)
     assert finfo.inertia == (inst.n, 0, 0)
     assert finfo.n_perturbed == 0
     A = O.instance_matrix(inst)
     eta = O.backward_error(A, X, inst.b)
-    assert eta <= 1e-10, eta
+    assert eta <= eta_tol, eta
+    rows = np.random.default_rng(0).choice(inst.n, 64, replace=False)
+    Ar = sp.csr_matrix(A)[rows]
+    scale = np.abs(Ar).sum(axis=1).A1 * np.max(np.abs(X)) + np.abs(inst.b[rows, 0])
+    assert np.all(np.abs(Ar @ X[:, 0] - inst.b[rows, 0]) <= eta_tol * scale)
