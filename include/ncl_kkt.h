@@ -203,6 +203,28 @@ ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t l
                            double* G_Hval, double* G_Jval, double* G_Sigma, double* G_scal,
                            ncl_stream_t stream, ncl_kkt_solve_info* info);
 
+/*
+ * ncl_kkt_solve_noalloc -- ncl_kkt_solve without any device allocation
+ * (the paper has no counterpart; this serves callers that cannot allocate
+ * device memory when they solve: code running while a stream is captured
+ * into a CUDA graph, real-time loops, or processes whose device memory is
+ * committed elsewhere).  Same arguments, results and refinement as
+ * ncl_kkt_solve, on a handle that has been factored.
+ * The sweep and refinement workspace comes from one static device array of
+ * 8 MiB inside the library (held by every GPU that loads the library until
+ * the process exits) instead of the handle's workspace.  It must hold
+ * min(nrhs, 8) * (dim + update and partial-sum vectors) solve values plus
+ * min(nrhs, 8) * dim FP64 residuals; larger problems get
+ * NCL_ERR_INVALID_ARG with the required size in ncl_kkt_last_error().
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the one array:
+ * calls whose work overlaps on the GPU (other threads or streams) race, so
+ * serialise them.  Not available while profiling is on (NCL_ERR_STATE).
+ */
+ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const double* B, int64_t ldb,
+                                 double* X, int64_t ldx, ncl_stream_t stream,
+                                 ncl_kkt_solve_info* info);
+
 /* Sizes and counts of the analysis (host struct). */
 ncl_status ncl_kkt_get_analysis_info(ncl_kkt_t h, ncl_kkt_analysis_info* out);
 

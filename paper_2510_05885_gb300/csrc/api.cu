@@ -1029,3 +1029,93 @@ const char* ncl_kkt_status_string(ncl_status st) {
 const char* ncl_kkt_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve without any device allocation.
+//
+// For callers that must not allocate device memory at the point where they
+// solve: code running while a stream is being captured into a CUDA graph,
+// real-time loops that cannot afford an allocator round trip, and processes
+// whose device memory is fully committed to other pools (for instance after
+// the factorisation was sized to the memory cap).  The workspace of the
+// triangular sweeps and of the refinement lives in one file-scope device
+// array of NCL_NOALLOC_SCRATCH_BYTES, which every GPU that loads this
+// library keeps until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t NCL_NOALLOC_SCRATCH_BYTES = size_t(8) << 20;  // 8 MiB per GPU
+__device__ __align__(256) unsigned char g_noalloc_scratch[NCL_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[256] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of a __device__ array is not its address).
+ncl_status noalloc_base(int dev, void** out) {
+  if (dev < 0 || dev >= 256) return fail(NCL_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(NCL_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return NCL_OK;
+}
+
+}  // namespace
+
+extern "C" ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const double* B, int64_t ldb, double* X,
+                                            int64_t ldx, ncl_stream_t stream, ncl_kkt_solve_info* info) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (nrhs <= 0) return fail(NCL_ERR_INVALID_ARG, "nrhs must be positive");
+  return guarded(h, [&]() -> ncl_status {
+    if (h->prof_on) return fail(NCL_ERR_STATE, "turn profiling off before the no-alloc solve");
+    void* base = nullptr;
+    ncl_status s = noalloc_base(h->device, &base);
+    if (s != NCL_OK) return s;
+    const size_t g = (size_t)std::min(nrhs, MAX_RHS_SWEEP);
+    const size_t esz = is_fp32(h) ? 4 : 8;
+    const size_t dim = (size_t)h->dp.dim;
+    const size_t b_xp = align256(dim * g * esz);
+    const size_t b_w = align256((size_t)std::max<int64_t>(h->dp.Wtot, 1) * g * esz);
+    const size_t b_pw = align256((size_t)std::max<int64_t>(h->dp.Ptot, 1) * g * esz);
+    const size_t b_r = align256(dim * g * 8);
+    const size_t b_n = align256(3 * (size_t)h->dp.ninst * MAX_RHS_SWEEP * 8);
+    const size_t need = b_xp + b_w + b_pw + b_r + b_n;
+    if (need > NCL_NOALLOC_SCRATCH_BYTES)
+      return fail(NCL_ERR_INVALID_ARG, "problem too large for the no-alloc solve: needs " + std::to_string(need) +
+                                           " bytes of workspace, the fixed scratch holds " +
+                                           std::to_string(NCL_NOALLOC_SCRATCH_BYTES));
+    char* p = (char*)base;
+    // run the regular solve on the static workspace, then give the handle
+    // its own workspace back
+    struct Swap {
+      ncl_kkt_s* h;
+      void *xp, *W, *Pw;
+      double* R;
+      unsigned long long* norms;
+      ~Swap() {
+        h->xp = xp;
+        h->W = W;
+        h->Pw = Pw;
+        h->R = R;
+        h->d_norms = norms;
+      }
+    } keep{h, h->xp, h->W, h->Pw, h->R, h->d_norms};
+    h->xp = p;
+    h->W = p + b_xp;
+    h->Pw = p + b_xp + b_w;
+    h->R = (double*)(p + b_xp + b_w + b_pw);
+    h->d_norms = (unsigned long long*)(p + b_xp + b_w + b_pw + b_r);
+    return do_solve(h, nrhs, B, ldb, X, ldx, (cudaStream_t)stream, info);
+  });
+}

@@ -84,6 +84,7 @@ _SIGS = {
     "ncl_kkt_factor": (I32, [P, P, P, P, D, D, P, ctypes.POINTER(FactorInfo)]),
     "ncl_kkt_batch_factor": (I32, [P, P, P, P, P, P, P, P]),
     "ncl_kkt_solve": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
+    "ncl_kkt_solve_noalloc": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_batch_factor_solve": (I32, [P, P, P, P, P, P, I32, P, I64, P, I64, P, P,
                                          ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_adjoint": (I32, [P, I32, P, I64, P, I64, P, I64, P, P, P, P, P, ctypes.POINTER(SolveInfo)]),
@@ -216,6 +217,17 @@ def ncl_kkt_batch_factor(h, H_val, J_val, Sigma, delta, rho, stream=None):
 def ncl_kkt_solve(h, nrhs, B, ldb, X, ldx, stream=None):
     info = SolveInfo()
     st = load().ncl_kkt_solve(h, nrhs, _ptr(B), ldb, _ptr(X), ldx, _stream_ptr(stream), ctypes.byref(info))
+    if st not in (OK, ERR_IR_NOT_CONVERGED):
+        _check(st)
+    info.status = st
+    return info
+
+
+def ncl_kkt_solve_noalloc(h, nrhs, B, ldb, X, ldx, stream=None):
+    """ncl_kkt_solve on the library's fixed static workspace (no device
+    allocation in the call)."""
+    info = SolveInfo()
+    st = load().ncl_kkt_solve_noalloc(h, nrhs, _ptr(B), ldb, _ptr(X), ldx, _stream_ptr(stream), ctypes.byref(info))
     if st not in (OK, ERR_IR_NOT_CONVERGED):
         _check(st)
     info.status = st
