@@ -304,6 +304,18 @@ ncl_status ncl_kkt_profile(ncl_kkt_t h, int32_t enable);
  * (NUL-terminated, truncated to buflen).  Returns NCL_OK. */
 ncl_status ncl_kkt_profile_report(ncl_kkt_t h, char* buf, int64_t buflen);
 
+/* Run the tensor-core (tcgen05, split-TF32) update kernel of the FP32
+ * factorisation on caller data, for testing it in isolation:
+ *   C[i][j] -= sum_{k<K} L[row_a+i][k] d[k] L[row_b+j][k],  0 <= j <= min(i, N-1), i < M
+ * L: device float, rows x ld row-major (ld >= K, ld % 4 == 0); d: device
+ * float[K]; C: device float, M x ldc row-major (only its lower part is
+ * touched).  N <= M, row_a + M <= rows, row_b + N <= rows.  Allocates its own
+ * temporary buffers; returns after completion.  INVALID_ARG, OOM, CUDA,
+ * TIMEOUT. */
+ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, int32_t K, const float* L,
+                                          const float* d, int32_t row_a, int32_t row_b, int32_t M,
+                                          int32_t N, float* C, int32_t ldc, ncl_stream_t stream);
+
 /* Number of instances of a handle (1 for ncl_kkt_analyze). */
 int32_t ncl_kkt_instance_count(ncl_kkt_t h);
 

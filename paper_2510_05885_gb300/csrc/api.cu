@@ -60,6 +60,9 @@ struct Step {
   int64_t prob_off = 0;
   int prob_cnt = 0;
   int64_t tiles = 0;
+  int64_t tc_off = 0;
+  int tc_cnt = 0;
+  int64_t tc_tiles = 0;
   Cost panel_cost, gemm_cost;
 };
 
@@ -72,6 +75,9 @@ struct Level {
   int64_t syrk_off = 0;
   int syrk_cnt = 0;
   int64_t syrk_tiles = 0;
+  int64_t tsyrk_off = 0;  // tensor-core update-block problems
+  int tsyrk_cnt = 0;
+  int64_t tsyrk_tiles = 0;
   int64_t list_off = 0;   // all supernodes of the level (solve)
   int list_cnt = 0;
   int64_t below_off = 0;  // (s, a0) solve items
@@ -98,6 +104,12 @@ struct HostSched {
   std::vector<int4> panelv;
   std::vector<int2> pdiagv;
   std::vector<GemmProb> probv;
+  // tensor-core path (FP32): problems, split-operand offsets, fronts in map order
+  bool tc = false;
+  std::vector<TcProb> tcv;
+  std::vector<int64_t> sn_Soff;
+  std::vector<int32_t> tc_fronts;
+  int64_t split_max = 0;
 };
 
 }  // namespace
@@ -134,6 +146,7 @@ struct ncl_kkt_s {
   int2* d_below = nullptr;
   // solve workspace
   void* xp = nullptr;
+  void* own_xp = nullptr;                  // the handle's own sweep workspace
   void* W = nullptr;
   void* Pw = nullptr;
   double* R = nullptr;
@@ -141,6 +154,19 @@ struct ncl_kkt_s {
   double* jg = nullptr;
   double* GBtmp = nullptr;
   double* Jcopy = nullptr;                 // condensed form: J values of the last factor (adjoint)
+  const double** d_valptr = nullptr;       // {H, J, Sigma} pointers of the current factor call
+  CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
+  TcProb* d_tc = nullptr;
+  int* d_err = nullptr;                    // device error flags (bounded waits)
+  // CUDA graphs: the factor and the triangular sweeps are captured once (on
+  // a private stream, after one direct call) and replayed
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t fgraph = nullptr;
+  cudaGraphExec_t sgraph[9] = {};
+  int factor_calls = 0;
+  int sweep_calls[9] = {};
+  int64_t fgraph_nodes = 0;
+  int64_t sgraph_nodes[9] = {};
   bool factored = false;
   // profiling
   int prof_on = 0;
@@ -183,6 +209,10 @@ struct ncl_kkt_s {
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    if (fgraph) cudaGraphExecDestroy(fgraph);
+    for (auto& g : sgraph)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     cudaSetDevice(cur);
   }
 };
@@ -190,6 +220,7 @@ struct ncl_kkt_s {
 namespace {
 
 bool is_fp32(const ncl_kkt_s* h) { return h->opt.prec == NCL_PREC_FP32_IR; }
+HostSched& hs_ref(ncl_kkt_s* h) { return h->hs; }
 
 // ---------------------------------------------------------------------------
 // device plan + schedule
@@ -206,6 +237,9 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<int4>& panelv = hs.panelv;
   std::vector<int2>& pdiagv = hs.pdiagv;
   std::vector<GemmProb>& probv = hs.probv;
+  hs.tc = is_fp32(h) && h->opt.use_tensor_cores;
+  hs.sn_Soff.assign(P.ns, -1);
+  std::vector<int32_t> fid(P.ns, -1);
   h->levels.assign(P.nlevels, Level{});
   for (int32_t l = 0; l < P.nlevels; l++) {
     Level& L = h->levels[l];
@@ -249,6 +283,16 @@ void build_schedule(ncl_kkt_s* h) {
     L.small_cnt = (int)(smallv.size() - L.small_off);
     L.list_cnt = (int)(listv.size() - L.list_off);
     L.below_cnt = (int)(belowv.size() - L.below_off);
+    if (hs.tc) {
+      int64_t off = 0;
+      for (int32_t s : large) {
+        fid[s] = (int32_t)hs.tc_fronts.size();
+        hs.tc_fronts.push_back(s);
+        hs.sn_Soff[s] = off;
+        off += (4 * (int64_t)P.sn_nrow[s] * P.sn_ncolp[s] + 31) / 32 * 32;
+      }
+      hs.split_max = std::max(hs.split_max, off);
+    }
     int maxp = 0;
     for (int32_t s : large) maxp = std::max(maxp, (P.sn_ncol[s] + PANEL_NB - 1) / PANEL_NB);
     L.steps.resize(maxp);
@@ -257,6 +301,7 @@ void build_schedule(ncl_kkt_s* h) {
       S.panel_off = (int64_t)panelv.size();
       S.pdiag_off = (int64_t)pdiagv.size();
       S.prob_off = (int64_t)probv.size();
+      S.tc_off = (int64_t)hs.tcv.size();
       int64_t tiles = 0;
       for (int32_t s : large) {
         const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
@@ -267,7 +312,25 @@ void build_schedule(ncl_kkt_s* h) {
         for (int r0 = pe; r0 < nrow; r0 += PANEL_ROWS) panelv.push_back(make_int4(s, p0, r0, 0));
         S.panel_cost.flops += (double)(nrow - pe) * (pe - p0) * (pe - p0) + 2.0 * (pe - p0) * (pe - p0) * (pe - p0) / 3.0;
         S.panel_cost.bytes += esz * 2.0 * (nrow - p0) * (pe - p0);
-        if (pe < ncol) {
+        if (pe < ncol && hs.tc) {
+          TcProb q{};
+          q.c_off = P.sn_Loff[s] + (int64_t)pe * ncp + pe;
+          q.ldc = ncp;
+          q.c_in_u = 0;
+          q.map = fid[s];
+          q.row_a = pe;
+          q.row_b = pe;
+          q.k0 = p0;
+          q.nk = 1;
+          q.M = nrow - pe;
+          q.N = ncol - pe;
+          q.tile0 = S.tc_tiles;
+          S.tc_tiles += tc_tiles(q.M, q.N, &q.Nt);
+          hs.tcv.push_back(q);
+          const double centries = (double)q.M * q.N - 0.5 * (double)q.N * (q.N - 1);
+          S.gemm_cost.flops += 2.0 * (pe - p0) * centries;
+          S.gemm_cost.bytes += esz * (2.0 * centries) + 16.0 * (double)(q.M + q.N) * (pe - p0);
+        } else if (pe < ncol) {
           GemmProb g{};
           g.c_off = P.sn_Loff[s] + (int64_t)pe * ncp + pe;
           g.a_off = P.sn_Loff[s] + (int64_t)pe * ncp + p0;
@@ -291,15 +354,37 @@ void build_schedule(ncl_kkt_s* h) {
       }
       S.panel_cnt = (int)(panelv.size() - S.panel_off);
       S.pdiag_cnt = (int)(pdiagv.size() - S.pdiag_off);
+      S.tc_cnt = (int)(hs.tcv.size() - S.tc_off);
       S.prob_cnt = (int)(probv.size() - S.prob_off);
       S.tiles = tiles;
     }
     L.syrk_off = (int64_t)probv.size();
+    L.tsyrk_off = (int64_t)hs.tcv.size();
     int64_t tiles = 0;
     for (int32_t s : large) {
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
       const int nb = nrow - ncol;
       if (nb == 0) continue;
+      if (hs.tc) {
+        TcProb q{};
+        q.c_off = P.sn_Uoff[s];
+        q.ldc = nb;
+        q.c_in_u = 1;
+        q.map = fid[s];
+        q.row_a = ncol;
+        q.row_b = ncol;
+        q.k0 = 0;
+        q.nk = (ncol + 31) / 32;
+        q.M = nb;
+        q.N = nb;
+        q.tile0 = L.tsyrk_tiles;
+        L.tsyrk_tiles += tc_tiles(q.M, q.N, &q.Nt);
+        hs.tcv.push_back(q);
+        const double centries = 0.5 * (double)nb * (nb + 1);
+        L.syrk_cost.flops += 2.0 * ncol * centries;
+        L.syrk_cost.bytes += esz * (2.0 * centries) + 16.0 * (double)nb * ncol;
+        continue;
+      }
       GemmProb g{};
       g.c_off = P.sn_Uoff[s];
       g.a_off = P.sn_Loff[s] + (int64_t)ncol * ncp;
@@ -321,6 +406,7 @@ void build_schedule(ncl_kkt_s* h) {
       L.syrk_cost.bytes += esz * (2.0 * centries + (double)nb * ncol);
     }
     L.syrk_cnt = (int)(probv.size() - L.syrk_off);
+    L.tsyrk_cnt = (int)(hs.tcv.size() - L.tsyrk_off);
     L.syrk_tiles = tiles;
   }
   // bounds of every launch item against its buffers, checked on the host
@@ -364,6 +450,14 @@ void build_schedule(ncl_kkt_s* h) {
     }
     for (const int2& it : pdiagv)
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_ncol[it.x]) bad("panel diag item");
+    for (const TcProb& q : hs.tcv) {
+      const int64_t csz = q.c_in_u ? Usz : Lsz;
+      if (q.map < 0 || q.map >= (int)hs.tc_fronts.size()) bad("tc map");
+      const int32_t s = hs.tc_fronts[q.map];
+      if (q.M <= 0 || q.N <= 0 || q.N > q.M || q.nk <= 0) bad("tc shape");
+      if (q.c_off < 0 || q.c_off + (int64_t)(q.M - 1) * q.ldc + q.N > csz) bad("tc C");
+      if (q.row_a + q.M > P.sn_nrow[s] || q.row_b + q.N > P.sn_nrow[s] || q.k0 % 4 != 0) bad("tc operands");
+    }
     for (const GemmProb& g : probv) {
       const int64_t csz = g.c_in_u ? Usz : Lsz;
       if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.N > g.M) bad("gemm shape");
@@ -468,6 +562,7 @@ void build_device(ncl_kkt_s* h) {
   if (is_fp32(h)) alloc_num(h->nf, float{});
   else alloc_num(h->nd, double{});
   h->xp = h->alloc<char>((int64_t)P.dim * MAX_RHS_SWEEP * esz);
+  h->own_xp = h->xp;
   h->W = h->alloc<char>(std::max<int64_t>(d.Wtot, 1) * MAX_RHS_SWEEP * esz);
   h->Pw = h->alloc<char>(std::max<int64_t>(d.Ptot, 1) * MAX_RHS_SWEEP * esz);
   h->R = h->alloc<double>((int64_t)P.dim * MAX_RHS_SWEEP);
@@ -475,6 +570,24 @@ void build_device(ncl_kkt_s* h) {
   h->jx = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
   h->jg = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
   if (P.form == 1) h->Jcopy = h->alloc<double>(std::max<int64_t>(d.nnzJ, 1));
+  h->d_valptr = h->alloc<const double*>(4);
+  if (hs_ref(h).tc) {
+    HostSched& hs = h->hs;
+    h->nf.S = h->alloc<float>(std::max<int64_t>(hs.split_max, 32));
+    d.sn_Soff = h->upload(hs.sn_Soff);
+    std::vector<CUtensorMap> maps(4 * std::max<size_t>(hs.tc_fronts.size(), 1));
+    for (size_t f = 0; f < hs.tc_fronts.size(); f++) {
+      const int32_t s = hs.tc_fronts[f];
+      std::string why;
+      if (!tc_encode_maps(h->nf.S + hs.sn_Soff[s], P.sn_nrow[s], P.sn_ncolp[s], &maps[4 * f], &why))
+        throw std::runtime_error("tensor map: " + why);
+    }
+    h->d_maps = reinterpret_cast<CUtensorMap*>(h->alloc<char>((int64_t)(maps.size() * sizeof(CUtensorMap))));
+    CK(cudaMemcpy(h->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    h->d_tc = h->upload(hs.tcv);
+  }
+  h->d_err = h->alloc<int>(4);
+  CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 
   HostSched& hs = h->hs;
   h->d_asm = h->upload(hs.asmv);
@@ -484,7 +597,7 @@ void build_device(ncl_kkt_s* h) {
   h->d_probs = h->upload(hs.probv);
   h->d_lists = h->upload(hs.listv);
   h->d_below = h->upload(hs.belowv);
-  CK(cudaMallocHost(&h->h_pinned, sizeof(double) * (size_t)(4 * ni + 64 + 3 * ni * MAX_RHS_SWEEP)));
+  CK(cudaMallocHost(&h->h_pinned, sizeof(double) * (size_t)(7 * ni + 64 + 3 * ni * MAX_RHS_SWEEP)));
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
 }
@@ -536,6 +649,38 @@ Cost scaled(Cost c, double f) {
   return c;
 }
 
+// Run `body(stream)` directly, or as a captured graph replayed on `st`.
+// The first call of a kind runs directly (it also loads the kernels), the
+// second captures on the handle's private stream, later calls replay.
+template <typename F>
+void run_graphed(ncl_kkt_s* h, cudaGraphExec_t* exec, int64_t* nodes, int* calls, bool allow, cudaStream_t st,
+                 F&& body) {
+  if (!allow || h->prof_on) {
+    body(st);
+    return;
+  }
+  if (!*exec && *calls >= 1) {
+    // capturing records the work without running it; the graph then runs on st
+    cudaGraph_t g = nullptr;
+    const int64_t l0 = g_kernel_launches.load();
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    body(h->cap_stream);
+    CK(cudaStreamEndCapture(h->cap_stream, &g));
+    *nodes = g_kernel_launches.load() - l0;
+    g_kernel_launches.fetch_sub(*nodes);
+    cudaError_t ie = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ie);
+  }
+  (*calls)++;
+  if (*exec) {
+    CK(cudaGraphLaunch(*exec, st));
+    g_kernel_launches.fetch_add(*nodes);
+  } else {
+    body(st);
+  }
+}
+
 template <typename T>
 void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
   const DevPlan& P = h->dp;
@@ -554,9 +699,17 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
               [&] { launch_panel_rows<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, st); });
       klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost,
               [&] { launch_gemm_simt<T>(N, h->d_probs + S.prob_off, S.prob_cnt, S.tiles, st); });
+      if constexpr (sizeof(T) == 4)
+        klaunch(h, st, "update_tc_f32", S.tc_tiles, S.gemm_cost, [&] {
+          launch_update_tc(N.L, N.U, h->d_tc + S.tc_off, S.tc_cnt, S.tc_tiles, h->d_maps, h->d_err, st);
+        });
     }
     klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", L.syrk_tiles, L.syrk_cost,
             [&] { launch_gemm_simt<T>(N, h->d_probs + L.syrk_off, L.syrk_cnt, L.syrk_tiles, st); });
+    if constexpr (sizeof(T) == 4)
+      klaunch(h, st, "update_tc_f32", L.tsyrk_tiles, L.syrk_cost, [&] {
+        launch_update_tc(N.L, N.U, h->d_tc + L.tsyrk_off, L.tsyrk_cnt, L.tsyrk_tiles, h->d_maps, h->d_err, st);
+      });
   }
   CK(cudaGetLastError());
 }
@@ -587,16 +740,22 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
 // X (+)= K^{-1} B with the low-precision factors (one sweep)
 void apply_inverse(ncl_kkt_s* h, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs, int accumulate,
                    cudaStream_t st) {
+  // graphs capture the handle's own workspace pointers
+  const bool own = h->xp == h->own_xp;
+  auto sweeps = [&](cudaStream_t s2) {
+    if (is_fp32(h)) run_sweeps<float>(h, h->nf, nrhs, s2);
+    else run_sweeps<double>(h, h->nd, nrhs, s2);
+  };
   if (is_fp32(h)) {
     klaunch(h, st, "perm_in", h->dp.dim, Cost{0, 12.0 * h->dp.dim * nrhs},
             [&] { launch_perm_in<float>(h->dp, (float*)h->xp, B, ldb, nrhs, st); });
-    run_sweeps<float>(h, h->nf, nrhs, st);
+    run_graphed(h, &h->sgraph[nrhs], &h->sgraph_nodes[nrhs], &h->sweep_calls[nrhs], own, st, sweeps);
     klaunch(h, st, "perm_out", h->dp.dim, Cost{0, 20.0 * h->dp.dim * nrhs},
             [&] { launch_perm_out<float>(h->dp, (const float*)h->xp, X, ldx, nrhs, accumulate, st); });
   } else {
     klaunch(h, st, "perm_in", h->dp.dim, Cost{0, 16.0 * h->dp.dim * nrhs},
             [&] { launch_perm_in<double>(h->dp, (double*)h->xp, B, ldb, nrhs, st); });
-    run_sweeps<double>(h, h->nd, nrhs, st);
+    run_graphed(h, &h->sgraph[nrhs], &h->sgraph_nodes[nrhs], &h->sweep_calls[nrhs], own, st, sweeps);
     klaunch(h, st, "perm_out", h->dp.dim, Cost{0, 24.0 * h->dp.dim * nrhs},
             [&] { launch_perm_out<double>(h->dp, (const double*)h->xp, X, ldx, nrhs, accumulate, st); });
   }
@@ -684,37 +843,52 @@ ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const dou
     hp[i] = delta[i];
     hp[ni + i] = rho[i];
   }
+  const double** vp = reinterpret_cast<const double**>(hp + 2 * ni + 4 * ni + 1 + ni);
+  vp[0] = Hv;
+  vp[1] = Jv;
+  vp[2] = S;
   CK(cudaEventRecord(h->ev0, st));
   CK(cudaMemcpyAsync(h->d_delta, hp, ni * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->d_rho, hp + ni, ni * sizeof(double), cudaMemcpyHostToDevice, st));
-  {
-    const double np = (double)h->plan.pair_p.size();
-    klaunch(h, st, "kkt_values_f64", h->dp.nnzA,
-            Cost{2.0 * np, 33.0 * h->dp.nnzA + 24.0 * np + 8.0 * (h->dp.nnzH + h->dp.nnzJ + h->dp.nvar)},
-            [&] { launch_kkt_values(h->dp, Hv, Jv, S, h->d_delta, h->d_rho, h->Klow, st); });
-  }
+  CK(cudaMemcpyAsync(h->d_valptr, vp, 3 * sizeof(double*), cudaMemcpyHostToDevice, st));
   if (h->Jcopy && h->dp.nnzJ)
     CK(cudaMemcpyAsync(h->Jcopy, Jv, h->dp.nnzJ * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), st));
-  klaunch(h, st, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
-          [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, st); });
-  CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), st));
-  if (is_fp32(h)) {
-    run_factor<float>(h, h->nf, st);
-    klaunch(h, st, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},
-            [&] { launch_inertia<float>(h->dp, h->nf, h->d_counts, st); });
-  } else {
-    run_factor<double>(h, h->nd, st);
-    klaunch(h, st, "inertia", h->dp.dim, Cost{0, 9.0 * h->dp.dim},
-            [&] { launch_inertia<double>(h->dp, h->nd, h->d_counts, st); });
-  }
+  auto body = [&](cudaStream_t s2) {
+    {
+      const double np = (double)h->plan.pair_p.size();
+      klaunch(h, s2, "kkt_values_f64", h->dp.nnzA,
+              Cost{2.0 * np, 33.0 * h->dp.nnzA + 24.0 * np + 8.0 * (h->dp.nnzH + h->dp.nnzJ + h->dp.nvar)},
+              [&] { launch_kkt_values(h->dp, h->d_valptr, h->d_delta, h->d_rho, h->Klow, s2); });
+    }
+    CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), s2));
+    klaunch(h, s2, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
+            [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, s2); });
+    CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), s2));
+    CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s2));
+    if (is_fp32(h)) {
+      run_factor<float>(h, h->nf, s2);
+      klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},
+              [&] { launch_inertia<float>(h->dp, h->nf, h->d_counts, s2); });
+    } else {
+      run_factor<double>(h, h->nd, s2);
+      klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 9.0 * h->dp.dim},
+              [&] { launch_inertia<double>(h->dp, h->nd, h->d_counts, s2); });
+    }
+  };
+  run_graphed(h, &h->fgraph, &h->fgraph_nodes, &h->factor_calls, true, st, body);
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev1, st));
   long long* hc = reinterpret_cast<long long*>(hp + 2 * ni);
   CK(cudaMemcpyAsync(hc, h->d_counts, (4 * ni + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
   unsigned long long* hk = reinterpret_cast<unsigned long long*>(hp + 2 * ni + 4 * ni + 1);
   CK(cudaMemcpyAsync(hk, h->d_knorm, ni * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  int* herr = reinterpret_cast<int*>(hp + 7 * ni + 8);
+  CK(cudaMemcpyAsync(herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (*herr) {
+    h->factored = false;
+    return fail(NCL_ERR_TIMEOUT, "a bounded device wait of the tensor-core update ran out");
+  }
   prof_collect(h);
   float ms = 0;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -1118,4 +1292,68 @@ extern "C" ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const dou
     h->d_norms = (unsigned long long*)(p + b_xp + b_w + b_pw + b_r);
     return do_solve(h, nrhs, B, ldb, X, ldx, (cudaStream_t)stream, info);
   });
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: the tensor-core update kernel on caller data
+// ---------------------------------------------------------------------------
+extern "C" ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, int32_t K, const float* L,
+                                                     const float* d, int32_t row_a, int32_t row_b, int32_t M,
+                                                     int32_t N, float* C, int32_t ldc, ncl_stream_t stream) {
+  if (!L || !d || !C || rows <= 0 || K <= 0 || ld < K || ld % 4 != 0 || M <= 0 || N <= 0 || N > M ||
+      row_a < 0 || row_b < 0 || row_a + M > rows || row_b + N > rows || ldc < N)
+    return fail(NCL_ERR_INVALID_ARG, "bad self-test arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  float* S = nullptr;
+  CUtensorMap* dmaps = nullptr;
+  TcProb* dp = nullptr;
+  int* derr = nullptr;
+  auto release = [&] {
+    if (S) cudaFree(S);
+    if (dmaps) cudaFree(dmaps);
+    if (dp) cudaFree(dp);
+    if (derr) cudaFree(derr);
+  };
+  const size_t plane = (size_t)rows * ld;
+  if (cudaMalloc(&S, 4 * plane * sizeof(float)) != cudaSuccess || cudaMalloc(&dmaps, 4 * sizeof(CUtensorMap)) ||
+      cudaMalloc(&dp, sizeof(TcProb)) || cudaMalloc(&derr, sizeof(int))) {
+    cudaGetLastError();
+    release();
+    return fail(NCL_ERR_OOM, "self-test allocation failed");
+  }
+  CUtensorMap maps[4];
+  std::string why;
+  if (!tc_encode_maps(S, rows, ld, maps, &why)) {
+    release();
+    return fail(NCL_ERR_CUDA, why);
+  }
+  TcProb q{};
+  q.c_off = 0;
+  q.ldc = ldc;
+  q.c_in_u = 0;
+  q.map = 0;
+  q.row_a = row_a;
+  q.row_b = row_b;
+  q.k0 = 0;
+  q.nk = (K + 31) / 32;
+  q.M = M;
+  q.N = N;
+  q.tile0 = 0;
+  const int64_t tiles = tc_tiles(M, N, &q.Nt);
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(dmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dp, &q, sizeof(q), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    launch_split_rows(L, d, rows, ld, K, S, st);
+    launch_update_tc(C, C, dp, 1, tiles, dmaps, derr, st);
+    g_kernel_launches.fetch_add(2);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release();
+  if (e != cudaSuccess) return fail(NCL_ERR_CUDA, std::string("self-test: ") + cudaGetErrorString(e));
+  if (herr) return fail(NCL_ERR_TIMEOUT, "self-test: a bounded wait ran out");
+  return NCL_OK;
 }

@@ -26,9 +26,13 @@ namespace ncl {
 //                  the product summed over the constraint rows shared by i, j
 //                  in a fixed order (no atomics).
 // ---------------------------------------------------------------------------
-__global__ void k_kkt_values(DevPlan P, const double* __restrict__ Hv, const double* __restrict__ Jv,
-                             const double* __restrict__ S, const double* __restrict__ delta,
+__global__ void k_kkt_values(DevPlan P, const double* const* __restrict__ vals, const double* __restrict__ delta,
                              const double* __restrict__ rho, double* __restrict__ Klow) {
+  // vals = {H values, J values, Sigma}: read from device memory so that a
+  // captured graph stays valid when the caller passes new arrays
+  const double* __restrict__ Hv = vals[0];
+  const double* __restrict__ Jv = vals[1];
+  const double* __restrict__ S = vals[2];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.nnzA;
        e += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
@@ -49,12 +53,12 @@ __global__ void k_kkt_values(DevPlan P, const double* __restrict__ Hv, const dou
   }
 }
 
-void launch_kkt_values(const DevPlan& P, const double* Hv, const double* Jv, const double* S,
-                       const double* delta, const double* rho, double* Klow, cudaStream_t st) {
+void launch_kkt_values(const DevPlan& P, const double* const* vals, const double* delta, const double* rho,
+                       double* Klow, cudaStream_t st) {
   if (P.nnzA == 0) return;
   int64_t blocks = (P.nnzA + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_kkt_values<<<(unsigned)blocks, 256, 0, st>>>(P, Hv, Jv, S, delta, rho, Klow);
+  k_kkt_values<<<(unsigned)blocks, 256, 0, st>>>(P, vals, delta, rho, Klow);
 }
 
 // ||K||_inf per instance (max absolute row sum), as the bit pattern of a
@@ -172,27 +176,26 @@ __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, co
   const int s = list[blockIdx.x];
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
   const int col0 = P.sn_col0[s];
+  __shared__ int8_t sgn[64];
   T* F = reinterpret_cast<T*>(smem_raw);
   T* w = F + (int64_t)nrow * ncp;
   T* Lg = N.L + P.sn_Loff[s];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int idx = threadIdx.x; idx < nrow * ncp; idx += blockDim.x) F[idx] = Lg[idx];
+  for (int k = threadIdx.x; k < ncol; k += blockDim.x) sgn[k] = P.col_sign[col0 + k];
   __syncthreads();
+  // pivot columns: right-looking, rows over warps, pivot columns over lanes
   for (int k = 0; k < ncol; k++) {
     int8_t stt;
-    const T dk = static_pivot<T>(F[k * ncp + k], P.col_sign[col0 + k], eps, policy, stt);
+    const T dk = static_pivot<T>(F[k * ncp + k], sgn[k], eps, policy, stt);
     for (int i = k + 1 + threadIdx.x; i < nrow; i += blockDim.x) w[i] = F[i * ncp + k];
     __syncthreads();
     const T invd = T(1) / dk;
-    const int nc = ncol - k - 1;
-    const int nr = nrow - k - 1;
-    if (nc > 0) {
-      for (int idx = threadIdx.x; idx < nr * nc; idx += blockDim.x) {
-        const int i = k + 1 + idx / nc;
-        const int j = k + 1 + idx % nc;
-        if (j <= i) F[i * ncp + j] -= (w[i] * invd) * w[j];
-      }
+    for (int i = k + 1 + warp; i < nrow; i += 8) {
+      const T li = w[i] * invd;
+      for (int j = k + 1 + lane; j < ncol && j <= i; j += 32) F[i * ncp + j] -= li * w[j];
+      if (lane == 0) F[i * ncp + k] = li;
     }
-    for (int i = k + 1 + threadIdx.x; i < nrow; i += blockDim.x) F[i * ncp + k] = w[i] * invd;
     if (threadIdx.x == 0) {
       F[k * ncp + k] = dk;
       N.D[col0 + k] = dk;
@@ -201,22 +204,55 @@ __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, co
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < nrow * ncp; idx += blockDim.x) Lg[idx] = F[idx];
-  // update block
+  // update block F22 -= L21 D1 L21^T, 4 x 4 register tiles of the lower triangle
   const int nb = nrow - ncol;
   if (nb == 0) return;
+  for (int k = threadIdx.x; k < ncol; k += blockDim.x) w[k] = F[k * ncp + k];
+  __syncthreads();
   T* Ug = N.U + P.sn_Uoff[s];
-  const int64_t ntri = (int64_t)nb * (nb + 1) / 2;
-  for (int64_t t = threadIdx.x; t < ntri; t += blockDim.x) {
-    // t -> (a, b), b <= a
-    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((int64_t)a * (a + 1) / 2 > t) a--;
-    while ((int64_t)(a + 1) * (a + 2) / 2 <= t) a++;
-    const int b = (int)(t - (int64_t)a * (a + 1) / 2);
-    const T* la = F + (int64_t)(ncol + a) * ncp;
-    const T* lb = F + (int64_t)(ncol + b) * ncp;
-    T acc = T(0);
-    for (int k = 0; k < ncol; k++) acc += la[k] * F[k * ncp + k] * lb[k];
-    Ug[(int64_t)a * nb + b] -= acc;
+  const int nbt = (nb + 3) >> 2;
+  const int ntile = nbt * (nbt + 1) / 2;
+  for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+    int ta = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (ta * (ta + 1) / 2 > t) ta--;
+    while ((ta + 1) * (ta + 2) / 2 <= t) ta++;
+    const int tb = t - ta * (ta + 1) / 2;
+    const int a0 = ta * 4, b0 = tb * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; x++)
+#pragma unroll
+      for (int y = 0; y < 4; y++) acc[x][y] = T(0);
+    const T* ra[4];
+    const T* rb[4];
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      ra[x] = F + (int64_t)(ncol + min(a0 + x, nb - 1)) * ncp;
+      rb[x] = F + (int64_t)(ncol + min(b0 + x, nb - 1)) * ncp;
+    }
+    for (int k = 0; k < ncol; k++) {
+      const T dk = w[k];
+      T av[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        av[x] = ra[x][k];
+        bv[x] = rb[x][k] * dk;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; x++)
+#pragma unroll
+        for (int y = 0; y < 4; y++) acc[x][y] += av[x] * bv[y];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; x++) {
+      const int a = a0 + x;
+      if (a >= nb) continue;
+#pragma unroll
+      for (int y = 0; y < 4; y++) {
+        const int b = b0 + y;
+        if (b <= a) Ug[(int64_t)a * nb + b] -= acc[x][y];
+      }
+    }
   }
 }
 
@@ -242,44 +278,59 @@ void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* li
 // of the same launch may be rewriting.)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) k_panel_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
-                                                   double eps, int policy) {
-  __shared__ T Db[PANEL_NB][PANEL_NB + 1];
-  __shared__ T wv[PANEL_NB];
+__global__ void __launch_bounds__(32) k_panel_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+                                                  double eps, int policy) {
+  // one warp: lane i holds row i of the 32 x 32 diagonal block in registers
   const int2 it = items[blockIdx.x];
   const int s = it.x, p0 = it.y;
   const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
   const int col0 = P.sn_col0[s];
   const int pe = min(p0 + PANEL_NB, ncol);
   const int nbk = pe - p0;
+  const int lane = threadIdx.x;
   T* Lb = N.L + P.sn_Loff[s];
-  for (int idx = threadIdx.x; idx < PANEL_NB * PANEL_NB; idx += blockDim.x) {
-    const int i = idx / PANEL_NB, j = idx % PANEL_NB;
-    Db[i][j] = (i < nbk && j <= i) ? Lb[(int64_t)(p0 + i) * ncp + p0 + j] : T(0);
-  }
-  __syncthreads();
-  for (int k = 0; k < nbk; k++) {
-    int8_t stt;
-    const T dk = static_pivot<T>(Db[k][k], P.col_sign[col0 + p0 + k], eps, policy, stt);
-    if (threadIdx.x < PANEL_NB) wv[threadIdx.x] = Db[threadIdx.x][k];
-    __syncthreads();
-    const T invd = T(1) / dk;
-    for (int idx = threadIdx.x; idx < PANEL_NB * PANEL_NB; idx += blockDim.x) {
-      const int i = idx / PANEL_NB, j = idx % PANEL_NB;
-      if (i > k && i < nbk && j > k && j <= i) Db[i][j] -= (wv[i] * invd) * wv[j];
+  T r[PANEL_NB];
+  const T* rp = Lb + (int64_t)(p0 + min(lane, nbk - 1)) * ncp + p0;
+#pragma unroll
+  for (int j = 0; j < PANEL_NB; j++) r[j] = (j <= lane && lane < nbk) ? rp[j] : T(0);
+  int8_t my_st = 0;
+  T my_d = T(0);
+  const int my_sign = lane < nbk ? P.col_sign[col0 + p0 + lane] : 1;
+#pragma unroll
+  for (int k = 0; k < PANEL_NB; k++) {
+    if (k < nbk) {
+      int8_t stt;
+      const int sg = __shfl_sync(0xffffffffu, my_sign, k);
+      const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
+      const T wk = r[k];                   // F[lane][k] before scaling
+      const T li = wk / dk;
+#pragma unroll
+      for (int j = k + 1; j < PANEL_NB; j++) {
+        const T wj = __shfl_sync(0xffffffffu, wk, j);
+        if (lane >= j) r[j] -= li * wj;
+      }
+      if (lane > k) r[k] = li;
+      if (lane == k) {
+        r[k] = dk;
+        my_d = dk;
+        my_st = stt;
+      }
     }
-    if (threadIdx.x > k && threadIdx.x < nbk) Db[threadIdx.x][k] = wv[threadIdx.x] * invd;
-    if (threadIdx.x == 0) {
-      Db[k][k] = dk;
-      N.D[col0 + p0 + k] = dk;
-      N.piv[col0 + p0 + k] = stt;
-    }
-    __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < nbk * nbk; idx += blockDim.x) {
-    const int i = idx / nbk, j = idx % nbk;
-    if (j <= i) Lb[(int64_t)(p0 + i) * ncp + p0 + j] = Db[i][j];
+  if (lane < nbk) {
+    T* wp = Lb + (int64_t)(p0 + lane) * ncp + p0;
+#pragma unroll
+    for (int j = 0; j < PANEL_NB; j++)
+      if (j <= lane) wp[j] = r[j];
+    N.D[col0 + p0 + lane] = my_d;
+    N.piv[col0 + p0 + lane] = my_st;
   }
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 template <typename T>
@@ -310,8 +361,31 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel_rows(DevPlan P, DevNum<T> 
       q[t] = acc;
     }
 #pragma unroll
-    for (int t = 0; t < PANEL_NB; t++)
-      if (t < nbk) row[t] = q[t] / Db[t][t];
+    for (int t = 0; t < PANEL_NB; t++) {
+      q[t] = (t < nbk) ? q[t] / Db[t][t] : T(0);
+      if (t < nbk) row[t] = q[t];
+    }
+    if constexpr (sizeof(T) == 4) {
+      // split TF32 operands of the tensor-core updates: L = hi + lo and
+      // W = L D = hi + lo, zero on the padding columns
+      const int64_t so = P.sn_Soff ? P.sn_Soff[s] : -1;
+      if (N.S && so >= 0) {
+        const int64_t plane = (int64_t)nrow * ncp;
+        float* sp = N.S + so + (int64_t)i * ncp + p0;
+#pragma unroll
+        for (int t = 0; t < PANEL_NB; t++) {
+          if (p0 + t < ncp) {
+            const float l = (float)q[t];
+            const float w = (t < nbk) ? l * (float)Db[t][t] : 0.f;
+            const float lh = round_tf32(l), wh = round_tf32(w);
+            sp[t] = lh;
+            sp[plane + t] = round_tf32(l - lh);
+            sp[2 * plane + t] = wh;
+            sp[3 * plane + t] = round_tf32(w - wh);
+          }
+        }
+      }
+    }
   }
 }
 
@@ -319,7 +393,7 @@ template <typename T>
 void launch_panel_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
                        cudaStream_t st) {
   if (count <= 0) return;
-  k_panel_diag<T><<<count, 128, 0, st>>>(P, N, items, eps, policy);
+  k_panel_diag<T><<<count, 32, 0, st>>>(P, N, items, eps, policy);
 }
 
 template <typename T>

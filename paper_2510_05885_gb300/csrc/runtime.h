@@ -1,7 +1,9 @@
 // Device-side plan, numeric state and kernel launchers (internal).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <string>
 
 namespace ncl {
 
@@ -66,6 +68,7 @@ struct DevPlan {
   const int32_t* con_inst;   // instance of each constraint
   int64_t nnzH, nnzJ, nvar, ncon;
   const int64_t* inst_row_off;  // ninst+1
+  const int64_t* sn_Soff;       // split-operand offset of a tensor-core front, -1 otherwise
 };
 
 // Numeric state for one precision T (float or double).
@@ -76,6 +79,7 @@ struct DevNum {
   T* D;            // pivots, permuted order
   int8_t* piv;     // pivot status: 0 ok, 1 perturbed, 2 zero (stop policy), 3 non-finite
   const double* Klow;  // FP64 lower KKT values (natural numbering)
+  float* S;        // split TF32 operands (L_hi, L_lo, W_hi, W_lo planes) of tensor-core fronts
 };
 
 // A dense update C -= A diag(d) B^T restricted to the lower part, over a
@@ -92,9 +96,25 @@ struct GemmProb {
   int64_t tile0;     // first global tile of this problem
 };
 
+// One dense update handled by the tensor-core kernel (tc_update.cu):
+//   C[i][j] -= sum_{k < 32 nk} L[row_a+i][k0+k] d[k0+k] L[row_b+j][k0+k], j <= i,
+// with the four split planes of the front addressed by tensor maps 4*map..4*map+3.
+struct TcProb {
+  int64_t c_off;
+  int64_t tile0;
+  int32_t ldc, c_in_u, map, row_a, row_b, k0, nk, M, N, Nt;
+};
+
+void launch_update_tc(float* L, float* U, const TcProb* probs, int nprob, int64_t ntiles, const CUtensorMap* maps,
+                      int* err, cudaStream_t st);
+bool tc_encode_maps(const float* split, int64_t rows, int64_t ld, CUtensorMap* out4, std::string* why);
+int64_t tc_tiles(int M, int N, int* Nt_out);
+int tc_smem_bytes();
+void launch_split_rows(const float* L, const float* d, int rows, int ld, int K, float* S, cudaStream_t st);
+
 // launchers (factor.cu)
-void launch_kkt_values(const DevPlan& P, const double* Hv, const double* Jv, const double* S,
-                       const double* delta, const double* rho, double* Klow, cudaStream_t st);
+void launch_kkt_values(const DevPlan& P, const double* const* vals, const double* delta, const double* rho,
+                       double* Klow, cudaStream_t st);
 void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st);
 template <typename T>
 void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st);

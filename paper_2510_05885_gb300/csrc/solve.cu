@@ -64,16 +64,19 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
 
 // ---------------------------------------------------------------------------
 // forward: pivot block of supernode s (one CTA): pull the children's updates
-// that land on the pivot rows, then L11 y = t by 32-column blocks (warp 0
-// solves the diagonal block with shuffles, all warps update the rest).
+// that land on the pivot rows, then L11 y = t by 32-column blocks: warp 0
+// solves the 32 x 32 diagonal block with shuffles (its row of the block
+// prefetched into registers), then every thread updates whole rows below
+// it (one 128-byte row segment per row, y of the block from shared memory).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(1024) k_fwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(512) k_fwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
                                                    T* __restrict__ xp, const T* __restrict__ W, int nrhs) {
+  __shared__ T ys[8][32];
   const int s = list[blockIdx.x];
   const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
   const T* Lb = N.L + P.sn_Loff[s];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
     const int c = P.child_list[k];
     const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
@@ -86,25 +89,33 @@ __global__ void __launch_bounds__(1024) k_fwd_diag(DevPlan P, DevNum<T> N, const
   for (int kb = 0; kb < ncol; kb += 32) {
     const int bw = min(32, ncol - kb);
     if (warp == 0) {
+      T lrow[32];
+      const T* rp = Lb + (int64_t)(kb + min(lane, bw - 1)) * ncp + kb;
+#pragma unroll
+      for (int u = 0; u < 32; u++) lrow[u] = (u < bw) ? rp[u] : T(0);
       for (int r = 0; r < nrhs; r++) {
         T* x = xp + r * P.dim + col0;
         T v = lane < bw ? x[kb + lane] : T(0);
-        for (int u = 0; u < bw; u++) {
+#pragma unroll
+        for (int u = 0; u < 32; u++) {
           const T yu = __shfl_sync(0xffffffffu, v, u);
-          if (lane > u && lane < bw) v -= Lb[(int64_t)(kb + lane) * ncp + kb + u] * yu;
+          if (lane > u) v -= lrow[u] * yu;
         }
         if (lane < bw) x[kb + lane] = v;
+        ys[r][lane] = lane < bw ? v : T(0);
       }
     }
     __syncthreads();
-    for (int i = kb + bw + warp; i < ncol; i += nw) {
+    for (int i = kb + bw + threadIdx.x; i < ncol; i += blockDim.x) {
       const T* row = Lb + (int64_t)i * ncp + kb;
-      for (int r = 0; r < nrhs; r++) {
-        T* x = xp + r * P.dim + col0;
-        T acc = lane < bw ? row[lane] * x[kb + lane] : T(0);
+      T lv[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) x[i] -= acc;
+      for (int u = 0; u < 32; u++) lv[u] = (u < bw) ? row[u] : T(0);
+      for (int r = 0; r < nrhs; r++) {
+        T acc = T(0);
+#pragma unroll
+        for (int u = 0; u < 32; u++) acc += lv[u] * ys[r][u];
+        xp[r * P.dim + col0 + i] -= acc;
       }
     }
     __syncthreads();
@@ -176,10 +187,13 @@ __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const
 }
 
 // backward: pivot block (one CTA): z = D^-1 y - sum of partials, then
-// L11^T x = z by 32-column blocks from the last one.
+// L11^T x = z by 32-column blocks from the last one: warp 0 solves the
+// diagonal block (lane u holds column u of the block in registers), then
+// every thread updates one earlier column u with the block's 32 rows.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_bwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(512) k_bwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
                                                    T* __restrict__ xp, const T* __restrict__ Pw, int nrhs) {
+  __shared__ T xs[8][32];
   const int s = list[blockIdx.x];
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
   const int nb = nrow - ncol;
@@ -200,23 +214,31 @@ __global__ void __launch_bounds__(1024) k_bwd_diag(DevPlan P, DevNum<T> N, const
     const int kb = bi * 32;
     const int bw = min(32, ncol - kb);
     if (warp == 0) {
+      T lcol[32];   // lcol[v] = L[kb+v][kb+lane]
+#pragma unroll
+      for (int v = 0; v < 32; v++) lcol[v] = (v < bw && lane < bw) ? Lb[(int64_t)(kb + v) * ncp + kb + lane] : T(0);
       for (int r = 0; r < nrhs; r++) {
         T* x = xp + r * P.dim + col0;
         T v = lane < bw ? x[kb + lane] : T(0);
-        for (int u = bw - 1; u >= 0; u--) {
+#pragma unroll
+        for (int u = 31; u >= 0; u--) {
           const T xu = __shfl_sync(0xffffffffu, v, u);
-          if (lane < u) v -= Lb[(int64_t)(kb + u) * ncp + kb + lane] * xu;
+          if (lane < u) v -= lcol[u] * xu;
         }
         if (lane < bw) x[kb + lane] = v;
+        xs[r][lane] = lane < bw ? v : T(0);
       }
     }
     __syncthreads();
     for (int u = threadIdx.x; u < kb; u += blockDim.x) {
+      T lv[32];
+#pragma unroll
+      for (int v = 0; v < 32; v++) lv[v] = (v < bw) ? Lb[(int64_t)(kb + v) * ncp + u] : T(0);
       for (int r = 0; r < nrhs; r++) {
-        T* x = xp + r * P.dim + col0;
         T acc = T(0);
-        for (int v = 0; v < bw; v++) acc += Lb[(int64_t)(kb + v) * ncp + u] * x[kb + v];
-        x[u] -= acc;
+#pragma unroll
+        for (int v = 0; v < 32; v++) acc += lv[v] * xs[r][v];
+        xp[r * P.dim + col0 + u] -= acc;
       }
     }
     __syncthreads();
@@ -226,7 +248,7 @@ __global__ void __launch_bounds__(1024) k_bwd_diag(DevPlan P, DevNum<T> N, const
 template <typename T>
 void launch_fwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp, T* W, int nrhs,
                      cudaStream_t st) {
-  if (count > 0) k_fwd_diag<T><<<count, 1024, 0, st>>>(P, N, list, xp, W, nrhs);
+  if (count > 0) k_fwd_diag<T><<<count, 512, 0, st>>>(P, N, list, xp, W, nrhs);
 }
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, T* xp, T* W, int nrhs,
@@ -241,7 +263,7 @@ void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, i
 template <typename T>
 void launch_bwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp, const T* Pw,
                      int nrhs, cudaStream_t st) {
-  if (count > 0) k_bwd_diag<T><<<count, 1024, 0, st>>>(P, N, list, xp, Pw, nrhs);
+  if (count > 0) k_bwd_diag<T><<<count, 512, 0, st>>>(P, N, list, xp, Pw, nrhs);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,356 @@
+// Split-TF32 dense updates on the 5th-generation tensor cores (sm_103a).
+//
+//   C[i][j] -= sum_k L[ra+i][k] * d[k] * L[rb+j][k]     (j <= i, lower part)
+//
+// which is the trailing update of a front's pivot columns and the update
+// block F22 -= L21 D1 L21^T of the multifrontal LDL^T.  Each FP32 operand is
+// split into two TF32 terms, x = x_hi + x_lo (x_hi = x rounded to TF32,
+// x_lo = the remainder rounded to TF32), and the product is accumulated in
+// FP32 as A_hi B_hi + A_hi B_lo + A_lo B_hi, which keeps FP32-level accuracy
+// (the dropped A_lo B_lo term is about 2^-22 relative).  The split operands
+// L_hi, L_lo, W_hi, W_lo (W = L D) are written by the panel kernel next to
+// L, so this kernel is a plain TMA -> tcgen05.mma -> TMEM -> epilogue.
+//
+// One CTA computes one 128 x 128 tile of C: thread 0 issues TMA loads
+// (128-byte swizzle, 3-stage mbarrier pipeline), thread 32 issues the MMAs
+// (M=128, N=128, K=8 per instruction, FP32 accumulator in 128 TMEM
+// columns) and commits them to the stage barriers, then all four warps read
+// their 32 accumulator lanes back with tcgen05.ld and update C.  Every wait
+// is bounded: on a timeout the kernel sets an error flag, skips the update,
+// frees its TMEM and returns.
+#include "runtime.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace ncl {
+
+namespace {
+
+constexpr int TC_M = 128, TC_N = 128, TC_BK = 32;
+constexpr int TC_STAGES = 3;
+constexpr int TC_TILE_BYTES = TC_M * TC_BK * 4;          // 16 KB
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;       // about 2 s at 2 GHz
+
+// instruction descriptor: dense, D = F32, A = B = TF32, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// K-major operand in 128-byte swizzled rows: 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int t = 0; t < 32; t++) v[t] = __uint_as_float(r[t]);
+}
+
+__device__ __forceinline__ void decode_lower_tile(int64_t t, int Nt, int& ti, int& tj) {
+  const int64_t tri = (int64_t)Nt * (Nt + 1) / 2;
+  if (t < tri) {
+    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)a * (a + 1) / 2 > t) a--;
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= t) a++;
+    ti = a;
+    tj = (int)(t - (int64_t)a * (a + 1) / 2);
+  } else {
+    const int64_t u = t - tri;
+    ti = Nt + (int)(u / Nt);
+    tj = (int)(u % Nt);
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) k_update_tc(float* __restrict__ Lbase, float* __restrict__ Ubase,
+                                                      const TcProb* __restrict__ probs, int nprob,
+                                                      const CUtensorMap* __restrict__ maps, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte alignment of the shared-window address (the swizzle atom)
+  unsigned char* sb = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sb + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* done = empty + TC_STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // problem and tile of this CTA
+  const int64_t gt = blockIdx.x;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile0 <= gt) lo = mid;
+    else hi = mid - 1;
+  }
+  const TcProb pb = probs[lo];
+  int ti, tj;
+  decode_lower_tile(gt - pb.tile0, pb.Nt, ti, tj);
+  const int i0 = ti * TC_M, j0 = tj * TC_N;
+  const CUtensorMap* mLhi = maps + 4 * pb.map;
+  const CUtensorMap* mLlo = mLhi + 1;
+  const CUtensorMap* mWhi = mLhi + 2;
+  const CUtensorMap* mWlo = mLhi + 3;
+
+  if (tid == 0) {
+    s_fail = 0;
+    for (int s = 0; s < TC_STAGES; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mLhi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mWhi)) : "memory");
+  }
+  if (warp == 0) tmem_alloc(tslot, TC_TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int nk = pb.nk;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kt = 0; kt < nk; kt++) {
+      const int s = kt % TC_STAGES;
+      if (kt >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((kt / TC_STAGES) - 1) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      unsigned char* st = sb + s * TC_STAGE_BYTES;
+      mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+      const int x = pb.k0 + kt * TC_BK;
+      tma_load_2d(st, mLhi, x, pb.row_a + i0, &full[s]);
+      tma_load_2d(st + TC_TILE_BYTES, mLlo, x, pb.row_a + i0, &full[s]);
+      tma_load_2d(st + 2 * TC_TILE_BYTES, mWhi, x, pb.row_b + j0, &full[s]);
+      tma_load_2d(st + 3 * TC_TILE_BYTES, mWlo, x, pb.row_b + j0, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    int kt = 0;
+    for (; kt < nk; kt++) {
+      const int s = kt % TC_STAGES;
+      if (!mbar_wait_bounded(&full[s], (kt / TC_STAGES) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_hi = smem_u32(sb + s * TC_STAGE_BYTES);
+      const uint32_t a_lo = a_hi + TC_TILE_BYTES;
+      const uint32_t b_hi = a_hi + 2 * TC_TILE_BYTES;
+      const uint32_t b_lo = a_hi + 3 * TC_TILE_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; kk++) {
+        const uint32_t off = kk * 32;   // 8 TF32 values = 32 bytes along K
+        umma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), (kt | kk) != 0);
+        umma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), 1);
+        umma_tf32(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1);
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+
+  // epilogue: lane (row) 32*warp + lane of the accumulator
+  const bool ok = mbar_wait_bounded(done, 0);
+  tc_fence_after();
+  __syncthreads();
+  if (!ok || s_fail) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    const int i = i0 + warp * 32 + lane;
+    float* C = (pb.c_in_u ? Ubase : Lbase) + pb.c_off;
+#pragma unroll 1
+    for (int c = 0; c < TC_N / 32; c++) {
+      float v[32];
+      tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+      const int jb = j0 + c * 32;
+      if (i < pb.M && jb < pb.N && jb <= i) {
+        float* crow = C + (int64_t)i * pb.ldc + jb;
+#pragma unroll
+        for (int t = 0; t < 32; t++)
+          if (jb + t < pb.N && jb + t <= i) crow[t] -= v[t];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+}
+
+// split x = hi + lo, both TF32 (round to nearest)
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__global__ void k_split_rows(const float* __restrict__ L, const float* __restrict__ d, int rows, int ld, int K,
+                             float* __restrict__ S) {
+  const int64_t plane = (int64_t)rows * ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % ld);
+    const float l = k < K ? L[e] : 0.f;
+    const float w = k < K ? l * d[k] : 0.f;
+    const float lh = to_tf32(l), wh = to_tf32(w);
+    S[e] = lh;
+    S[plane + e] = to_tf32(l - lh);
+    S[2 * plane + e] = wh;
+    S[3 * plane + e] = to_tf32(w - wh);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+}  // namespace
+
+bool tc_encode_maps(const float* split, int64_t rows, int64_t ld, CUtensorMap* out4, std::string* why) {
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        !fn) {
+      if (why) *why = "cuTensorMapEncodeTiled unavailable";
+      return false;
+    }
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int64_t plane = rows * ld;
+  for (int a = 0; a < 4; a++) {
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_M};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(&out4[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)(split + a * plane), dims, strides,
+                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      if (why) *why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+      return false;
+    }
+  }
+  return true;
+}
+
+int tc_smem_bytes() { return TC_SMEM; }
+
+int64_t tc_tiles(int M, int N, int* Nt_out) {
+  const int Mt = (M + TC_M - 1) / TC_M, Nt = (N + TC_N - 1) / TC_N;
+  *Nt_out = Nt;
+  return (int64_t)Nt * (Nt + 1) / 2 + (int64_t)(Mt - Nt) * Nt;
+}
+
+void launch_update_tc(float* L, float* U, const TcProb* probs, int nprob, int64_t ntiles, const CUtensorMap* maps,
+                      int* err, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    attr = true;
+  }
+  k_update_tc<<<(unsigned)ntiles, 128, TC_SMEM, st>>>(L, U, probs, nprob, maps, err);
+}
+
+void launch_split_rows(const float* L, const float* d, int rows, int ld, int K, float* S, cudaStream_t st) {
+  const int64_t n = (int64_t)rows * ld;
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  k_split_rows<<<(unsigned)b, 256, 0, st>>>(L, d, rows, ld, K, S);
+}
+
+}  // namespace ncl

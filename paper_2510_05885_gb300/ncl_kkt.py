@@ -93,6 +93,7 @@ _SIGS = {
     "ncl_kkt_get_supernodes": (I32, [P, P, P, P]),
     "ncl_kkt_instance_count": (I32, [P]),
     "ncl_kkt_kernel_launches": (I64, []),
+    "ncl_kkt_selftest_tensor_update": (I32, [I32, I32, I32, P, P, I32, I32, I32, I32, P, I32, P]),
     "ncl_kkt_profile": (I32, [P, I32]),
     "ncl_kkt_profile_report": (I32, [P, ctypes.c_char_p, I64]),
     "ncl_kkt_destroy": (None, [P]),
@@ -278,6 +279,14 @@ def ncl_kkt_get_supernodes(h, ns):
     nrow = np.empty(ns, np.int32)
     _check(load().ncl_kkt_get_supernodes(h, col0.ctypes.data, parent.ctypes.data, nrow.ctypes.data))
     return col0, parent, nrow
+
+
+def ncl_kkt_selftest_tensor_update(L, d, K, row_a, row_b, M, N, C, stream=None):
+    """C (M x ldc float32 CUDA) -= L[row_a:row_a+M, :K] diag(d) L[row_b:row_b+N, :K]^T, lower part,
+    on the tensor-core kernel.  L: (rows, ld) float32 CUDA tensor."""
+    rows, ld = L.shape
+    _check(load().ncl_kkt_selftest_tensor_update(rows, ld, K, _ptr(L), _ptr(d), row_a, row_b, M, N, _ptr(C),
+                                                 C.shape[1], _stream_ptr(stream)))
 
 
 def ncl_kkt_kernel_launches() -> int:
