@@ -45,6 +45,13 @@ struct CudaError {
   } while (0)
 
 constexpr int MAX_RHS_SWEEP = 8;
+// In the FP32 path the update block F22 -= L21 D1 L21^T of a front with at
+// least TC_MIN_K pivots runs on the tensor cores; shorter inner dimensions,
+// and the 32-wide trailing updates of the panels, do not amortise the fixed
+// cost of a tensor-core tile and stay on the SIMT kernel (measured; the
+// option value use_tensor_cores = 2 also puts the trailing updates on the
+// tensor cores).
+constexpr int TC_MIN_K = 256;
 
 // per-launch arithmetic (flops on the stored blocks) and minimum traffic
 // (bytes), used only for profiling reports
@@ -78,6 +85,7 @@ struct Level {
   int64_t tsyrk_off = 0;  // tensor-core update-block problems
   int tsyrk_cnt = 0;
   int64_t tsyrk_tiles = 0;
+  int tsyrk_stages = 1;
   int64_t list_off = 0;   // all supernodes of the level (solve)
   int list_cnt = 0;
   int64_t below_off = 0;  // (s, a0) solve items
@@ -110,6 +118,9 @@ struct HostSched {
   std::vector<int64_t> sn_Soff;
   std::vector<int32_t> tc_fronts;
   int64_t split_max = 0;
+  std::vector<int8_t> sn_flags;
+  std::vector<int2> invv;                 // (supernode, first column) of every 32 x 32 diagonal block
+  std::vector<int64_t> sn_Ioff;
 };
 
 }  // namespace
@@ -157,6 +168,7 @@ struct ncl_kkt_s {
   const double** d_valptr = nullptr;       // {H, J, Sigma} pointers of the current factor call
   CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
   TcProb* d_tc = nullptr;
+  int2* d_inv = nullptr;
   int* d_err = nullptr;                    // device error flags (bounded waits)
   // CUDA graphs: the factor and the triangular sweeps are captured once (on
   // a private stream, after one direct call) and replayed
@@ -239,6 +251,12 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<GemmProb>& probv = hs.probv;
   hs.tc = is_fp32(h) && h->opt.use_tensor_cores;
   hs.sn_Soff.assign(P.ns, -1);
+  hs.sn_flags.assign(P.ns, 0);
+  hs.sn_Ioff.assign(P.ns + 1, 0);
+  for (int32_t s = 0; s < P.ns; s++) {
+    for (int kb = 0; kb < P.sn_ncol[s]; kb += 32) hs.invv.push_back(make_int2(s, kb));
+    hs.sn_Ioff[s + 1] = hs.sn_Ioff[s] + (int64_t)((P.sn_ncol[s] + 31) / 32) * 1024;
+  }
   std::vector<int32_t> fid(P.ns, -1);
   h->levels.assign(P.nlevels, Level{});
   for (int32_t l = 0; l < P.nlevels; l++) {
@@ -286,6 +304,7 @@ void build_schedule(ncl_kkt_s* h) {
     if (hs.tc) {
       int64_t off = 0;
       for (int32_t s : large) {
+        if (P.sn_ncol[s] < TC_MIN_K || P.sn_nrow[s] == P.sn_ncol[s]) continue;
         fid[s] = (int32_t)hs.tc_fronts.size();
         hs.tc_fronts.push_back(s);
         hs.sn_Soff[s] = off;
@@ -293,6 +312,7 @@ void build_schedule(ncl_kkt_s* h) {
       }
       hs.split_max = std::max(hs.split_max, off);
     }
+    for (int32_t s : large) hs.sn_flags[s] = 1;
     int maxp = 0;
     for (int32_t s : large) maxp = std::max(maxp, (P.sn_ncol[s] + PANEL_NB - 1) / PANEL_NB);
     L.steps.resize(maxp);
@@ -312,7 +332,7 @@ void build_schedule(ncl_kkt_s* h) {
         for (int r0 = pe; r0 < nrow; r0 += PANEL_ROWS) panelv.push_back(make_int4(s, p0, r0, 0));
         S.panel_cost.flops += (double)(nrow - pe) * (pe - p0) * (pe - p0) + 2.0 * (pe - p0) * (pe - p0) * (pe - p0) / 3.0;
         S.panel_cost.bytes += esz * 2.0 * (nrow - p0) * (pe - p0);
-        if (pe < ncol && hs.tc) {
+        if (pe < ncol && fid[s] >= 0 && h->opt.use_tensor_cores > 1) {
           TcProb q{};
           q.c_off = P.sn_Loff[s] + (int64_t)pe * ncp + pe;
           q.ldc = ncp;
@@ -324,6 +344,8 @@ void build_schedule(ncl_kkt_s* h) {
           q.nk = 1;
           q.M = nrow - pe;
           q.N = ncol - pe;
+          q.front = s;
+          q.next_p0 = pe;
           q.tile0 = S.tc_tiles;
           S.tc_tiles += tc_tiles(q.M, q.N, &q.Nt);
           hs.tcv.push_back(q);
@@ -342,6 +364,8 @@ void build_schedule(ncl_kkt_s* h) {
           g.N = ncol - pe;
           g.K = pe - p0;
           g.c_in_u = 0;
+          g.front = s;
+          g.next_p0 = pe;
           const int Mt = (g.M + GEMM_TILE - 1) / GEMM_TILE, Nt = (g.N + GEMM_TILE - 1) / GEMM_TILE;
           g.Nt = Nt;
           g.tile0 = tiles;
@@ -365,7 +389,7 @@ void build_schedule(ncl_kkt_s* h) {
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
       const int nb = nrow - ncol;
       if (nb == 0) continue;
-      if (hs.tc) {
+      if (hs.tc && ncol >= TC_MIN_K && fid[s] >= 0) {
         TcProb q{};
         q.c_off = P.sn_Uoff[s];
         q.ldc = nb;
@@ -377,8 +401,11 @@ void build_schedule(ncl_kkt_s* h) {
         q.nk = (ncol + 31) / 32;
         q.M = nb;
         q.N = nb;
+        q.front = s;
+        q.next_p0 = -1;
         q.tile0 = L.tsyrk_tiles;
         L.tsyrk_tiles += tc_tiles(q.M, q.N, &q.Nt);
+        L.tsyrk_stages = std::max(L.tsyrk_stages, std::min(q.nk, 3));
         hs.tcv.push_back(q);
         const double centries = 0.5 * (double)nb * (nb + 1);
         L.syrk_cost.flops += 2.0 * ncol * centries;
@@ -396,6 +423,8 @@ void build_schedule(ncl_kkt_s* h) {
       g.N = nb;
       g.K = ncol;
       g.c_in_u = 1;
+      g.front = s;
+      g.next_p0 = -1;
       const int Nt = (nb + GEMM_TILE - 1) / GEMM_TILE;
       g.Nt = Nt;
       g.tile0 = tiles;
@@ -450,6 +479,8 @@ void build_schedule(ncl_kkt_s* h) {
     }
     for (const int2& it : pdiagv)
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_ncol[it.x]) bad("panel diag item");
+    for (const int2& b : hs.invv)
+      if (b.x < 0 || b.x >= P.ns || b.y < 0 || b.y >= P.sn_ncol[b.x] || b.y % 32) bad("inverse block");
     for (const TcProb& q : hs.tcv) {
       const int64_t csz = q.c_in_u ? Usz : Lsz;
       if (q.map < 0 || q.map >= (int)hs.tc_fronts.size()) bad("tc map");
@@ -557,6 +588,7 @@ void build_device(ncl_kkt_s* h) {
     N.U = h->alloc<T>(P.U_stored);
     N.D = h->alloc<T>(P.dim);
     N.piv = h->alloc<int8_t>(P.dim);
+    N.Linv = h->alloc<T>(h->hs.sn_Ioff[P.ns]);
     N.Klow = h->Klow;
   };
   if (is_fp32(h)) alloc_num(h->nf, float{});
@@ -587,6 +619,9 @@ void build_device(ncl_kkt_s* h) {
     h->d_tc = h->upload(hs.tcv);
   }
   h->d_err = h->alloc<int>(4);
+  d.sn_flags = h->upload(h->hs.sn_flags);
+  d.sn_Ioff = h->upload(h->hs.sn_Ioff);
+  h->d_inv = h->upload(h->hs.invv);
   CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 
   HostSched& hs = h->hs;
@@ -686,30 +721,39 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
   const DevPlan& P = h->dp;
   const bool f32 = sizeof(T) == 4;
   for (const Level& L : h->levels) {
-    klaunch(h, st, f32 ? "assemble_f32" : "assemble_f64", L.asm_cnt, L.asm_cost,
-            [&] { launch_assemble<T>(P, N, h->d_asm + L.asm_off, L.asm_cnt, st); });
+    klaunch(h, st, f32 ? "assemble_f32" : "assemble_f64", L.asm_cnt, L.asm_cost, [&] {
+      launch_assemble<T>(P, N, h->d_asm + L.asm_off, L.asm_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
+    });
     klaunch(h, st, f32 ? "factor_small_f32" : "factor_small_f64", L.small_cnt, L.small_cost, [&] {
       launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
     });
     for (const Step& S : L.steps) {
-      klaunch(h, st, f32 ? "panel_diag_f32" : "panel_diag_f64", S.pdiag_cnt, Cost{}, [&] {
-        launch_panel_diag<T>(P, N, h->d_pdiag + S.pdiag_off, S.pdiag_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
-      });
       klaunch(h, st, f32 ? "panel_rows_f32" : "panel_rows_f64", S.panel_cnt, S.panel_cost,
               [&] { launch_panel_rows<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, st); });
-      klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost,
-              [&] { launch_gemm_simt<T>(N, h->d_probs + S.prob_off, S.prob_cnt, S.tiles, st); });
+      klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost, [&] {
+        launch_gemm_simt<T>(P, N, h->d_probs + S.prob_off, S.prob_cnt, S.tiles, h->opt.pivot_eps,
+                            h->opt.pivot_policy, st);
+      });
       if constexpr (sizeof(T) == 4)
         klaunch(h, st, "update_tc_f32", S.tc_tiles, S.gemm_cost, [&] {
-          launch_update_tc(N.L, N.U, h->d_tc + S.tc_off, S.tc_cnt, S.tc_tiles, h->d_maps, h->d_err, st);
+          launch_update_tc(P, N, h->d_tc + S.tc_off, S.tc_cnt, S.tc_tiles, 1, h->d_maps, h->d_err, h->opt.pivot_eps,
+                           h->opt.pivot_policy, st);
         });
     }
-    klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", L.syrk_tiles, L.syrk_cost,
-            [&] { launch_gemm_simt<T>(N, h->d_probs + L.syrk_off, L.syrk_cnt, L.syrk_tiles, st); });
+    klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", L.syrk_tiles, L.syrk_cost, [&] {
+      launch_gemm_simt<T>(P, N, h->d_probs + L.syrk_off, L.syrk_cnt, L.syrk_tiles, h->opt.pivot_eps,
+                          h->opt.pivot_policy, st);
+    });
     if constexpr (sizeof(T) == 4)
       klaunch(h, st, "update_tc_f32", L.tsyrk_tiles, L.syrk_cost, [&] {
-        launch_update_tc(N.L, N.U, h->d_tc + L.tsyrk_off, L.tsyrk_cnt, L.tsyrk_tiles, h->d_maps, h->d_err, st);
+        launch_update_tc(P, N, h->d_tc + L.tsyrk_off, L.tsyrk_cnt, L.tsyrk_tiles, L.tsyrk_stages, h->d_maps,
+                         h->d_err, h->opt.pivot_eps, h->opt.pivot_policy, st);
       });
+  }
+  {
+    const int nb = (int)h->hs.invv.size();
+    klaunch(h, st, f32 ? "invert_diag_f32" : "invert_diag_f64", nb, Cost{nb * 32.0 * 32 * 32, nb * 2.0 * 1024 * sizeof(T)},
+            [&] { launch_invert_diag<T>(P, N, h->d_inv, nb, st); });
   }
   CK(cudaGetLastError());
 }
@@ -1339,14 +1383,20 @@ extern "C" ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, i
   q.M = M;
   q.N = N;
   q.tile0 = 0;
+  q.front = 0;
+  q.next_p0 = -1;
   const int64_t tiles = tc_tiles(M, N, &q.Nt);
+  DevPlan P0{};
+  DevNum<float> N0{};
+  N0.L = C;
+  N0.U = C;
   int herr = 0;
   cudaError_t e = cudaMemcpyAsync(dmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dp, &q, sizeof(q), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     launch_split_rows(L, d, rows, ld, K, S, st);
-    launch_update_tc(C, C, dp, 1, tiles, dmaps, derr, st);
+    launch_update_tc(P0, N0, dp, 1, tiles, 3, dmaps, derr, 1e-10, 0, st);
     g_kernel_launches.fetch_add(2);
     e = cudaGetLastError();
   }

@@ -12,6 +12,7 @@
 // +-eps with the sign of its block before reordering (case (ii)), or counted
 // as a zero eigenvalue (case (i)).
 #include "runtime.h"
+#include "diag32.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -80,23 +81,6 @@ void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knor
 }
 
 // ---------------------------------------------------------------------------
-// Static pivot (Section 3.1).  Returns the pivot to use and its status.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T static_pivot(T d, int sign, double eps, int policy, int8_t& st) {
-  if (!isfinite((double)d)) {
-    st = 3;
-    return d;
-  }
-  if (fabs((double)d) <= eps) {
-    st = policy == 0 ? 1 : 2;
-    return sign < 0 ? (T)(-eps) : (T)eps;
-  }
-  st = 0;
-  return d;
-}
-
-// ---------------------------------------------------------------------------
 // Front assembly.  One CTA per (supernode, run of ASM_ROWS front rows):
 // zero the rows, store the original entries, then add the children's update
 // blocks child by child (a child's rows map to distinct parent rows, so the
@@ -113,7 +97,9 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const int2* __restrict__ items, double eps,
+                                                  int policy) {
+  static_assert(ASM_ROWS == PANEL_NB, "the first assembly CTA owns the first diagonal block");
   const int2 it = items[blockIdx.x];
   const int s = it.x, r0 = it.y;
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
@@ -156,12 +142,19 @@ __global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const 
       }
     }
   }
+  // a front factored by panels: this CTA holds the complete first diagonal
+  // block (rows [0, 32)), so it factors it now
+  if (r0 == 0 && (P.sn_flags[s] & 1)) {
+    __syncthreads();
+    if (warp == 0) factor_diag32<T>(P, N, s, 0, eps, policy, lane);
+  }
 }
 
 template <typename T>
-void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st) {
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
+                     cudaStream_t st) {
   if (count <= 0) return;
-  k_assemble<T><<<count, 256, 0, st>>>(P, N, items);
+  k_assemble<T><<<count, 256, 0, st>>>(P, N, items, eps, policy);
 }
 
 // ---------------------------------------------------------------------------
@@ -277,56 +270,6 @@ void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* li
 // (Two launches: the row CTAs must read the factored block, which no CTA
 // of the same launch may be rewriting.)
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(32) k_panel_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
-                                                  double eps, int policy) {
-  // one warp: lane i holds row i of the 32 x 32 diagonal block in registers
-  const int2 it = items[blockIdx.x];
-  const int s = it.x, p0 = it.y;
-  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
-  const int col0 = P.sn_col0[s];
-  const int pe = min(p0 + PANEL_NB, ncol);
-  const int nbk = pe - p0;
-  const int lane = threadIdx.x;
-  T* Lb = N.L + P.sn_Loff[s];
-  T r[PANEL_NB];
-  const T* rp = Lb + (int64_t)(p0 + min(lane, nbk - 1)) * ncp + p0;
-#pragma unroll
-  for (int j = 0; j < PANEL_NB; j++) r[j] = (j <= lane && lane < nbk) ? rp[j] : T(0);
-  int8_t my_st = 0;
-  T my_d = T(0);
-  const int my_sign = lane < nbk ? P.col_sign[col0 + p0 + lane] : 1;
-#pragma unroll
-  for (int k = 0; k < PANEL_NB; k++) {
-    if (k < nbk) {
-      int8_t stt;
-      const int sg = __shfl_sync(0xffffffffu, my_sign, k);
-      const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
-      const T wk = r[k];                   // F[lane][k] before scaling
-      const T li = wk / dk;
-#pragma unroll
-      for (int j = k + 1; j < PANEL_NB; j++) {
-        const T wj = __shfl_sync(0xffffffffu, wk, j);
-        if (lane >= j) r[j] -= li * wj;
-      }
-      if (lane > k) r[k] = li;
-      if (lane == k) {
-        r[k] = dk;
-        my_d = dk;
-        my_st = stt;
-      }
-    }
-  }
-  if (lane < nbk) {
-    T* wp = Lb + (int64_t)(p0 + lane) * ncp + p0;
-#pragma unroll
-    for (int j = 0; j < PANEL_NB; j++)
-      if (j <= lane) wp[j] = r[j];
-    N.D[col0 + p0 + lane] = my_d;
-    N.piv[col0 + p0 + lane] = my_st;
-  }
-}
-
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -351,14 +294,31 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel_rows(DevPlan P, DevNum<T> 
   if (i < nrow && i >= pe && i < r0 + PANEL_ROWS) {
     T q[PANEL_NB];
     T* row = N.L + P.sn_Loff[s] + (int64_t)i * ncp + p0;
+    // the 32 values of the row are 16-byte aligned (ncp % 4 == 0, p0 % 32 == 0)
+    if (nbk == PANEL_NB) {
+      if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int t = 0; t < PANEL_NB; t++) q[t] = (t < nbk) ? row[t] : T(0);
+        for (int t = 0; t < PANEL_NB; t += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(row + t);
+          q[t] = v.x, q[t + 1] = v.y, q[t + 2] = v.z, q[t + 3] = v.w;
+        }
+      } else {
 #pragma unroll
-    for (int t = 1; t < PANEL_NB; t++) {
-      T acc = q[t];
+        for (int t = 0; t < PANEL_NB; t += 2) {
+          const double2 v = *reinterpret_cast<const double2*>(row + t);
+          q[t] = v.x, q[t + 1] = v.y;
+        }
+      }
+    } else {
 #pragma unroll
-      for (int u = 0; u < t; u++) acc -= Db[t][u] * q[u];
-      q[t] = acc;
+      for (int t = 0; t < PANEL_NB; t++) q[t] = (t < nbk) ? row[t] : T(0);
+    }
+    // forward substitution q = L11^-1 f, column by column (short dependency chains)
+#pragma unroll
+    for (int u = 0; u < PANEL_NB - 1; u++) {
+      const T qu = q[u];
+#pragma unroll
+      for (int t = u + 1; t < PANEL_NB; t++) q[t] -= Db[t][u] * qu;
     }
 #pragma unroll
     for (int t = 0; t < PANEL_NB; t++) {
@@ -390,13 +350,6 @@ __global__ void __launch_bounds__(PANEL_ROWS) k_panel_rows(DevPlan P, DevNum<T> 
 }
 
 template <typename T>
-void launch_panel_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
-                       cudaStream_t st) {
-  if (count <= 0) return;
-  k_panel_diag<T><<<count, 32, 0, st>>>(P, N, items, eps, policy);
-}
-
-template <typename T>
 void launch_panel_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st) {
   if (count <= 0) return;
   k_panel_rows<T><<<count, PANEL_ROWS, 0, st>>>(P, N, items);
@@ -422,7 +375,8 @@ __device__ __forceinline__ void decode_tile(int64_t t, int Nt, int& ti, int& tj)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_simt(DevNum<T> N, const GemmProb* __restrict__ probs, int nprob) {
+__global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const GemmProb* __restrict__ probs,
+                                                   int nprob, double eps, int policy) {
   constexpr int TB = GEMM_TILE, KC = 16;
   __shared__ T As[KC][TB + 1];
   __shared__ T Bs[KC][TB + 1];
@@ -482,12 +436,19 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevNum<T> N, const GemmProb* 
       C[(int64_t)i * pb.ldc + j] -= acc[a][b];
     }
   }
+  // tile (0,0) of a trailing update holds the next panel's diagonal block,
+  // now fully updated: factor it here
+  if (gt == pb.tile0 && pb.next_p0 >= 0) {
+    __syncthreads();
+    if (threadIdx.x < 32) factor_diag32<T>(P, N, pb.front, pb.next_p0, eps, policy, threadIdx.x);
+  }
 }
 
 template <typename T>
-void launch_gemm_simt(const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles, cudaStream_t st) {
+void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles,
+                      double eps, int policy, cudaStream_t st) {
   if (ntiles <= 0) return;
-  k_gemm_simt<T><<<(unsigned)ntiles, 256, 0, st>>>(N, probs, nprob);
+  k_gemm_simt<T><<<(unsigned)ntiles, 256, 0, st>>>(P, N, probs, nprob, eps, policy);
 }
 
 // ---------------------------------------------------------------------------
@@ -524,13 +485,13 @@ void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cud
 }
 
 #define NCL_INST(T)                                                                                     \
-  template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, int, cudaStream_t);   \
+  template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, int, double, int,     \
+                                   cudaStream_t);                                                       \
   template void launch_factor_small<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, double,   \
                                        int, cudaStream_t);                                              \
-  template void launch_panel_diag<T>(const DevPlan&, const DevNum<T>&, const int2*, int, double, int,   \
-                                     cudaStream_t);                                                     \
   template void launch_panel_rows<T>(const DevPlan&, const DevNum<T>&, const int4*, int, cudaStream_t); \
-  template void launch_gemm_simt<T>(const DevNum<T>&, const GemmProb*, int, int64_t, cudaStream_t);     \
+  template void launch_gemm_simt<T>(const DevPlan&, const DevNum<T>&, const GemmProb*, int, int64_t,    \
+                                    double, int, cudaStream_t);                                         \
   template void launch_inertia<T>(const DevPlan&, const DevNum<T>&, long long*, cudaStream_t);
 NCL_INST(float)
 NCL_INST(double)

@@ -69,6 +69,8 @@ struct DevPlan {
   int64_t nnzH, nnzJ, nvar, ncon;
   const int64_t* inst_row_off;  // ninst+1
   const int64_t* sn_Soff;       // split-operand offset of a tensor-core front, -1 otherwise
+  const int8_t* sn_flags;       // bit 0: front factored by panels (large front)
+  const int64_t* sn_Ioff;       // offset of the inverted 32 x 32 diagonal blocks of L11
 };
 
 // Numeric state for one precision T (float or double).
@@ -80,6 +82,7 @@ struct DevNum {
   int8_t* piv;     // pivot status: 0 ok, 1 perturbed, 2 zero (stop policy), 3 non-finite
   const double* Klow;  // FP64 lower KKT values (natural numbering)
   float* S;        // split TF32 operands (L_hi, L_lo, W_hi, W_lo planes) of tensor-core fronts
+  T* Linv;         // inverses of the unit lower 32 x 32 diagonal blocks of every L11 (row-major)
 };
 
 // A dense update C -= A diag(d) B^T restricted to the lower part, over a
@@ -94,6 +97,8 @@ struct GemmProb {
   int32_t c_in_u;    // 1: C lives in U storage, 0: in L storage
   int32_t Nt;        // column tiles
   int64_t tile0;     // first global tile of this problem
+  int32_t front;     // supernode of the front
+  int32_t next_p0;   // >= 0: after its tile (0,0) the CTA factors the diagonal block at next_p0
 };
 
 // One dense update handled by the tensor-core kernel (tc_update.cu):
@@ -103,10 +108,11 @@ struct TcProb {
   int64_t c_off;
   int64_t tile0;
   int32_t ldc, c_in_u, map, row_a, row_b, k0, nk, M, N, Nt;
+  int32_t front, next_p0;   // as in GemmProb
 };
 
-void launch_update_tc(float* L, float* U, const TcProb* probs, int nprob, int64_t ntiles, const CUtensorMap* maps,
-                      int* err, cudaStream_t st);
+void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, int nprob, int64_t ntiles,
+                      int stages, const CUtensorMap* maps, int* err, double eps, int policy, cudaStream_t st);
 bool tc_encode_maps(const float* split, int64_t rows, int64_t ld, CUtensorMap* out4, std::string* why);
 int64_t tc_tiles(int M, int N, int* Nt_out);
 int tc_smem_bytes();
@@ -117,7 +123,8 @@ void launch_kkt_values(const DevPlan& P, const double* const* vals, const double
                        double* Klow, cudaStream_t st);
 void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st);
 template <typename T>
-void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st);
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
+                     cudaStream_t st);
 template <typename T>
 void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count,
                          double eps, int policy, cudaStream_t st);
@@ -127,10 +134,13 @@ void launch_panel_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, 
 template <typename T>
 void launch_panel_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st);
 template <typename T>
-void launch_gemm_simt(const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles,
-                      cudaStream_t st);
+void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles,
+                      double eps, int policy, cudaStream_t st);
 template <typename T>
 void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st);
+
+template <typename T>
+void launch_invert_diag(const DevPlan& P, const DevNum<T>& N, const int2* blocks, int count, cudaStream_t st);
 
 // launchers (solve.cu)
 template <typename T>

@@ -63,6 +63,48 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
 }
 
 // ---------------------------------------------------------------------------
+// Inverses of the unit lower triangular 32 x 32 diagonal blocks of each
+// pivot block L11, computed once after the factorisation so that each step
+// of the blocked triangular sweeps is a dependency-free 32 x 32 product.
+// One warp per block: lane j forms column j of X = L_blk^-1 by forward
+// substitution, x_i = -sum_{k<i} L[i][k] x_k (x_j = 1, x_i = 0 for i < j).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_invert_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ blocks,
+                                                     int count) {
+  __shared__ T Ls[4][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * 4 + warp;
+  if (b >= count) return;
+  const int2 it = blocks[b];
+  const int s = it.x, kb = it.y;
+  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
+  const int bw = min(32, ncol - kb);
+  const T* Lb = N.L + P.sn_Loff[s];
+  for (int i = 0; i < 32; i++) {
+    const T v = (i < bw && lane < i) ? Lb[(int64_t)(kb + i) * ncp + kb + lane] : T(0);
+    Ls[warp][i][lane] = v;
+  }
+  __syncwarp();
+  T x[32];
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < i; k++) acc += Ls[warp][i][k] * x[k];
+    x[i] = (i == lane) ? T(1) : (i > lane ? -acc : T(0));
+  }
+  T* out = N.Linv + P.sn_Ioff[s] + (int64_t)(kb / 32) * 1024;
+#pragma unroll
+  for (int i = 0; i < 32; i++) out[i * 32 + lane] = x[i];
+}
+
+template <typename T>
+void launch_invert_diag(const DevPlan& P, const DevNum<T>& N, const int2* blocks, int count, cudaStream_t st) {
+  if (count > 0) k_invert_diag<T><<<(count + 3) / 4, 128, 0, st>>>(P, N, blocks, count);
+}
+
+// ---------------------------------------------------------------------------
 // forward: pivot block of supernode s (one CTA): pull the children's updates
 // that land on the pivot rows, then L11 y = t by 32-column blocks: warp 0
 // solves the 32 x 32 diagonal block with shuffles (its row of the block
@@ -70,7 +112,7 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
 // it (one 128-byte row segment per row, y of the block from shared memory).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(512) k_fwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_fwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
                                                    T* __restrict__ xp, const T* __restrict__ W, int nrhs) {
   __shared__ T ys[8][32];
   const int s = list[blockIdx.x];
@@ -89,33 +131,47 @@ __global__ void __launch_bounds__(512) k_fwd_diag(DevPlan P, DevNum<T> N, const 
   for (int kb = 0; kb < ncol; kb += 32) {
     const int bw = min(32, ncol - kb);
     if (warp == 0) {
+      // y_blk = L_blk^-1 t_blk with the inverted diagonal block (row lane)
       T lrow[32];
-      const T* rp = Lb + (int64_t)(kb + min(lane, bw - 1)) * ncp + kb;
+      const T* ip = N.Linv + P.sn_Ioff[s] + (int64_t)(kb / 32) * 1024 + lane * 32;
 #pragma unroll
-      for (int u = 0; u < 32; u++) lrow[u] = (u < bw) ? rp[u] : T(0);
+      for (int u = 0; u < 32; u++) lrow[u] = ip[u];
       for (int r = 0; r < nrhs; r++) {
         T* x = xp + r * P.dim + col0;
-        T v = lane < bw ? x[kb + lane] : T(0);
+        const T t = lane < bw ? x[kb + lane] : T(0);
+        T v = T(0);
 #pragma unroll
-        for (int u = 0; u < 32; u++) {
-          const T yu = __shfl_sync(0xffffffffu, v, u);
-          if (lane > u) v -= lrow[u] * yu;
-        }
+        for (int u = 0; u < 32; u++) v += lrow[u] * __shfl_sync(0xffffffffu, t, u);
         if (lane < bw) x[kb + lane] = v;
         ys[r][lane] = lane < bw ? v : T(0);
       }
     }
     __syncthreads();
-    for (int i = kb + bw + threadIdx.x; i < ncol; i += blockDim.x) {
-      const T* row = Lb + (int64_t)i * ncp + kb;
+    // rows below the block, 32 per warp: lane u reads column kb+u of each
+    // row (coalesced), and a butterfly reduce-scatter leaves row r's sum in
+    // lane r (31 shuffles per 32 rows)
+    const int nw = blockDim.x >> 5;
+    for (int i0 = kb + bw + warp * 32; i0 < ncol; i0 += nw * 32) {
       T lv[32];
 #pragma unroll
-      for (int u = 0; u < 32; u++) lv[u] = (u < bw) ? row[u] : T(0);
+      for (int rr = 0; rr < 32; rr++)
+        lv[rr] = (lane < bw && i0 + rr < ncol) ? Lb[(int64_t)(i0 + rr) * ncp + kb + lane] : T(0);
       for (int r = 0; r < nrhs; r++) {
-        T acc = T(0);
+        const T yu = ys[r][lane];
+        T v[32];
 #pragma unroll
-        for (int u = 0; u < 32; u++) acc += lv[u] * ys[r][u];
-        xp[r * P.dim + col0 + i] -= acc;
+        for (int rr = 0; rr < 32; rr++) v[rr] = lv[rr] * yu;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+          const bool upper = (lane & o) != 0;
+#pragma unroll
+          for (int k = 0; k < o; k++) {
+            const T send = upper ? v[k] : v[k + o];
+            const T recv = __shfl_xor_sync(0xffffffffu, send, o);
+            v[k] = (upper ? v[k + o] : v[k]) + recv;
+          }
+        }
+        if (i0 + lane < ncol) xp[r * P.dim + col0 + i0 + lane] -= v[0];
       }
     }
     __syncthreads();
@@ -214,19 +270,19 @@ __global__ void __launch_bounds__(512) k_bwd_diag(DevPlan P, DevNum<T> N, const 
     const int kb = bi * 32;
     const int bw = min(32, ncol - kb);
     if (warp == 0) {
-      T lcol[32];   // lcol[v] = L[kb+v][kb+lane]
+      // x_blk = L_blk^-T z_blk with the inverted diagonal block (column lane)
+      T lcol[32];
+      const T* ip = N.Linv + P.sn_Ioff[s] + (int64_t)(kb / 32) * 1024 + lane;
 #pragma unroll
-      for (int v = 0; v < 32; v++) lcol[v] = (v < bw && lane < bw) ? Lb[(int64_t)(kb + v) * ncp + kb + lane] : T(0);
+      for (int v = 0; v < 32; v++) lcol[v] = ip[v * 32];
       for (int r = 0; r < nrhs; r++) {
         T* x = xp + r * P.dim + col0;
-        T v = lane < bw ? x[kb + lane] : T(0);
+        const T z = lane < bw ? x[kb + lane] : T(0);
+        T acc = T(0);
 #pragma unroll
-        for (int u = 31; u >= 0; u--) {
-          const T xu = __shfl_sync(0xffffffffu, v, u);
-          if (lane < u) v -= lcol[u] * xu;
-        }
-        if (lane < bw) x[kb + lane] = v;
-        xs[r][lane] = lane < bw ? v : T(0);
+        for (int v = 0; v < 32; v++) acc += lcol[v] * __shfl_sync(0xffffffffu, z, v);
+        if (lane < bw) x[kb + lane] = acc;
+        xs[r][lane] = lane < bw ? acc : T(0);
       }
     }
     __syncthreads();
@@ -248,7 +304,7 @@ __global__ void __launch_bounds__(512) k_bwd_diag(DevPlan P, DevNum<T> N, const 
 template <typename T>
 void launch_fwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp, T* W, int nrhs,
                      cudaStream_t st) {
-  if (count > 0) k_fwd_diag<T><<<count, 512, 0, st>>>(P, N, list, xp, W, nrhs);
+  if (count > 0) k_fwd_diag<T><<<count, sizeof(T) == 4 ? 512 : 256, 0, st>>>(P, N, list, xp, W, nrhs);
 }
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, T* xp, T* W, int nrhs,
@@ -447,6 +503,7 @@ void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64
 }
 
 #define NCL_INST(T)                                                                                               \
+  template void launch_invert_diag<T>(const DevPlan&, const DevNum<T>&, const int2*, int, cudaStream_t);          \
   template void launch_perm_in<T>(const DevPlan&, T*, const double*, int64_t, int, cudaStream_t);                 \
   template void launch_perm_out<T>(const DevPlan&, const T*, double*, int64_t, int, int, cudaStream_t);           \
   template void launch_fwd_diag<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, T*, T*, int,            \

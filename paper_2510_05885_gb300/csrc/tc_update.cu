@@ -19,6 +19,7 @@
 // is bounded: on a timeout the kernel sets an error flag, skips the update,
 // frees its TMEM and returns.
 #include "runtime.h"
+#include "diag32.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -36,6 +37,7 @@ constexpr int TC_STAGES = 3;
 constexpr int TC_TILE_BYTES = TC_M * TC_BK * 4;          // 16 KB
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A_hi, A_lo, B_hi, B_lo
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+constexpr int tc_smem_for(int stages) { return stages * TC_STAGE_BYTES + 1024 + 256; }
 constexpr uint32_t TC_TMEM_COLS = 128;
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;       // about 2 s at 2 GHz
 
@@ -154,13 +156,13 @@ __device__ __forceinline__ void decode_lower_tile(int64_t t, int Nt, int& ti, in
   }
 }
 
-__global__ void __launch_bounds__(128, 1) k_update_tc(float* __restrict__ Lbase, float* __restrict__ Ubase,
-                                                      const TcProb* __restrict__ probs, int nprob,
-                                                      const CUtensorMap* __restrict__ maps, int* err) {
+__global__ void __launch_bounds__(128) k_update_tc(DevPlan P, DevNum<float> Nm, const TcProb* __restrict__ probs,
+                                                   int nprob, const CUtensorMap* __restrict__ maps, int* err,
+                                                   int stages, double eps, int policy) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment of the shared-window address (the swizzle atom)
   unsigned char* sb = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sb + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sb + stages * TC_STAGE_BYTES);
   uint64_t* empty = full + TC_STAGES;
   uint64_t* done = empty + TC_STAGES;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(float* __restrict__ Lbase,
 
   if (tid == 0) {
     s_fail = 0;
-    for (int s = 0; s < TC_STAGES; s++) {
+    for (int s = 0; s < stages; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -205,8 +207,8 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(float* __restrict__ Lbase,
   if (warp == 0 && lane == 0) {
     // TMA producer
     for (int kt = 0; kt < nk; kt++) {
-      const int s = kt % TC_STAGES;
-      if (kt >= TC_STAGES && !mbar_wait_bounded(&empty[s], ((kt / TC_STAGES) - 1) & 1)) {
+      const int s = kt % stages;
+      if (kt >= stages && !mbar_wait_bounded(&empty[s], ((kt / stages) - 1) & 1)) {
         s_fail = 1;
         break;
       }
@@ -222,8 +224,8 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(float* __restrict__ Lbase,
     // MMA issuer
     int kt = 0;
     for (; kt < nk; kt++) {
-      const int s = kt % TC_STAGES;
-      if (!mbar_wait_bounded(&full[s], (kt / TC_STAGES) & 1)) {
+      const int s = kt % stages;
+      if (!mbar_wait_bounded(&full[s], (kt / stages) & 1)) {
         s_fail = 1;
         break;
       }
@@ -246,25 +248,49 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(float* __restrict__ Lbase,
   __syncwarp();
 
   // epilogue: lane (row) 32*warp + lane of the accumulator
-  const bool ok = mbar_wait_bounded(done, 0);
+  if (!mbar_wait_bounded(done, 0)) s_fail = 1;
   tc_fence_after();
   __syncthreads();
-  if (!ok || s_fail) {
+  if (s_fail) {
     if (tid == 0) atomicExch(err, 1);
   } else {
-    const int i = i0 + warp * 32 + lane;
-    float* C = (pb.c_in_u ? Ubase : Lbase) + pb.c_off;
+    // accumulator rows 32*warp .. 32*warp+31 are this warp's TMEM lanes;
+    // each 32 x 32 chunk goes through shared memory (the operand stages are
+    // free now) so that every global access of the update is one coalesced
+    // 128-byte row segment
+    float* C = (pb.c_in_u ? Nm.U : Nm.L) + pb.c_off;
+    float* stg = reinterpret_cast<float*>(sb) + warp * (32 * 33);
+    const int ib = i0 + warp * 32;
 #pragma unroll 1
     for (int c = 0; c < TC_N / 32; c++) {
       float v[32];
       tmem_ld_32x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
       const int jb = j0 + c * 32;
-      if (i < pb.M && jb < pb.N && jb <= i) {
-        float* crow = C + (int64_t)i * pb.ldc + jb;
 #pragma unroll
-        for (int t = 0; t < 32; t++)
-          if (jb + t < pb.N && jb + t <= i) crow[t] -= v[t];
+      for (int t = 0; t < 32; t++) stg[lane * 33 + t] = v[t];
+      __syncwarp();
+      const int j = jb + lane;
+      if (jb < pb.N && jb <= ib + 31 && ib < pb.M) {
+        // all 32 row loads first, then the updates: one memory latency per chunk
+        float cv[32];
+#pragma unroll
+        for (int rr = 0; rr < 32; rr++) {
+          const int i = ib + rr;
+          cv[rr] = (i < pb.M && j < pb.N && j <= i) ? C[(int64_t)i * pb.ldc + j] : 0.f;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 32; rr++) {
+          const int i = ib + rr;
+          if (i < pb.M && j < pb.N && j <= i) C[(int64_t)i * pb.ldc + j] = cv[rr] - stg[rr * 33 + lane];
+        }
       }
+      __syncwarp();
+    }
+    // tile (0,0) of a trailing update holds the next panel's diagonal
+    // block, now fully updated: factor it here
+    if (gt == pb.tile0 && pb.next_p0 >= 0) {
+      __syncthreads();
+      if (warp == 0) factor_diag32<float>(P, Nm, pb.front, pb.next_p0, eps, policy, lane);
     }
   }
   tc_fence_before();
@@ -334,15 +360,16 @@ int64_t tc_tiles(int M, int N, int* Nt_out) {
   return (int64_t)Nt * (Nt + 1) / 2 + (int64_t)(Mt - Nt) * Nt;
 }
 
-void launch_update_tc(float* L, float* U, const TcProb* probs, int nprob, int64_t ntiles, const CUtensorMap* maps,
-                      int* err, cudaStream_t st) {
+void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, int nprob, int64_t ntiles,
+                      int stages, const CUtensorMap* maps, int* err, double eps, int policy, cudaStream_t st) {
   if (ntiles <= 0) return;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     attr = true;
   }
-  k_update_tc<<<(unsigned)ntiles, 128, TC_SMEM, st>>>(L, U, probs, nprob, maps, err);
+  stages = stages < 1 ? 1 : (stages > TC_STAGES ? TC_STAGES : stages);
+  k_update_tc<<<(unsigned)ntiles, 128, tc_smem_for(stages), st>>>(P, N, probs, nprob, maps, err, stages, eps, policy);
 }
 
 void launch_split_rows(const float* L, const float* d, int rows, int ld, int K, float* S, cudaStream_t st) {
