@@ -103,6 +103,11 @@ typedef struct {
     int32_t leaf_size;        /* nested-dissection leaf size (default 96) */
     int32_t host_only;        /* 1: symbolic analysis only, no device memory; the
                                  handle then answers only the get_* queries */
+    int32_t precision_fallback; /* FP32_IR: 1 (default) refactor the same FP64 values in
+                                 FP64 when the FP32 factor cannot be trusted (an
+                                 inertia other than (n,m,0) / (n,0,0), which FP32
+                                 produces when rho*||J||^2 swamps H+Sigma+delta I) or
+                                 when refinement cannot reach ir_tol; 0: never */
     int64_t max_device_bytes; /* 0 = no limit */
 } ncl_kkt_options;
 
@@ -113,6 +118,7 @@ typedef struct {
     double flops;                  /* sum_j (c_j^2 + 3 c_j), c_j = nnz of column j of L
                                       below the diagonal */
     float ms;                      /* device time of the call */
+    int32_t fp64_fallback;         /* 1 if the factors in use are the FP64 refactorisation */
 } ncl_kkt_factor_info;
 
 typedef struct {
@@ -120,6 +126,7 @@ typedef struct {
     int32_t used_fgmres;           /* 1 if the FGMRES fallback ran */
     double backward_err;           /* final normwise backward error (max over RHS) */
     float ms;                      /* device time of the call */
+    int32_t fp64_fallback;         /* 1 if the FP64 refactorisation solved it */
 } ncl_kkt_solve_info;
 
 typedef struct {

@@ -165,6 +165,13 @@ struct ncl_kkt_s {
   double* jg = nullptr;
   double* GBtmp = nullptr;
   double* Jcopy = nullptr;                 // condensed form: J values of the last factor (adjoint)
+  // FGMRES refinement workspace (allocated on first use)
+  double* gm_V = nullptr;                  // (GM_M + 1) x dim Krylov basis
+  double* gm_Z = nullptr;                  // GM_M x dim preconditioned directions
+  double* gm_w = nullptr;
+  double* gm_part = nullptr;               // (GM_M + 1) x vec_grid() partial sums
+  double* gm_coef = nullptr;
+  double* gm_host = nullptr;               // pinned mirror of gm_part
   const double** d_valptr = nullptr;       // {H, J, Sigma} pointers of the current factor call
   CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
   TcProb* d_tc = nullptr;
@@ -177,6 +184,18 @@ struct ncl_kkt_s {
   cudaGraphExec_t sgraph[9] = {};
   int factor_calls = 0;
   int sweep_calls[9] = {};
+  bool capturing = false;
+  // FP64 twin used when the FP32 factor cannot be trusted (built on first use)
+  ncl_kkt_s* twin = nullptr;
+  bool use_twin = false;
+  bool skip_values = false;     // a twin factors the FP64 values copied from its parent
+  // one graph for factor + solve + refinement (batch_factor_solve)
+  cudaGraphExec_t fsgraph = nullptr;
+  int64_t fsgraph_nodes = 0;
+  int fs_calls = 0;
+  int fs_nir = 0;
+  const void* fs_key[2] = {nullptr, nullptr};
+  int64_t fs_keyi[3] = {0, 0, 0};
   int64_t fgraph_nodes = 0;
   int64_t sgraph_nodes[9] = {};
   bool factored = false;
@@ -218,10 +237,13 @@ struct ncl_kkt_s {
     cudaSetDevice(device);
     for (void* p : allocs) cudaFree(p);
     if (h_pinned) cudaFreeHost(h_pinned);
+    if (gm_host) cudaFreeHost(gm_host);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     if (fgraph) cudaGraphExecDestroy(fgraph);
+    if (fsgraph) cudaGraphExecDestroy(fsgraph);
+    delete twin;
     for (auto& g : sgraph)
       if (g) cudaGraphExecDestroy(g);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -690,7 +712,7 @@ Cost scaled(Cost c, double f) {
 template <typename F>
 void run_graphed(ncl_kkt_s* h, cudaGraphExec_t* exec, int64_t* nodes, int* calls, bool allow, cudaStream_t st,
                  F&& body) {
-  if (!allow || h->prof_on) {
+  if (!allow || h->prof_on || h->capturing) {
     body(st);
     return;
   }
@@ -699,7 +721,9 @@ void run_graphed(ncl_kkt_s* h, cudaGraphExec_t* exec, int64_t* nodes, int* calls
     cudaGraph_t g = nullptr;
     const int64_t l0 = g_kernel_launches.load();
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
     body(h->cap_stream);
+    h->capturing = false;
     CK(cudaStreamEndCapture(h->cap_stream, &g));
     *nodes = g_kernel_launches.load() - l0;
     g_kernel_launches.fetch_sub(*nodes);
@@ -806,12 +830,15 @@ void apply_inverse(ncl_kkt_s* h, const double* B, int64_t ldb, double* X, int64_
 }
 
 // backward error per (instance, rhs) from the norm slots; returns the max
-double backward_errors(ncl_kkt_s* h, int nrhs, cudaStream_t st, std::vector<double>* per = nullptr) {
+double backward_errors(ncl_kkt_s* h, int nrhs, cudaStream_t st, std::vector<double>* per = nullptr,
+                       const unsigned long long* copied = nullptr) {
   const int ni = h->dp.ninst;
   const size_t cnt = 3 * (size_t)ni * MAX_RHS_SWEEP;
-  CK(cudaMemcpyAsync(h->h_pinned, h->d_norms, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  const unsigned long long* u = reinterpret_cast<const unsigned long long*>(h->h_pinned);
+  if (!copied) {
+    CK(cudaMemcpyAsync(h->h_pinned, h->d_norms, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  const unsigned long long* u = copied ? copied : reinterpret_cast<const unsigned long long*>(h->h_pinned);
   auto as_d = [](unsigned long long v) {
     double d;
     std::memcpy(&d, &v, 8);
@@ -847,6 +874,126 @@ double residual_eta(ncl_kkt_s* h, const double* B, int64_t ldb, const double* X,
   return backward_errors(h, nrhs, st);
 }
 
+// ---------------------------------------------------------------------------
+// FGMRES(m)-IR (right preconditioned, flexible GMRES in FP64 with the
+// low-precision LDL^T as the preconditioner), for one right-hand side of a
+// single-instance handle; used when Richardson refinement stagnates.
+// ---------------------------------------------------------------------------
+constexpr int GM_M = 20;
+constexpr int GM_RESTARTS = 6;
+
+// sums of the per-block partial dot products, in block order
+void gm_dots(ncl_kkt_s* h, const double* V, int64_t ldv, int nv, const double* w, double* out, cudaStream_t st) {
+  const int G = vec_grid();
+  launch_multidot(h->dp.dim, V, ldv, nv, w, h->gm_part, st);
+  CK(cudaMemcpyAsync(h->gm_host, h->gm_part, sizeof(double) * G * nv, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < nv; i++) {
+    double acc = 0.0;
+    for (int b = 0; b < G; b++) acc += h->gm_host[i * G + b];
+    out[i] = acc;
+  }
+}
+
+void gm_axpy(ncl_kkt_s* h, const double* V, int64_t ldv, int nv, const double* c_host, double a, double* w,
+             cudaStream_t st) {
+  double* hc = h->gm_host + (GM_M + 1) * vec_grid();
+  for (int i = 0; i < nv; i++) hc[i] = c_host[i];
+  CK(cudaMemcpyAsync(h->gm_coef, hc, sizeof(double) * nv, cudaMemcpyHostToDevice, st));
+  launch_multi_axpy(h->dp.dim, V, ldv, nv, h->gm_coef, a, w, st);
+  CK(cudaStreamSynchronize(st));   // the pinned coefficients are reused
+}
+
+double residual_eta(ncl_kkt_s* h, const double* B, int64_t ldb, const double* X, int64_t ldx, int nrhs,
+                    cudaStream_t st);
+
+// refine column x (device) of b; returns the final backward error
+double fgmres_column(ncl_kkt_s* h, const double* b, double* x, cudaStream_t st, int* iters) {
+  const int64_t dim = h->dp.dim;
+  if (!h->gm_V) {
+    h->gm_V = h->alloc<double>((GM_M + 1) * dim);
+    h->gm_Z = h->alloc<double>(GM_M * dim);
+    h->gm_w = h->alloc<double>(dim);
+    h->gm_part = h->alloc<double>((GM_M + 1) * (int64_t)vec_grid());
+    h->gm_coef = h->alloc<double>(GM_M + 1);
+    CK(cudaMallocHost(&h->gm_host, sizeof(double) * ((GM_M + 1) * vec_grid() + GM_M + 8)));
+  }
+  const int ni = h->dp.ninst;
+  CK(cudaMemsetAsync(h->d_norms + 2 * ni * MAX_RHS_SWEEP, 0, (size_t)ni * MAX_RHS_SWEEP * 8, st));
+  launch_vec_norm(h->dp, b, dim, 1, h->d_norms + 2 * ni * MAX_RHS_SWEEP, st);
+  double eta = residual_eta(h, b, dim, x, dim, 1, st);   // h->R = b - K x
+  for (int rs = 0; rs < GM_RESTARTS && eta > h->opt.ir_tol && std::isfinite(eta); rs++) {
+    const unsigned long long* u = reinterpret_cast<const unsigned long long*>(h->h_pinned);
+    double xn, bn;
+    std::memcpy(&xn, &u[MAX_RHS_SWEEP * h->dp.ninst], 8);
+    std::memcpy(&bn, &u[2 * MAX_RHS_SWEEP * h->dp.ninst], 8);
+    const double target = 0.5 * h->opt.ir_tol * (h->knorm_host[0] * xn + bn);
+    double beta;
+    gm_dots(h, h->R, dim, 1, h->R, &beta, st);
+    beta = std::sqrt(beta);
+    if (!(beta > 0)) break;
+    const double inv = 1.0 / beta;
+    gm_axpy(h, h->R, dim, 1, &inv, 0.0, h->gm_V, st);
+    std::vector<double> H((GM_M + 1) * GM_M, 0.0), g(GM_M + 1, 0.0), cs(GM_M), sn(GM_M);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < GM_M; j++) {
+      double* Vj = h->gm_V + j * dim;
+      double* Zj = h->gm_Z + j * dim;
+      apply_inverse(h, Vj, dim, Zj, dim, 1, 0, st);
+      launch_spmv(h->dp, h->Klow, Zj, h->gm_w, st);
+      // classical Gram-Schmidt, twice
+      for (int pass = 0; pass < 2; pass++) {
+        double hc[GM_M + 1], nc[GM_M + 1];
+        gm_dots(h, h->gm_V, dim, j + 1, h->gm_w, hc, st);
+        for (int i = 0; i <= j; i++) {
+          H[i * GM_M + j] += hc[i];
+          nc[i] = -hc[i];
+        }
+        gm_axpy(h, h->gm_V, dim, j + 1, nc, 1.0, h->gm_w, st);
+      }
+      double hn;
+      gm_dots(h, h->gm_w, dim, 1, h->gm_w, &hn, st);
+      hn = std::sqrt(hn);
+      H[(j + 1) * GM_M + j] = hn;
+      if (hn > 0) {
+        const double ih = 1.0 / hn;
+        gm_axpy(h, h->gm_w, dim, 1, &ih, 0.0, h->gm_V + (j + 1) * dim, st);
+      }
+      // Givens rotations on column j of the Hessenberg matrix
+      for (int i = 0; i < j; i++) {
+        const double a = H[i * GM_M + j], c = H[(i + 1) * GM_M + j];
+        H[i * GM_M + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * GM_M + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[j * GM_M + j], c = H[(j + 1) * GM_M + j];
+      const double r = std::hypot(a, c);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? c / r : 0.0;
+      H[j * GM_M + j] = r;
+      H[(j + 1) * GM_M + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      (*iters)++;
+      if (std::fabs(g[j + 1]) <= target || !(hn > 0)) break;
+    }
+    // y = H^-1 g (upper triangular), x += Z y
+    std::vector<double> y(k, 0.0);
+    for (int i = k - 1; i >= 0; i--) {
+      double acc = g[i];
+      for (int t = i + 1; t < k; t++) acc -= H[i * GM_M + t] * y[t];
+      y[i] = H[i * GM_M + i] != 0 ? acc / H[i * GM_M + i] : 0.0;
+    }
+    gm_axpy(h, h->gm_Z, dim, k, y.data(), 1.0, x, st);
+    eta = residual_eta(h, b, dim, x, dim, 1, st);
+  }
+  return eta;
+}
+
+ncl_status refine_block(ncl_kkt_s* h, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                        cudaStream_t st, ncl_kkt_solve_info* info, double eta, int it);
+
 // solve nrhs <= MAX_RHS_SWEEP columns with Richardson refinement
 ncl_status solve_block(ncl_kkt_s* h, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
                        cudaStream_t st, ncl_kkt_solve_info* info) {
@@ -855,25 +1002,50 @@ ncl_status solve_block(ncl_kkt_s* h, int nrhs, const double* B, int64_t ldb, dou
   klaunch(h, st, "vec_norm", h->dp.dim, Cost{0, 8.0 * h->dp.dim * nrhs},
           [&] { launch_vec_norm(h->dp, B, ldb, nrhs, h->d_norms + 2 * ni * MAX_RHS_SWEEP, st); });
   apply_inverse(h, B, ldb, X, ldx, nrhs, 0, st);
-  double eta = residual_eta(h, B, ldb, X, ldx, nrhs, st);
-  int it = 0;
+  const double eta0 = residual_eta(h, B, ldb, X, ldx, nrhs, st);
+  return refine_block(h, nrhs, B, ldb, X, ldx, st, info, eta0, 0);
+}
+
+// Richardson refinement from the current X (h->R holds B - K X and eta its
+// backward error), FGMRES when it stagnates
+ncl_status refine_block(ncl_kkt_s* h, int nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                        cudaStream_t st, ncl_kkt_solve_info* info, double eta, int it) {
   const int maxit = h->opt.ir_max_iter;
+  bool stagnated = false;
   while (eta > h->opt.ir_tol && it < maxit && std::isfinite(eta)) {
     apply_inverse(h, h->R, h->dp.dim, X, ldx, nrhs, 1, st);
     it++;
+    const double prev = eta;
     eta = residual_eta(h, B, ldb, X, ldx, nrhs, st);
+    if (eta > 0.5 * prev && h->opt.use_fgmres && h->dp.ninst == 1) {
+      stagnated = true;   // Richardson stagnates (kappa * u_factor is not small): switch to FGMRES
+      break;
+    }
+  }
+  bool used_gm = false;
+  if (eta > h->opt.ir_tol && std::isfinite(eta) && h->opt.use_fgmres && h->dp.ninst == 1 &&
+      (stagnated || it >= maxit)) {
+    used_gm = true;
+    eta = 0.0;
+    for (int r = 0; r < nrhs; r++)
+      eta = std::max(eta, fgmres_column(h, B + r * ldb, X + r * ldx, st, &it));
   }
   if (info) {
     info->ir_iters = std::max(info->ir_iters, it);
     info->backward_err = std::max(info->backward_err, eta);
+    if (used_gm) info->used_fgmres = 1;
   }
   if (!std::isfinite(eta)) return fail(NCL_ERR_NUMERIC, "non-finite residual or solution");
   if (eta > h->opt.ir_tol) return NCL_ERR_IR_NOT_CONVERGED;
   return NCL_OK;
 }
 
-ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
-                     const double* rho, cudaStream_t st, ncl_kkt_factor_info* infos) {
+ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                    cudaStream_t st, ncl_kkt_solve_info* info, bool allow_escalate = true);
+
+// validate and stage the scalars and value pointers of a factor call
+ncl_status prepare_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
+                          const double* rho, cudaStream_t st) {
   const int ni = h->dp.ninst;
   for (int i = 0; i < ni; i++) {
     if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(NCL_ERR_INVALID_ARG, "rho must be positive and finite");
@@ -897,29 +1069,40 @@ ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const dou
   CK(cudaMemcpyAsync(h->d_valptr, vp, 3 * sizeof(double*), cudaMemcpyHostToDevice, st));
   if (h->Jcopy && h->dp.nnzJ)
     CK(cudaMemcpyAsync(h->Jcopy, Jv, h->dp.nnzJ * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  auto body = [&](cudaStream_t s2) {
-    {
-      const double np = (double)h->plan.pair_p.size();
-      klaunch(h, s2, "kkt_values_f64", h->dp.nnzA,
-              Cost{2.0 * np, 33.0 * h->dp.nnzA + 24.0 * np + 8.0 * (h->dp.nnzH + h->dp.nnzJ + h->dp.nvar)},
-              [&] { launch_kkt_values(h->dp, h->d_valptr, h->d_delta, h->d_rho, h->Klow, s2); });
-    }
-    CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), s2));
-    klaunch(h, s2, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
-            [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, s2); });
-    CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), s2));
-    CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s2));
-    if (is_fp32(h)) {
-      run_factor<float>(h, h->nf, s2);
-      klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},
-              [&] { launch_inertia<float>(h->dp, h->nf, h->d_counts, s2); });
-    } else {
-      run_factor<double>(h, h->nd, s2);
-      klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 9.0 * h->dp.dim},
-              [&] { launch_inertia<double>(h->dp, h->nd, h->d_counts, s2); });
-    }
-  };
-  run_graphed(h, &h->fgraph, &h->fgraph_nodes, &h->factor_calls, true, st, body);
+  h->h_delta.assign(delta, delta + ni);
+  h->h_rho.assign(rho, rho + ni);
+  return NCL_OK;
+}
+
+// all device work of a factorisation, on stream s2 (capturable)
+void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
+  const int ni = h->dp.ninst;
+  if (!h->skip_values) {
+    const double np = (double)h->plan.pair_p.size();
+    klaunch(h, s2, "kkt_values_f64", h->dp.nnzA,
+            Cost{2.0 * np, 33.0 * h->dp.nnzA + 24.0 * np + 8.0 * (h->dp.nnzH + h->dp.nnzJ + h->dp.nvar)},
+            [&] { launch_kkt_values(h->dp, h->d_valptr, h->d_delta, h->d_rho, h->Klow, s2); });
+  }
+  CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), s2));
+  klaunch(h, s2, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
+          [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, s2); });
+  CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), s2));
+  CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s2));
+  if (is_fp32(h)) {
+    run_factor<float>(h, h->nf, s2);
+    klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},
+            [&] { launch_inertia<float>(h->dp, h->nf, h->d_counts, s2); });
+  } else {
+    run_factor<double>(h, h->nd, s2);
+    klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 9.0 * h->dp.dim},
+            [&] { launch_inertia<double>(h->dp, h->nd, h->d_counts, s2); });
+  }
+}
+
+// read back inertia, norms and the error flag; fill the infos
+ncl_status finish_factor(ncl_kkt_s* h, cudaStream_t st, ncl_kkt_factor_info* infos) {
+  const int ni = h->dp.ninst;
+  double* hp = h->h_pinned;
   CK(cudaGetLastError());
   CK(cudaEventRecord(h->ev1, st));
   long long* hc = reinterpret_cast<long long*>(hp + 2 * ni);
@@ -955,13 +1138,169 @@ ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const dou
       stt = fail(NCL_ERR_ZERO_PIVOT, "zero pivot under the stop policy");
   }
   h->factored = (stt == NCL_OK || stt == NCL_ERR_ZERO_PIVOT);
-  h->h_delta.assign(delta, delta + ni);
-  h->h_rho.assign(rho, rho + ni);
   return stt;
 }
 
+void build_schedule(ncl_kkt_s* h);
+void build_device(ncl_kkt_s* h);
+
+// does the factor's inertia match the form's regular one for every instance?
+bool inertia_regular(ncl_kkt_s* h) {
+  const int ni = h->dp.ninst;
+  const long long* hc = reinterpret_cast<const long long*>(h->h_pinned + 2 * ni);
+  for (int i = 0; i < ni; i++) {
+    const Instance& I = h->plan.inst[i];
+    const long long np = hc[4 * i], nn = hc[4 * i + 1], nz = hc[4 * i + 2];
+    const long long want_neg = h->plan.form == 0 ? I.m : 0;
+    if (np != I.n || nn != want_neg || nz != 0) return false;
+  }
+  return true;
+}
+
+// refactor the parent's FP64 values in FP64 on the twin handle
+ncl_status escalate(ncl_kkt_s* h, cudaStream_t st, ncl_kkt_factor_info* infos) {
+  if (!h->twin) {
+    std::unique_ptr<ncl_kkt_s> t(new ncl_kkt_s());
+    t->plan = h->plan;
+    t->opt = h->opt;
+    t->opt.prec = NCL_PREC_FP64;
+    t->opt.ir_tol = h->opt.ir_tol;
+    t->opt.precision_fallback = 0;
+    t->device = h->device;
+    t->ninst = h->ninst;
+    t->dp.ninst = h->dp.ninst;
+    t->skip_values = true;
+    build_schedule(t.get());
+    build_device(t.get());
+    h->twin = t.release();
+  }
+  ncl_kkt_s* t = h->twin;
+  const int ni = h->dp.ninst;
+  CK(cudaEventRecord(t->ev0, st));
+  CK(cudaMemcpyAsync(t->Klow, h->Klow, h->dp.nnzA * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(t->d_delta, h->d_delta, ni * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(t->d_rho, h->d_rho, ni * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (t->Jcopy && h->Jcopy && h->dp.nnzJ)
+    CK(cudaMemcpyAsync(t->Jcopy, h->Jcopy, h->dp.nnzJ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  t->h_delta = h->h_delta;
+  t->h_rho = h->h_rho;
+  run_graphed(t, &t->fgraph, &t->fgraph_nodes, &t->factor_calls, true, st,
+              [&](cudaStream_t s2) { enqueue_factor(t, s2); });
+  ncl_status s = finish_factor(t, st, infos);
+  if (infos)
+    for (int i = 0; i < ni; i++) infos[i].fp64_fallback = 1;
+  h->use_twin = t->factored;
+  return s;
+}
+
+ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
+                     const double* rho, cudaStream_t st, ncl_kkt_factor_info* infos) {
+  h->use_twin = false;
+  ncl_status s0 = prepare_factor(h, Hv, Jv, S, delta, rho, st);
+  if (s0 != NCL_OK) return s0;
+  run_graphed(h, &h->fgraph, &h->fgraph_nodes, &h->factor_calls, true, st,
+              [&](cudaStream_t s2) { enqueue_factor(h, s2); });
+  ncl_status s1 = finish_factor(h, st, infos);
+  if (infos)
+    for (int i = 0; i < h->dp.ninst; i++) infos[i].fp64_fallback = 0;
+  if (is_fp32(h) && h->opt.precision_fallback && (s1 == NCL_OK || s1 == NCL_ERR_NUMERIC) && !inertia_regular(h))
+    return escalate(h, st, infos);
+  return s1;
+}
+
+// factor + solve of nrhs <= 8 columns + a fixed number of refinement steps
+// as one captured graph (after a direct first call that learns how many
+// refinement steps the systems need); the host checks the backward error
+// afterwards and refines further only if needed
+ncl_status do_factor_solve(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
+                           const double* rho, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                           cudaStream_t st, ncl_kkt_factor_info* infos, ncl_kkt_solve_info* sinfo) {
+  const int ni = h->dp.ninst;
+  const bool same_key = h->fs_key[0] == B && h->fs_key[1] == X && h->fs_keyi[0] == ldb && h->fs_keyi[1] == ldx &&
+                        h->fs_keyi[2] == nrhs;
+  if (!same_key && h->fsgraph) {
+    cudaGraphExecDestroy(h->fsgraph);
+    h->fsgraph = nullptr;
+    h->fs_calls = 0;
+  }
+  h->fs_key[0] = B;
+  h->fs_key[1] = X;
+  h->fs_keyi[0] = ldb;
+  h->fs_keyi[1] = ldx;
+  h->fs_keyi[2] = nrhs;
+  if (h->fs_calls == 0 || h->prof_on) {
+    // direct: the regular calls, which also tell how many steps are needed
+    ncl_status s1 = do_factor(h, Hv, Jv, S, delta, rho, st, infos);
+    if (s1 != NCL_OK && s1 != NCL_ERR_ZERO_PIVOT) return s1;
+    ncl_status s2 = do_solve(h, nrhs, B, ldb, X, ldx, st, sinfo);
+    if (!h->prof_on) {
+      h->fs_calls = 1;
+      h->fs_nir = sinfo ? sinfo->ir_iters : h->opt.ir_max_iter;
+      if (sinfo && sinfo->used_fgmres) h->fs_nir = 0;
+    }
+    return s2 != NCL_OK ? s2 : s1;
+  }
+  ncl_status s0 = prepare_factor(h, Hv, Jv, S, delta, rho, st);
+  if (s0 != NCL_OK) return s0;
+  if (sinfo) *sinfo = ncl_kkt_solve_info{};
+  unsigned long long* hn = reinterpret_cast<unsigned long long*>(h->h_pinned + 7 * ni + 64);
+  const int nir = h->fs_nir;
+  auto body = [&](cudaStream_t s2) {
+    enqueue_factor(h, s2);
+    CK(cudaMemsetAsync(h->d_norms, 0, 3 * (size_t)ni * MAX_RHS_SWEEP * sizeof(unsigned long long), s2));
+    klaunch(h, s2, "vec_norm", h->dp.dim, Cost{0, 8.0 * h->dp.dim * nrhs},
+            [&] { launch_vec_norm(h->dp, B, ldb, nrhs, h->d_norms + 2 * ni * MAX_RHS_SWEEP, s2); });
+    apply_inverse(h, B, ldb, X, ldx, nrhs, 0, s2);
+    for (int k = 0; k <= nir; k++) {
+      CK(cudaMemsetAsync(h->d_norms, 0, 2 * (size_t)ni * MAX_RHS_SWEEP * sizeof(unsigned long long), s2));
+      const double nnzF = (double)h->plan.F_col.size();
+      klaunch(h, s2, "residual_f64", h->dp.dim, Cost{2.0 * nnzF * nrhs, nnzF * 16.0}, [&] {
+        launch_residual(h->dp, h->Klow, B, ldb, X, ldx, h->R, h->dp.dim, nrhs, h->d_norms,
+                        h->d_norms + ni * MAX_RHS_SWEEP, s2);
+      });
+      if (k < nir) apply_inverse(h, h->R, h->dp.dim, X, ldx, nrhs, 1, s2);
+    }
+    CK(cudaMemcpyAsync(hn, h->d_norms, 3 * (size_t)ni * MAX_RHS_SWEEP * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s2));
+  };
+  h->use_twin = false;
+  run_graphed(h, &h->fsgraph, &h->fsgraph_nodes, &h->fs_calls, true, st, body);
+  ncl_status sf = finish_factor(h, st, infos);
+  if (infos)
+    for (int i = 0; i < ni; i++) infos[i].fp64_fallback = 0;
+  if (is_fp32(h) && h->opt.precision_fallback && (sf == NCL_OK || sf == NCL_ERR_NUMERIC) && !inertia_regular(h)) {
+    ncl_status se = escalate(h, st, infos);
+    if (se != NCL_OK && se != NCL_ERR_ZERO_PIVOT) return se;
+    ncl_status s2 = do_solve(h, nrhs, B, ldb, X, ldx, st, sinfo);
+    return s2 != NCL_OK ? s2 : se;
+  }
+  if (sf != NCL_OK && sf != NCL_ERR_ZERO_PIVOT) return sf;
+  const double eta = backward_errors(h, nrhs, st, nullptr, hn);
+  ncl_status sr = NCL_OK;
+  if (!(eta <= h->opt.ir_tol)) sr = refine_block(h, nrhs, B, ldb, X, ldx, st, sinfo, eta, nir);
+  else if (sinfo) {
+    sinfo->ir_iters = nir;
+    sinfo->backward_err = eta;
+  }
+  if (sr == NCL_ERR_IR_NOT_CONVERGED && is_fp32(h) && h->opt.precision_fallback) {
+    ncl_status se = escalate(h, st, nullptr);
+    if (se != NCL_OK && se != NCL_ERR_ZERO_PIVOT) return se;
+    return do_solve(h, nrhs, B, ldb, X, ldx, st, sinfo);
+  }
+  CK(cudaEventRecord(h->ev1, st));
+  CK(cudaEventSynchronize(h->ev1));
+  if (sinfo) cudaEventElapsedTime(&sinfo->ms, h->ev0, h->ev1);
+  if (sr == NCL_ERR_IR_NOT_CONVERGED) g_last_error = "iterative refinement did not reach ir_tol";
+  return sr != NCL_OK ? sr : sf;
+}
+
 ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
-                    cudaStream_t st, ncl_kkt_solve_info* info) {
+                    cudaStream_t st, ncl_kkt_solve_info* info, bool allow_escalate) {
+  if (h->use_twin) {
+    ncl_status s = do_solve(h->twin, nrhs, B, ldb, X, ldx, st, info, false);
+    if (info) info->fp64_fallback = 1;
+    return s;
+  }
   if (!h->factored) return fail(NCL_ERR_STATE, "solve before a successful factor");
   if (nrhs < 0 || (nrhs > 0 && (!B || !X)) || ldb < h->dp.dim || ldx < h->dp.dim)
     return fail(NCL_ERR_INVALID_ARG, "bad right-hand side block");
@@ -977,6 +1316,12 @@ ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, do
   CK(cudaEventSynchronize(h->ev1));
   prof_collect(h);
   if (info) cudaEventElapsedTime(&info->ms, h->ev0, h->ev1);
+  if (worst == NCL_ERR_IR_NOT_CONVERGED && allow_escalate && is_fp32(h) && h->opt.precision_fallback) {
+    // the FP32 factors cannot reach the tolerance: refactor in FP64, solve again
+    ncl_status se = escalate(h, st, nullptr);
+    if (se != NCL_OK && se != NCL_ERR_ZERO_PIVOT) return se;
+    return do_solve(h, nrhs, B, ldb, X, ldx, st, info, false);
+  }
   if (worst == NCL_ERR_IR_NOT_CONVERGED) g_last_error = "iterative refinement did not reach ir_tol";
   return worst;
 }
@@ -1058,6 +1403,7 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->use_tensor_cores = 1;
   o->leaf_size = 96;
   o->host_only = 0;
+  o->precision_fallback = 1;
   o->max_device_bytes = 0;
 }
 
@@ -1122,10 +1468,20 @@ ncl_status ncl_kkt_batch_factor_solve(ncl_kkt_t h, const double* H_val, const do
                                       const double* delta, const double* rho, int32_t nrhs, const double* B,
                                       int64_t ldb, double* X, int64_t ldx, ncl_stream_t stream,
                                       ncl_kkt_factor_info* infos, ncl_kkt_solve_info* sinfo) {
-  ncl_status s = ncl_kkt_batch_factor(h, H_val, J_val, Sigma, delta, rho, stream, infos);
-  if (s != NCL_OK && s != NCL_ERR_ZERO_PIVOT) return s;
-  ncl_status s2 = ncl_kkt_solve(h, nrhs, B, ldb, X, ldx, stream, sinfo);
-  return s2 != NCL_OK ? s2 : s;
+  if (!h || !delta || !rho) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (nrhs <= 0 || !B || !X || ldb < h->dp.dim || ldx < h->dp.dim)
+    return fail(NCL_ERR_INVALID_ARG, "bad right-hand side block");
+  if (nrhs > MAX_RHS_SWEEP) {
+    ncl_status s = ncl_kkt_batch_factor(h, H_val, J_val, Sigma, delta, rho, stream, infos);
+    if (s != NCL_OK && s != NCL_ERR_ZERO_PIVOT) return s;
+    ncl_status s2 = ncl_kkt_solve(h, nrhs, B, ldb, X, ldx, stream, sinfo);
+    return s2 != NCL_OK ? s2 : s;
+  }
+  return guarded(h, [&] {
+    return do_factor_solve(h, H_val, J_val, Sigma, delta, rho, nrhs, B, ldb, X, ldx, (cudaStream_t)stream, infos,
+                           sinfo);
+  });
 }
 
 ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t ldx, const double* GX, int64_t ldgx,
@@ -1297,6 +1653,10 @@ extern "C" ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const dou
   if (nrhs <= 0) return fail(NCL_ERR_INVALID_ARG, "nrhs must be positive");
   return guarded(h, [&]() -> ncl_status {
     if (h->prof_on) return fail(NCL_ERR_STATE, "turn profiling off before the no-alloc solve");
+    // the handle whose factors are in use (the FP64 twin after a precision
+    // fallback; it exists already, so nothing is allocated)
+    ncl_kkt_s* owner = h;
+    if (h->use_twin) h = h->twin;
     void* base = nullptr;
     ncl_status s = noalloc_base(h->device, &base);
     if (s != NCL_OK) return s;
@@ -1334,7 +1694,9 @@ extern "C" ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const dou
     h->Pw = p + b_xp + b_w;
     h->R = (double*)(p + b_xp + b_w + b_pw);
     h->d_norms = (unsigned long long*)(p + b_xp + b_w + b_pw + b_r);
-    return do_solve(h, nrhs, B, ldb, X, ldx, (cudaStream_t)stream, info);
+    ncl_status r = do_solve(h, nrhs, B, ldb, X, ldx, (cudaStream_t)stream, info, false);
+    if (info && h != owner) info->fp64_fallback = 1;
+    return r;
   });
 }
 

@@ -165,6 +165,12 @@ void launch_residual(const DevPlan& P, const double* Klow, const double* B, int6
                      unsigned long long* xnorm, cudaStream_t st);
 void launch_vec_norm(const DevPlan& P, const double* B, int64_t ldb, int nrhs, unsigned long long* out,
                      cudaStream_t st);
+void launch_spmv(const DevPlan& P, const double* Klow, const double* X, double* Y, cudaStream_t st);
+void launch_multidot(int64_t n, const double* V, int64_t ldv, int nv, const double* w, double* partial,
+                     cudaStream_t st);
+void launch_multi_axpy(int64_t n, const double* V, int64_t ldv, int nv, const double* c, double a, double* w,
+                       cudaStream_t st);
+int vec_grid();
 void launch_axpy_inplace(double* X, int64_t ldx, const double* Y, int64_t ldy, double a, int64_t dim,
                          int nrhs, cudaStream_t st);
 void launch_adjoint_values(const DevPlan& P, const double* Jv, const double* rho, const double* X,

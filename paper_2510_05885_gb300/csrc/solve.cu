@@ -387,6 +387,75 @@ void launch_axpy_inplace(double* X, int64_t ldx, const double* Y, int64_t ldy, d
 }
 
 // ---------------------------------------------------------------------------
+// FP64 vector kernels of the FGMRES refinement (single instance).
+// Reductions are two-pass with a fixed grid: per-block partial sums here,
+// summed on the host in block order (bitwise reproducible).
+// ---------------------------------------------------------------------------
+constexpr int VGRID = 256;
+
+// Y = K X (full FP64 CSR)
+__global__ void k_spmv(DevPlan P, const double* __restrict__ Klow, const double* __restrict__ X,
+                       double* __restrict__ Y) {
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t rb = gwarp * 4; rb < P.dim; rb += nwarp * 4) {
+    const int64_t row = rb + (lane >> 3);
+    const bool valid = row < P.dim;
+    const int64_t q0 = valid ? P.F_rowptr[row] : 0, q1 = valid ? P.F_rowptr[row + 1] : 0;
+    double acc = 0.0;
+    for (int64_t q = q0 + sub; q < q1; q += 8) acc = fma(Klow[P.F_src[q]], X[P.F_col[q]], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (valid && sub == 0) Y[row] = acc;
+  }
+}
+
+// partial[i * VGRID + block] = sum over the block's slice of V_i . w  (i < nv)
+__global__ void __launch_bounds__(256) k_multidot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
+                                                  const double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  for (int i = 0; i < nv; i++) {
+    double acc = 0.0;
+    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc = fma(V[i * ldv + e], w[e], acc);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[i * VGRID + blockIdx.x] = red[0];
+    __syncthreads();
+  }
+}
+
+// w = a * w + sum_i c[i] V_i   (c on the device)
+__global__ void k_multi_axpy(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
+                             const double* __restrict__ c, double a, double* __restrict__ w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = a != 0.0 ? a * w[e] : 0.0;
+    for (int i = 0; i < nv; i++) acc = fma(c[i], V[i * ldv + e], acc);
+    w[e] = acc;
+  }
+}
+
+void launch_spmv(const DevPlan& P, const double* Klow, const double* X, double* Y, cudaStream_t st) {
+  if (P.dim) k_spmv<<<grid_for(P.dim * 8), 256, 0, st>>>(P, Klow, X, Y);
+}
+void launch_multidot(int64_t n, const double* V, int64_t ldv, int nv, const double* w, double* partial,
+                     cudaStream_t st) {
+  if (nv > 0) k_multidot<<<VGRID, 256, 0, st>>>(n, V, ldv, nv, w, partial);
+}
+void launch_multi_axpy(int64_t n, const double* V, int64_t ldv, int nv, const double* c, double a, double* w,
+                       cudaStream_t st) {
+  k_multi_axpy<<<grid_for(n), 256, 0, st>>>(n, V, ldv, nv, c, a, w);
+}
+int vec_grid() { return VGRID; }
+
+// ---------------------------------------------------------------------------
 // Adjoint: dl/dK = -GB X^T folded onto the stored values (see ncl_kkt.h).
 // ---------------------------------------------------------------------------
 __global__ void k_adj_H(DevPlan P, const double* X, int64_t ldx, const double* GB, int64_t ldgb, int nrhs,

@@ -29,13 +29,14 @@ class Options(ctypes.Structure):
                 ("pivot_eps", ctypes.c_double), ("ir_tol", ctypes.c_double),
                 ("ir_max_iter", ctypes.c_int32), ("use_fgmres", ctypes.c_int32),
                 ("use_tensor_cores", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
-                ("host_only", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64)]
+                ("host_only", ctypes.c_int32), ("precision_fallback", ctypes.c_int32),
+                ("max_device_bytes", ctypes.c_int64)]
 
 
 class FactorInfo(ctypes.Structure):
     _fields_ = [("n_pos", ctypes.c_int64), ("n_neg", ctypes.c_int64), ("n_zero", ctypes.c_int64),
                 ("n_perturbed", ctypes.c_int64), ("nnz_L", ctypes.c_int64),
-                ("flops", ctypes.c_double), ("ms", ctypes.c_float)]
+                ("flops", ctypes.c_double), ("ms", ctypes.c_float), ("fp64_fallback", ctypes.c_int32)]
 
     @property
     def inertia(self):
@@ -47,7 +48,7 @@ class FactorInfo(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("ir_iters", ctypes.c_int32), ("used_fgmres", ctypes.c_int32),
-                ("backward_err", ctypes.c_double), ("ms", ctypes.c_float)]
+                ("backward_err", ctypes.c_double), ("ms", ctypes.c_float), ("fp64_fallback", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -249,3 +249,74 @@ def test_condensed_300x300_full_size(prec, rho, eta_tol):
     Ar = sp.csr_matrix(A)[rows]
     scale = np.abs(Ar).sum(axis=1).A1 * np.max(np.abs(X)) + np.abs(inst.b[rows, 0])
     assert np.all(np.abs(Ar @ X[:, 0] - inst.b[rows, 0]) <= eta_tol * scale)
+
+
+# ------------------------------------------------------------------ refinement beyond Richardson
+
+@pytest.mark.parametrize("side", [24, 40])
+def test_condensed_rho_1e7_needs_fgmres(side):
+    """rho = 1e7: kappa(K) ~ 3e8, kappa * u_fp32 > 1, so Richardson
+    refinement of the FP32 factorisation stagnates; the FGMRES fallback (FP64
+    Krylov vectors, FP32 LDL^T preconditioner) reaches 1e-10."""
+    inst = synth.condensed_grid(side, rho=1e7, draw=0)
+    K, finfo, X, sinfo = gpu_solve(inst, "fp32_ir")
+    assert finfo.inertia == (inst.n, 0, 0) and finfo.fp64_fallback == 0
+    assert sinfo.status == 0 and sinfo.used_fgmres == 1 and sinfo.fp64_fallback == 0
+    A = O.instance_matrix(inst)
+    assert O.backward_error(A, X, inst.b) <= 1e-10
+
+
+@pytest.mark.parametrize("form", ["condensed", "stabilized"])
+def test_rho_1e8_fp32_falls_back_to_fp64(form):
+    """rho = 1e8: in FP32 the O(1) part H + Sigma + delta I is lost against
+    rho J^T J (kappa ~ 3e9 > 1/u_fp32), and the FP32 pivots' signs are not
+    those of the matrix.  The FP32+IR handle detects the irregular inertia
+    and refactors the same FP64 values in FP64; without that fallback it
+    reports that refinement did not converge."""
+    if form == "condensed":
+        inst = synth.condensed_grid(24, rho=1e8, draw=0)
+    else:
+        inst = synth.random_instance(24, 24, seed=3, form="stabilized", rho=1e8)
+    want = (inst.n, inst.m, 0) if form == "stabilized" else (inst.n, 0, 0)
+    A = O.instance_matrix(inst)
+    K, finfo, X, sinfo = gpu_solve(inst, "fp32_ir")
+    assert finfo.fp64_fallback == 1 and finfo.inertia == want
+    assert sinfo.status == 0 and sinfo.fp64_fallback == 1
+    assert O.backward_error(A, X, inst.b) <= 1e-10     # the FP32+IR handle's target
+    K0, f0, X0, s0 = gpu_solve(inst, "fp32_ir", precision_fallback=0)
+    assert f0.fp64_fallback == 0 and f0.inertia != want
+    assert s0.status == 8
+    K64, f64, X64, s64 = gpu_solve(inst, "fp64")
+    assert f64.inertia == want
+    assert O.backward_error(A, X64, inst.b) <= 1e-12
+
+
+def test_batch_factor_solve_graph_replay():
+    """The one-graph factor + solve of a batch, replayed with new values on
+    the same patterns and buffers, against the oracle every time."""
+    rng = np.random.default_rng(5)
+    pats = [synth.make_pattern(10, 12, np.sort(rng.choice(len(synth.grid_edges(10, 12)), k, replace=False)))
+            for k in (1, 2, 3)]
+    K = nk().KKT.batch(0, [(p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind) for p in pats],
+                       prec="fp32_ir")
+    dim = K.dim
+    Hv = torch.empty(sum(p.nnz_H for p in pats), dtype=torch.float64, device=DEV)
+    Jv = torch.empty(sum(p.nnz_J for p in pats), dtype=torch.float64, device=DEV)
+    S = torch.empty(sum(p.n for p in pats), dtype=torch.float64, device=DEV)
+    Bc = torch.empty(3, dim, dtype=torch.float64, device=DEV)
+    Xc = torch.empty_like(Bc)
+    for draw in range(4):
+        insts = [synth.draw_instance(p, np.random.default_rng(100 * draw + i), form="stabilized", rho=1e4, nrhs=3)
+                 for i, p in enumerate(pats)]
+        Hv.copy_(_t(np.concatenate([i.H_val for i in insts])))
+        Jv.copy_(_t(np.concatenate([i.J_val for i in insts])))
+        S.copy_(_t(np.concatenate([i.Sigma for i in insts])))
+        Bc.copy_(_t(np.concatenate([i.b for i in insts], axis=0).T))
+        infos, sinfo = nk().ncl_kkt_batch_factor_solve(K._h, Hv, Jv, S, [i.delta for i in insts],
+                                                       [i.rho for i in insts], 3, Bc, dim, Xc, dim)
+        X = Xc.cpu().numpy().T
+        off = 0
+        for inst, fi in zip(insts, infos):
+            assert fi.inertia == (inst.n, inst.m, 0)
+            check_against_oracle(inst, "fp32_ir", X[off:off + inst.dim], fi, sinfo, 1e-10)
+            off += inst.dim
