@@ -1,17 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the NCL KKT factor + solve on GB300.
 
-Workload (default): the condensed system K = H + Sigma + delta I + rho J^T J
-of a 300 x 300-grid network (n = 360,000; nnz(J) = 1,795,200), rho = 1e5,
-values re-drawn on the fixed pattern for every step (Sigma jittered by
-U[0.5, 2]), as successive Newton steps do.  One step = FP64 assembly of K
-(rho J^T J as a sparse product) + FP32 LDL^T (split-TF32 updates) + solve +
-FP64 iterative refinement to a backward error <= 1e-10, all on the device
-with the step's inputs already resident in HBM.
+Default workload (the one the headline metric is quoted on): the condensed
+system K = H + Sigma + delta I + rho J^T J of a 300 x 300-grid network
+(n = 360,000; nnz(J) = 1,795,200), rho = 1e5, values re-drawn on the fixed
+pattern for every step (Sigma jittered by U[0.5, 2]) as successive Newton
+steps do.  One step = FP64 assembly of K (rho J^T J as a sparse product) +
+FP32 LDL^T (tensor-core split-TF32 update blocks) + solve + FP64 iterative
+refinement to a backward error <= 1e-10, on the device with the step's
+inputs already resident in HBM.  value = algorithmic factorisation flops
+(sum_j c_j^2 + 3 c_j under the library's ordering) / step time, GFLOP/s,
+summed over ranks (independent replicas).  The plain FP64 path on the same
+systems is reported beside it.
 
-value = algorithmic factorisation flops (sum_j c_j^2 + 3 c_j under the
-library's ordering) / (factor + solve time), GFLOP/s, summed over ranks.
-The plain FP64 path on the same systems is reported beside it.
+Other workloads (--workload): stabilized20x25, batch64 (64 scenario
+instances of a 100x100 grid, 4 RHS, one graph launch per batch), adjoint256
+(256 instances of side 10..70, forward + hand-written adjoint), large700
+(700x700 stabilized, n = 1.96M, m = 0.98M, rho = 1e6).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -35,6 +40,7 @@ from paper_2510_05885_gb300 import synth  # noqa: E402
 
 METRIC = "KKT factor+solve ms & GFLOP/s at rel. residual 1e-10: FP32+IR vs FP64 on 1 GB300"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+WORKLOADS = ("condensed300", "stabilized20x25", "batch64", "adjoint256", "large700")
 
 
 def parse():
@@ -43,8 +49,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--side", type=int, default=300)
-    ap.add_argument("--rho", type=float, default=1e5)
+    ap.add_argument("--workload", default="condensed300", choices=WORKLOADS)
+    ap.add_argument("--rho", type=float, default=None)
+    ap.add_argument("--rho-sweep", action="store_true", help="condensed300: also rho in {1e2, 1e5, 1e8}")
     ap.add_argument("--draws", type=int, default=4)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -62,10 +69,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, uuid: str | None):
+    def __init__(self, uuid):
         self.uuid = uuid
         self.proc = None
-        self.path = None
 
     def start(self):
         try:
@@ -97,8 +103,9 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda v: v.replace(".", "", 1).isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
@@ -113,17 +120,76 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
+# workloads: a list of instances per draw (a batch is several instances)
+# ---------------------------------------------------------------------------
+def workload_spec(name, rho):
+    if name == "condensed300":
+        return dict(form=1, rho=rho or 1e5, nrhs=1, desc="condensed KKT 300x300 grid", side=300)
+    if name == "stabilized20x25":
+        return dict(form=0, rho=rho or 1e4, nrhs=1, desc="stabilized KKT 20x25 grid", side=None)
+    if name == "batch64":
+        return dict(form=0, rho=rho or 1e4, nrhs=4, desc="64 stabilized 100x100-grid scenarios (1-3 edges "
+                    "deleted each), 4 RHS", side=100)
+    if name == "adjoint256":
+        return dict(form=0, rho=rho or 1e4, nrhs=1, desc="256 stabilized grids of side 10..70, forward + adjoint",
+                    side=None)
+    return dict(form=0, rho=rho or 1e6, nrhs=1, desc="stabilized KKT 700x700 grid", side=700)
+
+
+def make_patterns(name, rank):
+    """Patterns of the workload's instances (fixed across draws)."""
+    if name == "condensed300":
+        return [synth.make_pattern(300, 300)]
+    if name == "stabilized20x25":
+        return [synth.make_pattern(20, 25)]
+    if name == "large700":
+        return [synth.make_pattern(700, 700)]
+    if name == "batch64":
+        rng = np.random.Generator(np.random.PCG64(synth.seed_for(3, 0) + 7 * rank))
+        E = len(synth.grid_edges(100, 100))
+        return [synth.make_pattern(100, 100, np.sort(rng.choice(E, size=int(rng.integers(1, 4)), replace=False)))
+                for _ in range(64)]
+    sides = synth.adjoint_sides(256, 10, 70)
+    cache = {}
+    out = []
+    for s in sides:
+        s = int(s)
+        if s not in cache:
+            cache[s] = synth.make_pattern(s, s)
+        out.append(cache[s])
+    return out
+
+
+def draw_values(name, pats, spec, draw, rank, sig0):
+    """One draw of all instances (values re-drawn on the fixed patterns)."""
+    rng = np.random.Generator(np.random.PCG64(synth.seed_for(WORKLOADS.index(name) + 1, draw) + 100003 * rank))
+    form = "stabilized" if spec["form"] == 0 else "condensed"
+    out = []
+    for i, p in enumerate(pats):
+        s0 = sig0[i] if sig0 is not None else None
+        out.append(synth.draw_instance(p, rng, form=form, rho=spec["rho"], nrhs=spec["nrhs"], sigma0=s0))
+    return out
+
+
+# ---------------------------------------------------------------------------
 # the oracle's bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(side, rho):
+def oracle_sample(name, side, rho):
     import oracle as O
-    inst = synth.condensed_grid(side, rho=rho, draw=0)
+    if name == "condensed300":
+        inst = synth.condensed_grid(side, rho=rho or 1e5, draw=0)
+    elif name == "stabilized20x25":
+        inst = synth.stabilized_20x25()
+    else:
+        inst = synth.random_instance(side, side, synth.seed_for(WORKLOADS.index(name) + 1, 0), form="stabilized",
+                                     rho=rho or (1e6 if name == "large700" else 1e4))
     A = O.instance_matrix(inst)
     t0 = time.perf_counter()
     fac = O.LDLT(A, O.block_signs(inst.form, inst.n, inst.m))
     x, steps, eta = O.solve_ir(A, fac, inst.b, max_steps=3, tol=1e-12)
     dt = time.perf_counter() - t0
-    return {"seconds": dt, "flops": fac.flops, "gflops": fac.flops / dt / 1e9, "eta": eta, "n": inst.n}
+    return {"seconds": dt, "flops": fac.flops, "gflops": fac.flops / dt / 1e9, "eta": eta, "dim": inst.dim,
+            "desc": f"{'condensed' if inst.form == 'condensed' else 'stabilized'} grid of dimension {inst.dim}"}
 
 
 def run_reference(args):
@@ -133,22 +199,23 @@ def run_reference(args):
         return
     import oracle as O
     O.build_oracle()
+    side = args.cpu_side
     for _ in range(args.warmup):
-        oracle_sample(max(8, args.cpu_side // 4), args.rho)
-    times, fl = [], 0.0
+        oracle_sample(args.workload, max(8, side // 4), args.rho)
+    times, fl, desc = [], 0.0, ""
     for _ in range(args.steps):
-        r = oracle_sample(args.cpu_side, args.rho)
+        r = oracle_sample(args.workload, side, args.rho)
         times.append(r["seconds"])
-        fl = r["flops"]
+        fl, desc = r["flops"], r["desc"]
     total = sum(times)
     v = fl * args.steps / total / 1e9
-    sample = (f"condensed {args.cpu_side}x{args.cpu_side} grid (n={4 * args.cpu_side ** 2}), rho={args.rho:g}: "
-              f"oracle up-looking FP64 LDL^T (RCM order) + 3 FP64 refinement steps, per step")
+    sample = (f"{desc}: oracle up-looking FP64 LDL^T (RCM order) + up to 3 FP64 refinement steps, "
+              f"single thread, per step")
+    spec = workload_spec(args.workload, args.rho)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"condensed KKT {args.side}x{args.side} grid",
-                                            "rho": args.rho, "oracle_sample": sample},
+            "data": "synthetic", "config": {"workload": spec["desc"], "rho": spec["rho"], "oracle_sample": sample},
             "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -157,6 +224,63 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our path
 # ---------------------------------------------------------------------------
+class Runner:
+    """Device-resident draws and one handle per precision for a workload."""
+
+    def __init__(self, args, dev, rank):
+        import torch
+        from paper_2510_05885_gb300 import ncl_kkt as nk
+        self.torch, self.nk, self.args, self.dev = torch, nk, args, dev
+        self.name = args.workload
+        self.spec = workload_spec(self.name, args.rho)
+        self.pats = make_patterns(self.name, rank)
+        ndraws = max(1, min(args.draws, args.steps + args.warmup))
+        if self.name == "large700":
+            ndraws = min(ndraws, 2)
+        self.draws, sig0 = [], None
+        for d in range(ndraws):
+            insts = draw_values(self.name, self.pats, self.spec, d, rank, sig0)
+            sig0 = [i.sigma0 for i in insts]
+            self.draws.append(insts)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+        self.dev_draws = []
+        for insts in self.draws:
+            B = np.concatenate([i.b for i in insts], axis=0)            # dim x nrhs
+            self.dev_draws.append(dict(
+                H=T(np.concatenate([i.H_val for i in insts])), J=T(np.concatenate([i.J_val for i in insts])),
+                S=T(np.concatenate([i.Sigma for i in insts])), Bc=T(B.T.copy()),
+                delta=[i.delta for i in insts], rho=[i.rho for i in insts]))
+        self.batch = len(self.pats) > 1
+        self.Xc = torch.empty_like(self.dev_draws[0]["Bc"])
+
+    def make(self, prec):
+        nk = self.nk
+        f = self.spec["form"]
+        if self.batch:
+            return nk.KKT.batch(f, [(p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind) for p in self.pats],
+                                prec=prec)
+        p = self.pats[0]
+        return nk.KKT(f, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind, prec=prec)
+
+    def step(self, K, i, adjoint=False):
+        """factor + solve (+ adjoint) of draw i; returns (factor infos, solve info, adjoint ms)."""
+        nk = self.nk
+        d = self.dev_draws[i % len(self.dev_draws)]
+        nrhs = self.spec["nrhs"]
+        infos, si = nk.ncl_kkt_batch_factor_solve(K._h, d["H"], d["J"], d["S"], d["delta"], d["rho"], nrhs,
+                                                  d["Bc"], K.dim, self.Xc, K.dim)
+        adj_ms = None
+        if adjoint:
+            torch = self.torch
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            K.adjoint(self.Xc.t(), self.Xc.t())        # loss = 0.5 ||x||^2: g_x = x
+            e1.record()
+            e1.synchronize()
+            adj_ms = e0.elapsed_time(e1)
+        return infos, si, adj_ms
+
+
 def run_ours(args):
     import torch
     from paper_2510_05885_gb300 import ncl_kkt as nk
@@ -176,32 +300,21 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(v):
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     nk.load()
-    side, rho = args.side, args.rho
-    pat = synth.make_pattern(side, side)
-    ndraws = max(1, min(args.draws, args.steps + args.warmup))
-    draws, sig0 = [], None
-    for d in range(ndraws):
-        inst = synth.condensed_grid(side, rho=rho, draw=d + 1000 * rank, pat=pat, sigma0=sig0)
-        sig0 = inst.sigma0
-        draws.append(inst)
-    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    dev_draws = [(T(i.H_val), T(i.J_val), T(i.Sigma), i.delta, i.rho, T(i.b[:, 0])) for i in draws]
-
-    def make(prec):
-        return nk.KKT(1, pat.n, pat.m, pat.H_rowptr, pat.H_colind, pat.J_rowptr, pat.J_colind, prec=prec)
-
+    R = Runner(args, dev, rank)
+    adjoint = args.workload == "adjoint256"
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
 
-    def step(K, i, X=None):
-        Hv, Jv, S, dl, rh, b = dev_draws[i % ndraws]
-        fi = K.factor(Hv, Jv, S, dl, rh)
-        x, si = K.solve(b)
-        return fi, si
-
-    def timed(K, steps, warm):
+    def timed(K, steps, warm, runner=None):
+        R_ = runner if runner is not None else R
         for i in range(warm):
-            step(K, i)
+            R_.step(K, i, adjoint)
         barrier()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         res = []
@@ -209,15 +322,14 @@ def run_ours(args):
         for i in range(steps):
             flush.zero_()
             ev[i][0].record()
-            fi, si = step(K, warm + i)
+            out = R_.step(K, warm + i, adjoint)
             ev[i][1].record()
-            res.append((fi, si))
+            res.append(out)
         barrier()
         launches = (nk.ncl_kkt_kernel_launches() - l0) / steps
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return ms, res, launches
+        return [a.elapsed_time(b) for a, b in ev], res, launches
 
-    K = make("fp32_ir")
+    K = R.make("fp32_ir")
     ai = K.analysis
     flops = ai.flops
     uuid = None
@@ -229,31 +341,31 @@ def run_ours(args):
     clocks.start()
     ms, res, launches = timed(K, args.steps, args.warmup)
     ck = clocks.stop()
-    total_ms = sum(ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    etas = [si.backward_err for _, si in res]
-    iters = [si.ir_iters for _, si in res]
-    inert_ok = all(fi.inertia == (pat.n, 0, 0) for fi, _ in res)
-    factor_ms = statistics.median([fi.ms for fi, _ in res])
-    solve_ms = statistics.median([si.ms for _, si in res])
-
+    total_ms = max_over_ranks(sum(ms))
+    etas = [r[1].backward_err for r in res]
+    iters = [r[1].ir_iters for r in res]
+    inst_inertia = [(i.n, i.m if R.spec["form"] == 0 else 0, 0) for i in R.draws[0]]
+    inert_ok = all(tuple(f.inertia) == want for r in res for f, want in zip(r[0], inst_inertia))
+    spec = R.spec
     out = {
         "metric": METRIC, "value": world * flops * args.steps / (total_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (split-TF32) + f64 IR",
         "data": "synthetic",
-        "config": {"workload": f"condensed KKT {side}x{side} grid, FP32+IR", "n": pat.n, "m": pat.m,
-                   "nnz_J": pat.nnz_J, "rho": rho, "draws_cycled": ndraws, "l2": "flushed (256 MB write) before "
-                   "every timed step", "parallelism": f"replicas x{world}", "nnz_L": ai.nnz_L,
-                   "factor_flops": flops, "supernodes": ai.n_supernodes, "levels": ai.n_levels,
-                   "analyze_ms": ai.analyze_ms},
-        "factor_ms_median": factor_ms, "solve_ms_median": solve_ms,
+        "config": {"workload": spec["desc"] + ", FP32+IR", "instances": len(R.pats), "dim": ai.dim,
+                   "rho": spec["rho"], "nrhs": spec["nrhs"], "draws_cycled": len(R.draws),
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
+                   "nnz_L": ai.nnz_L, "factor_flops": flops, "supernodes": ai.n_supernodes,
+                   "levels": ai.n_levels, "analyze_ms": ai.analyze_ms, "device_bytes": ai.device_bytes},
+        "factor_ms_median": statistics.median([r[0][0].ms for r in res]),
+        "step_ms_median": statistics.median(ms),
         "backward_err_max": max(etas), "ir_iters": [min(iters), max(iters)], "inertia_ok": inert_ok,
+        "fgmres_used": any(r[1].used_fgmres for r in res),
+        "fp64_fallback": any(r[1].fp64_fallback for r in res),
         "gpu_launches": launches, "clocks": ck,
     }
+    if adjoint:
+        out["adjoint_ms_median"] = statistics.median([r[2] for r in res])
 
     # per-kernel device times (events around each launch, separate pass)
     roof = None
@@ -262,26 +374,25 @@ def run_ours(args):
         nk.ncl_kkt_profile(K._h, 1)
         for i in range(min(3, args.steps)):
             flush.zero_()
-            step(K, i)
+            R.step(K, i)
         torch.cuda.synchronize()
         nk.ncl_kkt_profile(K._h, 0)
         prof = nk.ncl_kkt_profile_report(K._h)
         out["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in prof.items()}
-        top = max(prof.items(), key=lambda kv: kv[1]["ms"])
-        name, st = top
+        factor_kernels = {k: v for k, v in prof.items() if k.startswith(("update_", "panel_", "factor_small",
+                                                                         "assemble"))}
+        name, st = max(prof.items(), key=lambda kv: kv[1]["ms"])
         pk = peaks()
         if name.startswith("update_tc"):
             bf16 = pk.get("bf16_tflops")
-            peak = bf16 / 2 / 3 if bf16 else 1900 / 2 / 3
+            peak = (bf16 if bf16 else 1900.0) / 2 / 3
             roof = {"kernel": name, "bound": "tensor", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
                     "peak": peak, "unit": "TFLOP/s",
-                    "peak_note": "TF32 = bf16 measured burst x 1/2 (nominal ratio), /3 for the 3-product split"}
-        elif "simt" in name or "small" in name or "panel" in name:
+                    "peak_note": "of measured: TF32 = bf16 burst x 1/2 (nominal ratio), /3 for the 3-product split"}
+        elif any(t in name for t in ("simt", "small", "panel", "invert")):
             clk = (ck or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
             f32 = "f32" in name
-            peak = 152 * (128 if f32 else 1) * 2 * clk * 1e6 / 1e12
-            if not f32:
-                peak = 1.25
+            peak = 152 * 128 * 2 * clk * 1e6 / 1e12 if f32 else 1.25
             roof = {"kernel": name, "bound": "alu", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
                     "peak": peak, "unit": "TFLOP/s",
                     "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock" if f32 else
@@ -289,71 +400,96 @@ def run_ours(args):
         else:
             hbm = pk.get("hbm_gbs") or 6800.0
             roof = {"kernel": name, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
-                    "peak": hbm, "unit": "GB/s", "peak_note": "measured copy bandwidth"}
+                    "peak": hbm, "unit": "GB/s", "peak_note": "of measured copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = None
         roof["avg_launch_ms"] = st["ms"] / st["launches"]
         roof["share_of_profiled_time"] = st["ms"] / sum(v["ms"] for v in prof.values())
+        tc = prof.get("update_tc_f32")
+        if tc:
+            bf16 = pk.get("bf16_tflops") or 1900.0
+            out["tensor_core_update"] = {"achieved_tflops_useful": tc["flops"] / (tc["ms"] * 1e-3) / 1e12,
+                                         "frac_of_split_tf32_peak": tc["flops"] / (tc["ms"] * 1e-3) / 1e12
+                                         / (bf16 / 2 / 3), "launches": tc["launches"]}
+        del factor_kernels
     out["roofline"] = roof
 
     # plain FP64 path on the same systems
     if not args.skip_fp64:
-        K64 = make("fp64")
+        K64 = R.make("fp64")
         n64 = max(2, args.steps // 3)
         ms64, res64, _ = timed(K64, n64, 1)
-        out["fp64"] = {"ms_per_step": sum(ms64) / n64, "gflops": flops / (sum(ms64) / n64 * 1e-3) / 1e9,
-                       "backward_err_max": max(si.backward_err for _, si in res64),
-                       "factor_ms_median": statistics.median([fi.ms for fi, _ in res64])}
+        t64 = max_over_ranks(sum(ms64))
+        out["fp64"] = {"ms_per_step": t64 / n64, "gflops": world * flops / (t64 / n64 * 1e-3) / 1e9,
+                       "backward_err_max": max(r[1].backward_err for r in res64),
+                       "factor_ms_median": statistics.median([r[0][0].ms for r in res64])}
+        if adjoint:
+            out["fp64"]["adjoint_ms_median"] = statistics.median([r[2] for r in res64])
         out["speedup_fp32ir_vs_fp64"] = out["fp64"]["ms_per_step"] / out["ms_per_step"]
         K64.close()
+
+    # rho sweep of the condensed workload
+    if args.rho_sweep and args.workload == "condensed300":
+        sweep = {}
+        for rho in (1e2, 1e5, 1e8):
+            a2 = argparse.Namespace(**vars(args))
+            a2.rho = rho
+            a2.draws = 2
+            R2 = Runner(a2, dev, rank)
+            entry = {}
+            for prec in ("fp32_ir", "fp64"):
+                Kx = R2.make(prec)
+                msx, resx, _ = timed(Kx, max(2, args.steps // 3), 1, R2)
+                entry[prec] = {"ms_per_step": sum(msx) / len(msx),
+                               "backward_err_max": max(r[1].backward_err for r in resx),
+                               "ir_iters": max(r[1].ir_iters for r in resx),
+                               "fgmres": any(r[1].used_fgmres for r in resx),
+                               "fp64_fallback": any(r[1].fp64_fallback for r in resx),
+                               "inertia": list(resx[-1][0][0].inertia)}
+                Kx.close()
+            sweep[f"{rho:g}"] = entry
+        out["rho_sweep"] = sweep
 
     # end to end through the C ABI with host buffers
     if not args.skip_e2e:
         host = []
-        for i in draws:
-            host.append(tuple(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
-                              for a in (i.H_val, i.J_val, i.Sigma, i.b[:, 0])))
-        dH = torch.empty_like(dev_draws[0][0])
-        dJ = torch.empty_like(dev_draws[0][1])
-        dS = torch.empty_like(dev_draws[0][2])
-        db = torch.empty_like(dev_draws[0][5])
-        xh = torch.empty(db.shape, dtype=torch.float64).pin_memory()
+        for d in R.dev_draws:
+            host.append({k: d[k].cpu().pin_memory() for k in ("H", "J", "S", "Bc")})
+        dd = {k: torch.empty_like(R.dev_draws[0][k]) for k in ("H", "J", "S", "Bc")}
+        xh = torch.empty(R.Xc.shape, dtype=torch.float64).pin_memory()
         ne = max(2, args.steps // 2)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for k in range(ne):
-            hH, hJ, hS, hb = host[k % ndraws]
-            dH.copy_(hH, non_blocking=True)
-            dJ.copy_(hJ, non_blocking=True)
-            dS.copy_(hS, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            inst = draws[k % ndraws]
-            K.factor(dH, dJ, dS, inst.delta, inst.rho)
-            x, _ = K.solve(db)
-            xh.copy_(x, non_blocking=True)
+            hk = host[k % len(host)]
+            for key in dd:
+                dd[key].copy_(hk[key], non_blocking=True)
+            d = R.dev_draws[k % len(R.dev_draws)]
+            nk.ncl_kkt_batch_factor_solve(K._h, dd["H"], dd["J"], dd["S"], d["delta"], d["rho"], spec["nrhs"],
+                                          dd["Bc"], K.dim, R.Xc, K.dim)
+            xh.copy_(R.Xc, non_blocking=True)
         e1.record()
         barrier()
-        ems = e0.elapsed_time(e1)
-        te = torch.tensor([ems], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        ems = float(te.item())
+        ems = max_over_ranks(e0.elapsed_time(e1))
+        npat = sum(p.nnz_H for p in R.pats), sum(p.nnz_J for p in R.pats), sum(p.n for p in R.pats)
         out["e2e"] = {"value": world * flops * ne / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
                       "ms_per_step": ems / ne,
-                      "h2d_bytes_per_step": 8 * (pat.nnz_H + pat.nnz_J + 2 * pat.n),
-                      "d2h_bytes_per_step": 8 * pat.n}
+                      "h2d_bytes_per_step": 8 * (npat[0] + npat[1] + npat[2] + ai.dim * spec["nrhs"]),
+                      "d2h_bytes_per_step": 8 * ai.dim * spec["nrhs"]}
 
     if rank == 0 and not args.skip_cpu:
         import oracle as O
         O.build_oracle()
-        r = oracle_sample(args.cpu_side, rho)
+        side = args.cpu_side if args.workload in ("condensed300", "large700") else 40
+        r = oracle_sample(args.workload, side, args.rho)
         out["cpu_baseline"] = {"value": r["gflops"], "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                               "sample": f"one factor+solve of the condensed {args.cpu_side}x{args.cpu_side} grid "
-                                         f"(n={r['n']}), rho={rho:g}, oracle RCM ordering, {r['seconds']:.1f} s; "
-                                         f"GFLOP/s of the oracle's own flop count"}
+                               "sample": f"one factor+solve of a {r['desc']} with the oracle (RCM ordering, "
+                                         f"FP64, single thread), {r['seconds']:.1f} s; GFLOP/s of the oracle's "
+                                         f"own flop count"}
     if rank == 0:
         print(json.dumps(out), flush=True)
+    K.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -326,6 +326,9 @@ class KKT:
         self.opt = default_options(**opts)
         self._h = ncl_kkt_analyze(form, n, m, H_rowptr, H_colind, J_rowptr, J_colind, self.opt)
         self.form, self.count = form, 1
+        self.nnz_H = int(np.asarray(H_rowptr)[-1]) if n > 0 else 0
+        self.nnz_J = int(np.asarray(J_rowptr)[-1]) if m > 0 else 0
+        self.n_var = int(n)
         self._post()
 
     @classmethod
@@ -338,12 +341,16 @@ class KKT:
         self._h = ncl_kkt_batch_analyze(form, ns, ms, [p[2] for p in patterns], [p[3] for p in patterns],
                                         [p[4] for p in patterns], [p[5] for p in patterns], self.opt)
         self.form, self.count = form, len(patterns)
+        self.nnz_H = sum(int(np.asarray(p[2])[-1]) if p[0] > 0 else 0 for p in patterns)
+        self.nnz_J = sum(int(np.asarray(p[4])[-1]) if p[1] > 0 else 0 for p in patterns)
+        self.n_var = sum(int(p[0]) for p in patterns)
         self._post()
         return self
 
     def _post(self):
         self.analysis = ncl_kkt_get_analysis_info(self._h)
         self.dim = int(self.analysis.dim)
+        self.generation = 0     # incremented by every factor call
 
     @property
     def permutation(self) -> np.ndarray:
@@ -353,6 +360,7 @@ class KKT:
         return ncl_kkt_get_supernodes(self._h, int(self.analysis.n_supernodes))
 
     def factor(self, H_val, J_val, Sigma, delta, rho, stream=None):
+        self.generation += 1
         if self.count == 1:
             return ncl_kkt_factor(self._h, H_val, J_val, Sigma, delta, rho, stream)
         return ncl_kkt_batch_factor(self._h, H_val, J_val, Sigma, delta, rho, stream)[0]
@@ -375,6 +383,9 @@ class KKT:
                 n_var=None):
         """Gradients of l(X) given GX = dl/dX (same shape as X)."""
         import torch
+        nnz_H = self.nnz_H if nnz_H is None else nnz_H
+        nnz_J = self.nnz_J if nnz_J is None else nnz_J
+        n_var = self.n_var if n_var is None else n_var
         one = X.dim() == 1
         Xc = X.reshape(self.dim, -1).t().contiguous()
         GXc = GX.reshape(self.dim, -1).t().contiguous()
