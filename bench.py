@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-profile", action="store_true")
     ap.add_argument("--cpu-side", type=int, default=64, help="grid side of the oracle's bounded sample")
+    ap.add_argument("--side", type=int, default=None, help="grid side of condensed300 / large700 (smaller captures)")
+    ap.add_argument("--ncu-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -119,6 +122,20 @@ def peaks():
         return {}
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
+    None when there is none or the kernel's source changed since."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))[kernel]
+        src = os.path.join(ROOT, rec["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["traffic_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 # ---------------------------------------------------------------------------
 # workloads: a list of instances per draw (a batch is several instances)
 # ---------------------------------------------------------------------------
@@ -136,14 +153,14 @@ def workload_spec(name, rho):
     return dict(form=0, rho=rho or 1e6, nrhs=1, desc="stabilized KKT 700x700 grid", side=700)
 
 
-def make_patterns(name, rank):
+def make_patterns(name, rank, side=None):
     """Patterns of the workload's instances (fixed across draws)."""
     if name == "condensed300":
-        return [synth.make_pattern(300, 300)]
+        return [synth.make_pattern(side or 300, side or 300)]
     if name == "stabilized20x25":
         return [synth.make_pattern(20, 25)]
     if name == "large700":
-        return [synth.make_pattern(700, 700)]
+        return [synth.make_pattern(side or 700, side or 700)]
     if name == "batch64":
         rng = np.random.Generator(np.random.PCG64(synth.seed_for(3, 0) + 7 * rank))
         E = len(synth.grid_edges(100, 100))
@@ -233,7 +250,10 @@ class Runner:
         self.torch, self.nk, self.args, self.dev = torch, nk, args, dev
         self.name = args.workload
         self.spec = workload_spec(self.name, args.rho)
-        self.pats = make_patterns(self.name, rank)
+        self.pats = make_patterns(self.name, rank, args.side)
+        if args.side and self.name in ("condensed300", "large700"):
+            self.spec["desc"] = self.spec["desc"].replace("300x300" if self.name == "condensed300" else "700x700",
+                                                          f"{args.side}x{args.side}")
         ndraws = max(1, min(args.draws, args.steps + args.warmup))
         if self.name == "large700":
             ndraws = min(ndraws, 2)
@@ -319,6 +339,8 @@ def run_ours(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         res = []
         l0 = nk.ncl_kkt_kernel_launches()
+        if args.ncu_range:
+            torch.cuda.profiler.start()
         for i in range(steps):
             flush.zero_()
             ev[i][0].record()
@@ -326,6 +348,8 @@ def run_ours(args):
             ev[i][1].record()
             res.append(out)
         barrier()
+        if args.ncu_range:
+            torch.cuda.profiler.stop()
         launches = (nk.ncl_kkt_kernel_launches() - l0) / steps
         return [a.elapsed_time(b) for a, b in ev], res, launches
 
@@ -402,7 +426,9 @@ def run_ours(args):
             roof = {"kernel": name, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
                     "peak": hbm, "unit": "GB/s", "peak_note": "of measured copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
+        roof["traffic"] = recorded_traffic(name)
+        roof["algorithmic_bytes_per_launch"] = st["bytes"] / st["launches"]
+        roof["algorithmic_flops_per_launch"] = st["flops"] / st["launches"]
         roof["avg_launch_ms"] = st["ms"] / st["launches"]
         roof["share_of_profiled_time"] = st["ms"] / sum(v["ms"] for v in prof.values())
         tc = prof.get("update_tc_f32")
