@@ -57,7 +57,10 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-profile", action="store_true")
-    ap.add_argument("--cpu-side", type=int, default=64, help="grid side of the oracle's bounded sample")
+    ap.add_argument("--cpu-side", type=int, default=96,
+                    help="grid side of the oracle's sample of condensed300 / large700")
+    ap.add_argument("--cpu-budget", type=float, default=5.0,
+                    help="seconds of oracle work per reference-arm step (cpu_baseline: twice this)")
     ap.add_argument("--side", type=int, default=None, help="grid side of condensed300 / large700 (smaller captures)")
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
@@ -153,60 +156,92 @@ def workload_spec(name, rho):
     return dict(form=0, rho=rho or 1e6, nrhs=1, desc="stabilized KKT 700x700 grid", side=700)
 
 
-def make_patterns(name, rank, side=None):
-    """Patterns of the workload's instances (fixed across draws)."""
+def iter_patterns(name, rank, side=None):
+    """Patterns of the workload's instances (fixed across draws), in order."""
     if name == "condensed300":
-        return [synth.make_pattern(side or 300, side or 300)]
-    if name == "stabilized20x25":
-        return [synth.make_pattern(20, 25)]
-    if name == "large700":
-        return [synth.make_pattern(side or 700, side or 700)]
-    if name == "batch64":
+        yield synth.make_pattern(side or 300, side or 300)
+    elif name == "stabilized20x25":
+        yield synth.make_pattern(20, 25)
+    elif name == "large700":
+        yield synth.make_pattern(side or 700, side or 700)
+    elif name == "batch64":
         rng = np.random.Generator(np.random.PCG64(synth.seed_for(3, 0) + 7 * rank))
         E = len(synth.grid_edges(100, 100))
-        return [synth.make_pattern(100, 100, np.sort(rng.choice(E, size=int(rng.integers(1, 4)), replace=False)))
-                for _ in range(64)]
-    sides = synth.adjoint_sides(256, 10, 70)
-    cache = {}
-    out = []
-    for s in sides:
-        s = int(s)
-        if s not in cache:
-            cache[s] = synth.make_pattern(s, s)
-        out.append(cache[s])
-    return out
+        for _ in range(64):
+            yield synth.make_pattern(100, 100, np.sort(rng.choice(E, size=int(rng.integers(1, 4)), replace=False)))
+    else:
+        cache = {}
+        for s in synth.adjoint_sides(256, 10, 70):
+            s = int(s)
+            if s not in cache:
+                cache[s] = synth.make_pattern(s, s)
+            yield cache[s]
+
+
+def make_patterns(name, rank, side=None):
+    return list(iter_patterns(name, rank, side))
+
+
+def iter_values(name, pats, spec, draw, rank, sig0=None):
+    """One draw of the instances on the patterns `pats` (values re-drawn on the
+    fixed patterns), generated in order."""
+    rng = np.random.Generator(np.random.PCG64(synth.seed_for(WORKLOADS.index(name) + 1, draw) + 100003 * rank))
+    form = "stabilized" if spec["form"] == 0 else "condensed"
+    for i, p in enumerate(pats):
+        s0 = sig0[i] if sig0 is not None else None
+        yield synth.draw_instance(p, rng, form=form, rho=spec["rho"], nrhs=spec["nrhs"], sigma0=s0)
 
 
 def draw_values(name, pats, spec, draw, rank, sig0):
-    """One draw of all instances (values re-drawn on the fixed patterns)."""
-    rng = np.random.Generator(np.random.PCG64(synth.seed_for(WORKLOADS.index(name) + 1, draw) + 100003 * rank))
-    form = "stabilized" if spec["form"] == 0 else "condensed"
-    out = []
-    for i, p in enumerate(pats):
-        s0 = sig0[i] if sig0 is not None else None
-        out.append(synth.draw_instance(p, rng, form=form, rho=spec["rho"], nrhs=spec["nrhs"], sigma0=s0))
-    return out
+    return list(iter_values(name, pats, spec, draw, rank, sig0))
 
 
 # ---------------------------------------------------------------------------
 # the oracle's bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(name, side, rho):
+def oracle_sample(name, rho, side, budget_s, rank=0):
+    """Run the oracle (assembly, factorisation, FP64 refinement; the adjoint
+    too for adjoint256) on the workload's own instances in order until
+    `budget_s` seconds of CPU work have been spent (at least one instance).
+    The single-system workloads too large for the oracle (condensed300,
+    large700) are sampled as grids of side `side` with the same generator."""
     import oracle as O
-    if name == "condensed300":
-        inst = synth.condensed_grid(side, rho=rho or 1e5, draw=0)
+    spec = workload_spec(name, rho)
+    if name in ("condensed300", "large700"):
+        def gen():
+            d = 0
+            while True:
+                yield from iter_values(name, make_patterns(name, rank, side), spec, d, rank)
+                d += 1
+        what = f"{'condensed' if spec['form'] else 'stabilized'} {side}x{side} grid"
     elif name == "stabilized20x25":
-        inst = synth.stabilized_20x25()
+        def gen():
+            pats, d = make_patterns(name, rank), 0
+            while True:
+                yield from iter_values(name, pats, spec, d, rank)
+                d += 1
+        what = "stabilized 20x25 grid (successive draws)"
     else:
-        inst = synth.random_instance(side, side, synth.seed_for(WORKLOADS.index(name) + 1, 0), form="stabilized",
-                                     rho=rho or (1e6 if name == "large700" else 1e4))
-    A = O.instance_matrix(inst)
-    t0 = time.perf_counter()
-    fac = O.LDLT(A, O.block_signs(inst.form, inst.n, inst.m))
-    x, steps, eta = O.solve_ir(A, fac, inst.b, max_steps=3, tol=1e-12)
-    dt = time.perf_counter() - t0
-    return {"seconds": dt, "flops": fac.flops, "gflops": fac.flops / dt / 1e9, "eta": eta, "dim": inst.dim,
-            "desc": f"{'condensed' if inst.form == 'condensed' else 'stabilized'} grid of dimension {inst.dim}"}
+        def gen():
+            yield from iter_values(name, iter_patterns(name, rank), spec, 0, rank)
+        what = "instances of the batch, in order"
+    flops, secs, count, dim, worst = 0.0, 0.0, 0, 0, 0.0
+    for inst in gen():
+        t0 = time.perf_counter()
+        A = O.instance_matrix(inst)
+        fac = O.LDLT(A, O.block_signs(inst.form, inst.n, inst.m))
+        x, _, eta = O.solve_ir(A, fac, inst.b, max_steps=3, tol=1e-12)
+        if name == "adjoint256":
+            O.adjoint(inst, fac, A, x, np.ones_like(x))
+        secs += time.perf_counter() - t0
+        flops += fac.flops
+        count += 1
+        dim += inst.dim
+        worst = max(worst, float(eta))
+        if secs >= budget_s:
+            break
+    return {"seconds": secs, "flops": flops, "gflops": flops / secs / 1e9, "eta": worst, "count": count,
+            "desc": f"{count} x {what} (total dimension {dim}), {secs:.1f} s"}
 
 
 def run_reference(args):
@@ -218,16 +253,17 @@ def run_reference(args):
     O.build_oracle()
     side = args.cpu_side
     for _ in range(args.warmup):
-        oracle_sample(args.workload, max(8, side // 4), args.rho)
+        oracle_sample(args.workload, args.rho, max(8, side // 4), 0.0)
     times, fl, desc = [], 0.0, ""
     for _ in range(args.steps):
-        r = oracle_sample(args.workload, side, args.rho)
+        r = oracle_sample(args.workload, args.rho, side, args.cpu_budget)
         times.append(r["seconds"])
-        fl, desc = r["flops"], r["desc"]
+        fl += r["flops"]
+        desc = r["desc"]
     total = sum(times)
-    v = fl * args.steps / total / 1e9
-    sample = (f"{desc}: oracle up-looking FP64 LDL^T (RCM order) + up to 3 FP64 refinement steps, "
-              f"single thread, per step")
+    v = fl / total / 1e9
+    sample = (f"per step {desc} (last step): oracle up-looking FP64 LDL^T (RCM order) + up to 3 FP64 "
+              f"refinement steps, single thread; GFLOP/s of the oracle's own flop count")
     spec = workload_spec(args.workload, args.rho)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
@@ -507,12 +543,10 @@ def run_ours(args):
     if rank == 0 and not args.skip_cpu:
         import oracle as O
         O.build_oracle()
-        side = args.cpu_side if args.workload in ("condensed300", "large700") else 40
-        r = oracle_sample(args.workload, side, args.rho)
+        r = oracle_sample(args.workload, args.rho, args.cpu_side, 2 * args.cpu_budget)
         out["cpu_baseline"] = {"value": r["gflops"], "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                               "sample": f"one factor+solve of a {r['desc']} with the oracle (RCM ordering, "
-                                         f"FP64, single thread), {r['seconds']:.1f} s; GFLOP/s of the oracle's "
-                                         f"own flop count"}
+                               "sample": f"{r['desc']} with the oracle (RCM ordering, FP64, up to 3 refinement "
+                                         f"steps, single thread); GFLOP/s of the oracle's own flop count"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     K.close()
