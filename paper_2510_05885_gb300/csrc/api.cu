@@ -59,18 +59,20 @@ struct Cost {
   double flops = 0, bytes = 0;
 };
 
-struct Step {
-  int64_t pdiag_off = 0;
-  int pdiag_cnt = 0;
-  int64_t panel_off = 0;
-  int panel_cnt = 0;
-  int64_t prob_off = 0;
+struct Step {                 // one macro panel of every large front of a level
+  int64_t diag_off = 0;       // (s, q0) diagonal-block items
+  int diag_cnt = 0;
+  int64_t rows_off = 0;       // (s, q0, r0) row items
+  int rows_cnt = 0;
+  int64_t prob_off = 0;       // SIMT trailing updates
   int prob_cnt = 0;
   int64_t tiles = 0;
-  int64_t tc_off = 0;
+  int64_t tp_off = 0;
+  int64_t tc_off = 0;         // tensor-core trailing updates
   int tc_cnt = 0;
   int64_t tc_tiles = 0;
-  Cost panel_cost, gemm_cost;
+  int64_t ttp_off = 0;
+  Cost diag_cost, rows_cost, gemm_cost, tc_cost;
 };
 
 struct Level {
@@ -78,13 +80,16 @@ struct Level {
   int asm_cnt = 0;
   int64_t small_off = 0;
   int small_cnt = 0;
+  int64_t small_smem = 0;     // dynamic shared memory of the small-front launch
   std::vector<Step> steps;
   int64_t syrk_off = 0;
   int syrk_cnt = 0;
   int64_t syrk_tiles = 0;
+  int64_t syrk_tp_off = 0;
   int64_t tsyrk_off = 0;  // tensor-core update-block problems
   int tsyrk_cnt = 0;
   int64_t tsyrk_tiles = 0;
+  int64_t tsyrk_tp_off = 0;
   int tsyrk_stages = 1;
   int64_t list_off = 0;   // all supernodes of the level (solve)
   int list_cnt = 0;
@@ -109,9 +114,10 @@ std::atomic<int64_t> g_kernel_launches{0};
 struct HostSched {
   std::vector<int2> asmv, belowv;
   std::vector<int32_t> smallv, listv;
-  std::vector<int4> panelv;
-  std::vector<int2> pdiagv;
+  std::vector<int4> rowsv;
+  std::vector<int2> diagv;
   std::vector<GemmProb> probv;
+  std::vector<int32_t> tilep, tilep_tc;   // problem of every tile, per launch
   // tensor-core path (FP32): problems, split-operand offsets, fronts in map order
   bool tc = false;
   std::vector<TcProb> tcv;
@@ -119,7 +125,6 @@ struct HostSched {
   std::vector<int32_t> tc_fronts;
   int64_t split_max = 0;
   std::vector<int8_t> sn_flags;
-  std::vector<int2> invv;                 // (supernode, first column) of every 32 x 32 diagonal block
   std::vector<int64_t> sn_Ioff;
 };
 
@@ -150,9 +155,11 @@ struct ncl_kkt_s {
   HostSched hs;
   int2* d_asm = nullptr;
   int32_t* d_small = nullptr;
-  int4* d_panel = nullptr;
-  int2* d_pdiag = nullptr;
+  int4* d_rows = nullptr;
+  int2* d_diag = nullptr;
   GemmProb* d_probs = nullptr;
+  int32_t* d_tilep = nullptr;
+  int32_t* d_tilep_tc = nullptr;
   int32_t* d_lists = nullptr;
   int2* d_below = nullptr;
   // solve workspace
@@ -175,7 +182,6 @@ struct ncl_kkt_s {
   const double** d_valptr = nullptr;       // {H, J, Sigma} pointers of the current factor call
   CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
   TcProb* d_tc = nullptr;
-  int2* d_inv = nullptr;
   int* d_err = nullptr;                    // device error flags (bounded waits)
   // CUDA graphs: the factor and the triangular sweeps are captured once (on
   // a private stream, after one direct call) and replayed
@@ -268,17 +274,42 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<int2>& belowv = hs.belowv;
   std::vector<int32_t>& smallv = hs.smallv;
   std::vector<int32_t>& listv = hs.listv;
-  std::vector<int4>& panelv = hs.panelv;
-  std::vector<int2>& pdiagv = hs.pdiagv;
+  std::vector<int4>& rowsv = hs.rowsv;
+  std::vector<int2>& diagv = hs.diagv;
   std::vector<GemmProb>& probv = hs.probv;
   hs.tc = is_fp32(h) && h->opt.use_tensor_cores;
   hs.sn_Soff.assign(P.ns, -1);
   hs.sn_flags.assign(P.ns, 0);
   hs.sn_Ioff.assign(P.ns + 1, 0);
-  for (int32_t s = 0; s < P.ns; s++) {
-    for (int kb = 0; kb < P.sn_ncol[s]; kb += 32) hs.invv.push_back(make_int2(s, kb));
+  for (int32_t s = 0; s < P.ns; s++)
     hs.sn_Ioff[s + 1] = hs.sn_Ioff[s] + (int64_t)((P.sn_ncol[s] + 31) / 32) * 1024;
-  }
+  // problems of one launch are pushed consecutively; each launch's tiles map
+  // to its problems through a contiguous run of the per-tile index arrays
+  auto push_gemm = [&](GemmProb g, int64_t prob_base, int64_t& tiles, Cost& c) {
+    const int Mt = (g.M + GEMM_TILE - 1) / GEMM_TILE, Nt = (g.N + GEMM_TILE - 1) / GEMM_TILE;
+    g.Nt = Nt;
+    g.tile0 = tiles;
+    const int64_t nt = (int64_t)Nt * (Nt + 1) / 2 + (int64_t)(Mt - Nt) * Nt;
+    const int32_t idx = (int32_t)((int64_t)probv.size() - prob_base);
+    probv.push_back(g);
+    hs.tilep.insert(hs.tilep.end(), (size_t)nt, idx);
+    tiles += nt;
+    const double centries = (double)g.M * g.N - 0.5 * (double)g.N * (g.N - 1);
+    c.flops += 2.0 * g.K * centries;
+    c.bytes += esz * (2.0 * centries + (double)(g.M + g.N) * g.K);
+  };
+  auto push_tc = [&](TcProb q, int64_t prob_base, int64_t& tiles, Cost& c) {
+    q.tile0 = tiles;
+    const int64_t nt = tc_tiles(q.M, q.N, &q.Nt);
+    const int32_t idx = (int32_t)((int64_t)hs.tcv.size() - prob_base);
+    hs.tcv.push_back(q);
+    hs.tilep_tc.insert(hs.tilep_tc.end(), (size_t)nt, idx);
+    tiles += nt;
+    const double centries = (double)q.M * q.N - 0.5 * (double)q.N * (q.N - 1);
+    const double K = 32.0 * q.nk;
+    c.flops += 2.0 * K * centries;
+    c.bytes += 4.0 * (2.0 * centries) + 16.0 * (double)(q.M + q.N) * K;
+  };
   std::vector<int32_t> fid(P.ns, -1);
   h->levels.assign(P.nlevels, Level{});
   for (int32_t l = 0; l < P.nlevels; l++) {
@@ -287,17 +318,22 @@ void build_schedule(ncl_kkt_s* h) {
     L.small_off = (int64_t)smallv.size();
     L.list_off = (int64_t)listv.size();
     L.below_off = (int64_t)belowv.size();
-    std::vector<int32_t> large;
+    std::vector<int32_t> large, small;
     for (int32_t k = P.level_ptr[l]; k < P.level_ptr[l + 1]; k++) {
       const int32_t s = P.level_list[k];
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
       for (int r0 = 0; r0 < nrow; r0 += ASM_ROWS) asmv.push_back(make_int2(s, r0));
       listv.push_back(s);
       for (int a0 = 0; a0 < nrow - ncol; a0 += SOLVE_ROWS) belowv.push_back(make_int2(s, a0));
-      const bool small = ncol <= 64 && nrow <= 512 && (int64_t)nrow * ncp * (int64_t)esz <= SMALL_SMEM;
-      if (small) smallv.push_back(s);
-      else large.push_back(s);
-      const double nb = nrow - ncol, lent = (double)nrow * ncol - 0.5 * ncol * (ncol - 1.0);
+      const bool is_small = ncol <= 64 && nrow <= 512 && (int64_t)nrow * ncp * (int64_t)esz <= SMALL_SMEM;
+      if (is_small) {
+        smallv.push_back(s);
+        small.push_back(s);
+        L.small_smem = std::max<int64_t>(L.small_smem, (small_front_smem(nrow, ncp, (int)esz) + 15) / 16 * 16);
+      } else {
+        large.push_back(s);
+      }
+      const double nb = nrow - ncol;
       // assembly writes the L and U blocks, reads the children's U blocks
       double child_u = 0;
       for (int32_t k2 = P.child_ptr[s]; k2 < P.child_ptr[s + 1]; k2++) {
@@ -306,9 +342,9 @@ void build_schedule(ncl_kkt_s* h) {
       }
       L.asm_cost.bytes += esz * ((double)nrow * ncp + 0.5 * nb * (nb + 1) + child_u) +
                           12.0 * (double)(P.amap_ptr[P.sn_rows_off[s + 1]] - P.amap_ptr[P.sn_rows_off[s]]);
-      if (small) {
-        L.small_cost.flops += 2.0 * (ncol * (double)ncol * ncol / 3.0 + nb * ncol * ncol) + 2.0 * ncol * 0.5 * nb * (nb + 1);
-        L.small_cost.bytes += esz * (2.0 * nrow * ncp + nb * (nb + 1));
+      if (is_small) {
+        L.small_cost.flops += 2.0 * (ncol * (double)ncol * ncol / 3.0 + nb * ncol * ncol);
+        L.small_cost.bytes += esz * 2.0 * nrow * ncp;
       }
       L.fdiag_cost.bytes += esz * 0.5 * ncol * (ncol + 1.0);
       L.fdiag_cost.flops += (double)ncol * ncol;
@@ -317,7 +353,6 @@ void build_schedule(ncl_kkt_s* h) {
       L.bdiag_cost = L.fdiag_cost;
       L.bbelow_cost.bytes += esz * nb * ncol;
       L.bbelow_cost.flops += 2.0 * nb * ncol;
-      (void)lent;
     }
     L.asm_cnt = (int)(asmv.size() - L.asm_off);
     L.small_cnt = (int)(smallv.size() - L.small_off);
@@ -335,105 +370,90 @@ void build_schedule(ncl_kkt_s* h) {
       hs.split_max = std::max(hs.split_max, off);
     }
     for (int32_t s : large) hs.sn_flags[s] = 1;
-    int maxp = 0;
-    for (int32_t s : large) maxp = std::max(maxp, (P.sn_ncol[s] + PANEL_NB - 1) / PANEL_NB);
-    L.steps.resize(maxp);
-    for (int p = 0; p < maxp; p++) {
-      Step& S = L.steps[p];
-      S.panel_off = (int64_t)panelv.size();
-      S.pdiag_off = (int64_t)pdiagv.size();
+    int maxm = 0;
+    for (int32_t s : large) maxm = std::max(maxm, (P.sn_ncol[s] + MACRO_NB - 1) / MACRO_NB);
+    L.steps.resize(maxm);
+    for (int m = 0; m < maxm; m++) {
+      Step& S = L.steps[m];
+      S.diag_off = (int64_t)diagv.size();
+      S.rows_off = (int64_t)rowsv.size();
       S.prob_off = (int64_t)probv.size();
+      S.tp_off = (int64_t)hs.tilep.size();
       S.tc_off = (int64_t)hs.tcv.size();
-      int64_t tiles = 0;
+      S.ttp_off = (int64_t)hs.tilep_tc.size();
       for (int32_t s : large) {
         const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
-        const int p0 = p * PANEL_NB;
-        if (p0 >= ncol) continue;
-        const int pe = std::min(p0 + PANEL_NB, ncol);
-        pdiagv.push_back(make_int2(s, p0));
-        for (int r0 = pe; r0 < nrow; r0 += PANEL_ROWS) panelv.push_back(make_int4(s, p0, r0, 0));
-        S.panel_cost.flops += (double)(nrow - pe) * (pe - p0) * (pe - p0) + 2.0 * (pe - p0) * (pe - p0) * (pe - p0) / 3.0;
-        S.panel_cost.bytes += esz * 2.0 * (nrow - p0) * (pe - p0);
-        if (pe < ncol && fid[s] >= 0 && h->opt.use_tensor_cores > 1) {
+        const int q0 = m * MACRO_NB;
+        if (q0 >= ncol) continue;
+        const int qe = std::min(q0 + MACRO_NB, ncol), w = qe - q0;
+        diagv.push_back(make_int2(s, q0));
+        S.diag_cost.flops += 2.0 * w * (double)w * w / 3.0 + 32.0 * 32 * w;
+        S.diag_cost.bytes += esz * ((double)w * (w + 1) + 1024.0 * ((w + 31) / 32) + 2.0 * w);
+        for (int r0 = qe; r0 < nrow; r0 += MACRO_ROWS) rowsv.push_back(make_int4(s, q0, r0, 0));
+        S.rows_cost.flops += (double)(nrow - qe) * w * (w + 1.0);
+        S.rows_cost.bytes += esz * 2.0 * (nrow - qe) * w + (fid[s] >= 0 ? 16.0 * (nrow - qe) * w : 0.0);
+        if (qe >= ncol) continue;
+        if (fid[s] >= 0 && h->opt.use_tensor_cores > 1 && w % 32 == 0) {
           TcProb q{};
-          q.c_off = P.sn_Loff[s] + (int64_t)pe * ncp + pe;
+          q.c_off = P.sn_Loff[s] + (int64_t)qe * ncp + qe;
           q.ldc = ncp;
           q.c_in_u = 0;
           q.map = fid[s];
-          q.row_a = pe;
-          q.row_b = pe;
-          q.k0 = p0;
-          q.nk = 1;
-          q.M = nrow - pe;
-          q.N = ncol - pe;
-          q.front = s;
-          q.next_p0 = pe;
-          q.tile0 = S.tc_tiles;
-          S.tc_tiles += tc_tiles(q.M, q.N, &q.Nt);
-          hs.tcv.push_back(q);
-          const double centries = (double)q.M * q.N - 0.5 * (double)q.N * (q.N - 1);
-          S.gemm_cost.flops += 2.0 * (pe - p0) * centries;
-          S.gemm_cost.bytes += esz * (2.0 * centries) + 16.0 * (double)(q.M + q.N) * (pe - p0);
-        } else if (pe < ncol) {
+          q.row_a = qe;
+          q.row_b = qe;
+          q.k0 = q0;
+          q.nk = w / 32;
+          q.M = nrow - qe;
+          q.N = ncol - qe;
+          push_tc(q, S.tc_off, S.tc_tiles, S.tc_cost);
+        } else {
           GemmProb g{};
-          g.c_off = P.sn_Loff[s] + (int64_t)pe * ncp + pe;
-          g.a_off = P.sn_Loff[s] + (int64_t)pe * ncp + p0;
+          g.c_off = P.sn_Loff[s] + (int64_t)qe * ncp + qe;
+          g.a_off = P.sn_Loff[s] + (int64_t)qe * ncp + q0;
           g.b_off = g.a_off;
-          g.d_off = P.sn_col0[s] + p0;
+          g.d_off = P.sn_col0[s] + q0;
           g.ldc = ncp;
           g.lda = ncp;
-          g.M = nrow - pe;
-          g.N = ncol - pe;
-          g.K = pe - p0;
+          g.M = nrow - qe;
+          g.N = ncol - qe;
+          g.K = w;
           g.c_in_u = 0;
-          g.front = s;
-          g.next_p0 = pe;
-          const int Mt = (g.M + GEMM_TILE - 1) / GEMM_TILE, Nt = (g.N + GEMM_TILE - 1) / GEMM_TILE;
-          g.Nt = Nt;
-          g.tile0 = tiles;
-          tiles += (int64_t)Nt * (Nt + 1) / 2 + (int64_t)(Mt - Nt) * Nt;
-          probv.push_back(g);
-          const double centries = (double)g.M * g.N - 0.5 * (double)g.N * (g.N - 1);
-          S.gemm_cost.flops += 2.0 * g.K * centries;
-          S.gemm_cost.bytes += esz * (2.0 * centries + (double)(g.M + g.N) * g.K);
+          push_gemm(g, S.prob_off, S.tiles, S.gemm_cost);
         }
       }
-      S.panel_cnt = (int)(panelv.size() - S.panel_off);
-      S.pdiag_cnt = (int)(pdiagv.size() - S.pdiag_off);
-      S.tc_cnt = (int)(hs.tcv.size() - S.tc_off);
+      S.diag_cnt = (int)(diagv.size() - S.diag_off);
+      S.rows_cnt = (int)(rowsv.size() - S.rows_off);
       S.prob_cnt = (int)(probv.size() - S.prob_off);
-      S.tiles = tiles;
+      S.tc_cnt = (int)(hs.tcv.size() - S.tc_off);
     }
+    // update blocks F22 -= L21 D1 L21^T: tensor cores for the fronts with
+    // enough pivots, the SIMT kernel for the rest (small fronts included)
     L.syrk_off = (int64_t)probv.size();
+    L.syrk_tp_off = (int64_t)hs.tilep.size();
     L.tsyrk_off = (int64_t)hs.tcv.size();
-    int64_t tiles = 0;
+    L.tsyrk_tp_off = (int64_t)hs.tilep_tc.size();
     for (int32_t s : large) {
+      const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s];
+      const int nb = nrow - ncol;
+      if (nb == 0 || !(hs.tc && ncol >= TC_MIN_K && fid[s] >= 0)) continue;
+      TcProb q{};
+      q.c_off = P.sn_Uoff[s];
+      q.ldc = nb;
+      q.c_in_u = 1;
+      q.map = fid[s];
+      q.row_a = ncol;
+      q.row_b = ncol;
+      q.k0 = 0;
+      q.nk = (ncol + 31) / 32;
+      q.M = nb;
+      q.N = nb;
+      L.tsyrk_stages = std::max(L.tsyrk_stages, std::min(q.nk, 3));
+      push_tc(q, L.tsyrk_off, L.tsyrk_tiles, L.syrk_cost);
+    }
+    auto push_syrk = [&](int32_t s) {
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
       const int nb = nrow - ncol;
-      if (nb == 0) continue;
-      if (hs.tc && ncol >= TC_MIN_K && fid[s] >= 0) {
-        TcProb q{};
-        q.c_off = P.sn_Uoff[s];
-        q.ldc = nb;
-        q.c_in_u = 1;
-        q.map = fid[s];
-        q.row_a = ncol;
-        q.row_b = ncol;
-        q.k0 = 0;
-        q.nk = (ncol + 31) / 32;
-        q.M = nb;
-        q.N = nb;
-        q.front = s;
-        q.next_p0 = -1;
-        q.tile0 = L.tsyrk_tiles;
-        L.tsyrk_tiles += tc_tiles(q.M, q.N, &q.Nt);
-        L.tsyrk_stages = std::max(L.tsyrk_stages, std::min(q.nk, 3));
-        hs.tcv.push_back(q);
-        const double centries = 0.5 * (double)nb * (nb + 1);
-        L.syrk_cost.flops += 2.0 * ncol * centries;
-        L.syrk_cost.bytes += esz * (2.0 * centries) + 16.0 * (double)nb * ncol;
-        continue;
-      }
+      if (nb == 0 || (hs.tc && ncol >= TC_MIN_K && fid[s] >= 0)) return;
       GemmProb g{};
       g.c_off = P.sn_Uoff[s];
       g.a_off = P.sn_Loff[s] + (int64_t)ncol * ncp;
@@ -445,20 +465,12 @@ void build_schedule(ncl_kkt_s* h) {
       g.N = nb;
       g.K = ncol;
       g.c_in_u = 1;
-      g.front = s;
-      g.next_p0 = -1;
-      const int Nt = (nb + GEMM_TILE - 1) / GEMM_TILE;
-      g.Nt = Nt;
-      g.tile0 = tiles;
-      tiles += (int64_t)Nt * (Nt + 1) / 2;
-      probv.push_back(g);
-      const double centries = 0.5 * (double)nb * (nb + 1);
-      L.syrk_cost.flops += 2.0 * ncol * centries;
-      L.syrk_cost.bytes += esz * (2.0 * centries + (double)nb * ncol);
-    }
+      push_gemm(g, L.syrk_off, L.syrk_tiles, L.syrk_cost);
+    };
+    for (int32_t s : large) push_syrk(s);
+    for (int32_t s : small) push_syrk(s);
     L.syrk_cnt = (int)(probv.size() - L.syrk_off);
     L.tsyrk_cnt = (int)(hs.tcv.size() - L.tsyrk_off);
-    L.syrk_tiles = tiles;
   }
   // bounds of every launch item against its buffers, checked on the host
   // before anything runs on the device
@@ -491,18 +503,20 @@ void build_schedule(ncl_kkt_s* h) {
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x]) bad("assembly item");
     for (const int2& it : belowv)
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x] - P.sn_ncol[it.x]) bad("solve item");
-    for (int32_t s : smallv) {
-      const int64_t nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
-      if (nrow * ncp * (int64_t)esz > SMALL_SMEM || nrow * (int64_t)esz > 4096) bad("small front smem");
-    }
-    for (const int4& it : panelv) {
+    for (int32_t s : smallv)
+      if (small_front_smem(P.sn_nrow[s], P.sn_ncolp[s], (int)esz) > SMALL_SMEM_MAX || P.sn_ncol[s] > 64 ||
+          P.sn_nrow[s] > 512)
+        bad("small front smem");
+    for (const Level& L : h->levels)
+      if (L.small_smem > SMALL_SMEM_MAX) bad("small front smem");
+    for (const int2& it : diagv)
+      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_ncol[it.x] || it.y % MACRO_NB) bad("macro diag item");
+    for (const int4& it : rowsv) {
       const int s = it.x;
-      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.z < 0 || it.z >= P.sn_nrow[s]) bad("panel item");
+      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.y % MACRO_NB ||
+          it.z < std::min(it.y + MACRO_NB, P.sn_ncol[s]) || it.z >= P.sn_nrow[s])
+        bad("macro rows item");
     }
-    for (const int2& it : pdiagv)
-      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_ncol[it.x]) bad("panel diag item");
-    for (const int2& b : hs.invv)
-      if (b.x < 0 || b.x >= P.ns || b.y < 0 || b.y >= P.sn_ncol[b.x] || b.y % 32) bad("inverse block");
     for (const TcProb& q : hs.tcv) {
       const int64_t csz = q.c_in_u ? Usz : Lsz;
       if (q.map < 0 || q.map >= (int)hs.tc_fronts.size()) bad("tc map");
@@ -518,6 +532,22 @@ void build_schedule(ncl_kkt_s* h) {
       if (g.a_off < 0 || g.a_off + (int64_t)(g.M - 1) * g.lda + g.K > Lsz) bad("gemm A");
       if (g.b_off < 0 || g.b_off + (int64_t)(g.N - 1) * g.lda + g.K > Lsz) bad("gemm B");
       if (g.d_off < 0 || g.d_off + g.K > P.dim) bad("gemm d");
+    }
+    // every tile index of a launch names a problem of that launch
+    for (const Level& L : h->levels) {
+      auto check = [&](int64_t tp_off, int64_t tiles, int64_t prob_off, int cnt, size_t tp_size, size_t nprob,
+                       const std::vector<int32_t>& tp) {
+        if (tiles == 0) return;
+        if (tp_off < 0 || tp_off + tiles > (int64_t)tp_size || prob_off + cnt > (int64_t)nprob) bad("tile index");
+        for (int64_t t = 0; t < tiles; t++)
+          if (tp[tp_off + t] < 0 || tp[tp_off + t] >= cnt) bad("tile index");
+      };
+      for (const Step& S : L.steps) {
+        check(S.tp_off, S.tiles, S.prob_off, S.prob_cnt, hs.tilep.size(), probv.size(), hs.tilep);
+        check(S.ttp_off, S.tc_tiles, S.tc_off, S.tc_cnt, hs.tilep_tc.size(), hs.tcv.size(), hs.tilep_tc);
+      }
+      check(L.syrk_tp_off, L.syrk_tiles, L.syrk_off, L.syrk_cnt, hs.tilep.size(), probv.size(), hs.tilep);
+      check(L.tsyrk_tp_off, L.tsyrk_tiles, L.tsyrk_off, L.tsyrk_cnt, hs.tilep_tc.size(), hs.tcv.size(), hs.tilep_tc);
     }
   }
 }
@@ -639,19 +669,20 @@ void build_device(ncl_kkt_s* h) {
     h->d_maps = reinterpret_cast<CUtensorMap*>(h->alloc<char>((int64_t)(maps.size() * sizeof(CUtensorMap))));
     CK(cudaMemcpy(h->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     h->d_tc = h->upload(hs.tcv);
+    h->d_tilep_tc = h->upload(hs.tilep_tc);
   }
   h->d_err = h->alloc<int>(4);
   d.sn_flags = h->upload(h->hs.sn_flags);
   d.sn_Ioff = h->upload(h->hs.sn_Ioff);
-  h->d_inv = h->upload(h->hs.invv);
   CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 
   HostSched& hs = h->hs;
   h->d_asm = h->upload(hs.asmv);
   h->d_small = h->upload(hs.smallv);
-  h->d_panel = h->upload(hs.panelv);
-  h->d_pdiag = h->upload(hs.pdiagv);
+  h->d_rows = h->upload(hs.rowsv);
+  h->d_diag = h->upload(hs.diagv);
   h->d_probs = h->upload(hs.probv);
+  h->d_tilep = h->upload(hs.tilep);
   h->d_lists = h->upload(hs.listv);
   h->d_below = h->upload(hs.belowv);
   CK(cudaMallocHost(&h->h_pinned, sizeof(double) * (size_t)(7 * ni + 64 + 3 * ni * MAX_RHS_SWEEP)));
@@ -744,40 +775,36 @@ template <typename T>
 void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
   const DevPlan& P = h->dp;
   const bool f32 = sizeof(T) == 4;
+  const double eps = h->opt.pivot_eps;
+  const int pol = h->opt.pivot_policy;
   for (const Level& L : h->levels) {
-    klaunch(h, st, f32 ? "assemble_f32" : "assemble_f64", L.asm_cnt, L.asm_cost, [&] {
-      launch_assemble<T>(P, N, h->d_asm + L.asm_off, L.asm_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
-    });
+    klaunch(h, st, f32 ? "assemble_f32" : "assemble_f64", L.asm_cnt, L.asm_cost,
+            [&] { launch_assemble<T>(P, N, h->d_asm + L.asm_off, L.asm_cnt, st); });
     klaunch(h, st, f32 ? "factor_small_f32" : "factor_small_f64", L.small_cnt, L.small_cost, [&] {
-      launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, h->opt.pivot_eps, h->opt.pivot_policy, st);
+      launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, (int)L.small_smem, eps, pol, st);
     });
     for (const Step& S : L.steps) {
-      klaunch(h, st, f32 ? "panel_rows_f32" : "panel_rows_f64", S.panel_cnt, S.panel_cost,
-              [&] { launch_panel_rows<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, st); });
+      klaunch(h, st, f32 ? "macro_diag_f32" : "macro_diag_f64", S.diag_cnt, S.diag_cost,
+              [&] { launch_macro_diag<T>(P, N, h->d_diag + S.diag_off, S.diag_cnt, eps, pol, st); });
+      klaunch(h, st, f32 ? "macro_rows_f32" : "macro_rows_f64", S.rows_cnt, S.rows_cost,
+              [&] { launch_macro_rows<T>(P, N, h->d_rows + S.rows_off, S.rows_cnt, st); });
       klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost, [&] {
-        launch_gemm_simt<T>(P, N, h->d_probs + S.prob_off, S.prob_cnt, S.tiles, h->opt.pivot_eps,
-                            h->opt.pivot_policy, st);
+        launch_gemm_simt<T>(P, N, h->d_probs + S.prob_off, h->d_tilep + S.tp_off, S.tiles, st);
       });
       if constexpr (sizeof(T) == 4)
-        klaunch(h, st, "update_tc_f32", S.tc_tiles, S.gemm_cost, [&] {
-          launch_update_tc(P, N, h->d_tc + S.tc_off, S.tc_cnt, S.tc_tiles, 1, h->d_maps, h->d_err, h->opt.pivot_eps,
-                           h->opt.pivot_policy, st);
+        klaunch(h, st, "update_tc_f32", S.tc_tiles, S.tc_cost, [&] {
+          launch_update_tc(P, N, h->d_tc + S.tc_off, h->d_tilep_tc + S.ttp_off, S.tc_tiles, 3, h->d_maps,
+                           h->d_err, st);
         });
     }
     klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", L.syrk_tiles, L.syrk_cost, [&] {
-      launch_gemm_simt<T>(P, N, h->d_probs + L.syrk_off, L.syrk_cnt, L.syrk_tiles, h->opt.pivot_eps,
-                          h->opt.pivot_policy, st);
+      launch_gemm_simt<T>(P, N, h->d_probs + L.syrk_off, h->d_tilep + L.syrk_tp_off, L.syrk_tiles, st);
     });
     if constexpr (sizeof(T) == 4)
       klaunch(h, st, "update_tc_f32", L.tsyrk_tiles, L.syrk_cost, [&] {
-        launch_update_tc(P, N, h->d_tc + L.tsyrk_off, L.tsyrk_cnt, L.tsyrk_tiles, L.tsyrk_stages, h->d_maps,
-                         h->d_err, h->opt.pivot_eps, h->opt.pivot_policy, st);
+        launch_update_tc(P, N, h->d_tc + L.tsyrk_off, h->d_tilep_tc + L.tsyrk_tp_off, L.tsyrk_tiles,
+                         L.tsyrk_stages, h->d_maps, h->d_err, st);
       });
-  }
-  {
-    const int nb = (int)h->hs.invv.size();
-    klaunch(h, st, f32 ? "invert_diag_f32" : "invert_diag_f64", nb, Cost{nb * 32.0 * 32 * 32, nb * 2.0 * 1024 * sizeof(T)},
-            [&] { launch_invert_diag<T>(P, N, h->d_inv, nb, st); });
   }
   CK(cudaGetLastError());
 }
@@ -1714,11 +1741,13 @@ extern "C" ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, i
   CUtensorMap* dmaps = nullptr;
   TcProb* dp = nullptr;
   int* derr = nullptr;
+  int32_t* dtp = nullptr;
   auto release = [&] {
     if (S) cudaFree(S);
     if (dmaps) cudaFree(dmaps);
     if (dp) cudaFree(dp);
     if (derr) cudaFree(derr);
+    if (dtp) cudaFree(dtp);
   };
   const size_t plane = (size_t)rows * ld;
   if (cudaMalloc(&S, 4 * plane * sizeof(float)) != cudaSuccess || cudaMalloc(&dmaps, 4 * sizeof(CUtensorMap)) ||
@@ -1745,9 +1774,12 @@ extern "C" ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, i
   q.M = M;
   q.N = N;
   q.tile0 = 0;
-  q.front = 0;
-  q.next_p0 = -1;
   const int64_t tiles = tc_tiles(M, N, &q.Nt);
+  if (cudaMalloc(&dtp, tiles * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(NCL_ERR_OOM, "self-test allocation failed");
+  }
   DevPlan P0{};
   DevNum<float> N0{};
   N0.L = C;
@@ -1756,9 +1788,10 @@ extern "C" ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, i
   cudaError_t e = cudaMemcpyAsync(dmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dp, &q, sizeof(q), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dtp, 0, tiles * sizeof(int32_t), st);
   if (e == cudaSuccess) {
     launch_split_rows(L, d, rows, ld, K, S, st);
-    launch_update_tc(P0, N0, dp, 1, tiles, 3, dmaps, derr, 1e-10, 0, st);
+    launch_update_tc(P0, N0, dp, dtp, tiles, 3, dmaps, derr, st);
     g_kernel_launches.fetch_add(2);
     e = cudaGetLastError();
   }

@@ -12,7 +12,7 @@
 // +-eps with the sign of its block before reordering (case (ii)), or counted
 // as a zero eigenvalue (case (i)).
 #include "runtime.h"
-#include "diag32.cuh"
+#include "pivot.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -97,9 +97,7 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const int2* __restrict__ items, double eps,
-                                                  int policy) {
-  static_assert(ASM_ROWS == PANEL_NB, "the first assembly CTA owns the first diagonal block");
+__global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const int2* __restrict__ items) {
   const int2 it = items[blockIdx.x];
   const int s = it.x, r0 = it.y;
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
@@ -142,217 +140,12 @@ __global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const 
       }
     }
   }
-  // a front factored by panels: this CTA holds the complete first diagonal
-  // block (rows [0, 32)), so it factors it now
-  if (r0 == 0 && (P.sn_flags[s] & 1)) {
-    __syncthreads();
-    if (warp == 0) factor_diag32<T>(P, N, s, 0, eps, policy, lane);
-  }
 }
 
 template <typename T>
-void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
-                     cudaStream_t st) {
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st) {
   if (count <= 0) return;
-  k_assemble<T><<<count, 256, 0, st>>>(P, N, items, eps, policy);
-}
-
-// ---------------------------------------------------------------------------
-// Small fronts: one CTA factors the whole front in shared memory.
-// Right-looking over the ncol pivots (only the L part is updated), then the
-// update block F22 -= L21 D1 L21^T straight from shared memory.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
-                                                      double eps, int policy) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int s = list[blockIdx.x];
-  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
-  const int col0 = P.sn_col0[s];
-  __shared__ int8_t sgn[64];
-  T* F = reinterpret_cast<T*>(smem_raw);
-  T* w = F + (int64_t)nrow * ncp;
-  T* Lg = N.L + P.sn_Loff[s];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int idx = threadIdx.x; idx < nrow * ncp; idx += blockDim.x) F[idx] = Lg[idx];
-  for (int k = threadIdx.x; k < ncol; k += blockDim.x) sgn[k] = P.col_sign[col0 + k];
-  __syncthreads();
-  // pivot columns: right-looking, rows over warps, pivot columns over lanes
-  for (int k = 0; k < ncol; k++) {
-    int8_t stt;
-    const T dk = static_pivot<T>(F[k * ncp + k], sgn[k], eps, policy, stt);
-    for (int i = k + 1 + threadIdx.x; i < nrow; i += blockDim.x) w[i] = F[i * ncp + k];
-    __syncthreads();
-    const T invd = T(1) / dk;
-    for (int i = k + 1 + warp; i < nrow; i += 8) {
-      const T li = w[i] * invd;
-      for (int j = k + 1 + lane; j < ncol && j <= i; j += 32) F[i * ncp + j] -= li * w[j];
-      if (lane == 0) F[i * ncp + k] = li;
-    }
-    if (threadIdx.x == 0) {
-      F[k * ncp + k] = dk;
-      N.D[col0 + k] = dk;
-      N.piv[col0 + k] = stt;
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < nrow * ncp; idx += blockDim.x) Lg[idx] = F[idx];
-  // update block F22 -= L21 D1 L21^T, 4 x 4 register tiles of the lower triangle
-  const int nb = nrow - ncol;
-  if (nb == 0) return;
-  for (int k = threadIdx.x; k < ncol; k += blockDim.x) w[k] = F[k * ncp + k];
-  __syncthreads();
-  T* Ug = N.U + P.sn_Uoff[s];
-  const int nbt = (nb + 3) >> 2;
-  const int ntile = nbt * (nbt + 1) / 2;
-  for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
-    int ta = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while (ta * (ta + 1) / 2 > t) ta--;
-    while ((ta + 1) * (ta + 2) / 2 <= t) ta++;
-    const int tb = t - ta * (ta + 1) / 2;
-    const int a0 = ta * 4, b0 = tb * 4;
-    T acc[4][4];
-#pragma unroll
-    for (int x = 0; x < 4; x++)
-#pragma unroll
-      for (int y = 0; y < 4; y++) acc[x][y] = T(0);
-    const T* ra[4];
-    const T* rb[4];
-#pragma unroll
-    for (int x = 0; x < 4; x++) {
-      ra[x] = F + (int64_t)(ncol + min(a0 + x, nb - 1)) * ncp;
-      rb[x] = F + (int64_t)(ncol + min(b0 + x, nb - 1)) * ncp;
-    }
-    for (int k = 0; k < ncol; k++) {
-      const T dk = w[k];
-      T av[4], bv[4];
-#pragma unroll
-      for (int x = 0; x < 4; x++) {
-        av[x] = ra[x][k];
-        bv[x] = rb[x][k] * dk;
-      }
-#pragma unroll
-      for (int x = 0; x < 4; x++)
-#pragma unroll
-        for (int y = 0; y < 4; y++) acc[x][y] += av[x] * bv[y];
-    }
-#pragma unroll
-    for (int x = 0; x < 4; x++) {
-      const int a = a0 + x;
-      if (a >= nb) continue;
-#pragma unroll
-      for (int y = 0; y < 4; y++) {
-        const int b = b0 + y;
-        if (b <= a) Ug[(int64_t)a * nb + b] -= acc[x][y];
-      }
-    }
-  }
-}
-
-template <typename T>
-void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, double eps,
-                         int policy, cudaStream_t st) {
-  if (count <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_factor_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SMEM + 4096);
-    attr = true;
-  }
-  k_factor_small<T><<<count, 256, SMALL_SMEM + 4096, st>>>(P, N, list, eps, policy);
-}
-
-// ---------------------------------------------------------------------------
-// Panel of a large front: pivot columns [p0, pe), pe - p0 <= PANEL_NB.
-// k_panel_diag (one CTA per front) factors the diagonal block in shared
-// memory and writes L11 and D1 back; then k_panel_rows solves the rows
-// below it, PANEL_ROWS rows per CTA, one row per thread:
-//   q = L11^-1 f_i (forward substitution), l_i = D1^-1 q.
-// (Two launches: the row CTAs must read the factored block, which no CTA
-// of the same launch may be rewriting.)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float round_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(PANEL_ROWS) k_panel_rows(DevPlan P, DevNum<T> N, const int4* __restrict__ items) {
-  __shared__ T Db[PANEL_NB][PANEL_NB + 1];
-  const int4 it = items[blockIdx.x];
-  const int s = it.x, p0 = it.y, r0 = it.z;
-  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
-  const int pe = min(p0 + PANEL_NB, ncol);
-  const int nbk = pe - p0;
-  const T* Lc = N.L + P.sn_Loff[s];
-  for (int idx = threadIdx.x; idx < PANEL_NB * PANEL_NB; idx += blockDim.x) {
-    const int i = idx / PANEL_NB, j = idx % PANEL_NB;
-    Db[i][j] = (i < nbk && j <= i) ? Lc[(int64_t)(p0 + i) * ncp + p0 + j] : T(1);
-  }
-  __syncthreads();
-  const int i = r0 + threadIdx.x;
-  if (i < nrow && i >= pe && i < r0 + PANEL_ROWS) {
-    T q[PANEL_NB];
-    T* row = N.L + P.sn_Loff[s] + (int64_t)i * ncp + p0;
-    // the 32 values of the row are 16-byte aligned (ncp % 4 == 0, p0 % 32 == 0)
-    if (nbk == PANEL_NB) {
-      if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int t = 0; t < PANEL_NB; t += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(row + t);
-          q[t] = v.x, q[t + 1] = v.y, q[t + 2] = v.z, q[t + 3] = v.w;
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < PANEL_NB; t += 2) {
-          const double2 v = *reinterpret_cast<const double2*>(row + t);
-          q[t] = v.x, q[t + 1] = v.y;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < PANEL_NB; t++) q[t] = (t < nbk) ? row[t] : T(0);
-    }
-    // forward substitution q = L11^-1 f, column by column (short dependency chains)
-#pragma unroll
-    for (int u = 0; u < PANEL_NB - 1; u++) {
-      const T qu = q[u];
-#pragma unroll
-      for (int t = u + 1; t < PANEL_NB; t++) q[t] -= Db[t][u] * qu;
-    }
-#pragma unroll
-    for (int t = 0; t < PANEL_NB; t++) {
-      q[t] = (t < nbk) ? q[t] / Db[t][t] : T(0);
-      if (t < nbk) row[t] = q[t];
-    }
-    if constexpr (sizeof(T) == 4) {
-      // split TF32 operands of the tensor-core updates: L = hi + lo and
-      // W = L D = hi + lo, zero on the padding columns
-      const int64_t so = P.sn_Soff ? P.sn_Soff[s] : -1;
-      if (N.S && so >= 0) {
-        const int64_t plane = (int64_t)nrow * ncp;
-        float* sp = N.S + so + (int64_t)i * ncp + p0;
-#pragma unroll
-        for (int t = 0; t < PANEL_NB; t++) {
-          if (p0 + t < ncp) {
-            const float l = (float)q[t];
-            const float w = (t < nbk) ? l * (float)Db[t][t] : 0.f;
-            const float lh = round_tf32(l), wh = round_tf32(w);
-            sp[t] = lh;
-            sp[plane + t] = round_tf32(l - lh);
-            sp[2 * plane + t] = wh;
-            sp[3 * plane + t] = round_tf32(w - wh);
-          }
-        }
-      }
-    }
-  }
-}
-
-template <typename T>
-void launch_panel_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st) {
-  if (count <= 0) return;
-  k_panel_rows<T><<<count, PANEL_ROWS, 0, st>>>(P, N, items);
+  k_assemble<T><<<count, 256, 0, st>>>(P, N, items);
 }
 
 // ---------------------------------------------------------------------------
@@ -376,19 +169,12 @@ __device__ __forceinline__ void decode_tile(int64_t t, int Nt, int& ti, int& tj)
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const GemmProb* __restrict__ probs,
-                                                   int nprob, double eps, int policy) {
+                                                   const int32_t* __restrict__ tile_prob) {
   constexpr int TB = GEMM_TILE, KC = 16;
   __shared__ T As[KC][TB + 1];
   __shared__ T Bs[KC][TB + 1];
-  // find the problem of this tile
   const int64_t gt = blockIdx.x;
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].tile0 <= gt) lo = mid;
-    else hi = mid - 1;
-  }
-  const GemmProb pb = probs[lo];
+  const GemmProb pb = probs[tile_prob[gt]];
   int ti, tj;
   decode_tile(gt - pb.tile0, pb.Nt, ti, tj);
   const int i0 = ti * TB, j0 = tj * TB;
@@ -436,19 +222,13 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const
       C[(int64_t)i * pb.ldc + j] -= acc[a][b];
     }
   }
-  // tile (0,0) of a trailing update holds the next panel's diagonal block,
-  // now fully updated: factor it here
-  if (gt == pb.tile0 && pb.next_p0 >= 0) {
-    __syncthreads();
-    if (threadIdx.x < 32) factor_diag32<T>(P, N, pb.front, pb.next_p0, eps, policy, threadIdx.x);
-  }
 }
 
 template <typename T>
-void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles,
-                      double eps, int policy, cudaStream_t st) {
+void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* probs, const int32_t* tile_prob,
+                      int64_t ntiles, cudaStream_t st) {
   if (ntiles <= 0) return;
-  k_gemm_simt<T><<<(unsigned)ntiles, 256, 0, st>>>(P, N, probs, nprob, eps, policy);
+  k_gemm_simt<T><<<(unsigned)ntiles, 256, 0, st>>>(P, N, probs, tile_prob);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,13 +265,9 @@ void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cud
 }
 
 #define NCL_INST(T)                                                                                     \
-  template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, int, double, int,     \
-                                   cudaStream_t);                                                       \
-  template void launch_factor_small<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, double,   \
-                                       int, cudaStream_t);                                              \
-  template void launch_panel_rows<T>(const DevPlan&, const DevNum<T>&, const int4*, int, cudaStream_t); \
-  template void launch_gemm_simt<T>(const DevPlan&, const DevNum<T>&, const GemmProb*, int, int64_t,    \
-                                    double, int, cudaStream_t);                                         \
+  template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, int, cudaStream_t);    \
+  template void launch_gemm_simt<T>(const DevPlan&, const DevNum<T>&, const GemmProb*, const int32_t*,  \
+                                    int64_t, cudaStream_t);                                             \
   template void launch_inertia<T>(const DevPlan&, const DevNum<T>&, long long*, cudaStream_t);
 NCL_INST(float)
 NCL_INST(double)

@@ -1,0 +1,434 @@
+// Dense front kernels (sm_103a): macro panels of a large front, and whole
+// small fronts.
+//
+// The pivot columns of a large front are processed MACRO_NB = 128 at a time
+// (right-looking blocked LDL^T with D diagonal and static pivoting, Section
+// 3.1).  For macro panel [q0, qe):
+//
+//   k_macro_diag  one CTA per front: the w x w diagonal block (w <= 128) is
+//                 factored in shared memory by 32-column sub-blocks (one warp
+//                 factors and inverts the sub-block in registers; all warps
+//                 form the rows below it inside the block and update the
+//                 rest of the block).  Writes L11, D1, the pivot status and
+//                 the inverses of the 32 x 32 unit diagonal sub-blocks (used
+//                 by the row kernel and by the triangular sweeps).
+//   k_macro_rows  one CTA per 64 rows below the panel: block forward
+//                 substitution X = F21 L11^-T with the inverted sub-blocks,
+//                 then L21 = X D1^-1.  For a tensor-core front it also writes
+//                 the split TF32 operands of L21 and of W = L21 D1 = X.
+//   (then the trailing update of the remaining pivot columns with K = w, on
+//    the SIMT or the tensor-core update kernel.)
+#include "runtime.h"
+#include "pivot.cuh"
+
+namespace ncl {
+
+namespace {
+
+constexpr int MNB = MACRO_NB;
+constexpr int LDM = MNB + 1;       // shared row stride of the diagonal block
+constexpr int RB = MACRO_ROWS;     // rows per row CTA
+constexpr int LDS = 33;            // stride of the 32 x 32 shared blocks
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+}  // namespace
+
+int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + 32 * LDS + 32) * esz; }
+int macro_rows_smem(int esz) { return (RB * LDM + 10 * 32 * LDS + MNB) * esz; }
+
+// LDL^T of a 32 x 32 diagonal sub-block in shared memory (row stride ld,
+// cw <= 32 valid rows) by one warp, lane i holding row i in registers:
+// right-looking with column broadcasts by shuffles.  Writes the unit lower
+// factor (strictly below the diagonal) and D on the diagonal back, D and the
+// pivot status to global memory, and the inverse of the unit lower factor
+// (identity on the padding rows) to iv (stride LDS) and to inv_out
+// (row-major 32 x 32): lane j forms column j by forward substitution in
+// registers.  Returns lane's pivot (1 on the padding).
+template <typename T>
+__device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, const int8_t* sign, T* D, int8_t* piv, T* iv,
+                                       T* inv_out, double eps, int policy, int lane) {
+  T r[32];
+#pragma unroll
+  for (int j = 0; j < 32; j++) r[j] = (j <= lane && lane < cw) ? blk[lane * ld + j] : T(0);
+  int8_t my_st = 0;
+  T my_d = T(1);
+  const int my_sign = lane < cw ? sign[lane] : 1;
+#pragma unroll
+  for (int k = 0; k < 32; k++) {
+    if (k < cw) {
+      int8_t stt;
+      const int sg = __shfl_sync(0xffffffffu, my_sign, k);
+      const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
+      const T wk = r[k];
+      const T li = wk * (T(1) / dk);
+      // branch-free update (a predicated branch around each shuffle costs a
+      // reconvergence per shuffle)
+#pragma unroll
+      for (int j = k + 1; j < 32; j++) {
+        const T wj = __shfl_sync(0xffffffffu, wk, j);
+        r[j] -= (lane >= j ? li : T(0)) * wj;
+      }
+      r[k] = lane > k ? li : (lane == k ? dk : r[k]);
+      my_d = lane == k ? dk : my_d;
+      my_st = lane == k ? stt : my_st;
+    }
+  }
+  if (lane < cw) {
+#pragma unroll
+    for (int j = 0; j < 32; j++)
+      if (j <= lane) blk[lane * ld + j] = r[j];
+    D[lane] = my_d;
+    piv[lane] = my_st;
+  }
+  __syncwarp();
+  // inverse: x_i = -sum_{k<i} L[i][k] x_k, x_lane = 1, x_i = 0 above
+  T x[32];
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    T a0 = T(0), a1 = T(0);
+#pragma unroll
+    for (int k = 0; k + 1 < i; k += 2) {
+      a0 += blk[i * ld + k] * x[k];
+      a1 += blk[i * ld + k + 1] * x[k + 1];
+    }
+    if (i & 1) a0 += blk[i * ld + i - 1] * x[i - 1];
+    x[i] = (i == lane) ? T(1) : ((i > lane && i < cw) ? -(a0 + a1) : T(0));
+  }
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    iv[i * LDS + lane] = x[i];
+    inv_out[i * 32 + lane] = x[i];
+  }
+  return my_d;
+}
+
+// q <- L^-1 q for the unit lower 32 x 32 block Ls (row stride LD; only the
+// entries strictly below the diagonal are read, and they are zero on the
+// padding): forward substitution of one row, the block read from shared
+// memory by broadcast.
+template <typename T, int LD>
+__device__ __forceinline__ void row_subst32(T (&q)[32], const T* Ls) {
+#pragma unroll
+  for (int u = 0; u < 31; u++) {
+    const T qu = q[u];
+#pragma unroll
+    for (int t = u + 1; t < 32; t++) q[t] -= Ls[t * LD + u] * qu;
+  }
+}
+
+// One CTA (256 threads) factors the w x w diagonal block (w <= 128) of a
+// macro panel in shared memory, by 32-column sub-blocks: one warp factors
+// and inverts the sub-block (factor_sub32); the rows below it inside the
+// block are solved one per thread, X = F21 L_jj^-T by forward substitution
+// and L21 = X D^-1; then all warps update the rest of the block,
+// A[r][c] -= sum_u X[r][u] L21[c][u], with register tiles (12 rows x 3
+// columns per thread).
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+                                                       double eps, int policy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);   // w x w block, row stride LDM
+  T* Xs = A + MNB * LDM;                   // X of the rows below the sub-block
+  T* Iv = Xs + (MNB - 32) * LDS;           // inverse of the unit lower sub-block
+  T* dsh = Iv + 32 * LDS;                  // pivots of the sub-block
+  const int2 it = items[blockIdx.x];
+  const int s = it.x, q0 = it.y;
+  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+  const int w = min(MNB, ncol - q0);
+  T* Lb = N.L + P.sn_Loff[s] + (int64_t)q0 * ncp + q0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int idx = tid; idx < w * MNB; idx += blockDim.x) {
+    const int r = idx / MNB, c = idx % MNB;
+    A[r * LDM + c] = (c <= r) ? Lb[(int64_t)r * ncp + c] : T(0);
+  }
+  __syncthreads();
+  constexpr int MR = (MNB - 32) / 8;   // rows per thread below a sub-block
+  constexpr int GC = (MNB - 32) / 32;  // column groups per thread
+  for (int c0 = 0; c0 < w; c0 += 32) {
+    const int cw = min(32, w - c0);
+    if (warp == 0) {
+      dsh[lane] = factor_sub32<T>(A + c0 * LDM + c0, LDM, cw, P.col_sign + col0 + q0 + c0, N.D + col0 + q0 + c0,
+                                  N.piv + col0 + q0 + c0, Iv,
+                                  N.Linv + P.sn_Ioff[s] + (int64_t)((q0 + c0) >> 5) * 1024, eps, policy, lane);
+    }
+    __syncthreads();
+    const int rb = c0 + 32;
+    const int nr = w - rb;
+    if (nr > 0) {
+      // rows below the sub-block, one per thread: X = F21 L_jj^-T by forward
+      // substitution, L21 = X D^-1 (X kept for the update)
+      if (tid < nr) {
+        T q[32];
+        T* row = A + (rb + tid) * LDM + c0;
+#pragma unroll
+        for (int t = 0; t < 32; t++) q[t] = row[t];
+        row_subst32<T, LDM>(q, A + c0 * LDM + c0);
+#pragma unroll
+        for (int t = 0; t < 32; t++) {
+          Xs[tid * LDS + t] = q[t];
+          row[t] = q[t] * (T(1) / dsh[t]);
+        }
+      }
+      __syncthreads();
+      // A[r][c] -= sum_u X[r][u] L21[c][u], rb <= c <= r < w
+      T acc[MR][GC];
+#pragma unroll
+      for (int m = 0; m < MR; m++)
+#pragma unroll
+        for (int g = 0; g < GC; g++) acc[m][g] = T(0);
+#pragma unroll 2
+      for (int u = 0; u < 32; u++) {
+        T bv[GC];
+#pragma unroll
+        for (int g = 0; g < GC; g++) bv[g] = A[min(rb + 32 * g + lane, w - 1) * LDM + c0 + u];
+#pragma unroll
+        for (int m = 0; m < MR; m++) {
+          const T a = Xs[min(warp + 8 * m, nr - 1) * LDS + u];
+#pragma unroll
+          for (int g = 0; g < GC; g++) acc[m][g] += a * bv[g];
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MR; m++) {
+        const int r = rb + warp + 8 * m;
+#pragma unroll
+        for (int g = 0; g < GC; g++) {
+          const int c = rb + 32 * g + lane;
+          if (r < w && c <= r) A[r * LDM + c] -= acc[m][g];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < w * MNB; idx += blockDim.x) {
+    const int r = idx / MNB, c = idx % MNB;
+    if (c <= r) Lb[(int64_t)r * ncp + c] = A[r * LDM + c];
+  }
+}
+
+// Rows below a macro panel, RB per CTA: for each 32-column sub-block j,
+// X_j = R_j L_jj^-T by forward substitution (one row per thread), then
+// R_i -= X_j L_ij^T for the later sub-blocks (lane = column, the rows of a
+// warp in registers); finally L21 = X D1^-1.
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_macro_rows(DevPlan P, DevNum<T> N, const int4* __restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* R = reinterpret_cast<T*>(smem_raw);   // RB rows x w columns, stride LDM
+  T* Ld = R + RB * LDM;                    // 4 unit lower diagonal sub-blocks of L11
+  T* Lo = Ld + 4 * 32 * LDS;               // 6 off-diagonal sub-blocks (i > j) of L11
+  T* dsh = Lo + 6 * 32 * LDS;              // D1
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, q0 = it.y, r0 = it.z;
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+  const int w = min(MNB, ncol - q0);
+  const int nbk = (w + 31) / 32;
+  const int nr = min(RB, nrow - r0);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  T* Lb = N.L + P.sn_Loff[s];
+  for (int i = 0; i < nbk; i++)
+    for (int j = 0; j <= i; j++) {
+      T* dst = (i == j) ? Ld + i * 32 * LDS : Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
+      for (int e = tid; e < 1024; e += blockDim.x) {
+        const int rr = e >> 5, cc = e & 31;
+        const int row = 32 * i + rr, col = 32 * j + cc;
+        dst[rr * LDS + cc] = (row < w && (i > j || cc < rr)) ? Lb[(int64_t)(q0 + row) * ncp + q0 + col] : T(0);
+      }
+    }
+  for (int c = tid; c < MNB; c += blockDim.x) dsh[c] = c < w ? N.D[col0 + q0 + c] : T(1);
+  for (int idx = tid; idx < RB * MNB; idx += blockDim.x) {
+    const int r = idx / MNB, c = idx % MNB;
+    R[r * LDM + c] = (r < nr && c < w) ? Lb[(int64_t)(r0 + r) * ncp + q0 + c] : T(0);
+  }
+  __syncthreads();
+  constexpr int KR = RB / 8;   // rows per warp in the updates (lane = column)
+  T* Rw = R + warp * LDM;      // row warp + 8 k is Rw[8 k LDM + ...]
+  for (int j = 0; j < nbk; j++) {
+    if (tid < nr) {
+      T q[32];
+      T* row = R + tid * LDM + 32 * j;
+#pragma unroll
+      for (int t = 0; t < 32; t++) q[t] = row[t];
+      row_subst32<T, LDS>(q, Ld + j * 32 * LDS);
+#pragma unroll
+      for (int t = 0; t < 32; t++) row[t] = q[t];
+    }
+    __syncthreads();
+    for (int i = j + 1; i < nbk; i++) {
+      const T* lij = Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
+      T x[KR];
+#pragma unroll
+      for (int k = 0; k < KR; k++) x[k] = T(0);
+#pragma unroll 4
+      for (int u = 0; u < 32; u++) {
+        const T b = lij[lane * LDS + u];
+#pragma unroll
+        for (int k = 0; k < KR; k++) x[k] += Rw[8 * k * LDM + 32 * j + u] * b;
+      }
+#pragma unroll
+      for (int k = 0; k < KR; k++) Rw[8 * k * LDM + 32 * i + lane] -= x[k];
+    }
+    __syncthreads();
+  }
+  // L21 = X D1^-1 (+ split operands of L21 and W = X for a tensor-core front)
+  int64_t so = -1;
+  if constexpr (sizeof(T) == 4) so = (N.S && P.sn_Soff) ? P.sn_Soff[s] : -1;
+  const int64_t plane = (int64_t)nrow * ncp;
+  const int cend = (q0 + w == ncol) ? ncp - q0 : w;   // the last panel also clears the padding columns
+  for (int j = 0; 32 * j < cend; j++) {
+    const int c = 32 * j + lane;
+    if (c >= cend) continue;
+    const T invd = c < w ? T(1) / dsh[c] : T(0);
+#pragma unroll
+    for (int k = 0; k < KR; k++) {
+      const int r = warp + 8 * k;
+      if (r >= nr) continue;
+      const T xv = c < w ? R[r * LDM + c] : T(0);
+      const T l = xv * invd;
+      if (c < w) Lb[(int64_t)(r0 + r) * ncp + q0 + c] = l;
+      if constexpr (sizeof(T) == 4) {
+        if (so >= 0) {
+          float* sp = N.S + so + (int64_t)(r0 + r) * ncp + q0 + c;
+          const float lh = tf32_round(l), wh = tf32_round(xv);
+          sp[0] = lh;
+          sp[plane] = tf32_round(l - lh);
+          sp[2 * plane] = wh;
+          sp[3 * plane] = tf32_round(xv - wh);
+        }
+      }
+    }
+  }
+}
+
+// Small fronts (ncol <= 64): one CTA factors the pivot columns of the whole
+// front in shared memory by 32-column sub-blocks, as the diagonal-block
+// kernel does: one warp factors and inverts the sub-block (factor_sub32),
+// then every thread solves rows below it by forward substitution,
+//   L21 = F21 L_jj^-T D^-1,
+// and, when a second sub-block follows, the warps update its columns.  The update
+// block F22 -= L21 D1 L21^T is left to the SIMT update kernel, which spreads
+// it over many CTAs.
+int small_front_smem(int nrow, int ncp, int esz) { return (nrow * (ncp + 1) + 2 * 32 * LDS + 96) * esz; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
+                                                      double eps, int policy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = list[blockIdx.x];
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+  const int ldf = ncp + 1;   // odd: column accesses by lanes are conflict-free
+  T* F = reinterpret_cast<T*>(smem_raw);
+  T* Iv = F + nrow * ldf;     // inverse of the sub-block (written for the solve)
+  T* Ls = Iv + 32 * LDS;      // the sub-block's unit lower factor
+  T* dsh = Ls + 32 * LDS;     // pivots
+  T* Id = dsh + 64;           // reciprocal pivots of the sub-block
+  T* Lg = N.L + P.sn_Loff[s];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int idx = tid; idx < nrow * ncp; idx += blockDim.x) F[(idx / ncp) * ldf + idx % ncp] = Lg[idx];
+  __syncthreads();
+  constexpr int RW = 8;   // rows per register batch of a warp
+  for (int c0 = 0; c0 < ncol; c0 += 32) {
+    const int cw = min(32, ncol - c0);
+    if (warp == 0) {
+      const T d = factor_sub32<T>(F + c0 * ldf + c0, ldf, cw, P.col_sign + col0 + c0, N.D + col0 + c0,
+                                  N.piv + col0 + c0, Iv, N.Linv + P.sn_Ioff[s] + (int64_t)(c0 >> 5) * 1024, eps,
+                                  policy, lane);
+      dsh[c0 + lane] = d;
+      Id[lane] = T(1) / d;
+      // the unit lower sub-block, zero above the diagonal and on the padding
+#pragma unroll 4
+      for (int u = 0; u < 32; u++) Ls[lane * LDS + u] = (u < lane && lane < cw) ? F[(c0 + lane) * ldf + c0 + u] : T(0);
+    }
+    __syncthreads();
+    // rows below the sub-block, one per thread: forward substitution with
+    // the unit lower sub-block, then L21 = X D^-1
+    const int rb = c0 + cw;
+    for (int r = rb + tid; r < nrow; r += blockDim.x) {
+      T q[32];
+      T* row = F + r * ldf + c0;
+#pragma unroll
+      for (int t = 0; t < 32; t++) q[t] = t < cw ? row[t] : T(0);
+      row_subst32<T, LDS>(q, Ls);
+#pragma unroll
+      for (int t = 0; t < 32; t++)
+        if (t < cw) row[t] = q[t] * Id[t];
+    }
+    __syncthreads();
+    // update the next sub-block's columns: F[r][c] -= sum_u L[r][u] d_u L[c][u]
+    if (c0 + 32 < ncol) {
+      const int c = c0 + 32 + lane;
+      const bool cok = c < ncol;
+      for (int r0 = c0 + 32 + warp * RW; r0 < nrow; r0 += 8 * RW) {
+        T acc[RW];
+#pragma unroll
+        for (int m = 0; m < RW; m++) acc[m] = T(0);
+#pragma unroll 4
+        for (int u = 0; u < 32; u++) {
+          const T b = F[min(c, ncol - 1) * ldf + c0 + u] * dsh[c0 + u];
+#pragma unroll
+          for (int m = 0; m < RW; m++) acc[m] += F[min(r0 + m, nrow - 1) * ldf + c0 + u] * b;
+        }
+#pragma unroll
+        for (int m = 0; m < RW; m++)
+          if (cok && r0 + m < nrow && c <= r0 + m) F[(r0 + m) * ldf + c] -= acc[m];
+      }
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < nrow * ncp; idx += blockDim.x) Lg[idx] = F[(idx / ncp) * ldf + idx % ncp];
+}
+
+template <typename T>
+void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, int smem_bytes,
+                         double eps, int policy, cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_factor_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SMEM_MAX);
+    attr = true;
+  }
+  k_factor_small<T><<<count, 256, smem_bytes, st>>>(P, N, list, eps, policy);
+}
+
+template void launch_factor_small<float>(const DevPlan&, const DevNum<float>&, const int32_t*, int, int, double,
+                                         int, cudaStream_t);
+template void launch_factor_small<double>(const DevPlan&, const DevNum<double>&, const int32_t*, int, int, double,
+                                          int, cudaStream_t);
+
+template <typename T>
+void launch_macro_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
+                       cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  const int smem = macro_diag_smem((int)sizeof(T));
+  if (!attr) {
+    cudaFuncSetAttribute(k_macro_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  k_macro_diag<T><<<count, 256, smem, st>>>(P, N, items, eps, policy);
+}
+
+template <typename T>
+void launch_macro_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  const int smem = macro_rows_smem((int)sizeof(T));
+  if (!attr) {
+    cudaFuncSetAttribute(k_macro_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  k_macro_rows<T><<<count, 256, smem, st>>>(P, N, items);
+}
+
+template void launch_macro_diag<float>(const DevPlan&, const DevNum<float>&, const int2*, int, double, int,
+                                       cudaStream_t);
+template void launch_macro_diag<double>(const DevPlan&, const DevNum<double>&, const int2*, int, double, int,
+                                        cudaStream_t);
+template void launch_macro_rows<float>(const DevPlan&, const DevNum<float>&, const int4*, int, cudaStream_t);
+template void launch_macro_rows<double>(const DevPlan&, const DevNum<double>&, const int4*, int, cudaStream_t);
+
+}  // namespace ncl

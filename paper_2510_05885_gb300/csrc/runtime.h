@@ -9,11 +9,13 @@ namespace ncl {
 
 // Tile/chunk constants shared by the launch planner and the kernels.
 constexpr int ASM_ROWS = 32;      // front rows per assembly CTA
-constexpr int PANEL_NB = 32;      // pivot columns per panel
-constexpr int PANEL_ROWS = 128;   // rows below the panel per CTA
+constexpr int PANEL_NB = 32;      // pivot columns of a diagonal sub-block
+constexpr int MACRO_NB = 128;     // pivot columns per macro panel of a large front
+constexpr int MACRO_ROWS = 64;    // rows below the macro panel per CTA
 constexpr int GEMM_TILE = 64;     // SIMT update tile (rows x cols)
 constexpr int SOLVE_ROWS = 64;    // below rows per solve CTA
-constexpr int SMALL_SMEM = 64 * 1024;  // dynamic smem limit of a small front
+constexpr int SMALL_SMEM = 64 * 1024;      // front bytes (nrow x ncolp) of a small front, at most
+constexpr int SMALL_SMEM_MAX = 96 * 1024;  // dynamic smem limit of the small-front kernel
 
 // Pointers into device copies of the symbolic plan.
 struct DevPlan {
@@ -86,7 +88,8 @@ struct DevNum {
 };
 
 // A dense update C -= A diag(d) B^T restricted to the lower part, over a
-// set of fronts: problems are concatenated; each owns a run of tiles.
+// set of fronts: problems are concatenated; each owns a run of tiles, and a
+// per-tile array gives each CTA its problem.
 struct GemmProb {
   int64_t c_off;     // C element offset (in L or U storage)
   int64_t a_off;     // A = rows of a factor block
@@ -96,9 +99,7 @@ struct GemmProb {
   int32_t M, N, K;   // C is M x N (lower part: row + diag_shift >= col), inner dim K
   int32_t c_in_u;    // 1: C lives in U storage, 0: in L storage
   int32_t Nt;        // column tiles
-  int64_t tile0;     // first global tile of this problem
-  int32_t front;     // supernode of the front
-  int32_t next_p0;   // >= 0: after its tile (0,0) the CTA factors the diagonal block at next_p0
+  int64_t tile0;     // first tile of this problem in its launch
 };
 
 // One dense update handled by the tensor-core kernel (tc_update.cu):
@@ -108,11 +109,10 @@ struct TcProb {
   int64_t c_off;
   int64_t tile0;
   int32_t ldc, c_in_u, map, row_a, row_b, k0, nk, M, N, Nt;
-  int32_t front, next_p0;   // as in GemmProb
 };
 
-void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, int nprob, int64_t ntiles,
-                      int stages, const CUtensorMap* maps, int* err, double eps, int policy, cudaStream_t st);
+void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, const int32_t* tile_prob,
+                      int64_t ntiles, int stages, const CUtensorMap* maps, int* err, cudaStream_t st);
 bool tc_encode_maps(const float* split, int64_t rows, int64_t ld, CUtensorMap* out4, std::string* why);
 int64_t tc_tiles(int M, int N, int* Nt_out);
 int tc_smem_bytes();
@@ -123,24 +123,26 @@ void launch_kkt_values(const DevPlan& P, const double* const* vals, const double
                        double* Klow, cudaStream_t st);
 void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st);
 template <typename T>
-void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
-                     cudaStream_t st);
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st);
 template <typename T>
-void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count,
+void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, int smem_bytes,
                          double eps, int policy, cudaStream_t st);
 template <typename T>
-void launch_panel_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps,
-                       int policy, cudaStream_t st);
+void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* probs, const int32_t* tile_prob,
+                      int64_t ntiles, cudaStream_t st);
+
+// launchers (panel.cu)
+int small_front_smem(int nrow, int ncp, int esz);
+int macro_diag_smem(int esz);
+int macro_rows_smem(int esz);
 template <typename T>
-void launch_panel_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st);
+void launch_macro_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
+                       cudaStream_t st);
 template <typename T>
-void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* probs, int nprob, int64_t ntiles,
-                      double eps, int policy, cudaStream_t st);
+void launch_macro_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st);
 template <typename T>
 void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st);
 
-template <typename T>
-void launch_invert_diag(const DevPlan& P, const DevNum<T>& N, const int2* blocks, int count, cudaStream_t st);
 
 // launchers (solve.cu)
 template <typename T>

@@ -63,48 +63,6 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
 }
 
 // ---------------------------------------------------------------------------
-// Inverses of the unit lower triangular 32 x 32 diagonal blocks of each
-// pivot block L11, computed once after the factorisation so that each step
-// of the blocked triangular sweeps is a dependency-free 32 x 32 product.
-// One warp per block: lane j forms column j of X = L_blk^-1 by forward
-// substitution, x_i = -sum_{k<i} L[i][k] x_k (x_j = 1, x_i = 0 for i < j).
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(128) k_invert_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ blocks,
-                                                     int count) {
-  __shared__ T Ls[4][32][33];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x * 4 + warp;
-  if (b >= count) return;
-  const int2 it = blocks[b];
-  const int s = it.x, kb = it.y;
-  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
-  const int bw = min(32, ncol - kb);
-  const T* Lb = N.L + P.sn_Loff[s];
-  for (int i = 0; i < 32; i++) {
-    const T v = (i < bw && lane < i) ? Lb[(int64_t)(kb + i) * ncp + kb + lane] : T(0);
-    Ls[warp][i][lane] = v;
-  }
-  __syncwarp();
-  T x[32];
-#pragma unroll
-  for (int i = 0; i < 32; i++) {
-    T acc = T(0);
-#pragma unroll
-    for (int k = 0; k < i; k++) acc += Ls[warp][i][k] * x[k];
-    x[i] = (i == lane) ? T(1) : (i > lane ? -acc : T(0));
-  }
-  T* out = N.Linv + P.sn_Ioff[s] + (int64_t)(kb / 32) * 1024;
-#pragma unroll
-  for (int i = 0; i < 32; i++) out[i * 32 + lane] = x[i];
-}
-
-template <typename T>
-void launch_invert_diag(const DevPlan& P, const DevNum<T>& N, const int2* blocks, int count, cudaStream_t st) {
-  if (count > 0) k_invert_diag<T><<<(count + 3) / 4, 128, 0, st>>>(P, N, blocks, count);
-}
-
-// ---------------------------------------------------------------------------
 // forward: pivot block of supernode s (one CTA): pull the children's updates
 // that land on the pivot rows, then L11 y = t by 32-column blocks: warp 0
 // solves the 32 x 32 diagonal block with shuffles (its row of the block
@@ -572,7 +530,6 @@ void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64
 }
 
 #define NCL_INST(T)                                                                                               \
-  template void launch_invert_diag<T>(const DevPlan&, const DevNum<T>&, const int2*, int, cudaStream_t);          \
   template void launch_perm_in<T>(const DevPlan&, T*, const double*, int64_t, int, cudaStream_t);                 \
   template void launch_perm_out<T>(const DevPlan&, const T*, double*, int64_t, int, int, cudaStream_t);           \
   template void launch_fwd_diag<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, T*, T*, int,            \

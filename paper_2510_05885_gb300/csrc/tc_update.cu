@@ -8,8 +8,8 @@
 // x_lo = the remainder rounded to TF32), and the product is accumulated in
 // FP32 as A_hi B_hi + A_hi B_lo + A_lo B_hi, which keeps FP32-level accuracy
 // (the dropped A_lo B_lo term is about 2^-22 relative).  The split operands
-// L_hi, L_lo, W_hi, W_lo (W = L D) are written by the panel kernel next to
-// L, so this kernel is a plain TMA -> tcgen05.mma -> TMEM -> epilogue.
+// L_hi, L_lo, W_hi, W_lo (W = L D) are written by the macro-panel row kernel
+// next to L, so this kernel is a plain TMA -> tcgen05.mma -> TMEM -> epilogue.
 //
 // One CTA computes one 128 x 128 tile of C: thread 0 issues TMA loads
 // (128-byte swizzle, 3-stage mbarrier pipeline), thread 32 issues the MMAs
@@ -19,7 +19,6 @@
 // is bounded: on a timeout the kernel sets an error flag, skips the update,
 // frees its TMEM and returns.
 #include "runtime.h"
-#include "diag32.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -156,9 +155,9 @@ __device__ __forceinline__ void decode_lower_tile(int64_t t, int Nt, int& ti, in
   }
 }
 
-__global__ void __launch_bounds__(128) k_update_tc(DevPlan P, DevNum<float> Nm, const TcProb* __restrict__ probs,
-                                                   int nprob, const CUtensorMap* __restrict__ maps, int* err,
-                                                   int stages, double eps, int policy) {
+__global__ void __launch_bounds__(128) k_update_tc(DevNum<float> Nm, const TcProb* __restrict__ probs,
+                                                   const int32_t* __restrict__ tile_prob,
+                                                   const CUtensorMap* __restrict__ maps, int* err, int stages) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment of the shared-window address (the swizzle atom)
   unsigned char* sb = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -171,13 +170,7 @@ __global__ void __launch_bounds__(128) k_update_tc(DevPlan P, DevNum<float> Nm, 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // problem and tile of this CTA
   const int64_t gt = blockIdx.x;
-  int lo = 0, hi = nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].tile0 <= gt) lo = mid;
-    else hi = mid - 1;
-  }
-  const TcProb pb = probs[lo];
+  const TcProb pb = probs[tile_prob[gt]];
   int ti, tj;
   decode_lower_tile(gt - pb.tile0, pb.Nt, ti, tj);
   const int i0 = ti * TC_M, j0 = tj * TC_N;
@@ -286,12 +279,6 @@ __global__ void __launch_bounds__(128) k_update_tc(DevPlan P, DevNum<float> Nm, 
       }
       __syncwarp();
     }
-    // tile (0,0) of a trailing update holds the next panel's diagonal
-    // block, now fully updated: factor it here
-    if (gt == pb.tile0 && pb.next_p0 >= 0) {
-      __syncthreads();
-      if (warp == 0) factor_diag32<float>(P, Nm, pb.front, pb.next_p0, eps, policy, lane);
-    }
   }
   tc_fence_before();
   __syncthreads();
@@ -360,8 +347,9 @@ int64_t tc_tiles(int M, int N, int* Nt_out) {
   return (int64_t)Nt * (Nt + 1) / 2 + (int64_t)(Mt - Nt) * Nt;
 }
 
-void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, int nprob, int64_t ntiles,
-                      int stages, const CUtensorMap* maps, int* err, double eps, int policy, cudaStream_t st) {
+void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, const int32_t* tile_prob,
+                      int64_t ntiles, int stages, const CUtensorMap* maps, int* err, cudaStream_t st) {
+  (void)P;
   if (ntiles <= 0) return;
   static bool attr = false;
   if (!attr) {
@@ -369,7 +357,7 @@ void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* pr
     attr = true;
   }
   stages = stages < 1 ? 1 : (stages > TC_STAGES ? TC_STAGES : stages);
-  k_update_tc<<<(unsigned)ntiles, 128, tc_smem_for(stages), st>>>(P, N, probs, nprob, maps, err, stages, eps, policy);
+  k_update_tc<<<(unsigned)ntiles, 128, tc_smem_for(stages), st>>>(N, probs, tile_prob, maps, err, stages);
 }
 
 void launch_split_rows(const float* L, const float* d, int rows, int ld, int K, float* S, cudaStream_t st) {
