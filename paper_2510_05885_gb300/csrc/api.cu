@@ -114,6 +114,8 @@ std::atomic<int64_t> g_kernel_launches{0};
 struct HostSched {
   std::vector<int2> asmv, belowv;
   std::vector<int32_t> smallv, listv;
+  std::vector<int32_t> asm_cptr;          // per assembly item: its run of child row ranges
+  std::vector<int4> asm_cran;             // (child, alo, ahi, 0)
   std::vector<int4> rowsv;
   std::vector<int2> diagv;
   std::vector<GemmProb> probv;
@@ -154,6 +156,8 @@ struct ncl_kkt_s {
   std::vector<Level> levels;
   HostSched hs;
   int2* d_asm = nullptr;
+  int32_t* d_asm_cptr = nullptr;
+  int4* d_asm_cran = nullptr;
   int32_t* d_small = nullptr;
   int4* d_rows = nullptr;
   int2* d_diag = nullptr;
@@ -281,6 +285,7 @@ void build_schedule(ncl_kkt_s* h) {
   hs.sn_Soff.assign(P.ns, -1);
   hs.sn_flags.assign(P.ns, 0);
   hs.sn_Ioff.assign(P.ns + 1, 0);
+  hs.asm_cptr.assign(1, 0);
   for (int32_t s = 0; s < P.ns; s++)
     hs.sn_Ioff[s + 1] = hs.sn_Ioff[s] + (int64_t)((P.sn_ncol[s] + 31) / 32) * 1024;
   // problems of one launch are pushed consecutively; each launch's tiles map
@@ -322,7 +327,21 @@ void build_schedule(ncl_kkt_s* h) {
     for (int32_t k = P.level_ptr[l]; k < P.level_ptr[l + 1]; k++) {
       const int32_t s = P.level_list[k];
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
-      for (int r0 = 0; r0 < nrow; r0 += ASM_ROWS) asmv.push_back(make_int2(s, r0));
+      for (int r0 = 0; r0 < nrow; r0 += ASM_ROWS) {
+        asmv.push_back(make_int2(s, r0));
+        // rows [alo, ahi) of each child's update block that land on the
+        // item's rows [r0, r1) (the relative map is increasing)
+        const int r1 = std::min(r0 + ASM_ROWS, nrow);
+        for (int32_t k2 = P.child_ptr[s]; k2 < P.child_ptr[s + 1]; k2++) {
+          const int32_t c = P.child_list[k2];
+          const int32_t* rel = P.relmap.data() + P.relmap_off[c];
+          const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
+          const int alo = (int)(std::lower_bound(rel, rel + nbc, r0) - rel);
+          const int ahi = (int)(std::lower_bound(rel, rel + nbc, r1) - rel);
+          if (ahi > alo) hs.asm_cran.push_back(make_int4(c, alo, ahi, 0));
+        }
+        hs.asm_cptr.push_back((int32_t)hs.asm_cran.size());
+      }
       listv.push_back(s);
       for (int a0 = 0; a0 < nrow - ncol; a0 += SOLVE_ROWS) belowv.push_back(make_int2(s, a0));
       const bool is_small = ncol <= 64 && nrow <= 512 && (int64_t)nrow * ncp * (int64_t)esz <= SMALL_SMEM;
@@ -499,8 +518,19 @@ void build_schedule(ncl_kkt_s* h) {
             bad("assembly map");
       }
     }
-    for (const int2& it : asmv)
+    if (hs.asm_cptr.size() != asmv.size() + 1) bad("assembly child ranges");
+    for (size_t i = 0; i < asmv.size(); i++) {
+      const int2 it = asmv[i];
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x]) bad("assembly item");
+      if (hs.asm_cptr[i] > hs.asm_cptr[i + 1] || hs.asm_cptr[i + 1] > (int32_t)hs.asm_cran.size())
+        bad("assembly child ranges");
+      for (int32_t e = hs.asm_cptr[i]; e < hs.asm_cptr[i + 1]; e++) {
+        const int4 cr = hs.asm_cran[e];
+        if (cr.x < 0 || cr.x >= P.ns || P.sn_parent[cr.x] != it.x || cr.y < 0 || cr.y >= cr.z ||
+            cr.z > P.sn_nrow[cr.x] - P.sn_ncol[cr.x])
+          bad("assembly child ranges");
+      }
+    }
     for (const int2& it : belowv)
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x] - P.sn_ncol[it.x]) bad("solve item");
     for (int32_t s : smallv)
@@ -678,6 +708,8 @@ void build_device(ncl_kkt_s* h) {
 
   HostSched& hs = h->hs;
   h->d_asm = h->upload(hs.asmv);
+  h->d_asm_cptr = h->upload(hs.asm_cptr);
+  h->d_asm_cran = h->upload(hs.asm_cran);
   h->d_small = h->upload(hs.smallv);
   h->d_rows = h->upload(hs.rowsv);
   h->d_diag = h->upload(hs.diagv);
@@ -779,7 +811,9 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
   const int pol = h->opt.pivot_policy;
   for (const Level& L : h->levels) {
     klaunch(h, st, f32 ? "assemble_f32" : "assemble_f64", L.asm_cnt, L.asm_cost,
-            [&] { launch_assemble<T>(P, N, h->d_asm + L.asm_off, L.asm_cnt, st); });
+            [&] {
+              launch_assemble<T>(P, N, h->d_asm + L.asm_off, h->d_asm_cptr + L.asm_off, h->d_asm_cran, L.asm_cnt, st);
+            });
     klaunch(h, st, f32 ? "factor_small_f32" : "factor_small_f64", L.small_cnt, L.small_cost, [&] {
       launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, (int)L.small_smem, eps, pol, st);
     });

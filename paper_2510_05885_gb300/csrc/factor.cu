@@ -86,18 +86,10 @@ void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knor
 // blocks child by child (a child's rows map to distinct parent rows, so the
 // threads of one child never collide; children are added in a fixed order).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t v) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (a[mid] < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+                                                  const int32_t* __restrict__ cptr, const int4* __restrict__ cran) {
   const int2 it = items[blockIdx.x];
   const int s = it.x, r0 = it.y;
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
@@ -119,33 +111,51 @@ __global__ void __launch_bounds__(256) k_assemble(DevPlan P, DevNum<T> N, const 
     for (int64_t q = q0 + (threadIdx.x & 31); q < q1; q += 32)
       Lb[(int64_t)r * ncp + P.amap_col[q]] = (T)N.Klow[P.amap_src[q]];
   }
-  // children
+  // children, in a fixed order: the rows [alo, ahi) of child c's update
+  // block land on this CTA's rows (ranges found on the host).  Loads are
+  // batched four per lane before the read-modify-writes: the targets of one
+  // child row are distinct, and each warp owns whole rows.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
+  for (int e = cptr[blockIdx.x]; e < cptr[blockIdx.x + 1]; e++) {
     __syncthreads();
-    const int c = P.child_list[k];
+    const int4 cr = cran[e];
+    const int c = cr.x, alo = cr.y, ahi = cr.z;
     const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
     const int32_t* rel = P.relmap + P.relmap_off[c];
     const T* Uc = N.U + P.sn_Uoff[c];
-    const int alo = lower_bound_i32(rel, nbc, r0);
-    const int ahi = lower_bound_i32(rel, nbc, r1);
     for (int a = alo + warp; a < ahi; a += nw) {
       const int ra = rel[a];
       const T* urow = Uc + (int64_t)a * nbc;
-      for (int b = lane; b <= a; b += 32) {
-        const int rb = rel[b];
-        const T v = urow[b];
-        if (rb < ncol) Lb[(int64_t)ra * ncp + rb] += v;
-        else Ub[(int64_t)(ra - ncol) * nb + (rb - ncol)] += v;
+      T* lrow = Lb + (int64_t)ra * ncp;
+      T* urow_p = ra >= ncol ? Ub + (int64_t)(ra - ncol) * nb - ncol : Ub;   // indexed by rb >= ncol
+      for (int b0 = 0; b0 <= a; b0 += 128) {
+        int rb[4];
+        T v[4], old[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          const int b = b0 + lane + 32 * t;
+          rb[t] = b <= a ? rel[b] : -1;
+          v[t] = b <= a ? urow[b] : T(0);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+          if (rb[t] >= 0) old[t] = rb[t] < ncol ? lrow[rb[t]] : urow_p[rb[t]];
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+          if (rb[t] >= 0) {
+            if (rb[t] < ncol) lrow[rb[t]] = old[t] + v[t];
+            else urow_p[rb[t]] = old[t] + v[t];
+          }
       }
     }
   }
 }
 
 template <typename T>
-void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st) {
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
+                     int count, cudaStream_t st) {
   if (count <= 0) return;
-  k_assemble<T><<<count, 256, 0, st>>>(P, N, items);
+  k_assemble<T><<<count, 256, 0, st>>>(P, N, items, cptr, cran);
 }
 
 // ---------------------------------------------------------------------------
@@ -155,7 +165,7 @@ void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, in
 __device__ __forceinline__ void decode_tile(int64_t t, int Nt, int& ti, int& tj) {
   const int64_t tri = (int64_t)Nt * (Nt + 1) / 2;
   if (t < tri) {
-    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while ((int64_t)a * (a + 1) / 2 > t) a--;
     while ((int64_t)(a + 1) * (a + 2) / 2 <= t) a++;
     ti = a;
@@ -188,22 +198,37 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const
   for (int a = 0; a < 4; a++)
 #pragma unroll
     for (int b = 0; b < 4; b++) acc[a][b] = T(0);
+  // the next K chunk is fetched into registers while the current one is
+  // multiplied (thread: k = kk, rows rr + 16 q of A and of B)
+  const int kk = threadIdx.x & 15, rr = threadIdx.x >> 4;
+  T fa[4], fb[4];
+  auto fetch = [&](int k0) {
+    const int k = k0 + kk;
+    const bool kin = k < pb.K;
+    const T dk = kin ? d[k] : T(0);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int ia = i0 + rr + 16 * q, jb = j0 + rr + 16 * q;
+      fa[q] = (ia < pb.M && kin) ? A[(int64_t)ia * pb.lda + k] : T(0);
+      fb[q] = (jb < pb.N && kin) ? B[(int64_t)jb * pb.lda + k] * dk : T(0);
+    }
+  };
+  fetch(0);
   for (int k0 = 0; k0 < pb.K; k0 += KC) {
-    for (int idx = threadIdx.x; idx < TB * KC; idx += 256) {
-      const int r = idx / KC, kk = idx % KC;
-      const int k = k0 + kk;
-      const int ia = i0 + r, jb = j0 + r;
-      As[kk][r] = (ia < pb.M && k < pb.K) ? A[(int64_t)ia * pb.lda + k] : T(0);
-      Bs[kk][r] = (jb < pb.N && k < pb.K) ? B[(int64_t)jb * pb.lda + k] * d[k] : T(0);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      As[kk][rr + 16 * q] = fa[q];
+      Bs[kk][rr + 16 * q] = fb[q];
     }
     __syncthreads();
+    if (k0 + KC < pb.K) fetch(k0 + KC);
 #pragma unroll
-    for (int kk = 0; kk < KC; kk++) {
+    for (int k2 = 0; k2 < KC; k2++) {
       T av[4], bv[4];
 #pragma unroll
-      for (int a = 0; a < 4; a++) av[a] = As[kk][ty + 16 * a];
+      for (int a = 0; a < 4; a++) av[a] = As[k2][ty + 16 * a];
 #pragma unroll
-      for (int b = 0; b < 4; b++) bv[b] = Bs[kk][tx + 16 * b];
+      for (int b = 0; b < 4; b++) bv[b] = Bs[k2][tx + 16 * b];
 #pragma unroll
       for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -211,15 +236,24 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const
     }
     __syncthreads();
   }
+  // all 16 loads of C first, then the stores
+  T cv[4][4];
 #pragma unroll
   for (int a = 0; a < 4; a++) {
     const int i = i0 + ty + 16 * a;
-    if (i >= pb.M) continue;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
       const int j = j0 + tx + 16 * b;
-      if (j >= pb.N || j > i) continue;
-      C[(int64_t)i * pb.ldc + j] -= acc[a][b];
+      cv[a][b] = (i < pb.M && j < pb.N && j <= i) ? C[(int64_t)i * pb.ldc + j] : T(0);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int i = i0 + ty + 16 * a;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const int j = j0 + tx + 16 * b;
+      if (i < pb.M && j < pb.N && j <= i) C[(int64_t)i * pb.ldc + j] = cv[a][b] - acc[a][b];
     }
   }
 }
@@ -265,7 +299,8 @@ void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cud
 }
 
 #define NCL_INST(T)                                                                                     \
-  template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, int, cudaStream_t);    \
+  template void launch_assemble<T>(const DevPlan&, const DevNum<T>&, const int2*, const int32_t*,       \
+                                   const int4*, int, cudaStream_t);                                     \
   template void launch_gemm_simt<T>(const DevPlan&, const DevNum<T>&, const GemmProb*, const int32_t*,  \
                                     int64_t, cudaStream_t);                                             \
   template void launch_inertia<T>(const DevPlan&, const DevNum<T>&, long long*, cudaStream_t);

@@ -38,6 +38,29 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 }  // namespace
 
+// Copy a rows x cols tile from global memory (row stride lds) into shared
+// memory (row stride ldd), zero where keep(r, c) is false, with 8 loads in
+// flight per thread before the shared stores.
+template <typename T, typename Keep>
+__device__ __forceinline__ void load_tile(T* dst, int ldd, const T* src, int64_t lds, int rows, int cols, Keep keep) {
+  const int n = rows * cols;
+  for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int idx = base + k * blockDim.x;
+      const int r = idx / cols, c = idx - r * cols;
+      v[k] = (idx < n && keep(r, c)) ? src[(int64_t)r * lds + c] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int idx = base + k * blockDim.x;
+      const int r = idx / cols, c = idx - r * cols;
+      if (idx < n) dst[r * ldd + c] = v[k];
+    }
+  }
+}
+
 int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + 32 * LDS + 32) * esz; }
 int macro_rows_smem(int esz) { return (RB * LDM + 10 * 32 * LDS + MNB) * esz; }
 
@@ -142,10 +165,7 @@ __global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, c
   const int w = min(MNB, ncol - q0);
   T* Lb = N.L + P.sn_Loff[s] + (int64_t)q0 * ncp + q0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int idx = tid; idx < w * MNB; idx += blockDim.x) {
-    const int r = idx / MNB, c = idx % MNB;
-    A[r * LDM + c] = (c <= r) ? Lb[(int64_t)r * ncp + c] : T(0);
-  }
+  load_tile(A, LDM, Lb, ncp, w, MNB, [&](int r, int c) { return c <= r; });
   __syncthreads();
   constexpr int MR = (MNB - 32) / 8;   // rows per thread below a sub-block
   constexpr int GC = (MNB - 32) / 32;  // column groups per thread
@@ -233,17 +253,12 @@ __global__ void __launch_bounds__(256, 1) k_macro_rows(DevPlan P, DevNum<T> N, c
   for (int i = 0; i < nbk; i++)
     for (int j = 0; j <= i; j++) {
       T* dst = (i == j) ? Ld + i * 32 * LDS : Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
-      for (int e = tid; e < 1024; e += blockDim.x) {
-        const int rr = e >> 5, cc = e & 31;
-        const int row = 32 * i + rr, col = 32 * j + cc;
-        dst[rr * LDS + cc] = (row < w && (i > j || cc < rr)) ? Lb[(int64_t)(q0 + row) * ncp + q0 + col] : T(0);
-      }
+      const int rows = min(32, w - 32 * i);
+      load_tile(dst, LDS, Lb + (int64_t)(q0 + 32 * i) * ncp + q0 + 32 * j, ncp, 32, 32,
+                [&](int rr, int cc) { return rr < rows && (i > j || cc < rr); });
     }
   for (int c = tid; c < MNB; c += blockDim.x) dsh[c] = c < w ? N.D[col0 + q0 + c] : T(1);
-  for (int idx = tid; idx < RB * MNB; idx += blockDim.x) {
-    const int r = idx / MNB, c = idx % MNB;
-    R[r * LDM + c] = (r < nr && c < w) ? Lb[(int64_t)(r0 + r) * ncp + q0 + c] : T(0);
-  }
+  load_tile(R, LDM, Lb + (int64_t)r0 * ncp + q0, ncp, RB, MNB, [&](int r, int c) { return r < nr && c < w; });
   __syncthreads();
   constexpr int KR = RB / 8;   // rows per warp in the updates (lane = column)
   T* Rw = R + warp * LDM;      // row warp + 8 k is Rw[8 k LDM + ...]
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, co
   T* Id = dsh + 64;           // reciprocal pivots of the sub-block
   T* Lg = N.L + P.sn_Loff[s];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int idx = tid; idx < nrow * ncp; idx += blockDim.x) F[(idx / ncp) * ldf + idx % ncp] = Lg[idx];
+  load_tile(F, ldf, Lg, ncp, nrow, ncp, [](int, int) { return true; });
   __syncthreads();
   constexpr int RW = 8;   // rows per register batch of a warp
   for (int c0 = 0; c0 < ncol; c0 += 32) {

@@ -123,7 +123,8 @@ void launch_kkt_values(const DevPlan& P, const double* const* vals, const double
                        double* Klow, cudaStream_t st);
 void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st);
 template <typename T>
-void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st);
+void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
+                     int count, cudaStream_t st);
 template <typename T>
 void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, int smem_bytes,
                          double eps, int policy, cudaStream_t st);

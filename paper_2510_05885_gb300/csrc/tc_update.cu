@@ -143,7 +143,7 @@ __device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, float (&v)[32]) {
 __device__ __forceinline__ void decode_lower_tile(int64_t t, int Nt, int& ti, int& tj) {
   const int64_t tri = (int64_t)Nt * (Nt + 1) / 2;
   if (t < tri) {
-    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while ((int64_t)a * (a + 1) / 2 > t) a--;
     while ((int64_t)(a + 1) * (a + 2) / 2 <= t) a++;
     ti = a;
