@@ -44,7 +44,6 @@ struct CudaError {
     if (e_ != cudaSuccess) throw CudaError{e_, #x};            \
   } while (0)
 
-constexpr int MAX_RHS_SWEEP = 8;
 // In the FP32 path the update block F22 -= L21 D1 L21^T of a front with at
 // least TC_MIN_K pivots runs on the tensor cores; shorter inner dimensions,
 // and the 32-wide trailing updates of the panels, do not amortise the fixed
@@ -91,8 +90,9 @@ struct Level {
   int64_t tsyrk_tiles = 0;
   int64_t tsyrk_tp_off = 0;
   int tsyrk_stages = 1;
-  int64_t list_off = 0;   // all supernodes of the level (solve)
-  int list_cnt = 0;
+  int64_t chain_off = 0;  // block-row items of the level (sweeps)
+  int chain_cnt = 0;
+  int64_t chain_smem = 0; // dynamic shared memory of the chained sweep kernels
   int64_t below_off = 0;  // (s, a0) solve items
   int below_cnt = 0;
   Cost asm_cost, small_cost, syrk_cost, fdiag_cost, fbelow_cost, bdiag_cost, bbelow_cost;
@@ -113,7 +113,12 @@ std::atomic<int64_t> g_kernel_launches{0};
 
 struct HostSched {
   std::vector<int2> asmv, belowv;
-  std::vector<int32_t> smallv, listv;
+  std::vector<int32_t> smallv;
+  std::vector<int4> chainv;               // (supernode, first block-row, first 32-row block, 0) per block-row (sweeps)
+  std::vector<int32_t> chain_pptr;        // per global 32-row pivot block: its run of child ranges
+  std::vector<int4> chain_pran;           // (child, alo, ahi, 0): child W entries landing on the block
+  int64_t nblocks = 0;                    // 32-row pivot blocks in all
+  int64_t nbrows = 0;                     // block-rows of the chained sweeps in all
   std::vector<int32_t> asm_cptr;          // per assembly item: its run of child row ranges
   std::vector<int4> asm_cran;             // (child, alo, ahi, 0)
   std::vector<int4> rowsv;
@@ -164,7 +169,10 @@ struct ncl_kkt_s {
   GemmProb* d_probs = nullptr;
   int32_t* d_tilep = nullptr;
   int32_t* d_tilep_tc = nullptr;
-  int32_t* d_lists = nullptr;
+  int4* d_chain = nullptr;
+  int32_t* d_chain_pptr = nullptr;
+  int4* d_chain_pran = nullptr;
+  int* d_chain_sync = nullptr;              // tickets (fwd, bwd) then flags (fwd, bwd) of the pivot blocks
   int2* d_below = nullptr;
   // solve workspace
   void* xp = nullptr;
@@ -277,7 +285,6 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<int2>& asmv = hs.asmv;
   std::vector<int2>& belowv = hs.belowv;
   std::vector<int32_t>& smallv = hs.smallv;
-  std::vector<int32_t>& listv = hs.listv;
   std::vector<int4>& rowsv = hs.rowsv;
   std::vector<int2>& diagv = hs.diagv;
   std::vector<GemmProb>& probv = hs.probv;
@@ -286,6 +293,7 @@ void build_schedule(ncl_kkt_s* h) {
   hs.sn_flags.assign(P.ns, 0);
   hs.sn_Ioff.assign(P.ns + 1, 0);
   hs.asm_cptr.assign(1, 0);
+  hs.chain_pptr.assign(1, 0);
   for (int32_t s = 0; s < P.ns; s++)
     hs.sn_Ioff[s + 1] = hs.sn_Ioff[s] + (int64_t)((P.sn_ncol[s] + 31) / 32) * 1024;
   // problems of one launch are pushed consecutively; each launch's tiles map
@@ -321,7 +329,7 @@ void build_schedule(ncl_kkt_s* h) {
     Level& L = h->levels[l];
     L.asm_off = (int64_t)asmv.size();
     L.small_off = (int64_t)smallv.size();
-    L.list_off = (int64_t)listv.size();
+    L.chain_off = (int64_t)hs.chainv.size();
     L.below_off = (int64_t)belowv.size();
     std::vector<int32_t> large, small;
     for (int32_t k = P.level_ptr[l]; k < P.level_ptr[l + 1]; k++) {
@@ -342,7 +350,28 @@ void build_schedule(ncl_kkt_s* h) {
         }
         hs.asm_cptr.push_back((int32_t)hs.asm_cran.size());
       }
-      listv.push_back(s);
+      {
+        // block-rows of the chained sweeps (every item of the supernode
+        // carries its first block-row and first 32-row block) and, per
+        // 32-row block, the children's W entries that land on its rows
+        const int nblk = (ncol + 31) / 32, nbr = (ncol + CHAIN_ROWS - 1) / CHAIN_ROWS;
+        for (int B = 0; B < nbr; B++) hs.chainv.push_back(make_int4(s, (int32_t)hs.nbrows, (int32_t)hs.nblocks, 0));
+        L.chain_smem = std::max<int64_t>(L.chain_smem, chain_smem(std::min(CHAIN_ROWS, ncol), (int)esz));
+        for (int b = 0; b < nblk; b++) {
+          const int lo = 32 * b, hi = std::min(32 * b + 32, ncol);
+          for (int32_t k2 = P.child_ptr[s]; k2 < P.child_ptr[s + 1]; k2++) {
+            const int32_t c = P.child_list[k2];
+            const int32_t* rel = P.relmap.data() + P.relmap_off[c];
+            const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
+            const int alo = (int)(std::lower_bound(rel, rel + nbc, lo) - rel);
+            const int ahi = (int)(std::lower_bound(rel, rel + nbc, hi) - rel);
+            if (ahi > alo) hs.chain_pran.push_back(make_int4(c, alo, ahi, 0));
+          }
+          hs.chain_pptr.push_back((int32_t)hs.chain_pran.size());
+        }
+        hs.nblocks += nblk;
+        hs.nbrows += nbr;
+      }
       for (int a0 = 0; a0 < nrow - ncol; a0 += SOLVE_ROWS) belowv.push_back(make_int2(s, a0));
       const bool is_small = ncol <= 64 && nrow <= 512 && (int64_t)nrow * ncp * (int64_t)esz <= SMALL_SMEM;
       if (is_small) {
@@ -375,7 +404,7 @@ void build_schedule(ncl_kkt_s* h) {
     }
     L.asm_cnt = (int)(asmv.size() - L.asm_off);
     L.small_cnt = (int)(smallv.size() - L.small_off);
-    L.list_cnt = (int)(listv.size() - L.list_off);
+    L.chain_cnt = (int)(hs.chainv.size() - L.chain_off);
     L.below_cnt = (int)(belowv.size() - L.below_off);
     if (hs.tc) {
       int64_t off = 0;
@@ -517,6 +546,32 @@ void build_schedule(ncl_kkt_s* h) {
               P.amap_src[q] >= P.nnzA)
             bad("assembly map");
       }
+    }
+    if (hs.chain_pptr.size() != (size_t)hs.nblocks + 1 || hs.chainv.size() != (size_t)hs.nbrows) bad("pivot blocks");
+    for (size_t i = 0; i < hs.chainv.size(); i++) {
+      const int4 it = hs.chainv[i];
+      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y + (P.sn_ncol[it.x] + CHAIN_ROWS - 1) / CHAIN_ROWS > hs.nbrows ||
+          it.z < 0 || it.z + (P.sn_ncol[it.x] + 31) / 32 > hs.nblocks)
+        bad("pivot blocks");
+    }
+    for (const Level& L : h->levels)
+      if (L.chain_smem > chain_smem(CHAIN_ROWS, (int)esz)) bad("chain shared memory");
+    for (int64_t g = 0; g < hs.nblocks; g++) {
+      if (hs.chain_pptr[g] > hs.chain_pptr[g + 1] || hs.chain_pptr[g + 1] > (int32_t)hs.chain_pran.size())
+        bad("pivot block ranges");
+    }
+    for (size_t i = 0; i < hs.chainv.size(); i++) {
+      const int4 it = hs.chainv[i];
+      const int nblk = (P.sn_ncol[it.x] + 31) / 32;
+      for (int b = 0; b < nblk; b++)
+        for (int32_t e = hs.chain_pptr[it.z + b]; e < hs.chain_pptr[it.z + b + 1]; e++) {
+          const int4 cr = hs.chain_pran[e];
+          if (cr.x < 0 || cr.x >= P.ns || P.sn_parent[cr.x] != it.x || cr.y < 0 || cr.y >= cr.z ||
+              cr.z > P.sn_nrow[cr.x] - P.sn_ncol[cr.x])
+            bad("pivot block ranges");
+          const int32_t* rel = P.relmap.data() + P.relmap_off[cr.x];
+          if (rel[cr.y] < 32 * b || rel[cr.z - 1] >= std::min(32 * b + 32, (int)P.sn_ncol[it.x])) bad("pivot block ranges");
+        }
     }
     if (hs.asm_cptr.size() != asmv.size() + 1) bad("assembly child ranges");
     for (size_t i = 0; i < asmv.size(); i++) {
@@ -715,7 +770,10 @@ void build_device(ncl_kkt_s* h) {
   h->d_diag = h->upload(hs.diagv);
   h->d_probs = h->upload(hs.probv);
   h->d_tilep = h->upload(hs.tilep);
-  h->d_lists = h->upload(hs.listv);
+  h->d_chain = h->upload(hs.chainv);
+  h->d_chain_pptr = h->upload(hs.chain_pptr);
+  h->d_chain_pran = h->upload(hs.chain_pran);
+  h->d_chain_sync = h->alloc<int>(2 * (int64_t)P.ns + 2 * hs.nbrows);
   h->d_below = h->upload(hs.belowv);
   CK(cudaMallocHost(&h->h_pinned, sizeof(double) * (size_t)(7 * ni + 64 + 3 * ni * MAX_RHS_SWEEP)));
   CK(cudaEventCreate(&h->ev0));
@@ -850,9 +908,18 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
   T* W = (T*)h->W;
   T* Pw = (T*)h->Pw;
   const bool f32 = sizeof(T) == 4;
+  const int64_t ns = P.ns, nb = h->hs.nbrows;
+  int* tk_f = h->d_chain_sync;
+  int* tk_b = tk_f + ns;
+  int* fl_f = tk_b + ns;
+  int* fl_b = fl_f + nb;
+  int* serr = h->d_err + 1;
+  CK(cudaMemsetAsync(h->d_chain_sync, 0, (2 * ns + 2 * nb) * sizeof(int), st));
   for (const Level& L : h->levels) {
-    klaunch(h, st, f32 ? "fwd_diag_f32" : "fwd_diag_f64", L.list_cnt, scaled(L.fdiag_cost, nrhs),
-            [&] { launch_fwd_diag<T>(P, N, h->d_lists + L.list_off, L.list_cnt, xp, W, nrhs, st); });
+    klaunch(h, st, f32 ? "fwd_chain_f32" : "fwd_chain_f64", L.chain_cnt, scaled(L.fdiag_cost, nrhs), [&] {
+      launch_fwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, h->d_chain_pptr,
+                          h->d_chain_pran, xp, W, nrhs, tk_f, fl_f, serr, st);
+    });
     klaunch(h, st, f32 ? "fwd_below_f32" : "fwd_below_f64", L.below_cnt, scaled(L.fbelow_cost, nrhs),
             [&] { launch_fwd_below<T>(P, N, h->d_below + L.below_off, L.below_cnt, xp, W, nrhs, st); });
   }
@@ -860,8 +927,10 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
     const Level& L = h->levels[l];
     klaunch(h, st, f32 ? "bwd_below_f32" : "bwd_below_f64", L.below_cnt, scaled(L.bbelow_cost, nrhs),
             [&] { launch_bwd_below<T>(P, N, h->d_below + L.below_off, L.below_cnt, xp, Pw, nrhs, st); });
-    klaunch(h, st, f32 ? "bwd_diag_f32" : "bwd_diag_f64", L.list_cnt, scaled(L.bdiag_cost, nrhs),
-            [&] { launch_bwd_diag<T>(P, N, h->d_lists + L.list_off, L.list_cnt, xp, Pw, nrhs, st); });
+    klaunch(h, st, f32 ? "bwd_chain_f32" : "bwd_chain_f64", L.chain_cnt, scaled(L.bdiag_cost, nrhs), [&] {
+      launch_bwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, xp, Pw, nrhs, tk_b, fl_b,
+                          serr, st);
+    });
   }
   CK(cudaGetLastError());
 }
@@ -1273,6 +1342,14 @@ ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const dou
 // as one captured graph (after a direct first call that learns how many
 // refinement steps the systems need); the host checks the backward error
 // afterwards and refines further only if needed
+// did a bounded wait of the pivot-block sweeps run out since the factor?
+bool sweep_failed(ncl_kkt_s* h, cudaStream_t st) {
+  int* he = reinterpret_cast<int*>(h->h_pinned + 7 * h->dp.ninst + 9);
+  CK(cudaMemcpyAsync(he, h->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return *he != 0;
+}
+
 ncl_status do_factor_solve(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
                            const double* rho, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
                            cudaStream_t st, ncl_kkt_factor_info* infos, ncl_kkt_solve_info* sinfo) {
@@ -1351,6 +1428,7 @@ ncl_status do_factor_solve(ncl_kkt_s* h, const double* Hv, const double* Jv, con
   CK(cudaEventRecord(h->ev1, st));
   CK(cudaEventSynchronize(h->ev1));
   if (sinfo) cudaEventElapsedTime(&sinfo->ms, h->ev0, h->ev1);
+  if (sweep_failed(h, st)) return fail(NCL_ERR_TIMEOUT, "a bounded device wait of the triangular sweeps ran out");
   if (sr == NCL_ERR_IR_NOT_CONVERGED) g_last_error = "iterative refinement did not reach ir_tol";
   return sr != NCL_OK ? sr : sf;
 }
@@ -1377,6 +1455,7 @@ ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, do
   CK(cudaEventSynchronize(h->ev1));
   prof_collect(h);
   if (info) cudaEventElapsedTime(&info->ms, h->ev0, h->ev1);
+  if (sweep_failed(h, st)) return fail(NCL_ERR_TIMEOUT, "a bounded device wait of the triangular sweeps ran out");
   if (worst == NCL_ERR_IR_NOT_CONVERGED && allow_escalate && is_fp32(h) && h->opt.precision_fallback) {
     // the FP32 factors cannot reach the tolerance: refactor in FP64, solve again
     ncl_status se = escalate(h, st, nullptr);

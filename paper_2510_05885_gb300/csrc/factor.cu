@@ -13,6 +13,7 @@
 // as a zero eigenvalue (case (i)).
 #include "runtime.h"
 #include "pivot.cuh"
+#include "reduce.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -65,12 +66,22 @@ void launch_kkt_values(const DevPlan& P, const double* const* vals, const double
 // ||K||_inf per instance (max absolute row sum), as the bit pattern of a
 // non-negative double so that atomicMax on the integer orders it.
 __global__ void k_knorm(DevPlan P, const double* __restrict__ Klow, unsigned long long* knorm) {
+  int cur = -1;
+  unsigned long long mx = 0ull;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P.dim;
        r += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int64_t q = P.F_rowptr[r]; q < P.F_rowptr[r + 1]; q++) s += fabs(Klow[P.F_src[q]]);
-    atomicMax(&knorm[P.row_inst[r]], (unsigned long long)__double_as_longlong(s));
+    const int inst = P.row_inst[r];
+    if (inst != cur) {
+      if (cur >= 0) atomicMax(&knorm[cur], mx);
+      cur = inst;
+      mx = 0ull;
+    }
+    const unsigned long long v = dbits(s);
+    mx = v > mx ? v : mx;
   }
+  warp_flush_max(knorm, cur, mx);
 }
 
 void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st) {
@@ -271,31 +282,43 @@ void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* prob
 // counts[4*ninst] = number of non-finite pivots.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_inertia(DevPlan P, DevNum<T> N, long long* counts) {
+__global__ void k_inertia(DevPlan P, DevNum<T> N, unsigned long long* counts) {
+  int cur = -1;
+  unsigned c[4] = {0u, 0u, 0u, 0u}, nonfin = 0u;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P.dim;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int inst = P.col_inst[k];
+    if (inst != cur) {
+      if (cur >= 0)
+        for (int j = 0; j < 4; j++)
+          if (c[j]) atomicAdd(&counts[4 * cur + j], (unsigned long long)c[j]);
+      cur = inst;
+      c[0] = c[1] = c[2] = c[3] = 0u;
+    }
     const int8_t st = N.piv[k];
     const T d = N.D[k];
-    long long* c = counts + 4 * inst;
     if (st == 3) {
-      atomicAdd((unsigned long long*)&counts[4 * P.ninst], 1ull);
+      nonfin++;
       continue;
     }
-    if (st == 2) atomicAdd((unsigned long long*)&c[2], 1ull);
-    else if (d > T(0)) atomicAdd((unsigned long long*)&c[0], 1ull);
-    else if (d < T(0)) atomicAdd((unsigned long long*)&c[1], 1ull);
-    else atomicAdd((unsigned long long*)&c[2], 1ull);
-    if (st == 1) atomicAdd((unsigned long long*)&c[3], 1ull);
+    if (st == 2) c[2]++;
+    else if (d > T(0)) c[0]++;
+    else if (d < T(0)) c[1]++;
+    else c[2]++;
+    if (st == 1) c[3]++;
   }
+#pragma unroll
+  for (int j = 0; j < 4; j++) warp_flush_add(counts + j, cur < 0 ? -1 : 4 * cur, c[j]);
+  warp_flush_add(counts + 4 * P.ninst, 0, nonfin);
 }
 
 template <typename T>
 void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st) {
+  static_assert(sizeof(long long) == sizeof(unsigned long long), "count width");
   if (P.dim == 0) return;
   int64_t blocks = (P.dim + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_inertia<T><<<(unsigned)blocks, 256, 0, st>>>(P, N, counts);
+  k_inertia<T><<<(unsigned)blocks, 256, 0, st>>>(P, N, reinterpret_cast<unsigned long long*>(counts));
 }
 
 #define NCL_INST(T)                                                                                     \

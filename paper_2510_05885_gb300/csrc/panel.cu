@@ -61,26 +61,22 @@ __device__ __forceinline__ void load_tile(T* dst, int ldd, const T* src, int64_t
   }
 }
 
-int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + 32 * LDS + 32) * esz; }
+int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + MNB) * esz + 2 * MNB; }
 int macro_rows_smem(int esz) { return (RB * LDM + 10 * 32 * LDS + MNB) * esz; }
 
 // LDL^T of a 32 x 32 diagonal sub-block in shared memory (row stride ld,
 // cw <= 32 valid rows) by one warp, lane i holding row i in registers:
 // right-looking with column broadcasts by shuffles.  Writes the unit lower
-// factor (strictly below the diagonal) and D on the diagonal back, D and the
-// pivot status to global memory, and the inverse of the unit lower factor
-// (identity on the padding rows) to iv (stride LDS) and to inv_out
-// (row-major 32 x 32): lane j forms column j by forward substitution in
-// registers.  Returns lane's pivot (1 on the padding).
+// factor (strictly below the diagonal) and D on the diagonal back; returns
+// lane's pivot (1 on the padding) and its status in st.
 template <typename T>
-__device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, const int8_t* sign, T* D, int8_t* piv, T* iv,
-                                       T* inv_out, double eps, int policy, int lane) {
+__device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, double eps, int policy, int lane,
+                                       int8_t& st) {
   T r[32];
 #pragma unroll
   for (int j = 0; j < 32; j++) r[j] = (j <= lane && lane < cw) ? blk[lane * ld + j] : T(0);
   int8_t my_st = 0;
   T my_d = T(1);
-  const int my_sign = lane < cw ? sign[lane] : 1;
 #pragma unroll
   for (int k = 0; k < 32; k++) {
     if (k < cw) {
@@ -105,11 +101,18 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, const int8_t* sig
 #pragma unroll
     for (int j = 0; j < 32; j++)
       if (j <= lane) blk[lane * ld + j] = r[j];
-    D[lane] = my_d;
-    piv[lane] = my_st;
   }
   __syncwarp();
-  // inverse: x_i = -sum_{k<i} L[i][k] x_k, x_lane = 1, x_i = 0 above
+  st = my_st;
+  return my_d;
+}
+
+// Inverse of the unit lower 32 x 32 block blk (row stride ld, cw valid
+// rows; identity on the padding) by one warp, written row-major to out:
+// lane j forms column j by forward substitution in registers,
+// x_i = -sum_{k<i} L[i][k] x_k, x_j = 1, x_i = 0 for i < j.
+template <typename T>
+__device__ __noinline__ void invert_sub32(const T* blk, int ld, int cw, T* out, int lane) {
   T x[32];
 #pragma unroll
   for (int i = 0; i < 32; i++) {
@@ -123,42 +126,100 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, const int8_t* sig
     x[i] = (i == lane) ? T(1) : ((i > lane && i < cw) ? -(a0 + a1) : T(0));
   }
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
-    iv[i * LDS + lane] = x[i];
-    inv_out[i * 32 + lane] = x[i];
-  }
-  return my_d;
+  for (int i = 0; i < 32; i++) out[i * 32 + lane] = x[i];
 }
 
-// q <- L^-1 q for the unit lower 32 x 32 block Ls (row stride LD; only the
-// entries strictly below the diagonal are read, and they are zero on the
-// padding): forward substitution of one row, the block read from shared
-// memory by broadcast.
-template <typename T, int LD>
-__device__ __forceinline__ void row_subst32(T (&q)[32], const T* Ls) {
+// X = R L^-T for the rows [0, nrows) of R (shared, row stride ldr, ncols <=
+// 32 columns) and the unit lower 32 x 32 block L (shared, row stride ldl;
+// only the entries strictly below its diagonal are read, zero beyond
+// ncols): blocked forward
+// substitution with 8-column groups, four threads per row (thread g holds
+// columns 8g..8g+7).  Stage s: group s substitutes with the 8 x 8 diagonal
+// block, its 8 values go to the row's other threads by shuffles, and the
+// later groups subtract their products with the (g, s) block.  No inverse is
+// formed.  Called by all threads of the CTA (blockDim a multiple of 32).
+template <typename T>
+__device__ __forceinline__ void block_trsm32(T* R, int ldr, int nrows, int ncols, const T* L, int ldl) {
+  const int lane = threadIdx.x & 31, g = threadIdx.x & 3;
+  const int src0 = lane & ~3;
+  for (int r0 = 0; r0 < nrows; r0 += blockDim.x >> 2) {
+    const int row = r0 + (threadIdx.x >> 2);
+    const bool act = row < nrows;
+    T* rp = R + (act ? row : 0) * ldr + 8 * g;
+    T q[8];
 #pragma unroll
-  for (int u = 0; u < 31; u++) {
-    const T qu = q[u];
+    for (int t = 0; t < 8; t++) q[t] = (act && 8 * g + t < ncols) ? rp[t] : T(0);
 #pragma unroll
-    for (int t = u + 1; t < 32; t++) q[t] -= Ls[t * LD + u] * qu;
+    for (int st = 0; st < 4; st++) {
+      if (g == st) {
+        const T* Ld = L + (8 * st) * ldl + 8 * st;
+#pragma unroll
+        for (int u = 0; u < 7; u++)
+#pragma unroll
+          for (int t = u + 1; t < 8; t++) q[t] -= Ld[t * ldl + u] * q[u];
+      }
+      T xs[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) xs[u] = __shfl_sync(0xffffffffu, q[u], src0 | st);
+      if (g > st) {
+        const T* Lg = L + (8 * g) * ldl + 8 * st;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+          T acc = T(0);
+#pragma unroll
+          for (int u = 0; u < 8; u++) acc += Lg[t * ldl + u] * xs[u];
+          q[t] -= acc;
+        }
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int t = 0; t < 8; t++)
+        if (8 * g + t < ncols) rp[t] = q[t];
+    }
+  }
+}
+
+// Copy a tile from shared memory back to global memory (stores where
+// keep(r, c)), 8 shared loads in flight per thread before the stores.
+template <typename T, typename Keep>
+__device__ __forceinline__ void store_tile(T* dst, int64_t ldd, const T* src, int lds, int rows, int cols, Keep keep) {
+  const int n = rows * cols;
+  for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int idx = min(base + k * blockDim.x, n - 1);
+      const int r = idx / cols, c = idx - r * cols;
+      v[k] = src[r * lds + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int idx = base + k * blockDim.x;
+      const int r = idx / cols, c = idx - r * cols;
+      if (idx < n && keep(r, c)) dst[(int64_t)r * ldd + c] = v[k];
+    }
   }
 }
 
 // One CTA (256 threads) factors the w x w diagonal block (w <= 128) of a
 // macro panel in shared memory, by 32-column sub-blocks: one warp factors
-// and inverts the sub-block (factor_sub32); the rows below it inside the
-// block are solved one per thread, X = F21 L_jj^-T by forward substitution
-// and L21 = X D^-1; then all warps update the rest of the block,
+// the sub-block (factor_sub32); the rows below it inside the block are
+// solved by the blocked forward substitution, X = F21 L_jj^-T, and scaled,
+// L21 = X D^-1; then all warps update the rest of the block,
 // A[r][c] -= sum_u X[r][u] L21[c][u], with register tiles (12 rows x 3
-// columns per thread).
+// columns per thread).  At the end four warps invert the four unit lower
+// sub-blocks (for the triangular sweeps) while the block, D and the pivot
+// status are written back.
 template <typename T>
 __global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
                                                        double eps, int policy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);   // w x w block, row stride LDM
   T* Xs = A + MNB * LDM;                   // X of the rows below the sub-block
-  T* Iv = Xs + (MNB - 32) * LDS;           // inverse of the unit lower sub-block
-  T* dsh = Iv + 32 * LDS;                  // pivots of the sub-block
+  T* dsh = Xs + (MNB - 32) * LDS;          // pivots of the block (MNB)
+  int8_t* sg = reinterpret_cast<int8_t*>(dsh + MNB);   // block signs, then pivot status
+  int8_t* pst = sg + MNB;
   const int2 it = items[blockIdx.x];
   const int s = it.x, q0 = it.y;
   const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
@@ -166,33 +227,30 @@ __global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, c
   T* Lb = N.L + P.sn_Loff[s] + (int64_t)q0 * ncp + q0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   load_tile(A, LDM, Lb, ncp, w, MNB, [&](int r, int c) { return c <= r; });
+  for (int c = tid; c < MNB; c += blockDim.x) sg[c] = c < w ? P.col_sign[col0 + q0 + c] : 1;
   __syncthreads();
   constexpr int MR = (MNB - 32) / 8;   // rows per thread below a sub-block
   constexpr int GC = (MNB - 32) / 32;  // column groups per thread
   for (int c0 = 0; c0 < w; c0 += 32) {
     const int cw = min(32, w - c0);
     if (warp == 0) {
-      dsh[lane] = factor_sub32<T>(A + c0 * LDM + c0, LDM, cw, P.col_sign + col0 + q0 + c0, N.D + col0 + q0 + c0,
-                                  N.piv + col0 + q0 + c0, Iv,
-                                  N.Linv + P.sn_Ioff[s] + (int64_t)((q0 + c0) >> 5) * 1024, eps, policy, lane);
+      int8_t st;
+      const T d = factor_sub32<T>(A + c0 * LDM + c0, LDM, cw, sg[c0 + lane], eps, policy, lane, st);
+      dsh[c0 + lane] = d;
+      pst[c0 + lane] = st;
     }
     __syncthreads();
     const int rb = c0 + 32;
     const int nr = w - rb;
     if (nr > 0) {
-      // rows below the sub-block, one per thread: X = F21 L_jj^-T by forward
-      // substitution, L21 = X D^-1 (X kept for the update)
-      if (tid < nr) {
-        T q[32];
-        T* row = A + (rb + tid) * LDM + c0;
-#pragma unroll
-        for (int t = 0; t < 32; t++) q[t] = row[t];
-        row_subst32<T, LDM>(q, A + c0 * LDM + c0);
-#pragma unroll
-        for (int t = 0; t < 32; t++) {
-          Xs[tid * LDS + t] = q[t];
-          row[t] = q[t] * (T(1) / dsh[t]);
-        }
+      // rows below the sub-block: X = F21 L_jj^-T (kept), L21 = X D^-1
+      block_trsm32<T>(A + rb * LDM + c0, LDM, nr, 32, A + c0 * LDM + c0, LDM);
+      __syncthreads();
+      for (int idx = tid; idx < nr * 32; idx += blockDim.x) {
+        const int r = idx >> 5, c = idx & 31;
+        const T x = A[(rb + r) * LDM + c0 + c];
+        Xs[r * LDS + c] = x;
+        A[(rb + r) * LDM + c0 + c] = x / dsh[c0 + c];
       }
       __syncthreads();
       // A[r][c] -= sum_u X[r][u] L21[c][u], rb <= c <= r < w
@@ -225,14 +283,19 @@ __global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, c
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < w * MNB; idx += blockDim.x) {
-    const int r = idx / MNB, c = idx % MNB;
-    if (c <= r) Lb[(int64_t)r * ncp + c] = A[r * LDM + c];
+  const int nbk = (w + 31) / 32;
+  if (warp < nbk)
+    invert_sub32<T>(A + 32 * warp * LDM + 32 * warp, LDM, min(32, w - 32 * warp),
+                    N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + warp) * 1024, lane);
+  for (int c = tid; c < w; c += blockDim.x) {
+    N.D[col0 + q0 + c] = dsh[c];
+    N.piv[col0 + q0 + c] = pst[c];
   }
+  store_tile(Lb, ncp, A, LDM, w, MNB, [&](int r, int c) { return c <= r; });
 }
 
 // Rows below a macro panel, RB per CTA: for each 32-column sub-block j,
-// X_j = R_j L_jj^-T by forward substitution (one row per thread), then
+// X_j = R_j L_jj^-T by the blocked forward substitution, then
 // R_i -= X_j L_ij^T for the later sub-blocks (lane = column, the rows of a
 // warp in registers); finally L21 = X D1^-1.
 template <typename T>
@@ -263,15 +326,7 @@ __global__ void __launch_bounds__(256, 1) k_macro_rows(DevPlan P, DevNum<T> N, c
   constexpr int KR = RB / 8;   // rows per warp in the updates (lane = column)
   T* Rw = R + warp * LDM;      // row warp + 8 k is Rw[8 k LDM + ...]
   for (int j = 0; j < nbk; j++) {
-    if (tid < nr) {
-      T q[32];
-      T* row = R + tid * LDM + 32 * j;
-#pragma unroll
-      for (int t = 0; t < 32; t++) q[t] = row[t];
-      row_subst32<T, LDS>(q, Ld + j * 32 * LDS);
-#pragma unroll
-      for (int t = 0; t < 32; t++) row[t] = q[t];
-    }
+    block_trsm32<T>(R + 32 * j, LDM, nr, min(32, w - 32 * j), Ld + j * 32 * LDS, LDS);
     __syncthreads();
     for (int i = j + 1; i < nbk; i++) {
       const T* lij = Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
@@ -321,13 +376,13 @@ __global__ void __launch_bounds__(256, 1) k_macro_rows(DevPlan P, DevNum<T> N, c
 
 // Small fronts (ncol <= 64): one CTA factors the pivot columns of the whole
 // front in shared memory by 32-column sub-blocks, as the diagonal-block
-// kernel does: one warp factors and inverts the sub-block (factor_sub32),
-// then every thread solves rows below it by forward substitution,
-//   L21 = F21 L_jj^-T D^-1,
-// and, when a second sub-block follows, the warps update its columns.  The update
+// kernel does: one warp factors the sub-block (factor_sub32) and inverts it
+// (for the triangular sweeps), the rows below it are solved by the blocked
+// forward substitution, L21 = F21 L_jj^-T D^-1, and, when a second
+// sub-block follows, the warps update its columns.  The update
 // block F22 -= L21 D1 L21^T is left to the SIMT update kernel, which spreads
 // it over many CTAs.
-int small_front_smem(int nrow, int ncp, int esz) { return (nrow * (ncp + 1) + 2 * 32 * LDS + 96) * esz; }
+int small_front_smem(int nrow, int ncp, int esz) { return (nrow * (ncp + 1) + 32 * LDS + 64) * esz; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
@@ -337,10 +392,8 @@ __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, co
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
   const int ldf = ncp + 1;   // odd: column accesses by lanes are conflict-free
   T* F = reinterpret_cast<T*>(smem_raw);
-  T* Iv = F + nrow * ldf;     // inverse of the sub-block (written for the solve)
-  T* Ls = Iv + 32 * LDS;      // the sub-block's unit lower factor
+  T* Ls = F + nrow * ldf;     // the sub-block's unit lower factor, zero padded
   T* dsh = Ls + 32 * LDS;     // pivots
-  T* Id = dsh + 64;           // reciprocal pivots of the sub-block
   T* Lg = N.L + P.sn_Loff[s];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   load_tile(F, ldf, Lg, ncp, nrow, ncp, [](int, int) { return true; });
@@ -349,28 +402,29 @@ __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, co
   for (int c0 = 0; c0 < ncol; c0 += 32) {
     const int cw = min(32, ncol - c0);
     if (warp == 0) {
-      const T d = factor_sub32<T>(F + c0 * ldf + c0, ldf, cw, P.col_sign + col0 + c0, N.D + col0 + c0,
-                                  N.piv + col0 + c0, Iv, N.Linv + P.sn_Ioff[s] + (int64_t)(c0 >> 5) * 1024, eps,
-                                  policy, lane);
+      int8_t st;
+      const T d = factor_sub32<T>(F + c0 * ldf + c0, ldf, cw, lane < cw ? P.col_sign[col0 + c0 + lane] : 1, eps,
+                                  policy, lane, st);
       dsh[c0 + lane] = d;
-      Id[lane] = T(1) / d;
+      if (lane < cw) {
+        N.D[col0 + c0 + lane] = d;
+        N.piv[col0 + c0 + lane] = st;
+      }
       // the unit lower sub-block, zero above the diagonal and on the padding
 #pragma unroll 4
       for (int u = 0; u < 32; u++) Ls[lane * LDS + u] = (u < lane && lane < cw) ? F[(c0 + lane) * ldf + c0 + u] : T(0);
+      __syncwarp();
+      invert_sub32<T>(Ls, LDS, cw, N.Linv + P.sn_Ioff[s] + (int64_t)(c0 >> 5) * 1024, lane);
     }
     __syncthreads();
-    // rows below the sub-block, one per thread: forward substitution with
-    // the unit lower sub-block, then L21 = X D^-1
+    // rows below the sub-block: L21 = F21 L_jj^-T D^-1 (blocked forward
+    // substitution, then the scaling)
     const int rb = c0 + cw;
-    for (int r = rb + tid; r < nrow; r += blockDim.x) {
-      T q[32];
-      T* row = F + r * ldf + c0;
-#pragma unroll
-      for (int t = 0; t < 32; t++) q[t] = t < cw ? row[t] : T(0);
-      row_subst32<T, LDS>(q, Ls);
-#pragma unroll
-      for (int t = 0; t < 32; t++)
-        if (t < cw) row[t] = q[t] * Id[t];
+    block_trsm32<T>(F + rb * ldf + c0, ldf, nrow - rb, cw, Ls, LDS);
+    __syncthreads();
+    for (int idx = tid; idx < (nrow - rb) * 32; idx += blockDim.x) {
+      const int r = idx >> 5, c = idx & 31;
+      if (c < cw) F[(rb + r) * ldf + c0 + c] /= dsh[c0 + c];
     }
     __syncthreads();
     // update the next sub-block's columns: F[r][c] -= sum_u L[r][u] d_u L[c][u]

@@ -13,7 +13,9 @@ constexpr int PANEL_NB = 32;      // pivot columns of a diagonal sub-block
 constexpr int MACRO_NB = 128;     // pivot columns per macro panel of a large front
 constexpr int MACRO_ROWS = 64;    // rows below the macro panel per CTA
 constexpr int GEMM_TILE = 64;     // SIMT update tile (rows x cols)
-constexpr int SOLVE_ROWS = 64;    // below rows per solve CTA
+constexpr int SOLVE_ROWS = 64;     // below rows per solve CTA
+constexpr int MAX_RHS_SWEEP = 8;   // right-hand sides per triangular sweep
+constexpr int CHAIN_ROWS = 128;    // pivot rows per CTA of the chained sweeps
 constexpr int SMALL_SMEM = 64 * 1024;      // front bytes (nrow x ncolp) of a small front, at most
 constexpr int SMALL_SMEM_MAX = 96 * 1024;  // dynamic smem limit of the small-front kernel
 
@@ -151,9 +153,11 @@ void launch_perm_in(const DevPlan& P, T* xp, const double* B, int64_t ldb, int n
 template <typename T>
 void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int nrhs, int accumulate,
                      cudaStream_t st);
+int chain_smem(int rows, int esz);
 template <typename T>
-void launch_fwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp, T* W,
-                     int nrhs, cudaStream_t st);
+void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, const int32_t* pptr,
+                      const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags, int* err,
+                      cudaStream_t st);
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, T* xp, T* W,
                       int nrhs, cudaStream_t st);
@@ -161,8 +165,8 @@ template <typename T>
 void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const T* xp,
                       T* Pw, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_bwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp,
-                     const T* Pw, int nrhs, cudaStream_t st);
+void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, T* xp, const T* Pw,
+                      int nrhs, int* tickets, int* flags, int* err, cudaStream_t st);
 void launch_residual(const DevPlan& P, const double* Klow, const double* B, int64_t ldb, const double* X,
                      int64_t ldx, double* R, int64_t ldr, int nrhs, unsigned long long* rnorm,
                      unsigned long long* xnorm, cudaStream_t st);

@@ -9,6 +9,7 @@
 // (no atomics, bitwise reproducible).  The FP64 residual r = b - K x is
 // computed on the FP64 KKT values for iterative refinement (Section 4.3).
 #include "runtime.h"
+#include "reduce.cuh"
 
 namespace ncl {
 
@@ -63,59 +64,161 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
 }
 
 // ---------------------------------------------------------------------------
-// forward: pivot block of supernode s (one CTA): pull the children's updates
-// that land on the pivot rows, then L11 y = t by 32-column blocks: warp 0
-// solves the 32 x 32 diagonal block with shuffles (its row of the block
-// prefetched into registers), then every thread updates whole rows below
-// it (one 128-byte row segment per row, y of the block from shared memory).
+// Pivot blocks of the sweeps, chained over 128-row block-rows.
+//
+// Every supernode's pivot block L11 is cut into block-rows of CHAIN_ROWS =
+// 128 rows, one CTA (4 warps) each; warp w owns the block-row's 32-row
+// sub-block w.  A CTA takes its block-row from the supernode's ticket
+// counter, in order, so every block-row it waits for belongs to a CTA that is
+// already running: the waits cannot deadlock, whatever the order in which
+// CTAs are scheduled.  Waits are bounded: past the limit the CTA sets the
+// sweep's error flag, goes on with what it has and still publishes, so that
+// nobody waits on it; the host then reports the sweep as failed.
+//   forward:  y_B = L_BB^-1 (t_B - sum_{J<B} L_BJ y_J),
+//             t_B = the block-row's right-hand side plus the children's updates;
+//   backward: x_B = L_BB^-T (z_B - sum_{I>B} L_IB^T x_I),
+//             z_B = D^-1 y_B - the partial sums of L21^T x of the rows below.
+// The sums over published block-rows are formed by every warp for its rows
+// (lane = row, the published values by shuffles); the diagonal block-row
+// L_BB is then solved inside the CTA sub-block by sub-block with the
+// inverted 32 x 32 diagonal blocks, its strictly lower part staged in shared
+// memory while the CTA waits.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_fwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
-                                                   T* __restrict__ xp, const T* __restrict__ W, int nrhs) {
-  __shared__ T ys[8][32];
-  const int s = list[blockIdx.x];
-  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
-  const T* Lb = N.L + P.sn_Loff[s];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
-    const int c = P.child_list[k];
-    const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
-    const int32_t* rel = P.relmap + P.relmap_off[c];
-    const int ahi = lb_i32(rel, nbc, ncol);
-    for (int a = threadIdx.x; a < ahi; a += blockDim.x)
-      for (int r = 0; r < nrhs; r++) xp[r * P.dim + col0 + rel[a]] += W[r * P.Wtot + P.sn_Woff[c] + a];
-    __syncthreads();
-  }
-  for (int kb = 0; kb < ncol; kb += 32) {
-    const int bw = min(32, ncol - kb);
-    if (warp == 0) {
-      // y_blk = L_blk^-1 t_blk with the inverted diagonal block (row lane)
-      T lrow[32];
-      const T* ip = N.Linv + P.sn_Ioff[s] + (int64_t)(kb / 32) * 1024 + lane * 32;
-#pragma unroll
-      for (int u = 0; u < 32; u++) lrow[u] = ip[u];
-      for (int r = 0; r < nrhs; r++) {
-        T* x = xp + r * P.dim + col0;
-        const T t = lane < bw ? x[kb + lane] : T(0);
-        T v = T(0);
-#pragma unroll
-        for (int u = 0; u < 32; u++) v += lrow[u] * __shfl_sync(0xffffffffu, t, u);
-        if (lane < bw) x[kb + lane] = v;
-        ys[r][lane] = lane < bw ? v : T(0);
+constexpr long long CHAIN_WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// lane 0 waits (bounded) for the flag; the warp then proceeds together.
+// err is the sweep's error flag: once set, nobody waits any more.
+__device__ __forceinline__ void chain_wait(const int* flag, int* err) {
+  if ((threadIdx.x & 31) == 0 && !ld_acquire(flag) && !ld_acquire(err)) {
+    const long long t0 = clock64();
+    while (!ld_acquire(flag)) {
+      if (clock64() - t0 > CHAIN_WAIT_CYCLES || ld_acquire(err)) {
+        atomicExch(err, 1);
+        break;
       }
+      __nanosleep(32);
     }
-    __syncthreads();
-    // rows below the block, 32 per warp: lane u reads column kb+u of each
-    // row (coalesced), and a butterfly reduce-scatter leaves row r's sum in
-    // lane r (31 shuffles per 32 rows)
-    const int nw = blockDim.x >> 5;
-    for (int i0 = kb + bw + warp * 32; i0 < ncol; i0 += nw * 32) {
-      T lv[32];
+  }
+  __syncwarp();
+}
+
+// after a CTA barrier: thread 0 publishes the CTA's results
+__device__ __forceinline__ void chain_publish(int* flag) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flag, 1);
+  }
+}
+
+int chain_smem(int rows, int esz) {
+  return (rows * (rows + 1) + 2 * MAX_RHS_SWEEP * (CHAIN_ROWS + 1) + ((rows + 31) / 32) * 32 * 33) * esz;
+}
+
+// strictly lower part of the diagonal block-row tile (rows and columns
+// [R0, R0 + nr)) into shared memory, row stride nr + 1
+template <typename T>
+__device__ __forceinline__ void chain_stage_tile(T* Ls, const T* Lb, int64_t ncp, int R0, int nr) {
+  const int n = nr * nr, ld = nr + 1;
+  for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
+    T v[8];
 #pragma unroll
-      for (int rr = 0; rr < 32; rr++)
-        lv[rr] = (lane < bw && i0 + rr < ncol) ? Lb[(int64_t)(i0 + rr) * ncp + kb + lane] : T(0);
-      for (int r = 0; r < nrhs; r++) {
-        const T yu = ys[r][lane];
+    for (int k = 0; k < 8; k++) {
+      const int idx = base + k * blockDim.x;
+      const int i = idx / nr, c = idx - i * nr;
+      v[k] = (idx < n && c < i) ? Lb[(int64_t)(R0 + i) * ncp + R0 + c] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int idx = base + k * blockDim.x;
+      const int i = idx / nr, c = idx - i * nr;
+      if (idx < n) Ls[i * ld + c] = v[k];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
+                                                   const int32_t* __restrict__ pptr, const int4* __restrict__ pran,
+                                                   T* __restrict__ xp, const T* __restrict__ W, int nrhs,
+                                                   int* tickets, int* flags, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sb;
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, broff = it.y, boff = it.z;
+  if (threadIdx.x == 0) sb = atomicAdd(&tickets[s], 1);
+  __syncthreads();
+  const int B = sb;
+  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+  const int R0 = CHAIN_ROWS * B, nr = min(CHAIN_ROWS, ncol - R0), nsub = (nr + 31) / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ldt = nr + 1;
+  T* Ls = reinterpret_cast<T*>(smem_raw);              // nr x nr, strictly lower
+  T* tb = Ls + nr * ldt;                               // [MAX_RHS_SWEEP][CHAIN_ROWS + 1]
+  T* ys = tb + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);
+  T* Iv = ys + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);      // the inverted 32 x 32 diagonal blocks, stride 33
+  const T* Lb = N.L + P.sn_Loff[s];
+  chain_stage_tile(Ls, Lb, ncp, R0, nr);
+  const int rw = 32 * warp + lane;                     // this lane's row in the block-row
+  const bool mine = warp < nsub;
+  const bool valid = rw < nr;
+  if (mine) {
+    // the inverted diagonal block of this warp's sub-block (for the end)
+    const T* ip = N.Linv + P.sn_Ioff[s] + (int64_t)(4 * B + warp) * 1024;
+    T* iw = Iv + warp * 32 * 33;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) iw[i * 33 + lane] = ip[i * 32 + lane];
+    // t: the rows' entries plus the children's updates, child by child
+#pragma unroll
+    for (int r = 0; r < MAX_RHS_SWEEP; r++)
+      tb[r * (CHAIN_ROWS + 1) + rw] = (r < nrhs && valid) ? xp[(int64_t)r * P.dim + col0 + R0 + rw] : T(0);
+    __syncwarp();
+    const int k = 4 * B + warp;
+    for (int e = pptr[boff + k]; e < pptr[boff + k + 1]; e++) {
+      const int4 pr = pran[e];
+      const int c = pr.x;
+      const int32_t* rel = P.relmap + P.relmap_off[c];
+      for (int a = pr.y + lane; a < pr.z; a += 32)
+        for (int r = 0; r < nrhs; r++) tb[r * (CHAIN_ROWS + 1) + rel[a] - R0] += W[r * P.Wtot + P.sn_Woff[c] + a];
+      __syncwarp();
+    }
+  }
+  // sum over the published block-rows J < B (all 128 columns of J exist):
+  // the warp reads its 32 rows 32 columns at a time (one coalesced segment
+  // per row; the next segment is loaded before the current one is used and
+  // before waiting for its block-row), and a butterfly reduce-scatter leaves
+  // row rr's sum in lane rr
+  T acc[MAX_RHS_SWEEP];
+#pragma unroll
+  for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
+  if (mine && B > 0) {
+    const T* wrow = Lb + (int64_t)(R0 + 32 * warp) * ncp + lane;
+    const int nrw = min(32, nr - 32 * warp);
+    T lv[32], ln[32];
+#pragma unroll
+    for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp] : T(0);
+    const int nchunk = 4 * B;
+    for (int q = 0; q < nchunk; q++) {
+      const int c0 = 32 * q;
+#pragma unroll
+      for (int rr = 0; rr < 32; rr++) lv[rr] = ln[rr];
+      if (q + 1 < nchunk) {
+#pragma unroll
+        for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp + c0 + 32] : T(0);
+      }
+      if ((q & 3) == 0) chain_wait(flags + broff + (q >> 2), err);
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+        if (r >= nrhs) break;
+        const T yu = __ldcg(xp + (int64_t)r * P.dim + col0 + c0 + lane);
         T v[32];
 #pragma unroll
         for (int rr = 0; rr < 32; rr++) v[rr] = lv[rr] * yu;
@@ -129,11 +232,146 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_fwd_diag(DevPlan
             v[k] = (upper ? v[k + o] : v[k]) + recv;
           }
         }
-        if (i0 + lane < ncol) xp[r * P.dim + col0 + i0 + lane] -= v[0];
+        acc[r] += v[0];
+      }
+    }
+  }
+  __syncthreads();
+  // the diagonal block-row, sub-block by sub-block
+  for (int w2 = 0; w2 < nsub; w2++) {
+    if (warp == w2) {
+      const T* iw = Iv + warp * 32 * 33 + lane * 33;   // row lane of the inverted block
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+        if (r >= nrhs) break;
+        const T z = valid ? tb[r * (CHAIN_ROWS + 1) + rw] - acc[r] : T(0);
+        T v = T(0);
+#pragma unroll
+        for (int u = 0; u < 32; u++) v += iw[u] * __shfl_sync(0xffffffffu, z, u);
+        ys[r * (CHAIN_ROWS + 1) + rw] = valid ? v : T(0);
+        if (valid) xp[(int64_t)r * P.dim + col0 + R0 + rw] = v;
       }
     }
     __syncthreads();
+    if (warp > w2 && mine) {
+      const T* lr = Ls + min(rw, nr - 1) * ldt + 32 * w2;
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+        if (r >= nrhs) break;
+        const T* y = ys + r * (CHAIN_ROWS + 1) + 32 * w2;
+        T a = T(0);
+#pragma unroll 8
+        for (int u = 0; u < 32; u++) a += lr[u] * y[u];
+        acc[r] += a;
+      }
+    }
   }
+  chain_publish(flags + broff + B);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
+                                                   T* __restrict__ xp, const T* __restrict__ Pw, int nrhs,
+                                                   int* tickets, int* flags, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sb;
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, broff = it.y;
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+  const int nbr = (ncol + CHAIN_ROWS - 1) / CHAIN_ROWS;
+  if (threadIdx.x == 0) sb = nbr - 1 - atomicAdd(&tickets[s], 1);
+  __syncthreads();
+  const int B = sb;
+  const int R0 = CHAIN_ROWS * B, nr = min(CHAIN_ROWS, ncol - R0), nsub = (nr + 31) / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ldt = nr + 1;
+  T* Ls = reinterpret_cast<T*>(smem_raw);
+  T* zb = Ls + nr * ldt;
+  T* xs = zb + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);
+  T* Iv = xs + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);      // the inverted 32 x 32 diagonal blocks, stride 33
+  const T* Lb = N.L + P.sn_Loff[s];
+  chain_stage_tile(Ls, Lb, ncp, R0, nr);
+  const int rw = 32 * warp + lane;                     // this lane's column (unknown) in the block-row
+  const bool mine = warp < nsub;
+  const bool valid = rw < nr;
+  if (mine) {
+    // the inverted diagonal block of this warp's sub-block (for the end)
+    const T* ip = N.Linv + P.sn_Ioff[s] + (int64_t)(4 * B + warp) * 1024;
+    T* iw = Iv + warp * 32 * 33;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) iw[i * 33 + lane] = ip[i * 32 + lane];
+    // z = D^-1 y - the partial sums of the rows below
+    const int nb = nrow - ncol, nch = (nb + SOLVE_ROWS - 1) / SOLVE_ROWS;
+    const T dk = valid ? N.D[col0 + R0 + rw] : T(1);
+    for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+      T z = T(0);
+      if (r < nrhs && valid) {
+        z = xp[(int64_t)r * P.dim + col0 + R0 + rw] / dk;
+        for (int ch = 0; ch < nch; ch++) z -= Pw[r * P.Ptot + P.sn_Poff[s] + (int64_t)ch * ncol + R0 + rw];
+      }
+      zb[r * (CHAIN_ROWS + 1) + rw] = z;
+    }
+  }
+  // sum over the published block-rows I > B: L_IB^T x_I (lane = column)
+  T acc[MAX_RHS_SWEEP];
+#pragma unroll
+  for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
+  if (mine) {
+    const T* lcol = Lb + R0 + min(rw, nr - 1);
+    for (int I = nbr - 1; I > B; I--) {
+      chain_wait(flags + broff + I, err);
+      const int nri = min(CHAIN_ROWS, ncol - CHAIN_ROWS * I);
+#pragma unroll 1
+      for (int c = 0; c < 4; c++) {
+        const int q0 = CHAIN_ROWS * I + 32 * c, bwi = min(32, nri - 32 * c);
+        if (bwi <= 0) break;
+        T lv[32];
+#pragma unroll
+        for (int v = 0; v < 32; v++) lv[v] = v < bwi ? lcol[(int64_t)(q0 + v) * ncp] : T(0);
+        T xv[MAX_RHS_SWEEP];
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++)
+          xv[r] = (r < nrhs && lane < bwi) ? __ldcg(xp + (int64_t)r * P.dim + col0 + q0 + lane) : T(0);
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+          if (r >= nrhs) break;
+#pragma unroll
+          for (int v = 0; v < 32; v++) acc[r] += lv[v] * __shfl_sync(0xffffffffu, xv[r], v);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the diagonal block-row, sub-block by sub-block from the last
+  for (int w2 = nsub - 1; w2 >= 0; w2--) {
+    if (warp == w2) {
+      const T* iw = Iv + warp * 32 * 33 + lane;        // column lane of the inverted block
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+        if (r >= nrhs) break;
+        const T w = valid ? zb[r * (CHAIN_ROWS + 1) + rw] - acc[r] : T(0);
+        T v = T(0);
+#pragma unroll
+        for (int q = 0; q < 32; q++) v += iw[q * 33] * __shfl_sync(0xffffffffu, w, q);
+        xs[r * (CHAIN_ROWS + 1) + rw] = valid ? v : T(0);
+        if (valid) xp[(int64_t)r * P.dim + col0 + R0 + rw] = v;
+      }
+    }
+    __syncthreads();
+    if (warp < w2) {
+      // acc[col rw] += sum_v L[32 w2 + v][rw] x[32 w2 + v]
+      const int nv = min(32, nr - 32 * w2);
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+        if (r >= nrhs) break;
+        const T* x = xs + r * (CHAIN_ROWS + 1) + 32 * w2;
+        T a = T(0);
+        for (int v = 0; v < nv; v++) a += Ls[(32 * w2 + v) * ldt + rw] * x[v];
+        acc[r] += a;
+      }
+    }
+  }
+  chain_publish(flags + broff + B);
 }
 
 // forward: rows below supernode s, SOLVE_ROWS per CTA:
@@ -200,69 +438,17 @@ __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const
   }
 }
 
-// backward: pivot block (one CTA): z = D^-1 y - sum of partials, then
-// L11^T x = z by 32-column blocks from the last one: warp 0 solves the
-// diagonal block (lane u holds column u of the block in registers), then
-// every thread updates one earlier column u with the block's 32 rows.
 template <typename T>
-__global__ void __launch_bounds__(512) k_bwd_diag(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
-                                                   T* __restrict__ xp, const T* __restrict__ Pw, int nrhs) {
-  __shared__ T xs[8][32];
-  const int s = list[blockIdx.x];
-  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
-  const int nb = nrow - ncol;
-  const int nch = (nb + SOLVE_ROWS - 1) / SOLVE_ROWS;
-  const T* Lb = N.L + P.sn_Loff[s];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
-    const T dk = N.D[col0 + k];
-    for (int r = 0; r < nrhs; r++) {
-      T z = xp[r * P.dim + col0 + k] / dk;
-      for (int ch = 0; ch < nch; ch++) z -= Pw[r * P.Ptot + P.sn_Poff[s] + (int64_t)ch * ncol + k];
-      xp[r * P.dim + col0 + k] = z;
-    }
+void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, const int32_t* pptr,
+                      const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags, int* err,
+                      cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fwd_chain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain_smem(CHAIN_ROWS, sizeof(T)));
+    attr = true;
   }
-  __syncthreads();
-  const int nblk = (ncol + 31) / 32;
-  for (int bi = nblk - 1; bi >= 0; bi--) {
-    const int kb = bi * 32;
-    const int bw = min(32, ncol - kb);
-    if (warp == 0) {
-      // x_blk = L_blk^-T z_blk with the inverted diagonal block (column lane)
-      T lcol[32];
-      const T* ip = N.Linv + P.sn_Ioff[s] + (int64_t)(kb / 32) * 1024 + lane;
-#pragma unroll
-      for (int v = 0; v < 32; v++) lcol[v] = ip[v * 32];
-      for (int r = 0; r < nrhs; r++) {
-        T* x = xp + r * P.dim + col0;
-        const T z = lane < bw ? x[kb + lane] : T(0);
-        T acc = T(0);
-#pragma unroll
-        for (int v = 0; v < 32; v++) acc += lcol[v] * __shfl_sync(0xffffffffu, z, v);
-        if (lane < bw) x[kb + lane] = acc;
-        xs[r][lane] = lane < bw ? acc : T(0);
-      }
-    }
-    __syncthreads();
-    for (int u = threadIdx.x; u < kb; u += blockDim.x) {
-      T lv[32];
-#pragma unroll
-      for (int v = 0; v < 32; v++) lv[v] = (v < bw) ? Lb[(int64_t)(kb + v) * ncp + u] : T(0);
-      for (int r = 0; r < nrhs; r++) {
-        T acc = T(0);
-#pragma unroll
-        for (int v = 0; v < 32; v++) acc += lv[v] * xs[r][v];
-        xp[r * P.dim + col0 + u] -= acc;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <typename T>
-void launch_fwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp, T* W, int nrhs,
-                     cudaStream_t st) {
-  if (count > 0) k_fwd_diag<T><<<count, sizeof(T) == 4 ? 512 : 256, 0, st>>>(P, N, list, xp, W, nrhs);
+  k_fwd_chain<T><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err);
 }
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, T* xp, T* W, int nrhs,
@@ -275,9 +461,15 @@ void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, i
   if (count > 0) k_bwd_below<T><<<count, 256, 0, st>>>(P, N, items, xp, Pw, nrhs);
 }
 template <typename T>
-void launch_bwd_diag(const DevPlan& P, const DevNum<T>& N, const int32_t* list, int count, T* xp, const T* Pw,
-                     int nrhs, cudaStream_t st) {
-  if (count > 0) k_bwd_diag<T><<<count, 512, 0, st>>>(P, N, list, xp, Pw, nrhs);
+void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, T* xp, const T* Pw,
+                      int nrhs, int* tickets, int* flags, int* err, cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bwd_chain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain_smem(CHAIN_ROWS, sizeof(T)));
+    attr = true;
+  }
+  k_bwd_chain<T><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -290,27 +482,51 @@ __global__ void k_residual(DevPlan P, const double* __restrict__ Klow, const dou
   const int lane = threadIdx.x & 31, sub = lane & 7;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // running maxima of |r| and |x| for the instance of this lane's rows
+  int cur = -1;
+  unsigned long long rmx[MAX_RHS_SWEEP], xmx[MAX_RHS_SWEEP];
+#pragma unroll
+  for (int r = 0; r < MAX_RHS_SWEEP; r++) rmx[r] = xmx[r] = 0ull;
   // each warp takes 4 rows per trip (8 lanes per row); the trip count is
   // uniform across the warp so that the full-mask shuffles are safe
   for (int64_t rb = gwarp * 4; rb < P.dim; rb += nwarp * 4) {
     const int64_t row = rb + (lane >> 3);
     const bool valid = row < P.dim;
     const int64_t q0 = valid ? P.F_rowptr[row] : 0, q1 = valid ? P.F_rowptr[row + 1] : 0;
-    const int inst = valid ? P.row_inst[row] : 0;
-    for (int r = 0; r < nrhs; r++) {
+    const int inst = valid ? P.row_inst[row] : -1;
+    if (valid && sub == 0 && inst != cur) {
+      if (cur >= 0)
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++)
+          if (r < nrhs) {
+            atomicMax(&rnorm[cur * nrhs + r], rmx[r]);
+            atomicMax(&xnorm[cur * nrhs + r], xmx[r]);
+          }
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) rmx[r] = xmx[r] = 0ull;
+      cur = inst;
+    }
+#pragma unroll
+    for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+      if (r >= nrhs) break;
       const double* x = X + r * ldx;
       double acc = 0.0;
       for (int64_t q = q0 + sub; q < q1; q += 8) acc = fma(Klow[P.F_src[q]], x[P.F_col[q]], acc);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(FULL_MASK, acc, 4);
+      acc += __shfl_xor_sync(FULL_MASK, acc, 2);
+      acc += __shfl_xor_sync(FULL_MASK, acc, 1);
       if (valid && sub == 0) {
         const double res = B[r * ldb + row] - acc;
         R[r * ldr + row] = res;
-        atomicMax(&rnorm[inst * nrhs + r], (unsigned long long)__double_as_longlong(fabs(res)));
-        atomicMax(&xnorm[inst * nrhs + r], (unsigned long long)__double_as_longlong(fabs(x[row])));
+        const unsigned long long a = dbits(fabs(res)), b = dbits(fabs(x[row]));
+        rmx[r] = a > rmx[r] ? a : rmx[r];
+        xmx[r] = b > xmx[r] ? b : xmx[r];
       }
     }
+  }
+  for (int r = 0; r < nrhs; r++) {
+    warp_flush_max(rnorm + r, cur < 0 ? -1 : cur * nrhs, rmx[r]);
+    warp_flush_max(xnorm + r, cur < 0 ? -1 : cur * nrhs, xmx[r]);
   }
 }
 
@@ -322,10 +538,20 @@ void launch_residual(const DevPlan& P, const double* Klow, const double* B, int6
 }
 
 __global__ void k_vec_norm(DevPlan P, const double* __restrict__ B, int64_t ldb, int nrhs, unsigned long long* out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.dim; i += (int64_t)gridDim.x * blockDim.x) {
-    const int inst = P.row_inst[i];
-    for (int r = 0; r < nrhs; r++)
-      atomicMax(&out[inst * nrhs + r], (unsigned long long)__double_as_longlong(fabs(B[r * ldb + i])));
+  for (int r = 0; r < nrhs; r++) {
+    int cur = -1;
+    unsigned long long mx = 0ull;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.dim; i += (int64_t)gridDim.x * blockDim.x) {
+      const int inst = P.row_inst[i];
+      const unsigned long long v = dbits(fabs(B[r * ldb + i]));
+      if (inst != cur) {
+        if (cur >= 0) atomicMax(&out[cur * nrhs + r], mx);
+        cur = inst;
+        mx = 0ull;
+      }
+      mx = v > mx ? v : mx;
+    }
+    warp_flush_max(out + r, cur < 0 ? -1 : cur * nrhs, mx);
   }
 }
 
@@ -532,14 +758,14 @@ void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64
 #define NCL_INST(T)                                                                                               \
   template void launch_perm_in<T>(const DevPlan&, T*, const double*, int64_t, int, cudaStream_t);                 \
   template void launch_perm_out<T>(const DevPlan&, const T*, double*, int64_t, int, int, cudaStream_t);           \
-  template void launch_fwd_diag<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, T*, T*, int,            \
-                                   cudaStream_t);                                                                 \
+  template void launch_fwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, const int32_t*,     \
+                                    const int4*, T*, const T*, int, int*, int*, int*, cudaStream_t);              \
   template void launch_fwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, int, T*, T*, int,              \
                                     cudaStream_t);                                                                \
   template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, int, const T*, T*, int,        \
                                     cudaStream_t);                                                                \
-  template void launch_bwd_diag<T>(const DevPlan&, const DevNum<T>&, const int32_t*, int, T*, const T*, int,      \
-                                   cudaStream_t);
+  template void launch_bwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, T*, const T*, int,   \
+                                    int*, int*, int*, cudaStream_t);
 NCL_INST(float)
 NCL_INST(double)
 #undef NCL_INST
