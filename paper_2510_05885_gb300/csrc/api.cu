@@ -59,10 +59,8 @@ struct Cost {
 };
 
 struct Step {                 // one macro panel of every large front of a level
-  int64_t diag_off = 0;       // (s, q0) diagonal-block items
-  int diag_cnt = 0;
-  int64_t rows_off = 0;       // (s, q0, r0) row items
-  int rows_cnt = 0;
+  int64_t panel_off = 0;      // (s, q0, sync slot, 0): the diagonal CTA and the row CTAs of each front
+  int panel_cnt = 0;
   int64_t prob_off = 0;       // SIMT trailing updates
   int prob_cnt = 0;
   int64_t tiles = 0;
@@ -71,7 +69,7 @@ struct Step {                 // one macro panel of every large front of a level
   int tc_cnt = 0;
   int64_t tc_tiles = 0;
   int64_t ttp_off = 0;
-  Cost diag_cost, rows_cost, gemm_cost, tc_cost;
+  Cost panel_cost, gemm_cost, tc_cost;
 };
 
 struct Level {
@@ -95,6 +93,8 @@ struct Level {
   int64_t chain_smem = 0; // dynamic shared memory of the chained sweep kernels
   int64_t below_off = 0;  // (s, a0) solve items
   int below_cnt = 0;
+  int64_t bbelow_off = 0; // (s, a0, k0) backward solve items
+  int bbelow_cnt = 0;
   Cost asm_cost, small_cost, syrk_cost, fdiag_cost, fbelow_cost, bdiag_cost, bbelow_cost;
 };
 
@@ -119,10 +119,13 @@ struct HostSched {
   std::vector<int4> chain_pran;           // (child, alo, ahi, 0): child W entries landing on the block
   int64_t nblocks = 0;                    // 32-row pivot blocks in all
   int64_t nbrows = 0;                     // block-rows of the chained sweeps in all
+  std::vector<int4> bbelowv;              // (s, a0, k0, 0): backward below-rows items, 256 columns each
+  std::vector<int32_t> below_cptr;        // per below-rows solve item: its run of child ranges
+  std::vector<int4> below_cran;           // (child, lo, hi, 0)
   std::vector<int32_t> asm_cptr;          // per assembly item: its run of child row ranges
   std::vector<int4> asm_cran;             // (child, alo, ahi, 0)
-  std::vector<int4> rowsv;
-  std::vector<int2> diagv;
+  std::vector<int4> panelv;
+  int64_t panel_sync = 0;                 // ints of the panel tickets and sub-block flags
   std::vector<GemmProb> probv;
   std::vector<int32_t> tilep, tilep_tc;   // problem of every tile, per launch
   // tensor-core path (FP32): problems, split-operand offsets, fronts in map order
@@ -164,8 +167,8 @@ struct ncl_kkt_s {
   int32_t* d_asm_cptr = nullptr;
   int4* d_asm_cran = nullptr;
   int32_t* d_small = nullptr;
-  int4* d_rows = nullptr;
-  int2* d_diag = nullptr;
+  int4* d_panel = nullptr;
+  int* d_panel_sync = nullptr;
   GemmProb* d_probs = nullptr;
   int32_t* d_tilep = nullptr;
   int32_t* d_tilep_tc = nullptr;
@@ -174,6 +177,9 @@ struct ncl_kkt_s {
   int4* d_chain_pran = nullptr;
   int* d_chain_sync = nullptr;              // tickets (fwd, bwd) then flags (fwd, bwd) of the pivot blocks
   int2* d_below = nullptr;
+  int4* d_bbelow = nullptr;
+  int32_t* d_below_cptr = nullptr;
+  int4* d_below_cran = nullptr;
   // solve workspace
   void* xp = nullptr;
   void* own_xp = nullptr;                  // the handle's own sweep workspace
@@ -285,8 +291,7 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<int2>& asmv = hs.asmv;
   std::vector<int2>& belowv = hs.belowv;
   std::vector<int32_t>& smallv = hs.smallv;
-  std::vector<int4>& rowsv = hs.rowsv;
-  std::vector<int2>& diagv = hs.diagv;
+  std::vector<int4>& panelv = hs.panelv;
   std::vector<GemmProb>& probv = hs.probv;
   hs.tc = is_fp32(h) && h->opt.use_tensor_cores;
   hs.sn_Soff.assign(P.ns, -1);
@@ -294,6 +299,7 @@ void build_schedule(ncl_kkt_s* h) {
   hs.sn_Ioff.assign(P.ns + 1, 0);
   hs.asm_cptr.assign(1, 0);
   hs.chain_pptr.assign(1, 0);
+  hs.below_cptr.assign(1, 0);
   for (int32_t s = 0; s < P.ns; s++)
     hs.sn_Ioff[s + 1] = hs.sn_Ioff[s] + (int64_t)((P.sn_ncol[s] + 31) / 32) * 1024;
   // problems of one launch are pushed consecutively; each launch's tiles map
@@ -331,6 +337,7 @@ void build_schedule(ncl_kkt_s* h) {
     L.small_off = (int64_t)smallv.size();
     L.chain_off = (int64_t)hs.chainv.size();
     L.below_off = (int64_t)belowv.size();
+    L.bbelow_off = (int64_t)hs.bbelowv.size();
     std::vector<int32_t> large, small;
     for (int32_t k = P.level_ptr[l]; k < P.level_ptr[l + 1]; k++) {
       const int32_t s = P.level_list[k];
@@ -372,7 +379,21 @@ void build_schedule(ncl_kkt_s* h) {
         hs.nblocks += nblk;
         hs.nbrows += nbr;
       }
-      for (int a0 = 0; a0 < nrow - ncol; a0 += SOLVE_ROWS) belowv.push_back(make_int2(s, a0));
+      for (int a0 = 0; a0 < nrow - ncol; a0 += SOLVE_ROWS) {
+        belowv.push_back(make_int2(s, a0));
+        for (int k0 = 0; k0 < ncol; k0 += 256) hs.bbelowv.push_back(make_int4(s, a0, k0, 0));
+        // the children's W entries that land on the rows [a0, a1) below
+        const int a1 = std::min(a0 + SOLVE_ROWS, nrow - ncol);
+        for (int32_t k2 = P.child_ptr[s]; k2 < P.child_ptr[s + 1]; k2++) {
+          const int32_t c = P.child_list[k2];
+          const int32_t* rel = P.relmap.data() + P.relmap_off[c];
+          const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
+          const int lo = (int)(std::lower_bound(rel, rel + nbc, ncol + a0) - rel);
+          const int hi = (int)(std::lower_bound(rel, rel + nbc, ncol + a1) - rel);
+          if (hi > lo) hs.below_cran.push_back(make_int4(c, lo, hi, 0));
+        }
+        hs.below_cptr.push_back((int32_t)hs.below_cran.size());
+      }
       const bool is_small = ncol <= 64 && nrow <= 512 && (int64_t)nrow * ncp * (int64_t)esz <= SMALL_SMEM;
       if (is_small) {
         smallv.push_back(s);
@@ -406,6 +427,7 @@ void build_schedule(ncl_kkt_s* h) {
     L.small_cnt = (int)(smallv.size() - L.small_off);
     L.chain_cnt = (int)(hs.chainv.size() - L.chain_off);
     L.below_cnt = (int)(belowv.size() - L.below_off);
+    L.bbelow_cnt = (int)(hs.bbelowv.size() - L.bbelow_off);
     if (hs.tc) {
       int64_t off = 0;
       for (int32_t s : large) {
@@ -423,8 +445,7 @@ void build_schedule(ncl_kkt_s* h) {
     L.steps.resize(maxm);
     for (int m = 0; m < maxm; m++) {
       Step& S = L.steps[m];
-      S.diag_off = (int64_t)diagv.size();
-      S.rows_off = (int64_t)rowsv.size();
+      S.panel_off = (int64_t)panelv.size();
       S.prob_off = (int64_t)probv.size();
       S.tp_off = (int64_t)hs.tilep.size();
       S.tc_off = (int64_t)hs.tcv.size();
@@ -434,12 +455,14 @@ void build_schedule(ncl_kkt_s* h) {
         const int q0 = m * MACRO_NB;
         if (q0 >= ncol) continue;
         const int qe = std::min(q0 + MACRO_NB, ncol), w = qe - q0;
-        diagv.push_back(make_int2(s, q0));
-        S.diag_cost.flops += 2.0 * w * (double)w * w / 3.0 + 32.0 * 32 * w;
-        S.diag_cost.bytes += esz * ((double)w * (w + 1) + 1024.0 * ((w + 31) / 32) + 2.0 * w);
-        for (int r0 = qe; r0 < nrow; r0 += MACRO_ROWS) rowsv.push_back(make_int4(s, q0, r0, 0));
-        S.rows_cost.flops += (double)(nrow - qe) * w * (w + 1.0);
-        S.rows_cost.bytes += esz * 2.0 * (nrow - qe) * w + (fid[s] >= 0 ? 16.0 * (nrow - qe) * w : 0.0);
+        // one diagonal CTA and one CTA per MACRO_ROWS rows below, sharing a
+        // sync slot (ticket counter, four sub-block flags)
+        const int nrc = (nrow - qe + MACRO_ROWS - 1) / MACRO_ROWS;
+        for (int k = 0; k <= nrc; k++) panelv.push_back(make_int4(s, q0, (int32_t)hs.panel_sync, 0));
+        hs.panel_sync += 8;
+        S.panel_cost.flops += 2.0 * w * (double)w * w / 3.0 + 32.0 * 32 * w + (double)(nrow - qe) * w * (w + 1.0);
+        S.panel_cost.bytes += esz * ((double)w * (w + 1) + 1024.0 * ((w + 31) / 32) + 2.0 * w) +
+                              esz * 2.0 * (nrow - qe) * w + (fid[s] >= 0 ? 16.0 * (nrow - qe) * w : 0.0);
         if (qe >= ncol) continue;
         if (fid[s] >= 0 && h->opt.use_tensor_cores > 1 && w % 32 == 0) {
           TcProb q{};
@@ -469,8 +492,7 @@ void build_schedule(ncl_kkt_s* h) {
           push_gemm(g, S.prob_off, S.tiles, S.gemm_cost);
         }
       }
-      S.diag_cnt = (int)(diagv.size() - S.diag_off);
-      S.rows_cnt = (int)(rowsv.size() - S.rows_off);
+      S.panel_cnt = (int)(panelv.size() - S.panel_off);
       S.prob_cnt = (int)(probv.size() - S.prob_off);
       S.tc_cnt = (int)(hs.tcv.size() - S.tc_off);
     }
@@ -586,21 +608,47 @@ void build_schedule(ncl_kkt_s* h) {
           bad("assembly child ranges");
       }
     }
-    for (const int2& it : belowv)
+    for (const int4& it : hs.bbelowv)
+      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x] - P.sn_ncol[it.x] || it.y % SOLVE_ROWS ||
+          it.z < 0 || it.z >= P.sn_ncol[it.x] || it.z % 256)
+        bad("solve item");
+    if (hs.below_cptr.size() != belowv.size() + 1) bad("solve child ranges");
+    for (size_t i = 0; i < belowv.size(); i++) {
+      const int2 it = belowv[i];
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x] - P.sn_ncol[it.x]) bad("solve item");
+      if (hs.below_cptr[i] > hs.below_cptr[i + 1] || hs.below_cptr[i + 1] > (int32_t)hs.below_cran.size())
+        bad("solve child ranges");
+      const int a1 = std::min(it.y + SOLVE_ROWS, P.sn_nrow[it.x] - P.sn_ncol[it.x]);
+      for (int32_t e = hs.below_cptr[i]; e < hs.below_cptr[i + 1]; e++) {
+        const int4 cr = hs.below_cran[e];
+        if (cr.x < 0 || cr.x >= P.ns || P.sn_parent[cr.x] != it.x || cr.y < 0 || cr.y >= cr.z ||
+            cr.z > P.sn_nrow[cr.x] - P.sn_ncol[cr.x])
+          bad("solve child ranges");
+        const int32_t* rel = P.relmap.data() + P.relmap_off[cr.x];
+        if (rel[cr.y] < P.sn_ncol[it.x] + it.y || rel[cr.z - 1] >= P.sn_ncol[it.x] + a1) bad("solve child ranges");
+      }
+    }
     for (int32_t s : smallv)
       if (small_front_smem(P.sn_nrow[s], P.sn_ncolp[s], (int)esz) > SMALL_SMEM_MAX || P.sn_ncol[s] > 64 ||
           P.sn_nrow[s] > 512)
         bad("small front smem");
     for (const Level& L : h->levels)
       if (L.small_smem > SMALL_SMEM_MAX) bad("small front smem");
-    for (const int2& it : diagv)
-      if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_ncol[it.x] || it.y % MACRO_NB) bad("macro diag item");
-    for (const int4& it : rowsv) {
+    // every sync slot is shared by exactly 1 + (rows below / MACRO_ROWS) items
+    // of one front and panel (the roles come from the slot's ticket counter)
+    for (size_t i = 0; i < panelv.size();) {
+      const int4 it = panelv[i];
       const int s = it.x;
-      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.y % MACRO_NB ||
-          it.z < std::min(it.y + MACRO_NB, P.sn_ncol[s]) || it.z >= P.sn_nrow[s])
-        bad("macro rows item");
+      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.y % MACRO_NB || it.z < 0 ||
+          it.z + 8 > hs.panel_sync || it.z % 8)
+        bad("macro panel item");
+      const int qe = std::min(it.y + MACRO_NB, P.sn_ncol[s]);
+      const size_t n = 1 + (size_t)((P.sn_nrow[s] - qe + MACRO_ROWS - 1) / MACRO_ROWS);
+      if (i + n > panelv.size()) bad("macro panel item");
+      for (size_t k = 0; k < n; k++)
+        if (panelv[i + k].x != s || panelv[i + k].y != it.y || panelv[i + k].z != it.z) bad("macro panel item");
+      if (i + n < panelv.size() && panelv[i + n].z == it.z) bad("macro panel item");
+      i += n;
     }
     for (const TcProb& q : hs.tcv) {
       const int64_t csz = q.c_in_u ? Usz : Lsz;
@@ -766,8 +814,8 @@ void build_device(ncl_kkt_s* h) {
   h->d_asm_cptr = h->upload(hs.asm_cptr);
   h->d_asm_cran = h->upload(hs.asm_cran);
   h->d_small = h->upload(hs.smallv);
-  h->d_rows = h->upload(hs.rowsv);
-  h->d_diag = h->upload(hs.diagv);
+  h->d_panel = h->upload(hs.panelv);
+  h->d_panel_sync = h->alloc<int>(std::max<int64_t>(hs.panel_sync, 8));
   h->d_probs = h->upload(hs.probv);
   h->d_tilep = h->upload(hs.tilep);
   h->d_chain = h->upload(hs.chainv);
@@ -775,6 +823,9 @@ void build_device(ncl_kkt_s* h) {
   h->d_chain_pran = h->upload(hs.chain_pran);
   h->d_chain_sync = h->alloc<int>(2 * (int64_t)P.ns + 2 * hs.nbrows);
   h->d_below = h->upload(hs.belowv);
+  h->d_bbelow = h->upload(hs.bbelowv);
+  h->d_below_cptr = h->upload(hs.below_cptr);
+  h->d_below_cran = h->upload(hs.below_cran);
   CK(cudaMallocHost(&h->h_pinned, sizeof(double) * (size_t)(7 * ni + 64 + 3 * ni * MAX_RHS_SWEEP)));
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
@@ -876,10 +927,9 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
       launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, (int)L.small_smem, eps, pol, st);
     });
     for (const Step& S : L.steps) {
-      klaunch(h, st, f32 ? "macro_diag_f32" : "macro_diag_f64", S.diag_cnt, S.diag_cost,
-              [&] { launch_macro_diag<T>(P, N, h->d_diag + S.diag_off, S.diag_cnt, eps, pol, st); });
-      klaunch(h, st, f32 ? "macro_rows_f32" : "macro_rows_f64", S.rows_cnt, S.rows_cost,
-              [&] { launch_macro_rows<T>(P, N, h->d_rows + S.rows_off, S.rows_cnt, st); });
+      klaunch(h, st, f32 ? "macro_panel_f32" : "macro_panel_f64", S.panel_cnt, S.panel_cost, [&] {
+        launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->d_panel_sync, h->d_err, eps, pol, st);
+      });
       klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost, [&] {
         launch_gemm_simt<T>(P, N, h->d_probs + S.prob_off, h->d_tilep + S.tp_off, S.tiles, st);
       });
@@ -921,12 +971,15 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
                           h->d_chain_pran, xp, W, nrhs, tk_f, fl_f, serr, st);
     });
     klaunch(h, st, f32 ? "fwd_below_f32" : "fwd_below_f64", L.below_cnt, scaled(L.fbelow_cost, nrhs),
-            [&] { launch_fwd_below<T>(P, N, h->d_below + L.below_off, L.below_cnt, xp, W, nrhs, st); });
+            [&] {
+              launch_fwd_below<T>(P, N, h->d_below + L.below_off, h->d_below_cptr + L.below_off, h->d_below_cran,
+                                  L.below_cnt, xp, W, nrhs, st);
+            });
   }
   for (int l = (int)h->levels.size() - 1; l >= 0; l--) {
     const Level& L = h->levels[l];
-    klaunch(h, st, f32 ? "bwd_below_f32" : "bwd_below_f64", L.below_cnt, scaled(L.bbelow_cost, nrhs),
-            [&] { launch_bwd_below<T>(P, N, h->d_below + L.below_off, L.below_cnt, xp, Pw, nrhs, st); });
+    klaunch(h, st, f32 ? "bwd_below_f32" : "bwd_below_f64", L.bbelow_cnt, scaled(L.bbelow_cost, nrhs),
+            [&] { launch_bwd_below<T>(P, N, h->d_bbelow + L.bbelow_off, L.bbelow_cnt, xp, Pw, nrhs, st); });
     klaunch(h, st, f32 ? "bwd_chain_f32" : "bwd_chain_f64", L.chain_cnt, scaled(L.bdiag_cost, nrhs), [&] {
       launch_bwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, xp, Pw, nrhs, tk_b, fl_b,
                           serr, st);
@@ -1218,6 +1271,7 @@ void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
           [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, s2); });
   CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), s2));
   CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s2));
+  CK(cudaMemsetAsync(h->d_panel_sync, 0, std::max<int64_t>(h->hs.panel_sync, 8) * sizeof(int), s2));
   if (is_fp32(h)) {
     run_factor<float>(h, h->nf, s2);
     klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},

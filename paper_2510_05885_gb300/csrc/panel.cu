@@ -3,23 +3,21 @@
 //
 // The pivot columns of a large front are processed MACRO_NB = 128 at a time
 // (right-looking blocked LDL^T with D diagonal and static pivoting, Section
-// 3.1).  For macro panel [q0, qe):
-//
-//   k_macro_diag  one CTA per front: the w x w diagonal block (w <= 128) is
-//                 factored in shared memory by 32-column sub-blocks (one warp
-//                 factors and inverts the sub-block in registers; all warps
-//                 form the rows below it inside the block and update the
-//                 rest of the block).  Writes L11, D1, the pivot status and
-//                 the inverses of the 32 x 32 unit diagonal sub-blocks (used
-//                 by the row kernel and by the triangular sweeps).
-//   k_macro_rows  one CTA per 64 rows below the panel: block forward
-//                 substitution X = F21 L11^-T with the inverted sub-blocks,
-//                 then L21 = X D1^-1.  For a tensor-core front it also writes
-//                 the split TF32 operands of L21 and of W = L21 D1 = X.
-//   (then the trailing update of the remaining pivot columns with K = w, on
-//    the SIMT or the tensor-core update kernel.)
+// 3.1).  For macro panel [q0, qe) one launch (k_macro_panel) runs, for every
+// large front of the level:
+//   the diagonal role  one CTA: the w x w diagonal block (w <= 128) is
+//                      factored in shared memory by 32-column sub-blocks,
+//                      each published as soon as it is done;
+//   the row role       one CTA per 64 rows below the panel: as the
+//                      sub-blocks appear, the blocked forward substitution
+//                      L21 = F21 L11^-T D1^-1; for a tensor-core front also
+//                      the split TF32 operands of L21 and W = L21 D1.
+// Then the trailing update of the remaining pivot columns with K = w runs on
+// the SIMT or the tensor-core update kernel.
 #include "runtime.h"
 #include "pivot.cuh"
+
+#include <algorithm>
 
 namespace ncl {
 
@@ -61,8 +59,9 @@ __device__ __forceinline__ void load_tile(T* dst, int ldd, const T* src, int64_t
   }
 }
 
-int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + MNB) * esz + 2 * MNB; }
-int macro_rows_smem(int esz) { return (RB * LDM + 10 * 32 * LDS + MNB) * esz; }
+static int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + MNB) * esz + 2 * MNB; }
+static int macro_rows_smem(int esz) { return (RB * LDM + 10 * 32 * LDS + MNB) * esz; }
+int macro_panel_smem(int esz) { return std::max(macro_diag_smem(esz), macro_rows_smem(esz)); }
 
 // LDL^T of a 32 x 32 diagonal sub-block in shared memory (row stride ld,
 // cw <= 32 valid rows) by one warp, lane i holding row i in registers:
@@ -84,14 +83,13 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
       const int sg = __shfl_sync(0xffffffffu, my_sign, k);
       const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
       const T wk = r[k];
-      const T li = wk * (T(1) / dk);
-      // branch-free update (a predicated branch around each shuffle costs a
-      // reconvergence per shuffle)
+      // rows above the pivot get a zero multiplier, so the update needs no
+      // per-column select or branch (a predicated branch around each shuffle
+      // costs a reconvergence per shuffle); entries above a lane's diagonal
+      // are never read
+      const T li = lane > k ? wk * (T(1) / dk) : T(0);
 #pragma unroll
-      for (int j = k + 1; j < 32; j++) {
-        const T wj = __shfl_sync(0xffffffffu, wk, j);
-        r[j] -= (lane >= j ? li : T(0)) * wj;
-      }
+      for (int j = k + 1; j < 32; j++) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
       r[k] = lane > k ? li : (lane == k ? dk : r[k]);
       my_d = lane == k ? dk : my_d;
       my_st = lane == k ? stt : my_st;
@@ -202,26 +200,34 @@ __device__ __forceinline__ void store_tile(T* dst, int64_t ldd, const T* src, in
   }
 }
 
-// One CTA (256 threads) factors the w x w diagonal block (w <= 128) of a
-// macro panel in shared memory, by 32-column sub-blocks: one warp factors
-// the sub-block (factor_sub32); the rows below it inside the block are
-// solved by the blocked forward substitution, X = F21 L_jj^-T, and scaled,
-// L21 = X D^-1; then all warps update the rest of the block,
-// A[r][c] -= sum_u X[r][u] L21[c][u], with register tiles (12 rows x 3
-// columns per thread).  At the end four warps invert the four unit lower
-// sub-blocks (for the triangular sweeps) while the block, D and the pivot
-// status are written back.
+constexpr long long PANEL_WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
+
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Diagonal role of a macro panel (one CTA of 256 threads): factors the w x w
+// diagonal block (w <= 128) in shared memory by 32-column sub-blocks.  One
+// warp factors the sub-block (factor_sub32); the rows below it inside the
+// block are solved by the blocked forward substitution, X = F21 L_jj^-T,
+// and scaled, L21 = X D^-1; the sub-block's columns and pivots are then
+// published (global stores, fence, release flag j) for the row CTAs, and
+// all warps update the rest of the block, A[r][c] -= sum_u X[r][u] L21[c][u],
+// with register tiles (12 rows x 3 columns per thread).  At the end four
+// warps invert the four unit lower sub-blocks (for the triangular sweeps).
 template <typename T>
-__global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
-                                                       double eps, int policy) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int* flags,
+                                                double eps, int policy, unsigned char* smem_raw) {
   T* A = reinterpret_cast<T*>(smem_raw);   // w x w block, row stride LDM
   T* Xs = A + MNB * LDM;                   // X of the rows below the sub-block
   T* dsh = Xs + (MNB - 32) * LDS;          // pivots of the block (MNB)
   int8_t* sg = reinterpret_cast<int8_t*>(dsh + MNB);   // block signs, then pivot status
   int8_t* pst = sg + MNB;
-  const int2 it = items[blockIdx.x];
-  const int s = it.x, q0 = it.y;
   const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
   const int w = min(MNB, ncol - q0);
   T* Lb = N.L + P.sn_Loff[s] + (int64_t)q0 * ncp + q0;
@@ -253,6 +259,15 @@ __global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, c
         A[(rb + r) * LDM + c0 + c] = x / dsh[c0 + c];
       }
       __syncthreads();
+    }
+    // publish the sub-block's columns [c0, c0 + cw) of rows [c0, w) and its pivots
+    store_tile(Lb + (int64_t)c0 * ncp + c0, ncp, A + c0 * LDM + c0, LDM, w - c0, cw,
+               [&](int r, int c) { return c <= r; });
+    if (tid < cw) N.D[col0 + q0 + c0 + tid] = dsh[c0 + tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release_i32(flags + (c0 >> 5), 1);
+    if (nr > 0) {
       // A[r][c] -= sum_u X[r][u] L21[c][u], rb <= c <= r < w
       T acc[MR][GC];
 #pragma unroll
@@ -287,45 +302,57 @@ __global__ void __launch_bounds__(256, 1) k_macro_diag(DevPlan P, DevNum<T> N, c
   if (warp < nbk)
     invert_sub32<T>(A + 32 * warp * LDM + 32 * warp, LDM, min(32, w - 32 * warp),
                     N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + warp) * 1024, lane);
-  for (int c = tid; c < w; c += blockDim.x) {
-    N.D[col0 + q0 + c] = dsh[c];
-    N.piv[col0 + q0 + c] = pst[c];
-  }
-  store_tile(Lb, ncp, A, LDM, w, MNB, [&](int r, int c) { return c <= r; });
+  for (int c = tid; c < w; c += blockDim.x) N.piv[col0 + q0 + c] = pst[c];
 }
 
-// Rows below a macro panel, RB per CTA: for each 32-column sub-block j,
-// X_j = R_j L_jj^-T by the blocked forward substitution, then
-// R_i -= X_j L_ij^T for the later sub-blocks (lane = column, the rows of a
-// warp in registers); finally L21 = X D1^-1.
+// Row role of a macro panel (one CTA per RB rows below it): stages its rows
+// while the diagonal role works, then for each 32-column sub-block j, as
+// soon as it is published, X_j = R_j L_jj^-T by the blocked forward
+// substitution and R_i -= X_j L_ij^T for the later sub-blocks (lane =
+// column, the rows of a warp in registers); finally L21 = X D1^-1, and for a
+// tensor-core front the split TF32 operands of L21 and of W = L21 D1 = X.
 template <typename T>
-__global__ void __launch_bounds__(256, 1) k_macro_rows(DevPlan P, DevNum<T> N, const int4* __restrict__ items) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void panel_rows_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int r0,
+                                                const int* flags, int* err, unsigned char* smem_raw) {
   T* R = reinterpret_cast<T*>(smem_raw);   // RB rows x w columns, stride LDM
   T* Ld = R + RB * LDM;                    // 4 unit lower diagonal sub-blocks of L11
   T* Lo = Ld + 4 * 32 * LDS;               // 6 off-diagonal sub-blocks (i > j) of L11
   T* dsh = Lo + 6 * 32 * LDS;              // D1
-  const int4 it = items[blockIdx.x];
-  const int s = it.x, q0 = it.y, r0 = it.z;
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
   const int w = min(MNB, ncol - q0);
   const int nbk = (w + 31) / 32;
   const int nr = min(RB, nrow - r0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   T* Lb = N.L + P.sn_Loff[s];
-  for (int i = 0; i < nbk; i++)
-    for (int j = 0; j <= i; j++) {
-      T* dst = (i == j) ? Ld + i * 32 * LDS : Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
-      const int rows = min(32, w - 32 * i);
-      load_tile(dst, LDS, Lb + (int64_t)(q0 + 32 * i) * ncp + q0 + 32 * j, ncp, 32, 32,
-                [&](int rr, int cc) { return rr < rows && (i > j || cc < rr); });
-    }
-  for (int c = tid; c < MNB; c += blockDim.x) dsh[c] = c < w ? N.D[col0 + q0 + c] : T(1);
   load_tile(R, LDM, Lb + (int64_t)r0 * ncp + q0, ncp, RB, MNB, [&](int r, int c) { return r < nr && c < w; });
-  __syncthreads();
   constexpr int KR = RB / 8;   // rows per warp in the updates (lane = column)
   T* Rw = R + warp * LDM;      // row warp + 8 k is Rw[8 k LDM + ...]
   for (int j = 0; j < nbk; j++) {
+    // wait (bounded) for sub-block j, then fetch its published columns
+    if (tid == 0) {
+      if (!ld_acquire_i32(flags + j) && !ld_acquire_i32(err)) {
+        const long long t0 = clock64();
+        while (!ld_acquire_i32(flags + j)) {
+          if (clock64() - t0 > PANEL_WAIT_CYCLES || ld_acquire_i32(err)) {
+            atomicExch(err, 1);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = j; i < nbk; i++) {
+      T* dst = (i == j) ? Ld + i * 32 * LDS : Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
+      const int rows = min(32, w - 32 * i);
+      const T* src = Lb + (int64_t)(q0 + 32 * i) * ncp + q0 + 32 * j;
+      for (int e = tid; e < 1024; e += blockDim.x) {
+        const int rr = e >> 5, cc = e & 31;
+        dst[rr * LDS + cc] = (rr < rows && (i > j || cc < rr)) ? __ldcg(src + (int64_t)rr * ncp + cc) : T(0);
+      }
+    }
+    if (tid < 32) dsh[32 * j + tid] = 32 * j + tid < w ? __ldcg(N.D + col0 + q0 + 32 * j + tid) : T(1);
+    __syncthreads();
     block_trsm32<T>(R + 32 * j, LDM, nr, min(32, w - 32 * j), Ld + j * 32 * LDS, LDS);
     __syncthreads();
     for (int i = j + 1; i < nbk; i++) {
@@ -371,6 +398,33 @@ __global__ void __launch_bounds__(256, 1) k_macro_rows(DevPlan P, DevNum<T> N, c
         }
       }
     }
+  }
+}
+
+// One launch per macro panel step of a level: for each large front, one
+// CTA in the diagonal role and one per RB rows below the panel in the row
+// role.  A CTA's role comes from the front's ticket counter (the first CTA
+// to arrive takes the diagonal), so every CTA that waits waits for a CTA
+// that is already running: the waits cannot deadlock, whatever the order
+// in which CTAs are scheduled.  Waits are bounded (the factor's error flag
+// is set past the limit).
+// items: (front, q0, sync slot); sync[slot] = ticket counter, sync[slot + 1
+// + j] = flag of sub-block j.
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_macro_panel(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
+                                                        int* sync, int* err, double eps, int policy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int ticket;
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, q0 = it.y;
+  int* slot = sync + it.z;
+  if (threadIdx.x == 0) ticket = atomicAdd(slot, 1);
+  __syncthreads();
+  if (ticket == 0) {
+    panel_diag_role<T>(P, N, s, q0, slot + 1, eps, policy, smem_raw);
+  } else {
+    const int qe = min(q0 + MNB, P.sn_ncol[s]);
+    panel_rows_role<T>(P, N, s, q0, qe + RB * (ticket - 1), slot + 1, err, smem_raw);
   }
 }
 
@@ -469,35 +523,21 @@ template void launch_factor_small<double>(const DevPlan&, const DevNum<double>&,
                                           int, cudaStream_t);
 
 template <typename T>
-void launch_macro_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
-                       cudaStream_t st) {
+void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,
+                        double eps, int policy, cudaStream_t st) {
   if (count <= 0) return;
   static bool attr = false;
-  const int smem = macro_diag_smem((int)sizeof(T));
+  const int smem = macro_panel_smem((int)sizeof(T));
   if (!attr) {
-    cudaFuncSetAttribute(k_macro_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_macro_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  k_macro_diag<T><<<count, 256, smem, st>>>(P, N, items, eps, policy);
+  k_macro_panel<T><<<count, 256, smem, st>>>(P, N, items, sync, err, eps, policy);
 }
 
-template <typename T>
-void launch_macro_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st) {
-  if (count <= 0) return;
-  static bool attr = false;
-  const int smem = macro_rows_smem((int)sizeof(T));
-  if (!attr) {
-    cudaFuncSetAttribute(k_macro_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
-  k_macro_rows<T><<<count, 256, smem, st>>>(P, N, items);
-}
-
-template void launch_macro_diag<float>(const DevPlan&, const DevNum<float>&, const int2*, int, double, int,
-                                       cudaStream_t);
-template void launch_macro_diag<double>(const DevPlan&, const DevNum<double>&, const int2*, int, double, int,
-                                        cudaStream_t);
-template void launch_macro_rows<float>(const DevPlan&, const DevNum<float>&, const int4*, int, cudaStream_t);
-template void launch_macro_rows<double>(const DevPlan&, const DevNum<double>&, const int4*, int, cudaStream_t);
+template void launch_macro_panel<float>(const DevPlan&, const DevNum<float>&, const int4*, int, int*, int*, double,
+                                        int, cudaStream_t);
+template void launch_macro_panel<double>(const DevPlan&, const DevNum<double>&, const int4*, int, int*, int*, double,
+                                         int, cudaStream_t);
 
 }  // namespace ncl

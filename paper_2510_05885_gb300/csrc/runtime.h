@@ -136,13 +136,10 @@ void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* prob
 
 // launchers (panel.cu)
 int small_front_smem(int nrow, int ncp, int esz);
-int macro_diag_smem(int esz);
-int macro_rows_smem(int esz);
+int macro_panel_smem(int esz);
 template <typename T>
-void launch_macro_diag(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, double eps, int policy,
-                       cudaStream_t st);
-template <typename T>
-void launch_macro_rows(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, cudaStream_t st);
+void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,
+                        double eps, int policy, cudaStream_t st);
 template <typename T>
 void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st);
 
@@ -159,10 +156,10 @@ void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, i
                       const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags, int* err,
                       cudaStream_t st);
 template <typename T>
-void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, T* xp, T* W,
-                      int nrhs, cudaStream_t st);
+void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
+                      int count, T* xp, T* W, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const T* xp,
+void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, const T* xp,
                       T* Pw, int nrhs, cudaStream_t st);
 template <typename T>
 void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, T* xp, const T* Pw,

@@ -13,16 +13,6 @@
 
 namespace ncl {
 
-__device__ __forceinline__ int lb_i32(const int32_t* a, int n, int32_t v) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (a[mid] < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // ---------------------------------------------------------------------------
 // permutations
 // ---------------------------------------------------------------------------
@@ -316,28 +306,38 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
   T acc[MAX_RHS_SWEEP];
 #pragma unroll
   for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
-  if (mine) {
+  if (mine && B < nbr - 1) {
+    // chunks q = 0, 1, ...: 32 rows of block-row I = nbr - 1 - q / 4, the
+    // next chunk loaded before the current one is used and before waiting
     const T* lcol = Lb + R0 + min(rw, nr - 1);
-    for (int I = nbr - 1; I > B; I--) {
-      chain_wait(flags + broff + I, err);
-      const int nri = min(CHAIN_ROWS, ncol - CHAIN_ROWS * I);
-#pragma unroll 1
-      for (int c = 0; c < 4; c++) {
-        const int q0 = CHAIN_ROWS * I + 32 * c, bwi = min(32, nri - 32 * c);
-        if (bwi <= 0) break;
-        T lv[32];
+    const int nchunk = 4 * (nbr - 1 - B);
+    auto rows_of = [&](int q, int& q0, int& bwi) {
+      const int I = nbr - 1 - (q >> 2);
+      q0 = CHAIN_ROWS * I + 32 * (q & 3);
+      bwi = max(0, min(32, ncol - q0));
+    };
+    T lv[32], ln[32];
+    int nq0, nbw;
+    rows_of(0, nq0, nbw);
 #pragma unroll
-        for (int v = 0; v < 32; v++) lv[v] = v < bwi ? lcol[(int64_t)(q0 + v) * ncp] : T(0);
-        T xv[MAX_RHS_SWEEP];
+    for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
+    for (int q = 0; q < nchunk; q++) {
+      const int q0 = nq0, bwi = nbw;
 #pragma unroll
-        for (int r = 0; r < MAX_RHS_SWEEP; r++)
-          xv[r] = (r < nrhs && lane < bwi) ? __ldcg(xp + (int64_t)r * P.dim + col0 + q0 + lane) : T(0);
+      for (int v = 0; v < 32; v++) lv[v] = ln[v];
+      if (q + 1 < nchunk) {
+        rows_of(q + 1, nq0, nbw);
 #pragma unroll
-        for (int r = 0; r < MAX_RHS_SWEEP; r++) {
-          if (r >= nrhs) break;
+        for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
+      }
+      if ((q & 3) == 0) chain_wait(flags + broff + nbr - 1 - (q >> 2), err);
+      if (bwi <= 0) continue;
 #pragma unroll
-          for (int v = 0; v < 32; v++) acc[r] += lv[v] * __shfl_sync(0xffffffffu, xv[r], v);
-        }
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+        if (r >= nrhs) break;
+        const T xv = lane < bwi ? __ldcg(xp + (int64_t)r * P.dim + col0 + q0 + lane) : T(0);
+#pragma unroll
+        for (int v = 0; v < 32; v++) acc[r] += lv[v] * __shfl_sync(0xffffffffu, xv, v);
       }
     }
   }
@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
 //   W_s[a] = (children's updates landing on row a) - L21[a,:] y_s
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_below(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+                                                   const int32_t* __restrict__ cptr, const int4* __restrict__ cran,
                                                    const T* __restrict__ xp, T* __restrict__ W, int nrhs) {
   __shared__ T t[SOLVE_ROWS * 8];
   const int2 it = items[blockIdx.x];
@@ -388,12 +389,13 @@ __global__ void __launch_bounds__(256) k_fwd_below(DevPlan P, DevNum<T> N, const
   const T* Lb = N.L + P.sn_Loff[s];
   for (int idx = threadIdx.x; idx < SOLVE_ROWS * nrhs; idx += blockDim.x) t[idx] = T(0);
   __syncthreads();
-  for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
-    const int c = P.child_list[k];
-    const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
+  // children's updates landing on these rows (ranges found on the host),
+  // child by child
+  for (int e = cptr[blockIdx.x]; e < cptr[blockIdx.x + 1]; e++) {
+    const int4 cr = cran[e];
+    const int c = cr.x;
     const int32_t* rel = P.relmap + P.relmap_off[c];
-    const int lo = lb_i32(rel, nbc, ncol + a0), hi = lb_i32(rel, nbc, ncol + a1);
-    for (int a = lo + threadIdx.x; a < hi; a += blockDim.x)
+    for (int a = cr.y + threadIdx.x; a < cr.z; a += blockDim.x)
       for (int r = 0; r < nrhs; r++) t[r * SOLVE_ROWS + rel[a] - ncol - a0] += W[r * P.Wtot + P.sn_Woff[c] + a];
     __syncthreads();
   }
@@ -411,17 +413,21 @@ __global__ void __launch_bounds__(256) k_fwd_below(DevPlan P, DevNum<T> N, const
   }
 }
 
-// backward: partial sums of L21^T x_below over a run of SOLVE_ROWS rows
+// backward: partial sums of L21^T x_below over a run of SOLVE_ROWS rows and
+// a run of up to 256 columns (item (s, a0, k0)); for few columns, G groups
+// of threads split the rows and their sums are added in shared memory
 template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+__global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
                                                    const T* __restrict__ xp, T* __restrict__ Pw, int nrhs) {
-  __shared__ T xb[SOLVE_ROWS * 8];
-  const int2 it = items[blockIdx.x];
-  const int s = it.x, a0 = it.y;
+  __shared__ T xb[SOLVE_ROWS * MAX_RHS_SWEEP];
+  __shared__ T red[4][256];
+  const int4 it = items[blockIdx.x];
+  const int s = it.x, a0 = it.y, k0 = it.z;
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
   const int nb = nrow - ncol;
   const int a1 = min(a0 + SOLVE_ROWS, nb);
   const int chunk = a0 / SOLVE_ROWS;
+  const int kc = min(256, ncol - k0);
   const T* Lb = N.L + P.sn_Loff[s];
   const int32_t* rows = P.sn_rows + P.sn_rows_off[s] + ncol;
   for (int idx = threadIdx.x; idx < (a1 - a0) * nrhs; idx += blockDim.x) {
@@ -429,11 +435,33 @@ __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const
     xb[r * SOLVE_ROWS + a] = xp[r * P.dim + rows[a0 + a]];
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
-    for (int r = 0; r < nrhs; r++) {
-      T acc = T(0);
-      for (int a = a0; a < a1; a++) acc += Lb[(int64_t)(ncol + a) * ncp + k] * xb[r * SOLVE_ROWS + a - a0];
-      Pw[r * P.Ptot + P.sn_Poff[s] + (int64_t)chunk * ncol + k] = acc;
+  // G thread groups of blockDim / G >= kc threads each (a single group for
+  // the smallest fronts, whose CTAs are many and short)
+  const int cols = (kc + 31) & ~31;
+  const int G = (cols > 128 || cols <= 32) ? 1 : (cols > 64 ? 2 : 4);
+  const int tpg = blockDim.x / G, g = threadIdx.x / tpg, kl = threadIdx.x - g * tpg;
+  const int per = (a1 - a0 + G - 1) / G;
+  const int ga0 = a0 + g * per, ga1 = min(a1, ga0 + per);
+  const T* col = Lb + (int64_t)ncol * ncp + k0 + min(kl, kc - 1);
+  for (int r = 0; r < nrhs; r++) {
+    const T* x = xb + r * SOLVE_ROWS - a0;
+    T acc = T(0);
+    if (kl < kc) {
+#pragma unroll 16
+      for (int a = ga0; a < ga1; a++) acc += col[(int64_t)a * ncp] * x[a];
+    }
+    T* out = Pw + r * P.Ptot + P.sn_Poff[s] + (int64_t)chunk * ncol + k0;
+    if (G == 1) {
+      if (kl < kc) out[kl] = acc;
+    } else {
+      red[g][kl] = acc;
+      __syncthreads();
+      if (threadIdx.x < kc) {
+        T t = T(0);
+        for (int q = 0; q < G; q++) t += red[q][threadIdx.x];
+        out[threadIdx.x] = t;
+      }
+      __syncthreads();
     }
   }
 }
@@ -451,12 +479,12 @@ void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, i
   k_fwd_chain<T><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err);
 }
 template <typename T>
-void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, T* xp, T* W, int nrhs,
-                      cudaStream_t st) {
-  if (count > 0) k_fwd_below<T><<<count, 256, 0, st>>>(P, N, items, xp, W, nrhs);
+void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
+                      int count, T* xp, T* W, int nrhs, cudaStream_t st) {
+  if (count > 0) k_fwd_below<T><<<count, 256, 0, st>>>(P, N, items, cptr, cran, xp, W, nrhs);
 }
 template <typename T>
-void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const T* xp, T* Pw,
+void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, const T* xp, T* Pw,
                       int nrhs, cudaStream_t st) {
   if (count > 0) k_bwd_below<T><<<count, 256, 0, st>>>(P, N, items, xp, Pw, nrhs);
 }
@@ -760,9 +788,9 @@ void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64
   template void launch_perm_out<T>(const DevPlan&, const T*, double*, int64_t, int, int, cudaStream_t);           \
   template void launch_fwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, const int32_t*,     \
                                     const int4*, T*, const T*, int, int*, int*, int*, cudaStream_t);              \
-  template void launch_fwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, int, T*, T*, int,              \
-                                    cudaStream_t);                                                                \
-  template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, int, const T*, T*, int,        \
+  template void launch_fwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, const int32_t*, const int4*,  \
+                                    int, T*, T*, int, cudaStream_t);                                              \
+  template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int4*, int, const T*, T*, int,        \
                                     cudaStream_t);                                                                \
   template void launch_bwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, T*, const T*, int,   \
                                     int*, int*, int*, cudaStream_t);

@@ -50,7 +50,10 @@ def check_against_oracle(inst, prec, X, finfo, sinfo, eta_tol):
     assert eta <= eta_tol, eta
     assert sinfo.backward_err <= eta_tol * 1.0001
     kappa = O.cond1_estimate(A, fac) if A.shape[0] <= 60000 else 1e6
-    u = 2.0 ** -53 if prec == "fp64" else 1e-10
+    # two backward-stable solves with backward errors eta_1, eta_2 differ by
+    # about kappa (eta_1 + eta_2): FP64 is compared at its achieved backward
+    # errors (at least u), FP32 + refinement at its target 1e-10
+    u = max(2.0 ** -53, eta + eta_o) if prec == "fp64" else 1e-10
     tol = max(1e-9, 10 * kappa * u)
     err = np.max(np.abs(X - x_o)) / np.max(np.abs(x_o))
     assert err <= tol, (err, tol, kappa)
