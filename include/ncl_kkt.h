@@ -97,9 +97,9 @@ typedef struct {
                                  <= 0 selects 1e-10 (FP32_IR) or 1e-12 (FP64) */
     int32_t ir_max_iter;      /* refinement steps; < 0 selects 10 (FP32_IR) or 3 (FP64) */
     int32_t use_fgmres;       /* 1: FGMRES-IR when Richardson stagnates (default 1) */
-    int32_t use_tensor_cores; /* FP32_IR: 1 (default) tcgen05 split-TF32 update blocks of
-                                 fronts with >= 256 pivots; 2: also the panel trailing
-                                 updates; 0: SIMT FP32 everywhere */
+    int32_t use_tensor_cores; /* FP32_IR, fronts with >= 256 pivots: 2 (default) tcgen05
+                                 split-TF32 update blocks and panel trailing updates;
+                                 1: update blocks only; 0: SIMT FP32 everywhere */
     int32_t leaf_size;        /* nested-dissection leaf size (default 96) */
     int32_t host_only;        /* 1: symbolic analysis only, no device memory; the
                                  handle then answers only the get_* queries */

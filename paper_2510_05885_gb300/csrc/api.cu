@@ -44,12 +44,11 @@ struct CudaError {
     if (e_ != cudaSuccess) throw CudaError{e_, #x};            \
   } while (0)
 
-// In the FP32 path the update block F22 -= L21 D1 L21^T of a front with at
-// least TC_MIN_K pivots runs on the tensor cores; shorter inner dimensions,
-// and the 32-wide trailing updates of the panels, do not amortise the fixed
-// cost of a tensor-core tile and stay on the SIMT kernel (measured; the
-// option value use_tensor_cores = 2 also puts the trailing updates on the
-// tensor cores).
+// In the FP32 path the fronts with at least TC_MIN_K pivots get split TF32
+// operands: their update block F22 -= L21 D1 L21^T runs on the tensor cores,
+// and with use_tensor_cores = 2 (the default) also the K = 128 trailing
+// updates of their macro panels; shorter inner dimensions stay on the SIMT
+// kernel.
 constexpr int TC_MIN_K = 256;
 
 // per-launch arithmetic (flops on the stored blocks) and minimum traffic
@@ -1594,7 +1593,7 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->ir_tol = 0.0;
   o->ir_max_iter = -1;
   o->use_fgmres = 1;
-  o->use_tensor_cores = 1;
+  o->use_tensor_cores = 2;
   o->leaf_size = 96;
   o->host_only = 0;
   o->precision_fallback = 1;
