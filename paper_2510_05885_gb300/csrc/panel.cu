@@ -211,14 +211,57 @@ __device__ __forceinline__ void st_release_i32(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// barrier among warps 1..7 of a 256-thread CTA (warp 0 is busy meanwhile)
+__device__ __forceinline__ void bar_warps_1_7() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+
+// A[r][c] -= sum_u X[r - rb][u] L21[c][u] (L21 in the columns c0..c0+31 of
+// A) for rows [r_begin, w) and columns [c_begin, c_end) (at most 64), c <= r;
+// done by the nw warps wfirst.. of the CTA, lane = column, register tiles of
+// up to 8 rows per warp and trip
+template <typename T>
+__device__ __forceinline__ void block_update(T* A, const T* Xs, int c0, int rb, int w, int r_begin, int c_begin,
+                                             int c_end, int wfirst, int nw) {
+  const int warp = (threadIdx.x >> 5) - wfirst, lane = threadIdx.x & 31;
+  if (warp < 0 || warp >= nw || c_begin >= c_end) return;
+  constexpr int MRW = 8;
+  const int ng = (c_end - c_begin + 31) / 32;   // 1 or 2
+  for (int rr0 = r_begin + warp * MRW; rr0 < w; rr0 += nw * MRW) {
+    T acc[MRW][2];
+#pragma unroll
+    for (int m = 0; m < MRW; m++) acc[m][0] = acc[m][1] = T(0);
+#pragma unroll 2
+    for (int u = 0; u < 32; u++) {
+      T bv[2];
+#pragma unroll
+      for (int g = 0; g < 2; g++) bv[g] = g < ng ? A[min(c_begin + 32 * g + lane, c_end - 1) * LDM + c0 + u] : T(0);
+#pragma unroll
+      for (int m = 0; m < MRW; m++) {
+        const T a = Xs[(min(rr0 + m, w - 1) - rb) * LDS + u];
+        acc[m][0] += a * bv[0];
+        acc[m][1] += a * bv[1];
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < MRW; m++) {
+      const int r = rr0 + m;
+#pragma unroll
+      for (int g = 0; g < 2; g++) {
+        const int c = c_begin + 32 * g + lane;
+        if (g < ng && r < w && c < c_end && c <= r) A[r * LDM + c] -= acc[m][g];
+      }
+    }
+  }
+}
+
 // Diagonal role of a macro panel (one CTA of 256 threads): factors the w x w
-// diagonal block (w <= 128) in shared memory by 32-column sub-blocks.  One
-// warp factors the sub-block (factor_sub32); the rows below it inside the
-// block are solved by the blocked forward substitution, X = F21 L_jj^-T,
-// and scaled, L21 = X D^-1; the sub-block's columns and pivots are then
-// published (global stores, fence, release flag j) for the row CTAs, and
-// all warps update the rest of the block, A[r][c] -= sum_u X[r][u] L21[c][u],
-// with register tiles (12 rows x 3 columns per thread).  At the end four
+// diagonal block (w <= 128) in shared memory by 32-column sub-blocks.  For
+// sub-block j: the rows below it inside the block are solved by the blocked
+// forward substitution, X = F21 L_jj^-T, and scaled, L21 = X D^-1; the next
+// sub-block's columns are updated by all warps; then warp 0 factors the
+// next sub-block (factor_sub32) while warps 1..7 publish sub-block j (its
+// columns and pivots to global memory, fence, release flag j, for the row
+// CTAs) and update the columns beyond the next sub-block.  The rows below
+// the first sub-block are loaded while warp 0 factors it.  At the end four
 // warps invert the four unit lower sub-blocks (for the triangular sweeps).
 template <typename T>
 __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int* flags,
@@ -230,24 +273,33 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
   int8_t* pst = sg + MNB;
   const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
   const int w = min(MNB, ncol - q0);
+  const int nbk = (w + 31) / 32;
   T* Lb = N.L + P.sn_Loff[s] + (int64_t)q0 * ncp + q0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_tile(A, LDM, Lb, ncp, w, MNB, [&](int r, int c) { return c <= r; });
+  // the first sub-block's rows, then its factorisation by warp 0 while the
+  // other warps load the rest of the block
+  load_tile(A, LDM, Lb, ncp, min(32, w), MNB, [&](int r, int c) { return c <= r; });
   for (int c = tid; c < MNB; c += blockDim.x) sg[c] = c < w ? P.col_sign[col0 + q0 + c] : 1;
   __syncthreads();
-  constexpr int MR = (MNB - 32) / 8;   // rows per thread below a sub-block
-  constexpr int GC = (MNB - 32) / 32;  // column groups per thread
-  for (int c0 = 0; c0 < w; c0 += 32) {
-    const int cw = min(32, w - c0);
-    if (warp == 0) {
-      int8_t st;
-      const T d = factor_sub32<T>(A + c0 * LDM + c0, LDM, cw, sg[c0 + lane], eps, policy, lane, st);
-      dsh[c0 + lane] = d;
-      pst[c0 + lane] = st;
+  auto factor = [&](int c0) {
+    int8_t st;
+    const T d = factor_sub32<T>(A + c0 * LDM + c0, LDM, min(32, w - c0), sg[c0 + lane], eps, policy, lane, st);
+    dsh[c0 + lane] = d;
+    pst[c0 + lane] = st;
+  };
+  if (warp == 0) {
+    factor(0);
+  } else if (w > 32) {
+    const int n = (w - 32) * MNB;
+    for (int idx = tid - 32; idx < n; idx += 224) {
+      const int r = 32 + idx / MNB, c = idx % MNB;
+      A[r * LDM + c] = (c <= r) ? Lb[(int64_t)r * ncp + c] : T(0);
     }
-    __syncthreads();
-    const int rb = c0 + 32;
-    const int nr = w - rb;
+  }
+  __syncthreads();
+  for (int j = 0; j < nbk; j++) {
+    const int c0 = 32 * j, cw = min(32, w - c0);
+    const int rb = c0 + 32, nr = w - rb;
     if (nr > 0) {
       // rows below the sub-block: X = F21 L_jj^-T (kept), L21 = X D^-1
       block_trsm32<T>(A + rb * LDM + c0, LDM, nr, 32, A + c0 * LDM + c0, LDM);
@@ -259,46 +311,28 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
         A[(rb + r) * LDM + c0 + c] = x / dsh[c0 + c];
       }
       __syncthreads();
+      // the next sub-block's columns, by all warps
+      block_update<T>(A, Xs, c0, rb, w, rb, rb, min(rb + 32, w), 0, 8);
+      __syncthreads();
     }
-    // publish the sub-block's columns [c0, c0 + cw) of rows [c0, w) and its pivots
-    store_tile(Lb + (int64_t)c0 * ncp + c0, ncp, A + c0 * LDM + c0, LDM, w - c0, cw,
-               [&](int r, int c) { return c <= r; });
-    if (tid < cw) N.D[col0 + q0 + c0 + tid] = dsh[c0 + tid];
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) st_release_i32(flags + (c0 >> 5), 1);
-    if (nr > 0) {
-      // A[r][c] -= sum_u X[r][u] L21[c][u], rb <= c <= r < w
-      T acc[MR][GC];
-#pragma unroll
-      for (int m = 0; m < MR; m++)
-#pragma unroll
-        for (int g = 0; g < GC; g++) acc[m][g] = T(0);
-#pragma unroll 2
-      for (int u = 0; u < 32; u++) {
-        T bv[GC];
-#pragma unroll
-        for (int g = 0; g < GC; g++) bv[g] = A[min(rb + 32 * g + lane, w - 1) * LDM + c0 + u];
-#pragma unroll
-        for (int m = 0; m < MR; m++) {
-          const T a = Xs[min(warp + 8 * m, nr - 1) * LDS + u];
-#pragma unroll
-          for (int g = 0; g < GC; g++) acc[m][g] += a * bv[g];
-        }
+    if (warp == 0) {
+      if (j + 1 < nbk) factor(rb);
+    } else {
+      // publish sub-block j: columns [c0, c0 + cw) of rows [c0, w), pivots
+      const int n = (w - c0) * cw;
+      for (int idx = tid - 32; idx < n; idx += 224) {
+        const int r = idx / cw, c = idx - r * cw;
+        if (c <= r) Lb[(int64_t)(c0 + r) * ncp + c0 + c] = A[(c0 + r) * LDM + c0 + c];
       }
-#pragma unroll
-      for (int m = 0; m < MR; m++) {
-        const int r = rb + warp + 8 * m;
-#pragma unroll
-        for (int g = 0; g < GC; g++) {
-          const int c = rb + 32 * g + lane;
-          if (r < w && c <= r) A[r * LDM + c] -= acc[m][g];
-        }
-      }
+      if (tid - 32 < cw) N.D[col0 + q0 + c0 + tid - 32] = dsh[c0 + tid - 32];
+      __threadfence();
+      bar_warps_1_7();
+      if (tid == 32) st_release_i32(flags + j, 1);
+      // the columns beyond the next sub-block
+      if (nr > 32) block_update<T>(A, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
     }
     __syncthreads();
   }
-  const int nbk = (w + 31) / 32;
   if (warp < nbk)
     invert_sub32<T>(A + 32 * warp * LDM + 32 * warp, LDM, min(32, w - 32 * warp),
                     N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + warp) * 1024, lane);
