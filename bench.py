@@ -125,12 +125,15 @@ def peaks():
         return {}
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or
-    None when there is none or the kernel's source changed since."""
+    None when there is none, the capture ran another workload, or the
+    kernel's source changed since."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))[kernel]
+        if rec.get("workload") != workload:
+            return None
         src = os.path.join(ROOT, rec["source"])
         if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
             return None
@@ -488,7 +491,7 @@ def run_ours(args):
             roof = {"kernel": name, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
                     "peak": hbm, "unit": "GB/s", "peak_note": "of measured copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = recorded_traffic(name)
+        roof["traffic"] = recorded_traffic(name, args.workload)
         roof["algorithmic_bytes_per_launch"] = st["bytes"] / st["launches"]
         roof["algorithmic_flops_per_launch"] = st["flops"] / st["launches"]
         roof["avg_launch_ms"] = st["ms"] / st["launches"]
@@ -546,6 +549,13 @@ def run_ours(args):
             host.append({k: d[k].cpu().pin_memory() for k in ("H", "J", "S", "Bc")})
         dd = {k: torch.empty_like(R.dev_draws[0][k]) for k in ("H", "J", "S", "Bc")}
         xh = torch.empty(R.Xc.shape, dtype=torch.float64).pin_memory()
+        gh = None
+        if adjoint:   # the gradients come back to the host too
+            gh = {"b": torch.empty(R.Xc.shape, dtype=torch.float64).pin_memory(),
+                  "H": torch.empty(K.nnz_H, dtype=torch.float64).pin_memory(),
+                  "J": torch.empty(K.nnz_J, dtype=torch.float64).pin_memory(),
+                  "Sigma": torch.empty(K.n_var, dtype=torch.float64).pin_memory(),
+                  "scal": torch.empty(2 * K.count, dtype=torch.float64).pin_memory()}
         ne = max(2, args.steps // 2)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -558,6 +568,11 @@ def run_ours(args):
             nk.ncl_kkt_batch_factor_solve(K._h, dd["H"], dd["J"], dd["S"], d["delta"], d["rho"], spec["nrhs"],
                                           dd["Bc"], K.dim, R.Xc, K.dim)
             xh.copy_(R.Xc, non_blocking=True)
+            if adjoint:
+                g = K.adjoint(R.Xc.t(), R.Xc.t())      # loss = 0.5 ||x||^2: g_x = x
+                gh["b"].copy_(g["b"].t(), non_blocking=True)
+                for key in ("H", "J", "Sigma", "scal"):
+                    gh[key].copy_(g[key], non_blocking=True)
         e1.record()
         barrier()
         ems = max_over_ranks(e0.elapsed_time(e1))
@@ -565,7 +580,10 @@ def run_ours(args):
         out["e2e"] = {"value": world * flops * ne / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
                       "ms_per_step": ems / ne,
                       "h2d_bytes_per_step": 8 * (npat[0] + npat[1] + npat[2] + ai.dim * spec["nrhs"]),
-                      "d2h_bytes_per_step": 8 * ai.dim * spec["nrhs"]}
+                      "d2h_bytes_per_step": 8 * ai.dim * spec["nrhs"] + (
+                          8 * sum(t.numel() for t in gh.values()) if gh else 0)}
+        if adjoint:
+            out["e2e"]["includes"] = "factor + refined solve + adjoint, gradients copied to the host"
 
     if rank == 0 and not args.skip_cpu:
         import oracle as O

@@ -1297,7 +1297,7 @@ ncl_status finish_factor(ncl_kkt_s* h, cudaStream_t st, ncl_kkt_factor_info* inf
   CK(cudaStreamSynchronize(st));
   if (*herr) {
     h->factored = false;
-    return fail(NCL_ERR_TIMEOUT, "a bounded device wait of the tensor-core update ran out");
+    return fail(NCL_ERR_TIMEOUT, "a bounded device wait of the factorisation (macro panel or tensor-core update) ran out");
   }
   prof_collect(h);
   float ms = 0;
