@@ -90,6 +90,7 @@ struct Level {
   int64_t chain_off = 0;  // block-row items of the level (sweeps)
   int chain_cnt = 0;
   int64_t chain_smem = 0; // dynamic shared memory of the chained sweep kernels
+  bool chain_multi = false;  // some supernode of the level has more than one block-row
   int64_t below_off = 0;  // (s, a0) solve items
   int below_cnt = 0;
   int64_t bbelow_off = 0; // (s, a0, k0) backward solve items
@@ -363,6 +364,7 @@ void build_schedule(ncl_kkt_s* h) {
         const int nblk = (ncol + 31) / 32, nbr = (ncol + CHAIN_ROWS - 1) / CHAIN_ROWS;
         for (int B = 0; B < nbr; B++) hs.chainv.push_back(make_int4(s, (int32_t)hs.nbrows, (int32_t)hs.nblocks, 0));
         L.chain_smem = std::max<int64_t>(L.chain_smem, chain_smem(std::min(CHAIN_ROWS, ncol), (int)esz));
+        if (nbr > 1) L.chain_multi = true;
         for (int b = 0; b < nblk; b++) {
           const int lo = 32 * b, hi = std::min(32 * b + 32, ncol);
           for (int32_t k2 = P.child_ptr[s]; k2 < P.child_ptr[s + 1]; k2++) {
@@ -966,8 +968,8 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
   CK(cudaMemsetAsync(h->d_chain_sync, 0, (2 * ns + 2 * nb) * sizeof(int), st));
   for (const Level& L : h->levels) {
     klaunch(h, st, f32 ? "fwd_chain_f32" : "fwd_chain_f64", L.chain_cnt, scaled(L.fdiag_cost, nrhs), [&] {
-      launch_fwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, h->d_chain_pptr,
-                          h->d_chain_pran, xp, W, nrhs, tk_f, fl_f, serr, st);
+      launch_fwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, L.chain_multi,
+                          h->d_chain_pptr, h->d_chain_pran, xp, W, nrhs, tk_f, fl_f, serr, st);
     });
     klaunch(h, st, f32 ? "fwd_below_f32" : "fwd_below_f64", L.below_cnt, scaled(L.fbelow_cost, nrhs),
             [&] {
@@ -980,8 +982,8 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
     klaunch(h, st, f32 ? "bwd_below_f32" : "bwd_below_f64", L.bbelow_cnt, scaled(L.bbelow_cost, nrhs),
             [&] { launch_bwd_below<T>(P, N, h->d_bbelow + L.bbelow_off, L.bbelow_cnt, xp, Pw, nrhs, st); });
     klaunch(h, st, f32 ? "bwd_chain_f32" : "bwd_chain_f64", L.chain_cnt, scaled(L.bdiag_cost, nrhs), [&] {
-      launch_bwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, xp, Pw, nrhs, tk_b, fl_b,
-                          serr, st);
+      launch_bwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, L.chain_multi, xp, Pw,
+                          nrhs, tk_b, fl_b, serr, st);
     });
   }
   CK(cudaGetLastError());

@@ -152,9 +152,9 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
                      cudaStream_t st);
 int chain_smem(int rows, int esz);
 template <typename T>
-void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, const int32_t* pptr,
-                      const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags, int* err,
-                      cudaStream_t st);
+void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi,
+                      const int32_t* pptr, const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags,
+                      int* err, cudaStream_t st);
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
                       int count, T* xp, T* W, int nrhs, cudaStream_t st);
@@ -162,8 +162,8 @@ template <typename T>
 void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, const T* xp,
                       T* Pw, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, T* xp, const T* Pw,
-                      int nrhs, int* tickets, int* flags, int* err, cudaStream_t st);
+void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi, T* xp,
+                      const T* Pw, int nrhs, int* tickets, int* flags, int* err, cudaStream_t st);
 void launch_residual(const DevPlan& P, const double* Klow, const double* B, int64_t ldb, const double* X,
                      int64_t ldx, double* R, int64_t ldr, int nrhs, unsigned long long* rnorm,
                      unsigned long long* xnorm, cudaStream_t st);

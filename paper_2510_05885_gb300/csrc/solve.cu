@@ -135,7 +135,7 @@ __device__ __forceinline__ void chain_stage_tile(T* Ls, const T* Lb, int64_t ncp
   }
 }
 
-template <typename T>
+template <typename T, bool MULTI>
 __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
                                                    const int32_t* __restrict__ pptr, const int4* __restrict__ pran,
                                                    T* __restrict__ xp, const T* __restrict__ W, int nrhs,
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
   T* ys = tb + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);
   T* Iv = ys + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);      // the inverted 32 x 32 diagonal blocks, stride 33
   const T* Lb = N.L + P.sn_Loff[s];
-  chain_stage_tile(Ls, Lb, ncp, R0, nr);
+  if (nsub > 1) chain_stage_tile(Ls, Lb, ncp, R0, nr);
   const int rw = 32 * warp + lane;                     // this lane's row in the block-row
   const bool mine = warp < nsub;
   const bool valid = rw < nr;
@@ -185,17 +185,24 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
   // the warp reads its 32 rows 32 columns at a time (one coalesced segment
   // per row; the next segment is loaded before the current one is used and
   // before waiting for its block-row), and a butterfly reduce-scatter leaves
-  // row rr's sum in lane rr
+  // row rr's sum in lane rr.  Once J is published, its 128 values are loaded
+  // together.  (Levels whose supernodes all have one block-row compile
+  // without this part.)
   T acc[MAX_RHS_SWEEP];
 #pragma unroll
   for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
-  if (mine && B > 0) {
+  if (MULTI && mine && B > 0) {
     const T* wrow = Lb + (int64_t)(R0 + 32 * warp) * ncp + lane;
     const int nrw = min(32, nr - 32 * warp);
     T lv[32], ln[32];
 #pragma unroll
     for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp] : T(0);
     const int nchunk = 4 * B;
+    // the right-hand sides of the four chunks of a block-row, loaded
+    // together once it is published and rotated chunk by chunk (FP64: the
+    // first right-hand side only, for registers)
+    constexpr int YQ = sizeof(T) == 4 ? MAX_RHS_SWEEP : 1;
+    T yq[4][YQ];
     for (int q = 0; q < nchunk; q++) {
       const int c0 = 32 * q;
 #pragma unroll
@@ -204,11 +211,18 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
 #pragma unroll
         for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp + c0 + 32] : T(0);
       }
-      if ((q & 3) == 0) chain_wait(flags + broff + (q >> 2), err);
+      if ((q & 3) == 0) {
+        chain_wait(flags + broff + (q >> 2), err);
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+#pragma unroll
+          for (int r = 0; r < YQ; r++)
+            yq[c][r] = r < nrhs ? __ldcg(xp + (int64_t)r * P.dim + col0 + c0 + 32 * c + lane) : T(0);
+      }
 #pragma unroll
       for (int r = 0; r < MAX_RHS_SWEEP; r++) {
         if (r >= nrhs) break;
-        const T yu = __ldcg(xp + (int64_t)r * P.dim + col0 + c0 + lane);
+        const T yu = r < YQ ? yq[0][r] : __ldcg(xp + (int64_t)r * P.dim + col0 + c0 + lane);
         T v[32];
 #pragma unroll
         for (int rr = 0; rr < 32; rr++) v[rr] = lv[rr] * yu;
@@ -224,6 +238,10 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
         }
         acc[r] += v[0];
       }
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int r = 0; r < YQ; r++) yq[c][r] = yq[c + 1][r];
     }
   }
   __syncthreads();
@@ -259,7 +277,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
   chain_publish(flags + broff + B);
 }
 
-template <typename T>
+template <typename T, bool MULTI>
 __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
                                                    T* __restrict__ xp, const T* __restrict__ Pw, int nrhs,
                                                    int* tickets, int* flags, int* err) {
@@ -280,7 +298,7 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
   T* xs = zb + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);
   T* Iv = xs + MAX_RHS_SWEEP * (CHAIN_ROWS + 1);      // the inverted 32 x 32 diagonal blocks, stride 33
   const T* Lb = N.L + P.sn_Loff[s];
-  chain_stage_tile(Ls, Lb, ncp, R0, nr);
+  if (nsub > 1) chain_stage_tile(Ls, Lb, ncp, R0, nr);
   const int rw = 32 * warp + lane;                     // this lane's column (unknown) in the block-row
   const bool mine = warp < nsub;
   const bool valid = rw < nr;
@@ -302,11 +320,13 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
       zb[r * (CHAIN_ROWS + 1) + rw] = z;
     }
   }
-  // sum over the published block-rows I > B: L_IB^T x_I (lane = column)
+  // sum over the published block-rows I > B: L_IB^T x_I (lane = column);
+  // once I is published, its values are loaded together.  (Levels whose
+  // supernodes all have one block-row compile without this part.)
   T acc[MAX_RHS_SWEEP];
 #pragma unroll
   for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
-  if (mine && B < nbr - 1) {
+  if (MULTI && mine && B < nbr - 1) {
     // chunks q = 0, 1, ...: 32 rows of block-row I = nbr - 1 - q / 4, the
     // next chunk loaded before the current one is used and before waiting
     const T* lcol = Lb + R0 + min(rw, nr - 1);
@@ -321,6 +341,11 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
     rows_of(0, nq0, nbw);
 #pragma unroll
     for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
+    // the values of the four chunks of a block-row, loaded together once it
+    // is published and rotated chunk by chunk (FP64: the first right-hand
+    // side only, for registers)
+    constexpr int XQ = sizeof(T) == 4 ? MAX_RHS_SWEEP : 1;
+    T xq[4][XQ];
     for (int q = 0; q < nchunk; q++) {
       const int q0 = nq0, bwi = nbw;
 #pragma unroll
@@ -330,15 +355,30 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
 #pragma unroll
         for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
       }
-      if ((q & 3) == 0) chain_wait(flags + broff + nbr - 1 - (q >> 2), err);
-      if (bwi <= 0) continue;
+      if ((q & 3) == 0) {
+        chain_wait(flags + broff + nbr - 1 - (q >> 2), err);
 #pragma unroll
-      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
-        if (r >= nrhs) break;
-        const T xv = lane < bwi ? __ldcg(xp + (int64_t)r * P.dim + col0 + q0 + lane) : T(0);
+        for (int c = 0; c < 4; c++) {
+          const int bw = max(0, min(32, ncol - (q0 + 32 * c)));
 #pragma unroll
-        for (int v = 0; v < 32; v++) acc[r] += lv[v] * __shfl_sync(0xffffffffu, xv, v);
+          for (int r = 0; r < XQ; r++)
+            xq[c][r] = (r < nrhs && lane < bw) ? __ldcg(xp + (int64_t)r * P.dim + col0 + q0 + 32 * c + lane) : T(0);
+        }
       }
+      if (bwi > 0) {
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+          if (r >= nrhs) break;
+          const T xv = r < XQ ? xq[0][r]
+                              : (lane < bwi ? __ldcg(xp + (int64_t)r * P.dim + col0 + q0 + lane) : T(0));
+#pragma unroll
+          for (int v = 0; v < 32; v++) acc[r] += lv[v] * __shfl_sync(0xffffffffu, xv, v);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int r = 0; r < XQ; r++) xq[c][r] = xq[c + 1][r];
     }
   }
   __syncthreads();
@@ -374,12 +414,32 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
   chain_publish(flags + broff + B);
 }
 
+// 16-byte vectors of factor entries (rows of L start 16-byte aligned: the
+// blocks start at multiples of 32 elements and the row stride is a multiple
+// of 4 elements)
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
 // forward: rows below supernode s, SOLVE_ROWS per CTA:
 //   W_s[a] = (children's updates landing on row a) - L21[a,:] y_s
+// The products use tpr = 4..32 threads per row (by the supernode's width),
+// each reading 16-byte vectors of its row, and RPT rows per thread at a time,
+// so that a narrow supernode still has many loads in flight; the partial
+// sums are reduced by shuffles inside each group of tpr lanes.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd_below(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
                                                    const int32_t* __restrict__ cptr, const int4* __restrict__ cran,
                                                    const T* __restrict__ xp, T* __restrict__ W, int nrhs) {
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::n;
+  constexpr int RPT = 4;
   __shared__ T t[SOLVE_ROWS * 8];
   const int2 it = items[blockIdx.x];
   const int s = it.x, a0 = it.y;
@@ -399,28 +459,70 @@ __global__ void __launch_bounds__(256) k_fwd_below(DevPlan P, DevNum<T> N, const
       for (int r = 0; r < nrhs; r++) t[r * SOLVE_ROWS + rel[a] - ncol - a0] += W[r * P.Wtot + P.sn_Woff[c] + a];
     __syncthreads();
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int a = a0 + warp; a < a1; a += nw) {
-    const T* row = Lb + (int64_t)(ncol + a) * ncp;
-    for (int r = 0; r < nrhs; r++) {
-      const T* y = xp + r * P.dim + col0;
-      T acc = T(0);
-      for (int k = lane; k < ncol; k += 32) acc += row[k] * y[k];
+  const int nv = (ncol + VW - 1) / VW;                 // vectors per row
+  int tpr = 4;
+  while (tpr < 32 && 2 * tpr < nv) tpr *= 2;
+  const int q = threadIdx.x & (tpr - 1);
+  const int slots = blockDim.x / tpr, slot = threadIdx.x / tpr;
+  const int64_t ysz = (int64_t)P.dim;
+  // every thread runs the same number of passes (the shuffles below are
+  // warp-wide)
+  for (int base = a0; base < a1; base += RPT * slots) {
+    int ar[RPT];
+    bool ok[RPT];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) W[r * P.Wtot + P.sn_Woff[s] + a] = t[r * SOLVE_ROWS + a - a0] - acc;
+    for (int j = 0; j < RPT; j++) {
+      ar[j] = base + j * slots + slot;
+      ok[j] = ar[j] < a1;
+    }
+    T acc[RPT][MAX_RHS_SWEEP];
+#pragma unroll
+    for (int j = 0; j < RPT; j++)
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[j][r] = T(0);
+    for (int v = q; v < nv; v += tpr) {
+      V lv[RPT];
+#pragma unroll
+      for (int j = 0; j < RPT; j++) {
+        if (ok[j]) lv[j] = __ldg(reinterpret_cast<const V*>(Lb + (int64_t)(ncol + ar[j]) * ncp) + v);
+        else lv[j] = V{};
+      }
+#pragma unroll
+      for (int e = 0; e < VW; e++) {
+        const int k = v * VW + e;
+        if (k >= ncol) break;
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+          if (r >= nrhs) break;
+          const T y = __ldg(xp + r * ysz + col0 + k);
+#pragma unroll
+          for (int j = 0; j < RPT; j++) acc[j][r] += reinterpret_cast<const T*>(&lv[j])[e] * y;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RPT; j++) {
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+        if (r >= nrhs) break;
+        T a = acc[j][r];
+        for (int o = tpr >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (q == 0 && ok[j]) W[r * P.Wtot + P.sn_Woff[s] + ar[j]] = t[r * SOLVE_ROWS + ar[j] - a0] - a;
+      }
     }
   }
 }
 
 // backward: partial sums of L21^T x_below over a run of SOLVE_ROWS rows and
-// a run of up to 256 columns (item (s, a0, k0)); for few columns, G groups
-// of threads split the rows and their sums are added in shared memory
+// a run of up to 256 columns (item (s, a0, k0)); for 33..128 columns,
+// G = 256 / (columns rounded up to 32) groups of threads split the rows and
+// their sums are added in shared memory (a single group for the narrowest
+// supernodes, whose CTAs are many and short)
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
                                                    const T* __restrict__ xp, T* __restrict__ Pw, int nrhs) {
   __shared__ T xb[SOLVE_ROWS * MAX_RHS_SWEEP];
-  __shared__ T red[4][256];
+  __shared__ T red[256];
   const int4 it = items[blockIdx.x];
   const int s = it.x, a0 = it.y, k0 = it.z;
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
@@ -435,10 +537,9 @@ __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const
     xb[r * SOLVE_ROWS + a] = xp[r * P.dim + rows[a0 + a]];
   }
   __syncthreads();
-  // G thread groups of blockDim / G >= kc threads each (a single group for
-  // the smallest fronts, whose CTAs are many and short)
+  // G thread groups of blockDim / G >= kc threads each
   const int cols = (kc + 31) & ~31;
-  const int G = (cols > 128 || cols <= 32) ? 1 : (cols > 64 ? 2 : 4);
+  const int G = (cols > 128 || cols <= 32) ? 1 : blockDim.x / cols;
   const int tpg = blockDim.x / G, g = threadIdx.x / tpg, kl = threadIdx.x - g * tpg;
   const int per = (a1 - a0 + G - 1) / G;
   const int ga0 = a0 + g * per, ga1 = min(a1, ga0 + per);
@@ -454,11 +555,11 @@ __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const
     if (G == 1) {
       if (kl < kc) out[kl] = acc;
     } else {
-      red[g][kl] = acc;
+      red[g * tpg + kl] = acc;
       __syncthreads();
       if (threadIdx.x < kc) {
         T t = T(0);
-        for (int q = 0; q < G; q++) t += red[q][threadIdx.x];
+        for (int q = 0; q < G; q++) t += red[q * tpg + threadIdx.x];
         out[threadIdx.x] = t;
       }
       __syncthreads();
@@ -467,16 +568,22 @@ __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const
 }
 
 template <typename T>
-void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, const int32_t* pptr,
-                      const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags, int* err,
-                      cudaStream_t st) {
+void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi,
+                      const int32_t* pptr, const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags,
+                      int* err, cudaStream_t st) {
   if (count <= 0) return;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_fwd_chain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain_smem(CHAIN_ROWS, sizeof(T)));
+    cudaFuncSetAttribute(k_fwd_chain<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         chain_smem(CHAIN_ROWS, sizeof(T)));
+    cudaFuncSetAttribute(k_fwd_chain<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         chain_smem(CHAIN_ROWS, sizeof(T)));
     attr = true;
   }
-  k_fwd_chain<T><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err);
+  if (multi)
+    k_fwd_chain<T, true><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err);
+  else
+    k_fwd_chain<T, false><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err);
 }
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
@@ -489,15 +596,21 @@ void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, i
   if (count > 0) k_bwd_below<T><<<count, 256, 0, st>>>(P, N, items, xp, Pw, nrhs);
 }
 template <typename T>
-void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, T* xp, const T* Pw,
-                      int nrhs, int* tickets, int* flags, int* err, cudaStream_t st) {
+void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi, T* xp,
+                      const T* Pw, int nrhs, int* tickets, int* flags, int* err, cudaStream_t st) {
   if (count <= 0) return;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_bwd_chain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, chain_smem(CHAIN_ROWS, sizeof(T)));
+    cudaFuncSetAttribute(k_bwd_chain<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         chain_smem(CHAIN_ROWS, sizeof(T)));
+    cudaFuncSetAttribute(k_bwd_chain<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         chain_smem(CHAIN_ROWS, sizeof(T)));
     attr = true;
   }
-  k_bwd_chain<T><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err);
+  if (multi)
+    k_bwd_chain<T, true><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err);
+  else
+    k_bwd_chain<T, false><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -786,14 +899,15 @@ void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64
 #define NCL_INST(T)                                                                                               \
   template void launch_perm_in<T>(const DevPlan&, T*, const double*, int64_t, int, cudaStream_t);                 \
   template void launch_perm_out<T>(const DevPlan&, const T*, double*, int64_t, int, int, cudaStream_t);           \
-  template void launch_fwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, const int32_t*,     \
-                                    const int4*, T*, const T*, int, int*, int*, int*, cudaStream_t);              \
+  template void launch_fwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, bool,               \
+                                    const int32_t*, const int4*, T*, const T*, int, int*, int*, int*,            \
+                                    cudaStream_t);                                                                \
   template void launch_fwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, const int32_t*, const int4*,  \
                                     int, T*, T*, int, cudaStream_t);                                              \
   template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int4*, int, const T*, T*, int,        \
                                     cudaStream_t);                                                                \
-  template void launch_bwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, T*, const T*, int,   \
-                                    int*, int*, int*, cudaStream_t);
+  template void launch_bwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, bool, T*, const T*, \
+                                    int, int*, int*, int*, cudaStream_t);
 NCL_INST(float)
 NCL_INST(double)
 #undef NCL_INST
