@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--rho", type=float, default=None)
     ap.add_argument("--rho-sweep", action="store_true", help="condensed300: also rho in {1e2, 1e5, 1e8}")
     ap.add_argument("--draws", type=int, default=4)
+    ap.add_argument("--regularize", action="store_true",
+                    help="also time the inertia correction (Section 3.1) from delta = 0 on the first draw")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -319,14 +321,14 @@ class Runner:
     def stage(self, i):
         self.Bfix.copy_(self.dev_draws[i % len(self.dev_draws)]["Bc"])
 
-    def make(self, prec):
+    def make(self, prec, **opts):
         nk = self.nk
         f = self.spec["form"]
         if self.batch:
             return nk.KKT.batch(f, [(p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind) for p in self.pats],
-                                prec=prec)
+                                prec=prec, **opts)
         p = self.pats[0]
-        return nk.KKT(f, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind, prec=prec)
+        return nk.KKT(f, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind, prec=prec, **opts)
 
     def step(self, K, i, adjoint=False):
         """factor + solve (+ adjoint) of draw i; returns (factor infos, solve info, adjoint ms)."""
@@ -541,6 +543,37 @@ def run_ours(args):
                 Kx.close()
             sweep[f"{rho:g}"] = entry
         out["rho_sweep"] = sweep
+
+    # inertia correction (Section 3.1) from delta = 0 on the first draw: the
+    # draw's rho is taken as the unregularised penalty, rho-hat = rho + delta
+    if args.regularize:
+        d = R.dev_draws[0]
+        zero = [0.0] * len(d["delta"])
+        want = [(i.n, i.m if R.spec["form"] == 0 else 0, 0) for i in R.draws[0]]
+        reg = {"schedule": {"delta0": 0.0, "delta_first": 1e-4, "growth": 10.0, "max_tries": 20}}
+        # fp32_ir: an irregular FP32 inertia is confirmed by an FP64 refactorisation
+        # (precision_fallback, the default); fp32_ir_fp32_inertia: the FP32 inertia decides
+        legs = {"fp32_ir": lambda: K, "fp32_ir_fp32_inertia": lambda: R.make("fp32_ir", precision_fallback=0),
+                "fp64": lambda: R.make("fp64")}
+        for prec, mk in legs.items():
+            Kr = mk()
+            times = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                infos, dl, tries, st = Kr.factor_regularized(d["H"], d["J"], d["S"], zero, d["rho"], 1e-4, 10.0,
+                                                             20, raise_on_inertia=False)
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            reg[prec] = {"ms": statistics.median(times), "tries": tries, "status": st,
+                         "delta_min": float(min(dl)), "delta_max": float(max(dl)),
+                         "inertia_regular": all(tuple(f.inertia) == w for f, w in zip(infos, want)),
+                         "fp64_fallback": any(f.fp64_fallback for f in infos)}
+            if Kr is not K:
+                Kr.close()
+        out["regularize"] = reg
 
     # end to end through the C ABI with host buffers
     if not args.skip_e2e:

@@ -85,7 +85,9 @@ typedef enum {
     NCL_ERR_NUMERIC = 7,          /* a NaN or Inf pivot or solution */
     NCL_ERR_IR_NOT_CONVERGED = 8, /* refinement reached ir_max_iter above ir_tol;
                                      the best iterate is still returned */
-    NCL_ERR_TIMEOUT = 9           /* a bounded device wait ran out */
+    NCL_ERR_TIMEOUT = 9,          /* a bounded device wait ran out */
+    NCL_ERR_INERTIA = 10          /* ncl_kkt_factor_regularize: an instance's inertia
+                                     is still irregular after max_tries factorisations */
 } ncl_status;
 
 typedef struct {
@@ -276,6 +278,37 @@ ncl_status ncl_kkt_batch_analyze(int32_t count, int32_t form, const int32_t* n, 
 ncl_status ncl_kkt_batch_factor(ncl_kkt_t h, const double* H_val, const double* J_val,
                                 const double* Sigma, const double* delta, const double* rho,
                                 ncl_stream_t stream, ncl_kkt_factor_info* infos);
+
+/*
+ * ncl_kkt_factor_regularize -- the inertia correction of Section 3.1
+ * (regularised matrix Eq. K2): factor with the primal regularisation
+ * delta[i]; while instance i's inertia is not the regular one, (n_i, m_i, 0)
+ * for K2r or (n_i, 0, 0) for K, raise delta[i] and refactor on the same
+ * analysis.  As in Section 3.1 the regularisation also enters the penalty:
+ * the matrix uses rho-hat_i = rho[i] + delta[i] (the dual block -1/rho-hat of
+ * K2r, the rho-hat J^T J of K), so here rho[i] is the unregularised penalty.
+ * Works on single and batch handles (count = 1 for a single handle).
+ *   delta        host double[count]: in, the first delta of each instance
+ *                (>= 0); out, the delta of the factors in use
+ *   rho          host double[count], > 0
+ *   delta_first  the delta tried after a zero one (> 0)
+ *   growth       factor applied to a nonzero delta at each retry (> 1)
+ *   max_tries    factorisations at most (>= 1)
+ *   infos        host, may be NULL: the last factorisation's info per instance
+ *   tries        host, may be NULL: the number of factorisations done
+ * On an FP32_IR handle with precision_fallback, a try whose FP32 inertia is
+ * irregular is refactored in FP64 before its inertia is trusted, so each
+ * failed try costs an FP64 factorisation there; with precision_fallback = 0
+ * the FP32 inertia decides.  The paper fixes no growth schedule.
+ * Errors: INVALID_ARG (bad schedule or delta < 0), INERTIA (the factors of
+ * the last try stay usable; delta holds its values), and those of
+ * ncl_kkt_batch_factor.
+ */
+ncl_status ncl_kkt_factor_regularize(ncl_kkt_t h, const double* H_val, const double* J_val,
+                                     const double* Sigma, double* delta, const double* rho,
+                                     double delta_first, double growth, int32_t max_tries,
+                                     ncl_stream_t stream, ncl_kkt_factor_info* infos,
+                                     int32_t* tries);
 
 /* Factor + solve in one call; with the same handle, values and nrhs the
  * whole sequence is one CUDA-graph launch after the first call.

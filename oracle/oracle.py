@@ -16,6 +16,10 @@ What it computes, and where the paper defines it:
 * ``solve_ir``: Richardson iterative refinement in FP64 (Section 4.3).
 * ``backward_error``: the normwise backward error
   ``||b - K x||_inf / (||K||_inf ||x||_inf + ||b||_inf)``.
+* ``regularize``: the inertia correction of Section 3.1 (regularised matrix
+  Eq. K2): raise the primal regularisation delta until the inertia is the
+  regular one, with rho-hat = rho + delta in the matrix as the same section
+  defines it; the growth schedule is the caller's (the paper fixes none).
 * ``adjoint``: gradients of a loss of ``x = K^{-1} b`` with respect to b and
   to the stored values of H, J, Sigma (and delta, rho): ``g_b = K^{-1} g_x``
   and ``dl/dK = -g_b x^T`` folded onto the stored pattern.
@@ -37,7 +41,7 @@ from scipy.sparse.csgraph import reverse_cuthill_mckee
 
 __all__ = [
     "build_oracle", "kkt_stabilized", "kkt_condensed", "instance_matrix", "block_signs",
-    "LDLT", "solve_ir", "backward_error", "solve_instance", "adjoint", "cond1_estimate",
+    "LDLT", "solve_ir", "backward_error", "solve_instance", "adjoint", "cond1_estimate", "regularize",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -240,6 +244,33 @@ def solve_instance(inst, ir_steps: int = 3, eps: float = 1e-10, policy: int = 0,
     fac = LDLT(A, block_signs(inst.form, inst.n, inst.m), perm=perm, eps=eps, policy=policy)
     x, _, eta = solve_ir(A, fac, inst.b, max_steps=ir_steps)
     return x, fac, eta, A
+
+
+def regularize(inst, delta0: float = 0.0, delta_first: float = 1e-4, growth: float = 10.0, max_tries: int = 20,
+               eps: float = 1e-10, policy: int = 0, perm=None):
+    """Inertia correction of Section 3.1.  ``inst.rho`` is the unregularised
+    penalty rho_k; each try factors the matrix with delta and rho-hat =
+    rho_k + delta (Section 3.1, the definition of rho-hat after Eq. K2), and
+    while the inertia is not (n, m, 0) for K2r or (n, 0, 0) for K
+    (Section 3.1: the inertia a valid search direction needs), delta is
+    raised: to ``delta_first`` from zero, else multiplied by ``growth``.
+    Returns (fac, A, delta, tries, regular) of the last try."""
+    p = inst.pat
+    want = (inst.n, inst.m if inst.form == "stabilized" else 0, 0)
+    build = kkt_stabilized if inst.form == "stabilized" else kkt_condensed
+    sign = block_signs(inst.form, inst.n, inst.m)
+    delta = float(delta0)
+    t = 0
+    while True:
+        t += 1
+        A = build(p.n, p.m, p.H_rowptr, p.H_colind, inst.H_val, p.J_rowptr, p.J_colind, inst.J_val,
+                  inst.Sigma, delta, inst.rho + delta)
+        fac = LDLT(A, sign, perm=perm, eps=eps, policy=policy)
+        if fac.inertia == want:
+            return fac, A, delta, t, True
+        if t >= max_tries:
+            return fac, A, delta, t, False
+        delta = delta * growth if delta > 0 else delta_first
 
 
 def cond1_estimate(A, fac: LDLT) -> float:

@@ -1653,6 +1653,51 @@ ncl_status ncl_kkt_batch_factor(ncl_kkt_t h, const double* H_val, const double* 
   return guarded(h, [&] { return do_factor(h, H_val, J_val, Sigma, delta, rho, (cudaStream_t)stream, infos); });
 }
 
+// The inertia correction of Section 3.1: raise the primal regularisation of
+// every instance whose inertia is irregular and refactor, rho-hat = rho +
+// delta entering the matrix with it.
+ncl_status ncl_kkt_factor_regularize(ncl_kkt_t h, const double* H_val, const double* J_val, const double* Sigma,
+                                     double* delta, const double* rho, double delta_first, double growth,
+                                     int32_t max_tries, ncl_stream_t stream, ncl_kkt_factor_info* infos,
+                                     int32_t* tries) {
+  if (!h || !delta || !rho) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (!(delta_first > 0.0) || !std::isfinite(delta_first) || !(growth > 1.0) || !std::isfinite(growth) ||
+      max_tries < 1)
+    return fail(NCL_ERR_INVALID_ARG, "bad regularisation schedule");
+  const int ni = h->dp.ninst;
+  for (int i = 0; i < ni; i++) {
+    if (!(delta[i] >= 0.0) || !std::isfinite(delta[i])) return fail(NCL_ERR_INVALID_ARG, "delta must be >= 0");
+    if (!(rho[i] > 0.0) || !std::isfinite(rho[i])) return fail(NCL_ERR_INVALID_ARG, "rho must be > 0");
+  }
+  if (tries) *tries = 0;
+  std::vector<ncl_kkt_factor_info> own(ni);
+  ncl_kkt_factor_info* inf = infos ? infos : own.data();
+  return guarded(h, [&]() -> ncl_status {
+    std::vector<double> rho_hat(ni), next(ni);
+    for (int t = 1;; t++) {
+      for (int i = 0; i < ni; i++) rho_hat[i] = rho[i] + delta[i];
+      if (tries) *tries = t;
+      const ncl_status s = do_factor(h, H_val, J_val, Sigma, delta, rho_hat.data(), (cudaStream_t)stream, inf);
+      if (s != NCL_OK && s != NCL_ERR_ZERO_PIVOT) return s;
+      bool regular = true;
+      for (int i = 0; i < ni; i++) {
+        const Instance& I = h->plan.inst[i];
+        const int64_t want_neg = h->plan.form == 0 ? I.m : 0;
+        const bool ok = inf[i].n_pos == I.n && inf[i].n_neg == want_neg && inf[i].n_zero == 0;
+        next[i] = ok ? delta[i] : (delta[i] > 0.0 ? delta[i] * growth : delta_first);
+        regular = regular && ok;
+      }
+      if (regular) return s;
+      if (t >= max_tries) return fail(NCL_ERR_INERTIA, "inertia still irregular after max_tries factorisations");
+      for (int i = 0; i < ni; i++) {
+        if (!std::isfinite(next[i])) return fail(NCL_ERR_INERTIA, "the regularisation overflowed");
+        delta[i] = next[i];
+      }
+    }
+  });
+}
+
 ncl_status ncl_kkt_solve(ncl_kkt_t h, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
                          ncl_stream_t stream, ncl_kkt_solve_info* info) {
   if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
@@ -1791,6 +1836,7 @@ const char* ncl_kkt_status_string(ncl_status st) {
     case NCL_ERR_NUMERIC: return "NCL_ERR_NUMERIC";
     case NCL_ERR_IR_NOT_CONVERGED: return "NCL_ERR_IR_NOT_CONVERGED";
     case NCL_ERR_TIMEOUT: return "NCL_ERR_TIMEOUT";
+    case NCL_ERR_INERTIA: return "NCL_ERR_INERTIA";
   }
   return "NCL_ERR_UNKNOWN";
 }

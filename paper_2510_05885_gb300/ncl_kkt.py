@@ -20,8 +20,8 @@ PIVOT_PERTURB, PIVOT_STOP = 0, 1
 
 STATUS = ["NCL_OK", "NCL_ERR_INVALID_ARG", "NCL_ERR_PATTERN", "NCL_ERR_OOM", "NCL_ERR_CUDA",
           "NCL_ERR_STATE", "NCL_ERR_ZERO_PIVOT", "NCL_ERR_NUMERIC", "NCL_ERR_IR_NOT_CONVERGED",
-          "NCL_ERR_TIMEOUT"]
-OK, ERR_IR_NOT_CONVERGED, ERR_ZERO_PIVOT = 0, 8, 6
+          "NCL_ERR_TIMEOUT", "NCL_ERR_INERTIA"]
+OK, ERR_IR_NOT_CONVERGED, ERR_ZERO_PIVOT, ERR_INERTIA = 0, 8, 6, 10
 
 
 class Options(ctypes.Structure):
@@ -84,6 +84,7 @@ _SIGS = {
     "ncl_kkt_batch_analyze": (I32, [I32, I32, P, P, P, P, P, P, ctypes.POINTER(Options), ctypes.POINTER(P)]),
     "ncl_kkt_factor": (I32, [P, P, P, P, D, D, P, ctypes.POINTER(FactorInfo)]),
     "ncl_kkt_batch_factor": (I32, [P, P, P, P, P, P, P, P]),
+    "ncl_kkt_factor_regularize": (I32, [P, P, P, P, P, P, D, D, I32, P, P, P]),
     "ncl_kkt_solve": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_solve_noalloc": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_batch_factor_solve": (I32, [P, P, P, P, P, P, I32, P, I64, P, I64, P, P,
@@ -214,6 +215,26 @@ def ncl_kkt_batch_factor(h, H_val, J_val, Sigma, delta, rho, stream=None):
     if st not in (OK, ERR_ZERO_PIVOT):
         _check(st)
     return list(infos), st
+
+
+def ncl_kkt_factor_regularize(h, H_val, J_val, Sigma, delta, rho, delta_first=1e-4, growth=10.0, max_tries=20,
+                              stream=None, raise_on_inertia=True):
+    """Inertia correction (Section 3.1): returns (infos, delta per instance,
+    tries, status).  rho is the unregularised penalty; the matrix uses
+    rho + delta.  With raise_on_inertia=False an NCL_ERR_INERTIA outcome is
+    returned in the status instead of raised."""
+    lib = load()
+    count = lib.ncl_kkt_instance_count(h)
+    infos = (FactorInfo * count)()
+    dl = np.array(np.broadcast_to(np.asarray(delta, dtype=np.float64), (count,)))
+    rh = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (count,)))
+    tries = ctypes.c_int32(0)
+    st = lib.ncl_kkt_factor_regularize(h, _ptr(H_val), _ptr(J_val), _ptr(Sigma), dl.ctypes.data, rh.ctypes.data,
+                                       float(delta_first), float(growth), int(max_tries), _stream_ptr(stream),
+                                       ctypes.cast(infos, P), ctypes.byref(tries))
+    if st not in (OK, ERR_ZERO_PIVOT) and not (st == ERR_INERTIA and not raise_on_inertia):
+        _check(st)
+    return list(infos), dl, int(tries.value), st
 
 
 def ncl_kkt_solve(h, nrhs, B, ldb, X, ldx, stream=None):
@@ -364,6 +385,14 @@ class KKT:
         if self.count == 1:
             return ncl_kkt_factor(self._h, H_val, J_val, Sigma, delta, rho, stream)
         return ncl_kkt_batch_factor(self._h, H_val, J_val, Sigma, delta, rho, stream)[0]
+
+    def factor_regularized(self, H_val, J_val, Sigma, delta, rho, delta_first=1e-4, growth=10.0, max_tries=20,
+                           stream=None, raise_on_inertia=True):
+        """Inertia-corrected factorisation (Section 3.1); see
+        ncl_kkt_factor_regularize.  Returns (infos, delta, tries, status)."""
+        self.generation += 1
+        return ncl_kkt_factor_regularize(self._h, H_val, J_val, Sigma, delta, rho, delta_first, growth, max_tries,
+                                         stream, raise_on_inertia)
 
     def solve(self, B, X=None, stream=None):
         """B: (dim,) or (dim, nrhs) float64 CUDA tensor.  Returns (X, info)."""

@@ -365,3 +365,77 @@ def test_planted_mistake_transposed_J_in_condensed(monkeypatch):
     Jt = J.toarray()
     bad = Kgood.toarray() - inst.rho * Jt.T @ Jt + inst.rho * np.kron(np.eye(2), Jt @ Jt.T)[:n, :n]
     assert not np.allclose(bad @ u, f + inst.rho * (J.T @ g), rtol=1e-6, atol=1e-6)
+
+
+# ------------------------------------------------- inertia correction (Section 3.1)
+
+def _scalar_instance(form):
+    gd = read_golden(os.path.join(GOLDEN, "regularize_scalar.txt"))
+    inst = custom_instance(np.array([[gd["h"][0]]]), np.array([[1.0]]), np.zeros(1), 0.0, gd["rho"][0],
+                           np.ones(2 if form == "stabilized" else 1), form=form)
+    return inst, gd
+
+
+@pytest.mark.parametrize("form", ["stabilized", "condensed"])
+def test_regularize_golden_scalar(form):
+    inst, gd = _scalar_instance(form)
+    fac, A, delta, tries, regular = O.regularize(inst, 0.0, gd["delta_first"][0], gd["growth"][0])
+    assert regular and tries == int(gd["tries"][0]) and delta == gd["delta"][0]
+    assert fac.inertia == tuple(int(v) for v in gd[f"inertia_{form}"])
+
+
+def test_regularize_m0_is_the_shifted_spectrum():
+    """m = 0: the loop stops at the first delta of the schedule above
+    -lambda_min(H + Sigma) (textbook: H + Sigma + delta I is SPD iff
+    delta > -lambda_min)."""
+    lam = np.array([-2.5, 0.3, 1.0, 4.0, -0.7, 2.0])
+    Q, _ = np.linalg.qr(np.random.default_rng(5).standard_normal((6, 6)))
+    H = Q @ np.diag(lam) @ Q.T
+    inst = custom_instance(H, np.zeros((0, 6)), np.zeros(6), 0.0, 1.0, np.ones(6), form="condensed")
+    fac, A, delta, tries, regular = O.regularize(inst, 0.0, 1e-4, 10.0)
+    sched = [0.0] + [1e-4 * 10.0 ** k for k in range(20)]
+    want = next(i for i, d in enumerate(sched) if lam.min() + d > 0)
+    assert regular and tries == want + 1 and np.isclose(delta, sched[want], rtol=1e-12)
+    assert fac.inertia == (6, 0, 0)
+
+
+@pytest.mark.parametrize("form", ["stabilized", "condensed"])
+def test_regularize_matches_dense_eigenvalues(form):
+    """On a tiny grid started at delta = 0 the loop's stopping delta is the
+    first of the schedule at which the dense FP64 eigenvalues of the
+    regularised matrix (rho-hat = rho + delta) have the regular inertia."""
+    inst = _tiny(3, 3, 23, form, rho=0.5)
+    p = inst.pat
+    build = O.kkt_stabilized if form == "stabilized" else O.kkt_condensed
+    want = (inst.n, inst.m if form == "stabilized" else 0, 0)
+    sched = [0.0] + [1e-2 * 3.0 ** k for k in range(30)]
+    stop = None
+    for i, d in enumerate(sched):
+        K = build(p.n, p.m, p.H_rowptr, p.H_colind, inst.H_val, p.J_rowptr, p.J_colind, inst.J_val,
+                  inst.Sigma, d, inst.rho + d).toarray()
+        ev = np.linalg.eigvalsh(K)
+        assert np.min(np.abs(ev)) > 1e-8 * np.max(np.abs(ev))      # no decision near zero
+        if ((ev > 0).sum(), (ev < 0).sum(), 0) == want:
+            stop = i
+            break
+    assert stop is not None and stop > 0          # the test needs at least one correction
+    fac, A, delta, tries, regular = O.regularize(inst, 0.0, 1e-2, 3.0, max_tries=40)
+    assert regular and tries == stop + 1 and np.isclose(delta, sched[stop], rtol=1e-12)
+
+
+def test_regularize_gives_up_after_max_tries():
+    inst, gd = _scalar_instance("stabilized")
+    fac, A, delta, tries, regular = O.regularize(inst, 0.0, gd["delta_first"][0], gd["growth"][0], max_tries=2)
+    assert not regular and tries == 2 and delta == gd["delta_first"][0]
+
+
+def test_planted_mistake_rho_hat_not_raised(monkeypatch):
+    """Leaving rho-hat at rho while delta grows breaks the golden scalar pin."""
+    orig = O.kkt_stabilized
+    inst, gd = _scalar_instance("stabilized")
+
+    def bad(n, m, Hp, Hi, Hv, Jp, Ji, Jv, Sigma, delta, rho):
+        return orig(n, m, Hp, Hi, Hv, Jp, Ji, Jv, Sigma, delta, inst.rho)
+    monkeypatch.setattr(O.oracle, "kkt_stabilized", bad)
+    fac, A, delta, tries, regular = O.oracle.regularize(inst, 0.0, gd["delta_first"][0], gd["growth"][0])
+    assert (delta, tries) != (gd["delta"][0], int(gd["tries"][0]))
