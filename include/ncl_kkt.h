@@ -280,6 +280,63 @@ ncl_status ncl_kkt_batch_factor(ncl_kkt_t h, const double* H_val, const double* 
                                 ncl_stream_t stream, ncl_kkt_factor_info* infos);
 
 /*
+ * ncl_kkt_factor_k1s -- the condensed system with slacks, Eq. K1s (Section
+ * 3.3, proposition on the condensed KKT system): on a CONDENSED handle whose
+ * J rows are the constraints h = (c_E, c_I) of an NCO problem (Section 3.3),
+ * factor
+ *   K = H + Sigma + delta I + sum_r w_r J_r^T J_r,
+ *   w_r = rho for a row without slack, rho Omega_r for a row with slack,
+ *   Omega_r = Sigma_s,r / (rho + Sigma_s,r)  (so Omega_r -> 1 as Sigma_s,r -> inf).
+ *   Sigma_s  device double[m] (batch: concatenated by instance): the slack
+ *            barrier term of each constraint row, >= 0, or +inf for a row
+ *            without slack (an equality row)
+ *   H_val, J_val, Sigma (= Sigma_t of the paper), delta, rho, infos: as in
+ *            ncl_kkt_batch_factor (host arrays of length count; count = 1 for
+ *            a single handle); rho is the penalty of the matrix (rho-hat)
+ * ncl_kkt_k1s_rhs forms the right-hand side, ncl_kkt_solve then gives
+ * Delta t and ncl_kkt_k1s_slack_step Delta s.  The adjoint of a
+ * K1s factorisation differentiates through the weights (dl/dJ, dl/drho);
+ * dl/dSigma_s is not computed.
+ * Errors: INVALID_ARG (not a condensed handle, NULL Sigma_s), and those of
+ * ncl_kkt_batch_factor.
+ */
+ncl_status ncl_kkt_factor_k1s(ncl_kkt_t h, const double* H_val, const double* J_val,
+                              const double* Sigma, const double* Sigma_s, const double* delta,
+                              const double* rho, ncl_stream_t stream, ncl_kkt_factor_info* infos);
+
+/*
+ * ncl_kkt_k1s_rhs -- the right-hand side of Eq. K1s for the current
+ * condensed factorisation, as the elimination of Delta s in the proof of the
+ * proposition (Section 3.3) produces it:
+ *   OUT = RT + rho J_I^T (Sigma_s + rho I)^{-1} RS
+ * (the statement of Eq. K1s prints it without (Sigma_s + rho I)^{-1}; the
+ * proof's own steps, and the unreduced system they start from, give it
+ * with).  Rows without slack contribute nothing.
+ *   RT   device double, dim x nrhs column-major (ldt >= dim): r_t
+ *   RS   device double, m x nrhs (ldr >= m): r_s
+ *   OUT  device double, dim x nrhs (ldo >= dim); may be RT itself
+ * Errors: INVALID_ARG, STATE (no factor).
+ */
+ncl_status ncl_kkt_k1s_rhs(ncl_kkt_t h, int32_t nrhs, const double* RT, int64_t ldt,
+                           const double* RS, int64_t ldr, double* OUT, int64_t ldo,
+                           ncl_stream_t stream);
+
+/*
+ * ncl_kkt_k1s_slack_step -- the eliminated slack step of Eq. K1s:
+ *   Delta s_r = (rho (J Delta t)_r + r_s,r) / (Sigma_s,r + rho)
+ * for each row with slack, 0 for a row without (Sigma_s = +inf), with the
+ * Sigma_s and rho of the current factorisation (plain condensed factors: no
+ * row has a slack).
+ *   DT  device double, dim x nrhs column-major (ldt >= dim): Delta t
+ *   RS  device double, m x nrhs (ldr >= m): r_s (read on rows with slack)
+ *   DS  device double, m x nrhs (lds >= m): receives Delta s
+ * Errors: INVALID_ARG, STATE (no factor).
+ */
+ncl_status ncl_kkt_k1s_slack_step(ncl_kkt_t h, int32_t nrhs, const double* DT, int64_t ldt,
+                                  const double* RS, int64_t ldr, double* DS, int64_t lds,
+                                  ncl_stream_t stream);
+
+/*
  * ncl_kkt_factor_regularize -- the inertia correction of Section 3.1
  * (regularised matrix Eq. K2): factor with the primal regularisation
  * delta[i]; while instance i's inertia is not the regular one, (n_i, m_i, 0)

@@ -16,6 +16,15 @@ What it computes, and where the paper defines it:
 * ``solve_ir``: Richardson iterative refinement in FP64 (Section 4.3).
 * ``backward_error``: the normwise backward error
   ``||b - K x||_inf / (||K||_inf ||x||_inf + ||b||_inf)``.
+* ``kkt_condensed_slack``: the condensed system with slacks of Section 3.3
+  (Eq. K1s), ``H + Sigma_t + delta I + rho J_E^T J_E + rho J_I^T Omega J_I``,
+  ``Omega = Sigma_s (rho + Sigma_s)^{-1}``; rows with ``Sigma_s = +inf`` are
+  the equality rows E, the others the inequality rows I.
+  ``k1s_slack_step``: the eliminated slack step of the proposition's proof,
+  ``Delta s = (Sigma_s + rho I)^{-1} (rho J_I Delta t + r_s)`` (0 on E rows);
+  ``k1s_rhs``: the right-hand side that elimination produces,
+  ``r_t + rho J_I^T (Sigma_s + rho I)^{-1} r_s`` (the statement of Eq. K1s
+  prints it without the inverse; the proof's own steps give it with).
 * ``regularize``: the inertia correction of Section 3.1 (regularised matrix
   Eq. K2): raise the primal regularisation delta until the inertia is the
   regular one, with rho-hat = rho + delta in the matrix as the same section
@@ -42,6 +51,7 @@ from scipy.sparse.csgraph import reverse_cuthill_mckee
 __all__ = [
     "build_oracle", "kkt_stabilized", "kkt_condensed", "instance_matrix", "block_signs",
     "LDLT", "solve_ir", "backward_error", "solve_instance", "adjoint", "cond1_estimate", "regularize",
+    "kkt_condensed_slack", "k1s_slack_step", "k1s_rhs",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -112,6 +122,50 @@ def kkt_condensed(n, m, H_rowptr, H_colind, H_val, J_rowptr, J_colind, J_val,
                       shape=(m, n))
     K = H + sp.diags(np.asarray(Sigma, float) + delta) + rho * (J.T @ J)
     return sp.csc_matrix(K)
+
+
+def kkt_condensed_slack(n, m, H_rowptr, H_colind, H_val, J_rowptr, J_colind, J_val,
+                        Sigma_t, Sigma_s, delta, rho) -> sp.csc_matrix:
+    """K1s = H + Sigma_t + delta I + rho J_E^T J_E + rho J_I^T Omega J_I
+    (Section 3.3, Eq. K1s), Omega = Sigma_s / (rho + Sigma_s) on the rows
+    with a finite Sigma_s (I), the rows with Sigma_s = +inf forming E."""
+    H = _H_full(n, H_rowptr, H_colind, H_val)
+    J = sp.csr_matrix((np.asarray(J_val, float), np.asarray(J_colind), np.asarray(J_rowptr)),
+                      shape=(m, n))
+    Ss = np.asarray(Sigma_s, float)
+    eq = np.isposinf(Ss)
+    JE, JI = J[np.flatnonzero(eq)], J[np.flatnonzero(~eq)]
+    omega = Ss[~eq] / (rho + Ss[~eq])
+    K = (H + sp.diags(np.asarray(Sigma_t, float) + delta) + rho * (JE.T @ JE)
+         + rho * (JI.T @ sp.diags(omega) @ JI))
+    return sp.csc_matrix(K)
+
+
+def k1s_slack_step(m, J_rowptr, J_colind, J_val, n, Sigma_s, rho, dt, rs) -> np.ndarray:
+    """Delta s = (Sigma_s + rho I)^{-1} (rho J_I Delta t + r_s) on the rows
+    with a finite Sigma_s, 0 on the others (proof of the proposition on
+    Eq. K1s, Section 3.3)."""
+    J = sp.csr_matrix((np.asarray(J_val, float), np.asarray(J_colind), np.asarray(J_rowptr)),
+                      shape=(m, n))
+    Ss = np.asarray(Sigma_s, float)
+    dt = np.asarray(dt, float).reshape(n, -1)
+    rs = np.asarray(rs, float).reshape(m, -1)
+    ds = np.zeros_like(rs)
+    I = np.flatnonzero(~np.isposinf(Ss))
+    ds[I] = (rho * (J[I] @ dt) + rs[I]) / (Ss[I] + rho)[:, None]
+    return ds
+
+
+def k1s_rhs(m, J_rowptr, J_colind, J_val, n, Sigma_s, rho, rt, rs) -> np.ndarray:
+    """r_t + rho J_I^T (Sigma_s + rho I)^{-1} r_s: eliminating Delta s from the
+    second block row of Eq. K1' (Section 3.3) and moving it to the right."""
+    J = sp.csr_matrix((np.asarray(J_val, float), np.asarray(J_colind), np.asarray(J_rowptr)),
+                      shape=(m, n))
+    Ss = np.asarray(Sigma_s, float)
+    rt = np.asarray(rt, float).reshape(n, -1)
+    rs = np.asarray(rs, float).reshape(m, -1)
+    I = np.flatnonzero(~np.isposinf(Ss))
+    return rt + rho * (J[I].T @ (rs[I] / (Ss[I] + rho)[:, None]))
 
 
 def instance_matrix(inst) -> sp.csc_matrix:

@@ -18,6 +18,7 @@
 
 namespace ncl {
 void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64_t* inst_con_off, const double* rho,
+                            const double* dw,
                             const double* X, int64_t ldx, const double* GB, int64_t ldgb, int nrhs,
                             const double* jx, const double* jg, double* G_scal, cudaStream_t st);
 }
@@ -190,6 +191,9 @@ struct ncl_kkt_s {
   double* jg = nullptr;
   double* GBtmp = nullptr;
   double* Jcopy = nullptr;                 // condensed form: J values of the last factor (adjoint)
+  double* d_w = nullptr;                   // condensed form: row weights of J^T W J (Eq. K1 / K1s)
+  double* d_dw = nullptr;                  //   their derivative in rho (adjoint)
+  double* d_ss = nullptr;                  //   the slack terms Sigma_s (+inf: no slack)
   // FGMRES refinement workspace (allocated on first use)
   double* gm_V = nullptr;                  // (GM_M + 1) x dim Krylov basis
   double* gm_Z = nullptr;                  // GM_M x dim preconditioned directions
@@ -197,7 +201,7 @@ struct ncl_kkt_s {
   double* gm_part = nullptr;               // (GM_M + 1) x vec_grid() partial sums
   double* gm_coef = nullptr;
   double* gm_host = nullptr;               // pinned mirror of gm_part
-  const double** d_valptr = nullptr;       // {H, J, Sigma} pointers of the current factor call
+  const double** d_valptr = nullptr;       // {H, J, Sigma, Sigma_s} pointers of the current factor call
   CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
   TcProb* d_tc = nullptr;
   int* d_err = nullptr;                    // device error flags (bounded waits)
@@ -756,6 +760,23 @@ void build_device(ncl_kkt_s* h) {
   }
   ro[P.inst.size()] = P.dim;
   d.inst_row_off = h->upload(ro);
+  {
+    std::vector<int32_t> ci((size_t)std::max<int64_t>(P.mcon_total, 1), 0);
+    for (size_t i = 0; i < P.inst.size(); i++)
+      for (int64_t c = co[i]; c < co[i + 1]; c++) ci[c] = (int32_t)i;
+    d.con_inst = h->upload(ci);
+  }
+  if (P.form == 1) {
+    // J values by variable (KKT row), in constraint order: counting sort
+    std::vector<int64_t> tp((size_t)P.dim + 1, 0);
+    for (int32_t c : P.J_col) tp[(size_t)c + 1]++;
+    for (int64_t v = 0; v < P.dim; v++) tp[v + 1] += tp[v];
+    std::vector<int32_t> ti((size_t)std::max<int64_t>((int64_t)P.J_col.size(), 1), 0);
+    std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+    for (size_t e = 0; e < P.J_col.size(); e++) ti[fill[P.J_col[e]]++] = (int32_t)e;
+    d.JT_ptr = h->upload(tp);
+    d.JT_idx = h->upload(ti);
+  }
   h->d_inst_n = h->upload(in);
   h->d_inst_con_off = h->upload(co);
 
@@ -787,7 +808,12 @@ void build_device(ncl_kkt_s* h) {
   h->GBtmp = h->alloc<double>((int64_t)P.dim * MAX_RHS_SWEEP);
   h->jx = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
   h->jg = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
-  if (P.form == 1) h->Jcopy = h->alloc<double>(std::max<int64_t>(d.nnzJ, 1));
+  if (P.form == 1) {
+    h->Jcopy = h->alloc<double>(std::max<int64_t>(d.nnzJ, 1));
+    h->d_w = h->alloc<double>(std::max<int64_t>(d.ncon, 1));
+    h->d_dw = h->alloc<double>(std::max<int64_t>(d.ncon, 1));
+    h->d_ss = h->alloc<double>(std::max<int64_t>(d.ncon, 1));
+  }
   h->d_valptr = h->alloc<const double*>(4);
   if (hs_ref(h).tc) {
     HostSched& hs = h->hs;
@@ -1229,7 +1255,7 @@ ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, do
 
 // validate and stage the scalars and value pointers of a factor call
 ncl_status prepare_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
-                          const double* rho, cudaStream_t st) {
+                          const double* rho, cudaStream_t st, const double* Ss = nullptr) {
   const int ni = h->dp.ninst;
   for (int i = 0; i < ni; i++) {
     if (!(rho[i] > 0) || !std::isfinite(rho[i])) return fail(NCL_ERR_INVALID_ARG, "rho must be positive and finite");
@@ -1247,10 +1273,11 @@ ncl_status prepare_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, cons
   vp[0] = Hv;
   vp[1] = Jv;
   vp[2] = S;
+  vp[3] = Ss;
   CK(cudaEventRecord(h->ev0, st));
   CK(cudaMemcpyAsync(h->d_delta, hp, ni * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->d_rho, hp + ni, ni * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(h->d_valptr, vp, 3 * sizeof(double*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_valptr, vp, 4 * sizeof(double*), cudaMemcpyHostToDevice, st));
   if (h->Jcopy && h->dp.nnzJ)
     CK(cudaMemcpyAsync(h->Jcopy, Jv, h->dp.nnzJ * sizeof(double), cudaMemcpyDeviceToDevice, st));
   h->h_delta.assign(delta, delta + ni);
@@ -1263,9 +1290,12 @@ void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
   const int ni = h->dp.ninst;
   if (!h->skip_values) {
     const double np = (double)h->plan.pair_p.size();
+    if (h->dp.form == 1 && h->dp.ncon > 0)
+      klaunch(h, s2, "row_weights_f64", h->dp.ncon, Cost{4.0 * h->dp.ncon, 48.0 * h->dp.ncon},
+              [&] { launch_row_weights(h->dp, h->d_valptr, h->d_rho, h->d_w, h->d_dw, h->d_ss, s2); });
     klaunch(h, s2, "kkt_values_f64", h->dp.nnzA,
             Cost{2.0 * np, 33.0 * h->dp.nnzA + 24.0 * np + 8.0 * (h->dp.nnzH + h->dp.nnzJ + h->dp.nvar)},
-            [&] { launch_kkt_values(h->dp, h->d_valptr, h->d_delta, h->d_rho, h->Klow, s2); });
+            [&] { launch_kkt_values(h->dp, h->d_valptr, h->d_delta, h->d_rho, h->d_w, h->Klow, s2); });
   }
   CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), s2));
   klaunch(h, s2, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
@@ -1379,9 +1409,9 @@ ncl_status escalate(ncl_kkt_s* h, cudaStream_t st, ncl_kkt_factor_info* infos) {
 }
 
 ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
-                     const double* rho, cudaStream_t st, ncl_kkt_factor_info* infos) {
+                     const double* rho, cudaStream_t st, ncl_kkt_factor_info* infos, const double* Ss = nullptr) {
   h->use_twin = false;
-  ncl_status s0 = prepare_factor(h, Hv, Jv, S, delta, rho, st);
+  ncl_status s0 = prepare_factor(h, Hv, Jv, S, delta, rho, st, Ss);
   if (s0 != NCL_OK) return s0;
   run_graphed(h, &h->fgraph, &h->fgraph_nodes, &h->factor_calls, true, st,
               [&](cudaStream_t s2) { enqueue_factor(h, s2); });
@@ -1653,6 +1683,58 @@ ncl_status ncl_kkt_batch_factor(ncl_kkt_t h, const double* H_val, const double* 
   return guarded(h, [&] { return do_factor(h, H_val, J_val, Sigma, delta, rho, (cudaStream_t)stream, infos); });
 }
 
+// The condensed form with slacks, Eq. K1s: the condensed factorisation with
+// row weights rho Omega_r, Omega_r = Sigma_s,r / (rho + Sigma_s,r), from the
+// caller's slack terms (+inf for a row without slack).
+ncl_status ncl_kkt_factor_k1s(ncl_kkt_t h, const double* H_val, const double* J_val, const double* Sigma,
+                              const double* Sigma_s, const double* delta, const double* rho, ncl_stream_t stream,
+                              ncl_kkt_factor_info* infos) {
+  if (!h || !delta || !rho) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (h->plan.form != 1) return fail(NCL_ERR_INVALID_ARG, "the slack form needs a condensed handle");
+  if (h->dp.ncon > 0 && !Sigma_s) return fail(NCL_ERR_INVALID_ARG, "NULL Sigma_s");
+  return guarded(h, [&] {
+    return do_factor(h, H_val, J_val, Sigma, delta, rho, (cudaStream_t)stream, infos, Sigma_s);
+  });
+}
+
+// Right-hand side of Eq. K1s for the current condensed factorisation.
+ncl_status ncl_kkt_k1s_rhs(ncl_kkt_t h, int32_t nrhs, const double* RT, int64_t ldt, const double* RS, int64_t ldr,
+                           double* OUT, int64_t ldo, ncl_stream_t stream) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (h->plan.form != 1) return fail(NCL_ERR_INVALID_ARG, "the slack form needs a condensed handle");
+  if (!h->factored && !h->use_twin) return fail(NCL_ERR_STATE, "right-hand side before a successful factor");
+  const int64_t ncon = h->dp.ncon;
+  if (nrhs <= 0 || !RT || !OUT || (ncon > 0 && !RS) || ldt < h->dp.dim || ldo < h->dp.dim || ldr < ncon)
+    return fail(NCL_ERR_INVALID_ARG, "bad right-hand-side arguments");
+  return guarded(h, [&]() -> ncl_status {
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    launch_k1s_rhs(h->dp, h->Jcopy, h->d_rho, h->d_ss, nrhs, RT, ldt, RS, ldr, OUT, ldo, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NCL_OK;
+  });
+}
+
+// Slack recovery of Eq. K1s for the current condensed factorisation.
+ncl_status ncl_kkt_k1s_slack_step(ncl_kkt_t h, int32_t nrhs, const double* DT, int64_t ldt, const double* RS,
+                                  int64_t ldr, double* DS, int64_t lds, ncl_stream_t stream) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (h->plan.form != 1) return fail(NCL_ERR_INVALID_ARG, "the slack step needs a condensed handle");
+  if (!h->factored && !h->use_twin) return fail(NCL_ERR_STATE, "slack step before a successful factor");
+  const int64_t ncon = h->dp.ncon;
+  if (nrhs <= 0 || (ncon > 0 && (!DT || !RS || !DS)) || ldt < h->dp.dim || ldr < ncon || lds < ncon)
+    return fail(NCL_ERR_INVALID_ARG, "bad slack-step arguments");
+  return guarded(h, [&]() -> ncl_status {
+    if (ncon == 0) return NCL_OK;
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    launch_slack_step(h->dp, h->Jcopy, h->d_rho, h->d_ss, nrhs, DT, ldt, RS, ldr, DS, lds, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return NCL_OK;
+  });
+}
+
 // The inertia correction of Section 3.1: raise the primal regularisation of
 // every instance whose inertia is irregular and refactor, rho-hat = rho +
 // delta entering the matrix with it.
@@ -1742,10 +1824,10 @@ ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t l
     ncl_status s = do_solve(h, nrhs, GX, ldgx, gb, ld, st, info);
     if (s != NCL_OK && s != NCL_ERR_IR_NOT_CONVERGED) return s;
     g_kernel_launches.fetch_add(4, std::memory_order_relaxed);
-    launch_adjoint_values(h->dp, h->Jcopy, h->d_rho, X, ldx, gb, ld, nrhs, G_Hval, G_Jval, G_Sigma, G_scal,
+    launch_adjoint_values(h->dp, h->Jcopy, h->d_w, X, ldx, gb, ld, nrhs, G_Hval, G_Jval, G_Sigma, G_scal,
                           h->jx, h->jg, st);
     if (G_scal) {
-      launch_adjoint_scalars(h->dp, h->d_inst_n, h->d_inst_con_off, h->d_rho, X, ldx, gb, ld, nrhs, h->jx, h->jg,
+      launch_adjoint_scalars(h->dp, h->d_inst_n, h->d_inst_con_off, h->d_rho, h->d_dw, X, ldx, gb, ld, nrhs, h->jx, h->jg,
                              G_scal, st);
     }
     CK(cudaGetLastError());

@@ -15,21 +15,60 @@
 #include "pivot.cuh"
 #include "reduce.cuh"
 
+#include <math_constants.h>
+
 #include <cmath>
 #include <cstdio>
 
 namespace ncl {
 
 // ---------------------------------------------------------------------------
+// Row weights of the condensed form (Section 3.3): w_r = rho for a row
+// without slack (an equality row: Sigma_s = +inf, or no Sigma_s given), and
+// for an inequality row with slack barrier term Sigma_s,r (Eq. K1s)
+//   w_r = rho Omega_r,  Omega_r = Sigma_s,r / (rho + Sigma_s,r),
+// which tends to rho as Sigma_s,r -> inf.  dw_r = dw_r/drho (1, or
+// Sigma_s^2 / (rho + Sigma_s)^2) is kept for the adjoint, and the slack term
+// for the slack recovery.  rho is the penalty of the matrix (rho-hat).
+// ---------------------------------------------------------------------------
+__global__ void k_row_weights(DevPlan P, const double* const* __restrict__ vals, const double* __restrict__ rho,
+                              double* __restrict__ w, double* __restrict__ dw, double* __restrict__ ss) {
+  const double* __restrict__ Ss = vals[3];
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < P.ncon;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const double s = Ss ? Ss[c] : CUDART_INF;
+    ss[c] = s;
+    const double rh = rho[P.con_inst[c]];
+    if (isinf(s) && s > 0) {
+      w[c] = rh;
+      dw[c] = 1.0;
+    } else {
+      const double den = rh + s;
+      w[c] = rh * s / den;
+      dw[c] = (s / den) * (s / den);
+    }
+  }
+}
+
+void launch_row_weights(const DevPlan& P, const double* const* vals, const double* rho, double* w, double* dw,
+                        double* ss, cudaStream_t st) {
+  if (P.ncon == 0) return;
+  int64_t blocks = (P.ncon + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_row_weights<<<(unsigned)blocks, 256, 0, st>>>(P, vals, rho, w, dw, ss);
+}
+
+// ---------------------------------------------------------------------------
 // FP64 values of the lower KKT entries:
 //   K2r (Eq. K2r): H_ij, Sigma_i + delta on the primal diagonal, J_ri in the
 //                  (2,1) block, -1/rho on the dual diagonal;
-//   K   (Eq. K1):  H_ij + (Sigma_i + delta) [i=j] + rho * sum_r J_ri J_rj,
+//   K   (Eq. K1 / K1s): H_ij + (Sigma_i + delta) [i=j] + sum_r w_r J_ri J_rj,
 //                  the product summed over the constraint rows shared by i, j
-//                  in a fixed order (no atomics).
+//                  in a fixed order (no atomics); w_r = rho without slacks.
 // ---------------------------------------------------------------------------
 __global__ void k_kkt_values(DevPlan P, const double* const* __restrict__ vals, const double* __restrict__ delta,
-                             const double* __restrict__ rho, double* __restrict__ Klow) {
+                             const double* __restrict__ rho, const double* __restrict__ w,
+                             double* __restrict__ Klow) {
   // vals = {H values, J values, Sigma}: read from device memory so that a
   // captured graph stays valid when the caller passes new arrays
   const double* __restrict__ Hv = vals[0];
@@ -48,19 +87,22 @@ __global__ void k_kkt_values(DevPlan P, const double* const* __restrict__ vals, 
     int64_t p0 = P.pair_ptr[e], p1 = P.pair_ptr[e + 1];
     if (p1 > p0) {
       double s = 0.0;
-      for (int64_t p = p0; p < p1; p++) s = fma(Jv[P.pair_p[p]], Jv[P.pair_q[p]], s);
-      v = fma(rho[inst], s, v);
+      for (int64_t p = p0; p < p1; p++) {
+        const int32_t a = P.pair_p[p];
+        s = fma(w[P.J_con[a]] * Jv[a], Jv[P.pair_q[p]], s);
+      }
+      v += s;
     }
     Klow[e] = v;
   }
 }
 
 void launch_kkt_values(const DevPlan& P, const double* const* vals, const double* delta, const double* rho,
-                       double* Klow, cudaStream_t st) {
+                       const double* w, double* Klow, cudaStream_t st) {
   if (P.nnzA == 0) return;
   int64_t blocks = (P.nnzA + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_kkt_values<<<(unsigned)blocks, 256, 0, st>>>(P, vals, delta, rho, Klow);
+  k_kkt_values<<<(unsigned)blocks, 256, 0, st>>>(P, vals, delta, rho, w, Klow);
 }
 
 // ||K||_inf per instance (max absolute row sum), as the bit pattern of a

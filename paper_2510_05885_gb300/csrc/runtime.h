@@ -75,6 +75,9 @@ struct DevPlan {
   const int64_t* sn_Soff;       // split-operand offset of a tensor-core front, -1 otherwise
   const int8_t* sn_flags;       // bit 0: front factored by panels (large front)
   const int64_t* sn_Ioff;       // offset of the inverted 32 x 32 diagonal blocks of L11
+  // condensed form: the J values of each variable (KKT row), in constraint order
+  const int64_t* JT_ptr;        // dim+1
+  const int32_t* JT_idx;        // J value indices
 };
 
 // Numeric state for one precision T (float or double).
@@ -122,7 +125,15 @@ void launch_split_rows(const float* L, const float* d, int rows, int ld, int K, 
 
 // launchers (factor.cu)
 void launch_kkt_values(const DevPlan& P, const double* const* vals, const double* delta, const double* rho,
-                       double* Klow, cudaStream_t st);
+                       const double* w, double* Klow, cudaStream_t st);
+void launch_row_weights(const DevPlan& P, const double* const* vals, const double* rho, double* w, double* dw,
+                        double* ss, cudaStream_t st);
+void launch_k1s_rhs(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
+                    const double* RT, int64_t ldt, const double* RS, int64_t ldr, double* OUT, int64_t ldo,
+                    cudaStream_t st);
+void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
+                       const double* DT, int64_t ldt, const double* RS, int64_t ldr, double* DS, int64_t lds,
+                       cudaStream_t st);
 void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st);
 template <typename T>
 void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
@@ -177,7 +188,7 @@ void launch_multi_axpy(int64_t n, const double* V, int64_t ldv, int nv, const do
 int vec_grid();
 void launch_axpy_inplace(double* X, int64_t ldx, const double* Y, int64_t ldy, double a, int64_t dim,
                          int nrhs, cudaStream_t st);
-void launch_adjoint_values(const DevPlan& P, const double* Jv, const double* rho, const double* X,
+void launch_adjoint_values(const DevPlan& P, const double* Jv, const double* w, const double* X,
                            int64_t ldx, const double* GB, int64_t ldgb, int nrhs, double* G_H,
                            double* G_J, double* G_S, double* G_scal, double* jx, double* jg,
                            cudaStream_t st);

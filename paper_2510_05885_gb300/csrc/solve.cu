@@ -822,7 +822,9 @@ __global__ void k_jmul(DevPlan P, const double* Jv, const double* X, int64_t ldx
   }
 }
 
-__global__ void k_adj_J(DevPlan P, const double* rho, const double* X, int64_t ldx, const double* GB, int64_t ldgb,
+// dl/dJ: K2r from the (2,1) block; K from the product sum_r w_r J_r^T J_r
+// (w_r = rho, or rho Omega_r with slacks, Eq. K1s)
+__global__ void k_adj_J(DevPlan P, const double* w, const double* X, int64_t ldx, const double* GB, int64_t ldgb,
                         int nrhs, const double* jx, const double* jg, double* G_J) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.nnzJ; q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t con = P.J_con[q], c = P.J_col[q];
@@ -831,7 +833,7 @@ __global__ void k_adj_J(DevPlan P, const double* rho, const double* X, int64_t l
       const int32_t rr = P.con_row[con];
       for (int r = 0; r < nrhs; r++) g -= GB[r * ldgb + rr] * X[r * ldx + c] + GB[r * ldgb + c] * X[r * ldx + rr];
     } else {
-      const double rh = rho[P.J_inst[q]];
+      const double rh = w[con];
       for (int r = 0; r < nrhs; r++)
         g -= rh * (jg[r * P.ncon + con] * X[r * ldx + c] + jx[r * P.ncon + con] * GB[r * ldgb + c]);
     }
@@ -840,10 +842,11 @@ __global__ void k_adj_J(DevPlan P, const double* rho, const double* X, int64_t l
 }
 
 // per-instance scalar gradients (one CTA per instance, fixed reduction order)
+// (dl/drho of K uses dw_r/drho: 1 without slacks, Sigma_s^2/(rho+Sigma_s)^2 with)
 __global__ void __launch_bounds__(256) k_adj_scal(DevPlan P, const int64_t* inst_n, const int64_t* inst_con_off,
-                                                  const double* rho, const double* X, int64_t ldx,
-                                                  const double* GB, int64_t ldgb, int nrhs, const double* jx,
-                                                  const double* jg, double* G_scal) {
+                                                  const double* rho, const double* dw, const double* X,
+                                                  int64_t ldx, const double* GB, int64_t ldgb, int nrhs,
+                                                  const double* jx, const double* jg, double* G_scal) {
   __shared__ double red[2][256];
   const int inst = blockIdx.x;
   const int64_t r0 = P.inst_row_off[inst], r1 = P.inst_row_off[inst + 1];
@@ -861,7 +864,7 @@ __global__ void __launch_bounds__(256) k_adj_scal(DevPlan P, const int64_t* inst
   } else {
     gr = 0.0;
     for (int64_t c = inst_con_off[inst] + threadIdx.x; c < inst_con_off[inst + 1]; c += blockDim.x)
-      for (int r = 0; r < nrhs; r++) gr -= jg[r * P.ncon + c] * jx[r * P.ncon + c];
+      for (int r = 0; r < nrhs; r++) gr -= dw[c] * jg[r * P.ncon + c] * jx[r * P.ncon + c];
   }
   red[0][threadIdx.x] = gd;
   red[1][threadIdx.x] = gr;
@@ -879,21 +882,87 @@ __global__ void __launch_bounds__(256) k_adj_scal(DevPlan P, const int64_t* inst
   }
 }
 
-void launch_adjoint_values(const DevPlan& P, const double* Jv, const double* rho, const double* X, int64_t ldx,
+void launch_adjoint_values(const DevPlan& P, const double* Jv, const double* w, const double* X, int64_t ldx,
                            const double* GB, int64_t ldgb, int nrhs, double* G_H, double* G_J, double* G_S,
                            double* G_scal, double* jx, double* jg, cudaStream_t st) {
   if (G_H && P.nnzH) k_adj_H<<<grid_for(P.nnzH), 256, 0, st>>>(P, X, ldx, GB, ldgb, nrhs, G_H);
   if (G_S && P.nvar) k_adj_S<<<grid_for(P.nvar), 256, 0, st>>>(P, X, ldx, GB, ldgb, nrhs, G_S);
   const bool need_j = P.form == 1 && P.ncon && (G_J || G_scal);
   if (need_j) k_jmul<<<grid_for(P.ncon), 256, 0, st>>>(P, Jv, X, ldx, GB, ldgb, nrhs, jx, jg);
-  if (G_J && P.nnzJ) k_adj_J<<<grid_for(P.nnzJ), 256, 0, st>>>(P, rho, X, ldx, GB, ldgb, nrhs, jx, jg, G_J);
+  if (G_J && P.nnzJ) k_adj_J<<<grid_for(P.nnzJ), 256, 0, st>>>(P, w, X, ldx, GB, ldgb, nrhs, jx, jg, G_J);
   (void)G_scal;
 }
 
 void launch_adjoint_scalars(const DevPlan& P, const int64_t* inst_n, const int64_t* inst_con_off, const double* rho,
-                            const double* X, int64_t ldx, const double* GB, int64_t ldgb, int nrhs,
-                            const double* jx, const double* jg, double* G_scal, cudaStream_t st) {
-  k_adj_scal<<<P.ninst, 256, 0, st>>>(P, inst_n, inst_con_off, rho, X, ldx, GB, ldgb, nrhs, jx, jg, G_scal);
+                            const double* dw, const double* X, int64_t ldx, const double* GB, int64_t ldgb,
+                            int nrhs, const double* jx, const double* jg, double* G_scal, cudaStream_t st) {
+  k_adj_scal<<<P.ninst, 256, 0, st>>>(P, inst_n, inst_con_off, rho, dw, X, ldx, GB, ldgb, nrhs, jx, jg, G_scal);
+}
+
+// Slack step of the condensed form with slacks (Section 3.3, proof of the
+// proposition on Eq. K1s):  Delta s_r = (rho (J Delta t)_r + r_s,r) /
+// (Sigma_s,r + rho) for an inequality row; 0 for a row without slack
+// (Sigma_s = +inf).  rho is the penalty of the factored matrix (rho-hat).
+// One thread per (row, right-hand side).
+__global__ void k_slack_step(DevPlan P, const double* __restrict__ Jv, const double* __restrict__ rho,
+                             const double* __restrict__ ss, int nrhs, const double* __restrict__ DT, int64_t ldt,
+                             const double* __restrict__ RS, int64_t ldr, double* __restrict__ DS, int64_t lds) {
+  const int64_t total = P.ncon * (int64_t)nrhs;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx % P.ncon;
+    const int r = (int)(idx / P.ncon);
+    const double s = ss[c];
+    if (isinf(s) && s > 0) {
+      DS[r * lds + c] = 0.0;
+      continue;
+    }
+    double jt = 0.0;
+    for (int64_t q = P.J_rowptr[c]; q < P.J_rowptr[c + 1]; q++) jt = fma(Jv[q], DT[r * ldt + P.J_col[q]], jt);
+    const double rh = rho[P.con_inst[c]];
+    DS[r * lds + c] = fma(rh, jt, RS[r * ldr + c]) / (s + rh);
+  }
+}
+
+// Right-hand side of Eq. K1s as the proof's elimination of Delta s gives it:
+//   OUT = RT + rho J_I^T (Sigma_s + rho I)^{-1} RS,
+// one thread per (variable, right-hand side), the variable's J values in
+// constraint order (deterministic; OUT may alias RT).
+__global__ void k_k1s_rhs(DevPlan P, const double* __restrict__ Jv, const double* __restrict__ rho,
+                          const double* __restrict__ ss, int nrhs, const double* RT, int64_t ldt,
+                          const double* __restrict__ RS, int64_t ldr, double* OUT, int64_t ldo) {
+  const int64_t total = P.dim * (int64_t)nrhs;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = idx % P.dim;
+    const int r = (int)(idx / P.dim);
+    double acc = 0.0;
+    for (int64_t q = P.JT_ptr[v]; q < P.JT_ptr[v + 1]; q++) {
+      const int32_t e = P.JT_idx[q];
+      const int32_t c = P.J_con[e];
+      const double s = ss[c];
+      if (isinf(s) && s > 0) continue;
+      const double rh = rho[P.con_inst[c]];
+      acc = fma(rh * Jv[e], RS[r * ldr + c] / (s + rh), acc);
+    }
+    OUT[r * ldo + v] = RT[r * ldt + v] + acc;
+  }
+}
+
+void launch_k1s_rhs(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
+                    const double* RT, int64_t ldt, const double* RS, int64_t ldr, double* OUT, int64_t ldo,
+                    cudaStream_t st) {
+  const int64_t total = P.dim * (int64_t)nrhs;
+  if (total == 0) return;
+  k_k1s_rhs<<<grid_for(total), 256, 0, st>>>(P, Jv, rho, ss, nrhs, RT, ldt, RS, ldr, OUT, ldo);
+}
+
+void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
+                       const double* DT, int64_t ldt, const double* RS, int64_t ldr, double* DS, int64_t lds,
+                       cudaStream_t st) {
+  const int64_t total = P.ncon * (int64_t)nrhs;
+  if (total == 0) return;
+  k_slack_step<<<grid_for(total), 256, 0, st>>>(P, Jv, rho, ss, nrhs, DT, ldt, RS, ldr, DS, lds);
 }
 
 #define NCL_INST(T)                                                                                               \

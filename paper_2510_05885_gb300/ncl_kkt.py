@@ -85,6 +85,9 @@ _SIGS = {
     "ncl_kkt_factor": (I32, [P, P, P, P, D, D, P, ctypes.POINTER(FactorInfo)]),
     "ncl_kkt_batch_factor": (I32, [P, P, P, P, P, P, P, P]),
     "ncl_kkt_factor_regularize": (I32, [P, P, P, P, P, P, D, D, I32, P, P, P]),
+    "ncl_kkt_factor_k1s": (I32, [P, P, P, P, P, P, P, P, P]),
+    "ncl_kkt_k1s_slack_step": (I32, [P, I32, P, I64, P, I64, P, I64, P]),
+    "ncl_kkt_k1s_rhs": (I32, [P, I32, P, I64, P, I64, P, I64, P]),
     "ncl_kkt_solve": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_solve_noalloc": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_batch_factor_solve": (I32, [P, P, P, P, P, P, I32, P, I64, P, I64, P, P,
@@ -235,6 +238,30 @@ def ncl_kkt_factor_regularize(h, H_val, J_val, Sigma, delta, rho, delta_first=1e
     if st not in (OK, ERR_ZERO_PIVOT) and not (st == ERR_INERTIA and not raise_on_inertia):
         _check(st)
     return list(infos), dl, int(tries.value), st
+
+
+def ncl_kkt_factor_k1s(h, H_val, J_val, Sigma, Sigma_s, delta, rho, stream=None):
+    """Condensed factorisation with slacks (Eq. K1s); Sigma_s: device float64
+    per constraint row, +inf for a row without slack.  Returns (infos, status)."""
+    lib = load()
+    count = lib.ncl_kkt_instance_count(h)
+    infos = (FactorInfo * count)()
+    dl = np.ascontiguousarray(np.broadcast_to(np.asarray(delta, dtype=np.float64), (count,)))
+    rh = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (count,)))
+    st = lib.ncl_kkt_factor_k1s(h, _ptr(H_val), _ptr(J_val), _ptr(Sigma), _ptr(Sigma_s), dl.ctypes.data,
+                                rh.ctypes.data, _stream_ptr(stream), ctypes.cast(infos, P))
+    if st not in (OK, ERR_ZERO_PIVOT):
+        _check(st)
+    return list(infos), st
+
+
+def ncl_kkt_k1s_rhs(h, nrhs, RT, ldt, RS, ldr, OUT, ldo, stream=None):
+    _check(load().ncl_kkt_k1s_rhs(h, nrhs, _ptr(RT), ldt, _ptr(RS), ldr, _ptr(OUT), ldo, _stream_ptr(stream)))
+
+
+def ncl_kkt_k1s_slack_step(h, nrhs, DT, ldt, RS, ldr, DS, lds, stream=None):
+    _check(load().ncl_kkt_k1s_slack_step(h, nrhs, _ptr(DT), ldt, _ptr(RS), ldr, _ptr(DS), lds,
+                                         _stream_ptr(stream)))
 
 
 def ncl_kkt_solve(h, nrhs, B, ldb, X, ldx, stream=None):
@@ -393,6 +420,38 @@ class KKT:
         self.generation += 1
         return ncl_kkt_factor_regularize(self._h, H_val, J_val, Sigma, delta, rho, delta_first, growth, max_tries,
                                          stream, raise_on_inertia)
+
+    def factor_k1s(self, H_val, J_val, Sigma, Sigma_s, delta, rho, stream=None):
+        """Condensed factorisation with slacks (Eq. K1s); see ncl_kkt_factor_k1s."""
+        self.generation += 1
+        infos, _ = ncl_kkt_factor_k1s(self._h, H_val, J_val, Sigma, Sigma_s, delta, rho, stream)
+        return infos[0] if self.count == 1 else infos
+
+    def k1s_rhs(self, RT, RS, stream=None):
+        """r_t + rho J_I^T (Sigma_s + rho I)^{-1} r_s for the current K1s
+        factorisation; RT (dim,) or (dim, nrhs), RS (m,) or (m, nrhs)."""
+        import torch
+        one = RT.dim() == 1
+        Tc = RT.reshape(self.dim, -1).t().contiguous()
+        nrhs = Tc.shape[0]
+        ncon = RS.shape[0]
+        Rc = RS.reshape(ncon, -1).t().contiguous()
+        Oc = torch.empty_like(Tc)
+        ncl_kkt_k1s_rhs(self._h, nrhs, Tc, self.dim, Rc, max(ncon, 1), Oc, self.dim, stream)
+        return Oc.t()[:, 0] if one else Oc.t()
+
+    def slack_step(self, DT, RS, stream=None):
+        """Delta s of Eq. K1s from Delta t (dim,) or (dim, nrhs) and r_s (m,) or
+        (m, nrhs), float64 CUDA tensors."""
+        import torch
+        one = DT.dim() == 1
+        Tc = DT.reshape(self.dim, -1).t().contiguous()
+        nrhs = Tc.shape[0]
+        ncon = RS.shape[0]
+        Rc = RS.reshape(ncon, -1).t().contiguous()
+        Dc = torch.empty_like(Rc)
+        ncl_kkt_k1s_slack_step(self._h, nrhs, Tc, self.dim, Rc, max(ncon, 1), Dc, max(ncon, 1), stream)
+        return Dc.t()[:, 0] if one else Dc.t()
 
     def solve(self, B, X=None, stream=None):
         """B: (dim,) or (dim, nrhs) float64 CUDA tensor.  Returns (X, info)."""

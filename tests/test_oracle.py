@@ -439,3 +439,87 @@ def test_planted_mistake_rho_hat_not_raised(monkeypatch):
     monkeypatch.setattr(O.oracle, "kkt_stabilized", bad)
     fac, A, delta, tries, regular = O.oracle.regularize(inst, 0.0, gd["delta_first"][0], gd["growth"][0])
     assert (delta, tries) != (gd["delta"][0], int(gd["tries"][0]))
+
+
+# ------------------------------------------- condensed form with slacks (Eq. K1s)
+
+def _k1s_case(seed=31, R=3, C=4, rho=50.0):
+    inst = _tiny(R, C, seed, "condensed", rho=rho)
+    rng = np.random.default_rng(seed)
+    Ss = 10.0 ** rng.uniform(-2, 2, inst.m)
+    Ss[rng.random(inst.m) < 0.4] = np.inf          # equality rows
+    return inst, Ss
+
+
+def _k1s_matrix(inst, Ss):
+    p = inst.pat
+    return O.kkt_condensed_slack(p.n, p.m, p.H_rowptr, p.H_colind, inst.H_val, p.J_rowptr, p.J_colind,
+                                 inst.J_val, inst.Sigma, Ss, inst.delta, inst.rho)
+
+
+def test_k1s_matches_the_unreduced_slack_system():
+    """Solving Eq. K1s for Delta t and recovering Delta s gives the solution of
+    the unreduced two-block system in (Delta t, Delta s) of Section 3.3 (Eq.
+    K1'), assembled and solved densely here from its own blocks.  The
+    right-hand side is the one the proof's elimination of Delta s produces,
+    r_t + rho J_I^T (Sigma_s + rho I)^{-1} r_s (the statement of Eq. K1s
+    prints it without the inverse, which this pin rejects)."""
+    inst, Ss = _k1s_case()
+    p, rho = inst.pat, inst.rho
+    n, m = p.n, p.m
+    Hd = O.kkt_condensed(n, 0, p.H_rowptr, p.H_colind, inst.H_val, np.zeros(1, np.int32), np.zeros(0, np.int32),
+                         np.zeros(0), inst.Sigma, inst.delta, 1.0).toarray()
+    J = sp.csr_matrix((inst.J_val, p.J_colind, p.J_rowptr), shape=(m, n)).toarray()
+    I = np.flatnonzero(np.isfinite(Ss))
+    JI = J[I]
+    Kt = Hd + rho * J.T @ J                          # W_t + Sigma_t + delta I + rho (J_E^T J_E + J_I^T J_I)
+    big = np.block([[Kt, -rho * JI.T], [-rho * JI, np.diag(Ss[I] + rho)]])
+    rng = np.random.default_rng(4)
+    rt, rsI = rng.standard_normal(n), rng.standard_normal(len(I))
+    sol = np.linalg.solve(big, np.concatenate([rt, rsI]))
+    A = _k1s_matrix(inst, Ss)
+    fac = O.LDLT(A)
+    rs = np.zeros(m)
+    rs[I] = rsI
+    rhs = O.k1s_rhs(m, p.J_rowptr, p.J_colind, inst.J_val, n, Ss, rho, rt, rs)[:, 0]
+    assert not np.allclose(rhs, rt + rho * JI.T @ rsI)   # the printed form differs
+    dt, _, eta = O.solve_ir(A, fac, rhs)
+    assert eta <= 1e-12
+    assert np.allclose(dt, sol[:n], rtol=1e-9, atol=1e-12)
+    ds = O.k1s_slack_step(m, p.J_rowptr, p.J_colind, inst.J_val, n, Ss, rho, dt, rs)[:, 0]
+    assert np.allclose(ds[I], sol[n:], rtol=1e-9, atol=1e-12)
+    assert np.all(ds[np.isinf(Ss)] == 0.0)
+
+
+def test_k1s_limits():
+    """Sigma_s -> inf on every row gives Eq. K1 exactly (Omega = 1); Sigma_s = 0
+    removes the inequality rows (Omega = 0)."""
+    inst, _ = _k1s_case(seed=32)
+    p = inst.pat
+    K1 = O.kkt_condensed(p.n, p.m, p.H_rowptr, p.H_colind, inst.H_val, p.J_rowptr, p.J_colind, inst.J_val,
+                         inst.Sigma, inst.delta, inst.rho)
+    assert abs(_k1s_matrix(inst, np.full(p.m, np.inf)) - K1).max() == 0.0
+    mask = np.arange(p.m) % 2 == 0
+    Ss = np.where(mask, np.inf, 0.0)
+    J = sp.csr_matrix((inst.J_val, p.J_colind, p.J_rowptr), shape=(p.m, p.n))
+    JE = J[np.flatnonzero(mask)]
+    want = O.kkt_condensed(p.n, 0, p.H_rowptr, p.H_colind, inst.H_val, np.zeros(1, np.int32),
+                           np.zeros(0, np.int32), np.zeros(0), inst.Sigma, inst.delta, 1.0) + inst.rho * (JE.T @ JE)
+    assert abs(_k1s_matrix(inst, Ss) - want).max() <= 1e-12 * abs(want).max()
+
+
+def test_planted_mistake_inverted_omega(monkeypatch):
+    """Omega = rho / (rho + Sigma_s) instead of Sigma_s / (rho + Sigma_s)
+    breaks the unreduced-system pin."""
+    orig = O.kkt_condensed_slack
+
+    def bad(n, m, Hp, Hi, Hv, Jp, Ji, Jv, St, Ss, delta, rho):
+        Ss = np.asarray(Ss, float)
+        fin = np.isfinite(Ss)
+        alt = Ss.copy()
+        alt[fin] = rho * rho / np.maximum(Ss[fin], 1e-300)   # Omega' = rho / (rho + Sigma_s)
+        return orig(n, m, Hp, Hi, Hv, Jp, Ji, Jv, St, alt, delta, rho)
+    monkeypatch.setattr(O.oracle, "kkt_condensed_slack", bad)
+    monkeypatch.setattr(O, "kkt_condensed_slack", bad)
+    with pytest.raises(AssertionError):
+        test_k1s_matches_the_unreduced_slack_system()
