@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--draws", type=int, default=4)
     ap.add_argument("--regularize", action="store_true",
                     help="also time the inertia correction (Section 3.1) from delta = 0 on the first draw")
+    ap.add_argument("--k1s", action="store_true",
+                    help="condensed workloads: also time the step with slacks (Eq. K1s) on the first draw")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -574,6 +576,37 @@ def run_ours(args):
             if Kr is not K:
                 Kr.close()
         out["regularize"] = reg
+
+    # condensed system with slacks (Eq. K1s) on the first draw: 40% of the
+    # constraint rows without slack (Sigma_s = +inf), the others with
+    # Sigma_s = 10^U[-2,2]; one step = weighted factorisation + right-hand
+    # side + refined solve + slack step
+    if args.k1s and R.spec["form"] == 1:
+        d = R.dev_draws[0]
+        ncon = sum(i.m for i in R.draws[0])
+        rng = np.random.default_rng(7)
+        Ss = 10.0 ** rng.uniform(-2, 2, ncon)
+        Ss[rng.random(ncon) < 0.4] = np.inf
+        Ss_d = torch.as_tensor(Ss, device=dev)
+        RS = torch.as_tensor(rng.standard_normal((ncon, spec["nrhs"])), device=dev)
+        RT = d["Bc"].t()
+        times, etas = [], []
+        for rep in range(4):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            K.factor_k1s(d["H"], d["J"], d["S"], Ss_d, d["delta"], d["rho"])
+            rhs = K.k1s_rhs(RT, RS)
+            X, si = K.solve(rhs)
+            DS = K.slack_step(X, RS)
+            e1.record()
+            e1.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+                etas.append(si.backward_err)
+        out["k1s"] = {"ms": statistics.median(times), "backward_err_max": max(etas), "rows": ncon,
+                      "rows_without_slack": int(np.isinf(Ss).sum()),
+                      "steps": "factor_k1s + k1s_rhs + solve + slack_step, 3 timed after 1 warm-up"}
 
     # end to end through the C ABI with host buffers
     if not args.skip_e2e:
