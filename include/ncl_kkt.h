@@ -305,6 +305,56 @@ ncl_status ncl_kkt_factor_k1s(ncl_kkt_t h, const double* H_val, const double* J_
                               const double* rho, ncl_stream_t stream, ncl_kkt_factor_info* infos);
 
 /*
+ * Newton step of Algorithm NCL around the factorisation (Section 3.1-3.3).
+ * A Newton point holds device arrays over the concatenated primal variables
+ * (n-vectors) and constraints (m-vectors) of the handle's instances:
+ */
+typedef struct {
+    const double* grad_phi;   /* n: gradient of the objective at x */
+    const double* x;          /* n: current point, strictly inside its bounds */
+    const double* lower;      /* n: lower bounds l (-inf: none) */
+    const double* upper;      /* n: upper bounds u (+inf: none) */
+    const double* z_lower;    /* n: bound multipliers z_l (0 where l = -inf) */
+    const double* z_upper;    /* n: bound multipliers z_u (0 where u = +inf) */
+    const double* c;          /* m: constraint values c(x) */
+    const double* y;          /* m: current multipliers y */
+    const double* y_k;        /* m: multiplier estimate y_k of the outer iteration */
+    const double* r;          /* m: current residual variables r */
+} ncl_kkt_newton_point;
+
+/*
+ * ncl_kkt_newton_rhs -- the right-hand side of the factored system:
+ *   K2r (Eq. K2r, unknown [Delta x; -Delta y]):
+ *     -[grad_phi - J^T y - (X-L)^{-1} mu e + (U-X)^{-1} mu e ; c - (y_k - y)/rho]
+ *   K   (Eq. K1, unknown Delta x):
+ *     J^T (y_k - rho c) - (grad_phi - (X-L)^{-1} mu e + (U-X)^{-1} mu e)
+ * with the J values and rho (= rho-hat) of the current factorisation; an
+ * infinite bound contributes no barrier term.  Sigma passed to the factor is
+ * the caller's (X-L)^{-1} Z_l + (U-X)^{-1} Z_u (Section 3.1).
+ *   mu  host double[count]: barrier parameter per instance (>= 0)
+ *   B   device double[dim] (KKT row order of ncl_kkt_solve)
+ * Errors: INVALID_ARG, STATE (no factor).
+ */
+ncl_status ncl_kkt_newton_rhs(ncl_kkt_t h, const ncl_kkt_newton_point* pt, const double* mu,
+                              double* B, ncl_stream_t stream);
+
+/*
+ * ncl_kkt_newton_recover -- the full Newton direction from the solution X
+ * (device double[dim]) of the system ncl_kkt_newton_rhs set up:
+ *   dx  = Delta x
+ *   dy  = Delta y: minus the dual block of X (K2r), or
+ *         -rho (J Delta x + c) + y_k - y (K, Eq. K1 elimination)
+ *   dr  = (Delta y - y_k + y)/rho - r                (Eq. K2 elimination)
+ *   dz_lower = -(X-L)^{-1} (Z_l Delta x - mu e) - z_l
+ *   dz_upper =  (U-X)^{-1} (Z_u Delta x + mu e) - z_u  (eliminated from Eq. K3)
+ * dx, dz_lower, dz_upper: device double[n]; dy, dr: device double[m]; any
+ * of them may be NULL.  Errors: INVALID_ARG, STATE (no factor).
+ */
+ncl_status ncl_kkt_newton_recover(ncl_kkt_t h, const ncl_kkt_newton_point* pt, const double* mu,
+                                  const double* X, double* dx, double* dy, double* dr,
+                                  double* dz_lower, double* dz_upper, ncl_stream_t stream);
+
+/*
  * ncl_kkt_k1s_rhs -- the right-hand side of Eq. K1s for the current
  * condensed factorisation, as the elimination of Delta s in the proof of the
  * proposition (Section 3.3) produces it:

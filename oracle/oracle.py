@@ -25,6 +25,11 @@ What it computes, and where the paper defines it:
   ``k1s_rhs``: the right-hand side that elimination produces,
   ``r_t + rho J_I^T (Sigma_s + rho I)^{-1} r_s`` (the statement of Eq. K1s
   prints it without the inverse; the proof's own steps give it with).
+* ``newton_rhs`` / ``newton_recover``: the Newton step of Algorithm NCL
+  around the factored system: the right-hand side of Eq. K2r (unknown
+  ``[Delta x; -Delta y]``) or Eq. K1 (unknown ``Delta x``), and Delta y,
+  Delta r (Eq. K2 elimination), Delta z_l, Delta z_u (eliminated from
+  Eq. K3), Section 3.1-3.3.
 * ``regularize``: the inertia correction of Section 3.1 (regularised matrix
   Eq. K2): raise the primal regularisation delta until the inertia is the
   regular one, with rho-hat = rho + delta in the matrix as the same section
@@ -51,7 +56,7 @@ from scipy.sparse.csgraph import reverse_cuthill_mckee
 __all__ = [
     "build_oracle", "kkt_stabilized", "kkt_condensed", "instance_matrix", "block_signs",
     "LDLT", "solve_ir", "backward_error", "solve_instance", "adjoint", "cond1_estimate", "regularize",
-    "kkt_condensed_slack", "k1s_slack_step", "k1s_rhs",
+    "kkt_condensed_slack", "k1s_slack_step", "k1s_rhs", "newton_rhs", "newton_recover",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -166,6 +171,43 @@ def k1s_rhs(m, J_rowptr, J_colind, J_val, n, Sigma_s, rho, rt, rs) -> np.ndarray
     rs = np.asarray(rs, float).reshape(m, -1)
     I = np.flatnonzero(~np.isposinf(Ss))
     return rt + rho * (J[I].T @ (rs[I] / (Ss[I] + rho)[:, None]))
+
+
+def _J(m, n, J_rowptr, J_colind, J_val):
+    return sp.csr_matrix((np.asarray(J_val, float), np.asarray(J_colind), np.asarray(J_rowptr)), shape=(m, n))
+
+
+def newton_rhs(form, n, m, J_rowptr, J_colind, J_val, pt, mu, rho) -> np.ndarray:
+    """Right-hand side of the factored Newton system (Section 3.2, Eq. K2r;
+    Section 3.3, Eq. K1).  ``pt``: dict of numpy arrays grad_phi, x, lower,
+    upper (+-inf allowed), c, y, y_k; ``rho`` is the matrix's rho-hat."""
+    J = _J(m, n, J_rowptr, J_colind, J_val)
+    x, lo, up = pt["x"], pt["lower"], pt["upper"]
+    barrier = -mu / (x - lo) + mu / (up - x)          # -(X-L)^{-1} mu e + (U-X)^{-1} mu e
+    if form == "stabilized":
+        top = -(pt["grad_phi"] - J.T @ pt["y"] + barrier)
+        bot = -(pt["c"] - (pt["y_k"] - pt["y"]) / rho)
+        return np.concatenate([top, bot])
+    return J.T @ (pt["y_k"] - rho * pt["c"]) - (pt["grad_phi"] + barrier)
+
+
+def newton_recover(form, n, m, J_rowptr, J_colind, J_val, pt, mu, rho, X) -> dict:
+    """The Newton direction from the solution X of the factored system:
+    Delta y (dual block of Eq. K2r with its sign, or Eq. K1's elimination
+    -rho (J Delta x + c) + y_k - y), Delta r = (Delta y - y_k + y)/rho - r
+    (Eq. K2 elimination), and the bound multipliers eliminated from Eq. K3."""
+    J = _J(m, n, J_rowptr, J_colind, J_val)
+    X = np.asarray(X, float)
+    dx = X[:n].copy()
+    if form == "stabilized":
+        dy = -X[n:n + m]
+    else:
+        dy = -rho * (J @ dx + pt["c"]) + pt["y_k"] - pt["y"]
+    dr = (dy - pt["y_k"] + pt["y"]) / rho - pt["r"]
+    x, lo, up, zl, zu = pt["x"], pt["lower"], pt["upper"], pt["z_lower"], pt["z_upper"]
+    dzl = -(zl * dx - mu) / (x - lo) - zl
+    dzu = (zu * dx + mu) / (up - x) - zu
+    return {"dx": dx, "dy": dy, "dr": dr, "dz_lower": dzl, "dz_upper": dzu}
 
 
 def instance_matrix(inst) -> sp.csc_matrix:

@@ -190,7 +190,8 @@ struct ncl_kkt_s {
   double* jx = nullptr;
   double* jg = nullptr;
   double* GBtmp = nullptr;
-  double* Jcopy = nullptr;                 // condensed form: J values of the last factor (adjoint)
+  double* Jcopy = nullptr;                 // J values of the last factor (adjoint, K1s, Newton step)
+  double* d_mu = nullptr;                  // barrier parameter per instance (Newton step)
   double* d_w = nullptr;                   // condensed form: row weights of J^T W J (Eq. K1 / K1s)
   double* d_dw = nullptr;                  //   their derivative in rho (adjoint)
   double* d_ss = nullptr;                  //   the slack terms Sigma_s (+inf: no slack)
@@ -766,7 +767,7 @@ void build_device(ncl_kkt_s* h) {
       for (int64_t c = co[i]; c < co[i + 1]; c++) ci[c] = (int32_t)i;
     d.con_inst = h->upload(ci);
   }
-  if (P.form == 1) {
+  {
     // J values by variable (KKT row), in constraint order: counting sort
     std::vector<int64_t> tp((size_t)P.dim + 1, 0);
     for (int32_t c : P.J_col) tp[(size_t)c + 1]++;
@@ -776,6 +777,13 @@ void build_device(ncl_kkt_s* h) {
     for (size_t e = 0; e < P.J_col.size(); e++) ti[fill[P.J_col[e]]++] = (int32_t)e;
     d.JT_ptr = h->upload(tp);
     d.JT_idx = h->upload(ti);
+    // KKT row -> primal variable / constraint
+    std::vector<int32_t> rv((size_t)std::max<int64_t>(P.dim, 1), -1), rc((size_t)std::max<int64_t>(P.dim, 1), -1);
+    for (size_t v = 0; v < P.var_row.size(); v++) rv[P.var_row[v]] = (int32_t)v;
+    for (size_t c = 0; c < P.con_row.size(); c++)
+      if (P.con_row[c] >= 0) rc[P.con_row[c]] = (int32_t)c;
+    d.row_var = h->upload(rv);
+    d.row_con = h->upload(rc);
   }
   h->d_inst_n = h->upload(in);
   h->d_inst_con_off = h->upload(co);
@@ -808,8 +816,9 @@ void build_device(ncl_kkt_s* h) {
   h->GBtmp = h->alloc<double>((int64_t)P.dim * MAX_RHS_SWEEP);
   h->jx = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
   h->jg = h->alloc<double>(std::max<int64_t>(d.ncon, 1) * MAX_RHS_SWEEP);
+  h->Jcopy = h->alloc<double>(std::max<int64_t>(d.nnzJ, 1));
+  h->d_mu = h->alloc<double>(std::max<int64_t>(d.ninst, 1));
   if (P.form == 1) {
-    h->Jcopy = h->alloc<double>(std::max<int64_t>(d.nnzJ, 1));
     h->d_w = h->alloc<double>(std::max<int64_t>(d.ncon, 1));
     h->d_dw = h->alloc<double>(std::max<int64_t>(d.ncon, 1));
     h->d_ss = h->alloc<double>(std::max<int64_t>(d.ncon, 1));
@@ -1695,6 +1704,65 @@ ncl_status ncl_kkt_factor_k1s(ncl_kkt_t h, const double* H_val, const double* J_
   if (h->dp.ncon > 0 && !Sigma_s) return fail(NCL_ERR_INVALID_ARG, "NULL Sigma_s");
   return guarded(h, [&] {
     return do_factor(h, H_val, J_val, Sigma, delta, rho, (cudaStream_t)stream, infos, Sigma_s);
+  });
+}
+
+// Newton step around the factorisation: right-hand side of Eq. K2r / K1 and
+// the recovery of Delta y, Delta r, Delta z_l, Delta z_u (Section 3.1-3.3).
+static ncl_status newton_args(ncl_kkt_s* h, const ncl_kkt_newton_point* pt, const double* mu, NewtonDev* nd,
+                              cudaStream_t st) {
+  if (!h || !pt || !mu) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (!h->factored && !h->use_twin) return fail(NCL_ERR_STATE, "Newton step before a successful factor");
+  const bool nv = h->dp.nvar > 0, nc = h->dp.ncon > 0;
+  if (nv && (!pt->grad_phi || !pt->x || !pt->lower || !pt->upper || !pt->z_lower || !pt->z_upper))
+    return fail(NCL_ERR_INVALID_ARG, "NULL n-vector of the Newton point");
+  if (nc && (!pt->c || !pt->y || !pt->y_k || !pt->r)) return fail(NCL_ERR_INVALID_ARG, "NULL m-vector of the Newton point");
+  const int ni = h->dp.ninst;
+  for (int i = 0; i < ni; i++)
+    if (!(mu[i] >= 0.0) || !std::isfinite(mu[i])) return fail(NCL_ERR_INVALID_ARG, "mu must be >= 0");
+  double* hm = h->h_pinned + 7 * ni + 32;   // free slots of the pinned block (below the norms at 7 ni + 64)
+  if (ni > 32) {
+    std::vector<double> tmp(mu, mu + ni);
+    CK(cudaMemcpy(h->d_mu, tmp.data(), ni * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    for (int i = 0; i < ni; i++) hm[i] = mu[i];
+    CK(cudaMemcpyAsync(h->d_mu, hm, ni * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  *nd = NewtonDev{pt->grad_phi, pt->x, pt->lower, pt->upper, pt->z_lower, pt->z_upper, pt->c, pt->y, pt->y_k, pt->r};
+  return NCL_OK;
+}
+
+ncl_status ncl_kkt_newton_rhs(ncl_kkt_t h, const ncl_kkt_newton_point* pt, const double* mu, double* B,
+                              ncl_stream_t stream) {
+  if (!B) return fail(NCL_ERR_INVALID_ARG, "NULL B");
+  return guarded(h, [&]() -> ncl_status {
+    NewtonDev nd;
+    const cudaStream_t st = (cudaStream_t)stream;
+    ncl_status s = newton_args(h, pt, mu, &nd, st);
+    if (s != NCL_OK) return s;
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    launch_newton_rhs(h->dp, h->Jcopy, h->d_rho, h->d_mu, nd, B, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));   // the pinned mu slots are reused by the next call
+    return NCL_OK;
+  });
+}
+
+ncl_status ncl_kkt_newton_recover(ncl_kkt_t h, const ncl_kkt_newton_point* pt, const double* mu, const double* X,
+                                  double* dx, double* dy, double* dr, double* dz_lower, double* dz_upper,
+                                  ncl_stream_t stream) {
+  if (!X) return fail(NCL_ERR_INVALID_ARG, "NULL X");
+  return guarded(h, [&]() -> ncl_status {
+    NewtonDev nd;
+    const cudaStream_t st = (cudaStream_t)stream;
+    ncl_status s = newton_args(h, pt, mu, &nd, st);
+    if (s != NCL_OK) return s;
+    g_kernel_launches.fetch_add(2, std::memory_order_relaxed);
+    launch_newton_recover(h->dp, h->Jcopy, h->d_rho, h->d_mu, nd, X, dx, dy, dr, dz_lower, dz_upper, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return NCL_OK;
   });
 }
 

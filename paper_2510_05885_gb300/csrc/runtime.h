@@ -75,9 +75,18 @@ struct DevPlan {
   const int64_t* sn_Soff;       // split-operand offset of a tensor-core front, -1 otherwise
   const int8_t* sn_flags;       // bit 0: front factored by panels (large front)
   const int64_t* sn_Ioff;       // offset of the inverted 32 x 32 diagonal blocks of L11
-  // condensed form: the J values of each variable (KKT row), in constraint order
+  // the J values of each variable (by its KKT row), in constraint order
   const int64_t* JT_ptr;        // dim+1
   const int32_t* JT_idx;        // J value indices
+  const int32_t* row_var;       // primal variable of each KKT row, -1 for a dual row
+  const int32_t* row_con;       // constraint of each KKT row (K2r dual rows), -1 otherwise
+};
+
+// Device pointers of a Newton point (Section 3.1, Eq. K3): n-vectors over the
+// concatenated primal variables, m-vectors over the concatenated constraints.
+struct NewtonDev {
+  const double *g, *x, *lo, *up, *zl, *zu;   // n
+  const double *c, *y, *yk, *r;              // m
 };
 
 // Numeric state for one precision T (float or double).
@@ -131,6 +140,11 @@ void launch_row_weights(const DevPlan& P, const double* const* vals, const doubl
 void launch_k1s_rhs(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
                     const double* RT, int64_t ldt, const double* RS, int64_t ldr, double* OUT, int64_t ldo,
                     cudaStream_t st);
+void launch_newton_rhs(const DevPlan& P, const double* Jv, const double* rho, const double* mu, NewtonDev pt,
+                       double* B, cudaStream_t st);
+void launch_newton_recover(const DevPlan& P, const double* Jv, const double* rho, const double* mu, NewtonDev pt,
+                           const double* X, double* dx, double* dy, double* dr, double* dzl, double* dzu,
+                           cudaStream_t st);
 void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
                        const double* DT, int64_t ldt, const double* RS, int64_t ldr, double* DS, int64_t lds,
                        cudaStream_t st);

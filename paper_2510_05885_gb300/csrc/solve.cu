@@ -957,6 +957,92 @@ void launch_k1s_rhs(const DevPlan& P, const double* Jv, const double* rho, const
   k_k1s_rhs<<<grid_for(total), 256, 0, st>>>(P, Jv, rho, ss, nrhs, RT, ldt, RS, ldr, OUT, ldo);
 }
 
+// ---------------------------------------------------------------------------
+// Newton step of Algorithm NCL around the factorisation (Section 3.1-3.3):
+// the right-hand side of Eq. K2r (unknown [Delta x; -Delta y]) or Eq. K1
+// (unknown Delta x), and the recovery of the other components from Eq. K3:
+//   Delta y   = -(second block of the K2r solution), or
+//             = -rho (J Delta x + c) + y_k - y          (Eq. K1, elimination)
+//   Delta r   = (Delta y - y_k + y) / rho - r            (Eq. K2, elimination)
+//   Delta z_l = -(X - L)^{-1} (Z_l Delta x - mu e) - z_l (eliminated from Eq. K3)
+//   Delta z_u =  (U - X)^{-1} (Z_u Delta x + mu e) - z_u
+// rho is the penalty of the factored matrix (rho-hat).  An infinite bound
+// gives (x - l)^{-1} = 0 (IEEE), so its barrier terms vanish.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double barrier_grad(const NewtonDev& pt, int64_t v, double mu) {
+  // -(X - L)^{-1} mu e + (U - X)^{-1} mu e, component v
+  return -mu / (pt.x[v] - pt.lo[v]) + mu / (pt.up[v] - pt.x[v]);
+}
+
+__global__ void k_newton_rhs(DevPlan P, const double* __restrict__ Jv, const double* __restrict__ rho,
+                             const double* __restrict__ mu, NewtonDev pt, double* __restrict__ B) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P.dim;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t inst = P.row_inst[k];
+    const double rh = rho[inst], m = mu[inst];
+    const int32_t v = P.row_var[k];
+    if (v >= 0) {
+      // J^T y (K2r) or J^T (y_k - rho c) (K), the variable's J values in constraint order
+      double jt = 0.0;
+      for (int64_t q = P.JT_ptr[k]; q < P.JT_ptr[k + 1]; q++) {
+        const int32_t e = P.JT_idx[q], c = P.J_con[e];
+        const double wv = P.form == 0 ? pt.y[c] : pt.yk[c] - rh * pt.c[c];
+        jt = fma(Jv[e], wv, jt);
+      }
+      const double gb = pt.g[v] + barrier_grad(pt, v, m);
+      B[k] = P.form == 0 ? -(gb - jt) : jt - gb;
+    } else {
+      const int32_t c = P.row_con[k];
+      B[k] = -(pt.c[c] - (pt.yk[c] - pt.y[c]) / rh);
+    }
+  }
+}
+
+__global__ void k_newton_recover_var(DevPlan P, const double* __restrict__ mu, NewtonDev pt,
+                                     const double* __restrict__ X, double* __restrict__ dx,
+                                     double* __restrict__ dzl, double* __restrict__ dzu) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.nvar;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = P.var_row[v];
+    const double m = mu[P.row_inst[k]];
+    const double d = X[k];
+    if (dx) dx[v] = d;
+    if (dzl) dzl[v] = -(pt.zl[v] * d - m) / (pt.x[v] - pt.lo[v]) - pt.zl[v];
+    if (dzu) dzu[v] = (pt.zu[v] * d + m) / (pt.up[v] - pt.x[v]) - pt.zu[v];
+  }
+}
+
+__global__ void k_newton_recover_con(DevPlan P, const double* __restrict__ Jv, const double* __restrict__ rho,
+                                     NewtonDev pt, const double* __restrict__ X, double* __restrict__ dy,
+                                     double* __restrict__ dr) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < P.ncon;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const double rh = rho[P.con_inst[c]];
+    double d;
+    if (P.form == 0) {
+      d = -X[P.con_row[c]];
+    } else {
+      double jx = 0.0;
+      for (int64_t q = P.J_rowptr[c]; q < P.J_rowptr[c + 1]; q++) jx = fma(Jv[q], X[P.J_col[q]], jx);
+      d = -rh * (jx + pt.c[c]) + pt.yk[c] - pt.y[c];
+    }
+    if (dy) dy[c] = d;
+    if (dr) dr[c] = (d - pt.yk[c] + pt.y[c]) / rh - pt.r[c];
+  }
+}
+
+void launch_newton_rhs(const DevPlan& P, const double* Jv, const double* rho, const double* mu, NewtonDev pt,
+                       double* B, cudaStream_t st) {
+  if (P.dim) k_newton_rhs<<<grid_for(P.dim), 256, 0, st>>>(P, Jv, rho, mu, pt, B);
+}
+
+void launch_newton_recover(const DevPlan& P, const double* Jv, const double* rho, const double* mu, NewtonDev pt,
+                           const double* X, double* dx, double* dy, double* dr, double* dzl, double* dzu,
+                           cudaStream_t st) {
+  if (P.nvar) k_newton_recover_var<<<grid_for(P.nvar), 256, 0, st>>>(P, mu, pt, X, dx, dzl, dzu);
+  if (P.ncon && (dy || dr)) k_newton_recover_con<<<grid_for(P.ncon), 256, 0, st>>>(P, Jv, rho, pt, X, dy, dr);
+}
+
 void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
                        const double* DT, int64_t ldt, const double* RS, int64_t ldr, double* DS, int64_t lds,
                        cudaStream_t st) {

@@ -66,6 +66,12 @@ class AnalysisInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class NewtonPoint(ctypes.Structure):
+    """Device pointers of a Newton point (ncl_kkt_newton_point)."""
+    _fields_ = [(k, ctypes.c_void_p) for k in ("grad_phi", "x", "lower", "upper", "z_lower", "z_upper",
+                                               "c", "y", "y_k", "r")]
+
+
 class NclError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS[status] if 0 <= status < len(STATUS) else status}: {msg}")
@@ -88,6 +94,8 @@ _SIGS = {
     "ncl_kkt_factor_k1s": (I32, [P, P, P, P, P, P, P, P, P]),
     "ncl_kkt_k1s_slack_step": (I32, [P, I32, P, I64, P, I64, P, I64, P]),
     "ncl_kkt_k1s_rhs": (I32, [P, I32, P, I64, P, I64, P, I64, P]),
+    "ncl_kkt_newton_rhs": (I32, [P, ctypes.POINTER(NewtonPoint), P, P, P]),
+    "ncl_kkt_newton_recover": (I32, [P, ctypes.POINTER(NewtonPoint), P, P, P, P, P, P, P, P]),
     "ncl_kkt_solve": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_solve_noalloc": (I32, [P, I32, P, I64, P, I64, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_batch_factor_solve": (I32, [P, P, P, P, P, P, I32, P, I64, P, I64, P, P,
@@ -253,6 +261,25 @@ def ncl_kkt_factor_k1s(h, H_val, J_val, Sigma, Sigma_s, delta, rho, stream=None)
     if st not in (OK, ERR_ZERO_PIVOT):
         _check(st)
     return list(infos), st
+
+
+def _newton_point(pt: dict) -> NewtonPoint:
+    return NewtonPoint(*[_ptr(pt[k]) if pt.get(k) is not None else None for k, _ in NewtonPoint._fields_])
+
+
+def ncl_kkt_newton_rhs(h, pt: dict, mu, B, stream=None):
+    count = load().ncl_kkt_instance_count(h)
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(mu, dtype=np.float64), (count,)))
+    np_ = _newton_point(pt)
+    _check(load().ncl_kkt_newton_rhs(h, ctypes.byref(np_), m.ctypes.data, _ptr(B), _stream_ptr(stream)))
+
+
+def ncl_kkt_newton_recover(h, pt: dict, mu, X, dx=None, dy=None, dr=None, dzl=None, dzu=None, stream=None):
+    count = load().ncl_kkt_instance_count(h)
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(mu, dtype=np.float64), (count,)))
+    np_ = _newton_point(pt)
+    _check(load().ncl_kkt_newton_recover(h, ctypes.byref(np_), m.ctypes.data, _ptr(X), _ptr(dx), _ptr(dy),
+                                         _ptr(dr), _ptr(dzl), _ptr(dzu), _stream_ptr(stream)))
 
 
 def ncl_kkt_k1s_rhs(h, nrhs, RT, ldt, RS, ldr, OUT, ldo, stream=None):
@@ -426,6 +453,27 @@ class KKT:
         self.generation += 1
         infos, _ = ncl_kkt_factor_k1s(self._h, H_val, J_val, Sigma, Sigma_s, delta, rho, stream)
         return infos[0] if self.count == 1 else infos
+
+    def newton_rhs(self, pt: dict, mu, stream=None):
+        """Right-hand side of Eq. K2r / K1 at the Newton point ``pt`` (dict of
+        float64 CUDA tensors: grad_phi, x, lower, upper, z_lower, z_upper, c,
+        y, y_k, r)."""
+        import torch
+        B = torch.empty(self.dim, dtype=torch.float64, device=pt["x"].device)
+        ncl_kkt_newton_rhs(self._h, pt, mu, B, stream)
+        return B
+
+    def newton_recover(self, pt: dict, mu, X, stream=None):
+        """The Newton direction (dx, dy, dr, dz_lower, dz_upper) from the
+        solution X of the system newton_rhs set up."""
+        import torch
+        dev = pt["x"].device
+        n, m = int(pt["x"].numel()), int(pt["c"].numel()) if pt.get("c") is not None else 0
+        out = {k: torch.empty(sz, dtype=torch.float64, device=dev)
+               for k, sz in (("dx", n), ("dy", m), ("dr", m), ("dz_lower", n), ("dz_upper", n))}
+        ncl_kkt_newton_recover(self._h, pt, mu, X.contiguous(), out["dx"], out["dy"], out["dr"], out["dz_lower"],
+                               out["dz_upper"], stream)
+        return out
 
     def k1s_rhs(self, RT, RS, stream=None):
         """r_t + rho J_I^T (Sigma_s + rho I)^{-1} r_s for the current K1s

@@ -50,3 +50,24 @@ def read_golden(path):
             k, *v = line.split()
             out[k] = [float(t) for t in v]
     return out
+
+
+def newton_point(inst, seed, frac_unbounded=0.3):
+    """A seeded interior point of the instance's NCL subproblem (Section 3.1):
+    bounds around x (some infinite, with zero multipliers there), positive
+    multipliers, and the Sigma = (X-L)^{-1} Z_l + (U-X)^{-1} Z_u they imply.
+    Returns (point dict of numpy arrays, Sigma)."""
+    rng = np.random.default_rng(seed)
+    n, m = inst.n, inst.m
+    x = rng.standard_normal(n)
+    lo = x - rng.uniform(0.1, 2.0, n)
+    up = x + rng.uniform(0.1, 2.0, n)
+    lo[rng.random(n) < frac_unbounded] = -np.inf
+    up[rng.random(n) < frac_unbounded] = np.inf
+    zl = np.where(np.isinf(lo), 0.0, rng.uniform(0.01, 1.0, n))
+    zu = np.where(np.isinf(up), 0.0, rng.uniform(0.01, 1.0, n))
+    pt = {"grad_phi": rng.standard_normal(n), "x": x, "lower": lo, "upper": up, "z_lower": zl, "z_upper": zu,
+          "c": rng.standard_normal(m), "y": rng.standard_normal(m), "y_k": rng.standard_normal(m),
+          "r": rng.standard_normal(m)}
+    sigma = zl / (x - lo) + zu / (up - x)
+    return pt, sigma

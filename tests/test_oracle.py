@@ -523,3 +523,81 @@ def test_planted_mistake_inverted_omega(monkeypatch):
     monkeypatch.setattr(O, "kkt_condensed_slack", bad)
     with pytest.raises(AssertionError):
         test_k1s_matches_the_unreduced_slack_system()
+
+
+# ------------------------------------------------ Newton step (Section 3.1-3.3)
+
+def _k3_dense(inst, pt, mu):
+    """Eq. K3 assembled from its blocks (finite bounds only carry a z row and
+    column; an infinite bound has no multiplier) and solved densely.
+    Returns dx, dr, dy, dz_lower, dz_upper (zeros where the bound is infinite)."""
+    p = inst.pat
+    n, m, rho = p.n, p.m, inst.rho
+    H = O.kkt_condensed(n, 0, p.H_rowptr, p.H_colind, inst.H_val, np.zeros(1, np.int32), np.zeros(0, np.int32),
+                        np.zeros(0), np.zeros(n), 0.0, 1.0).toarray()
+    J = sp.csr_matrix((inst.J_val, p.J_colind, p.J_rowptr), shape=(m, n)).toarray()
+    x, lo, up, zl, zu = pt["x"], pt["lower"], pt["upper"], pt["z_lower"], pt["z_upper"]
+    BL, BU = np.flatnonzero(np.isfinite(lo)), np.flatnonzero(np.isfinite(up))
+    nl, nu = len(BL), len(BU)
+    N = n + 2 * m + nl + nu
+    K = np.zeros((N, N))
+    ix, ir, iy = slice(0, n), slice(n, n + m), slice(n + m, n + 2 * m)
+    il, iu = n + 2 * m + np.arange(nl), n + 2 * m + nl + np.arange(nu)
+    K[ix, ix] = H
+    K[ix, iy] = -J.T
+    K[BL, il] = -1.0
+    K[BU, iu] = 1.0
+    K[ir, ir] = rho * np.eye(m)
+    K[ir, iy] = -np.eye(m)
+    K[iy, ix] = J
+    K[iy, ir] = np.eye(m)
+    K[il, BL] = zl[BL]
+    K[il, il] = (x - lo)[BL]
+    K[iu, BU] = -zu[BU]
+    K[iu, iu] = (up - x)[BU]
+    rhs = -np.concatenate([pt["grad_phi"] - J.T @ pt["y"] - zl + zu, pt["y_k"] + rho * pt["r"] - pt["y"],
+                           pt["c"] + pt["r"], zl[BL] * (x - lo)[BL] - mu, zu[BU] * (up - x)[BU] - mu])
+    sol = np.linalg.solve(K, rhs)
+    dzl, dzu = np.zeros(n), np.zeros(n)
+    dzl[BL], dzu[BU] = sol[il], sol[iu]
+    return sol[ix], sol[ir], sol[iy], dzl, dzu
+
+
+def _newton_case(form, seed=41):
+    from tests.helpers import newton_point
+    inst = _tiny(2, 3, seed, form, rho=20.0)
+    pt, sigma = newton_point(inst, seed)
+    return inst, pt, sigma
+
+
+@pytest.mark.parametrize("form", ["stabilized", "condensed"])
+def test_newton_step_matches_the_full_newton_system(form):
+    """Solving the factored system (Eq. K2r or K1, with Sigma from the point,
+    delta = 0) with the oracle's right-hand side and recovering the other
+    components reproduces the dense solution of Eq. K3."""
+    inst, pt, sigma = _newton_case(form)
+    p, mu = inst.pat, 0.05
+    build = O.kkt_stabilized if form == "stabilized" else O.kkt_condensed
+    A = build(p.n, p.m, p.H_rowptr, p.H_colind, inst.H_val, p.J_rowptr, p.J_colind, inst.J_val, sigma, 0.0,
+              inst.rho)
+    b = O.newton_rhs(form, p.n, p.m, p.J_rowptr, p.J_colind, inst.J_val, pt, mu, inst.rho)
+    X, _, eta = O.solve_ir(A, O.LDLT(A, O.block_signs(form, p.n, p.m)), b)
+    assert eta <= 1e-12
+    rec = O.newton_recover(form, p.n, p.m, p.J_rowptr, p.J_colind, inst.J_val, pt, mu, inst.rho, X)
+    dx, dr, dy, dzl, dzu = _k3_dense(inst, pt, mu)
+    scale = max(1.0, np.max(np.abs(np.concatenate([dx, dr, dy, dzl, dzu]))))
+    for got, want in ((rec["dx"], dx), (rec["dr"], dr), (rec["dy"], dy), (rec["dz_lower"], dzl),
+                      (rec["dz_upper"], dzu)):
+        assert np.max(np.abs(got - want)) <= 1e-9 * scale
+
+
+def test_planted_mistake_dropped_barrier_term(monkeypatch):
+    """Dropping the barrier gradient from the right-hand side breaks the
+    full-Newton-system pin."""
+    orig = O.newton_rhs
+
+    def bad(form, n, m, Jp, Ji, Jv, pt, mu, rho):
+        return orig(form, n, m, Jp, Ji, Jv, pt, 0.0, rho)
+    monkeypatch.setattr(O, "newton_rhs", bad)
+    with pytest.raises(AssertionError):
+        test_newton_step_matches_the_full_newton_system("stabilized")
