@@ -10,13 +10,34 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <exception>
+#include <mutex>
 #include <cstring>
 #include <numeric>
 #include <stdexcept>
+#include <thread>
 
 namespace ncl {
 namespace {
+
+// Run f(lo, hi) over [0, n) split into contiguous ranges on up to 16 host
+// threads (each range is processed by exactly one thread, so results do not
+// depend on the thread count when f writes only its own range).
+template <typename F>
+void parallel_ranges(int64_t n, int64_t min_chunk, F&& f) {
+  const int64_t hw = std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)std::thread::hardware_concurrency()));
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, min_chunk)));
+  if (nt <= 1) {
+    f((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; t++) th.emplace_back([&, t] { f(n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+}
 
 struct Contrib {
   uint64_t key;   // col * dim + row  (lower: row >= col)
@@ -150,24 +171,48 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
     con0 += I.m;
   }
 
-  std::sort(C.begin(), C.end(), [](const Contrib& x, const Contrib& y) {
-    if (x.key != y.key) return x.key < y.key;
-    if (x.type != y.type) return x.type < y.type;
-    if (x.a != y.a) return x.a < y.a;
-    return x.b < y.b;
-  });
+  // order by (key, type, a, b): a counting sort by column, then each
+  // column's few contributions by (row, type, a, b), columns in parallel
+  {
+    auto less = [](const Contrib& x, const Contrib& y) {
+      if (x.key != y.key) return x.key < y.key;
+      if (x.type != y.type) return x.type < y.type;
+      if (x.a != y.a) return x.a < y.a;
+      return x.b < y.b;
+    };
+    std::vector<int64_t> cp((size_t)P.dim + 1, 0);
+    for (const Contrib& c : C) cp[c.key / D + 1]++;
+    for (int64_t i = 0; i < P.dim; i++) cp[i + 1] += cp[i];
+    std::vector<Contrib> S(C.size());
+    {
+      std::vector<int64_t> f(cp.begin(), cp.end() - 1);
+      for (const Contrib& c : C) S[f[c.key / D]++] = c;
+    }
+    std::vector<Contrib>().swap(C);
+    parallel_ranges(P.dim, 4096, [&](int64_t lo, int64_t hi) {
+      for (int64_t c = lo; c < hi; c++)
+        if (cp[c + 1] - cp[c] > 1) std::sort(S.begin() + cp[c], S.begin() + cp[c + 1], less);
+    });
+    C.swap(S);
+  }
 
-  // group into entries
+  // group into entries (sizes counted first)
+  size_t nent = 0, npair = 0;
+  for (size_t q = 0; q < C.size(); q++) {
+    if (q == 0 || C[q].key != C[q - 1].key) nent++;
+    if (C[q].type == 4) npair++;
+  }
   P.A_colptr.assign(P.dim + 1, 0);
-  P.A_row.clear();
-  P.e_h.clear();
-  P.e_j.clear();
-  P.e_kind.clear();
-  P.e_var.clear();
-  P.pair_ptr.assign(1, 0);
-  P.pair_p.clear();
-  P.pair_q.clear();
-  size_t k = 0;
+  P.A_row.resize(nent);
+  P.e_h.resize(nent);
+  P.e_j.resize(nent);
+  P.e_kind.resize(nent);
+  P.e_var.resize(nent);
+  P.pair_ptr.resize(nent + 1);
+  P.pair_ptr[0] = 0;
+  P.pair_p.resize(npair);
+  P.pair_q.resize(npair);
+  size_t k = 0, e = 0, np = 0;
   while (k < C.size()) {
     uint64_t key = C[k].key;
     int64_t col = (int64_t)(key / D), rw = (int64_t)(key % D);
@@ -180,15 +225,19 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
         case 1: j = c.a; break;
         case 2: kind = DIAG_PRIMAL; var = c.a; break;
         case 3: kind = DIAG_DUAL; var = c.a; break;
-        case 4: P.pair_p.push_back(c.a); P.pair_q.push_back(c.b); break;
+        case 4:
+          P.pair_p[np] = c.a;
+          P.pair_q[np++] = c.b;
+          break;
       }
     }
-    P.A_row.push_back((int32_t)rw);
-    P.e_h.push_back(h);
-    P.e_j.push_back(j);
-    P.e_kind.push_back(kind);
-    P.e_var.push_back(var);
-    P.pair_ptr.push_back((int64_t)P.pair_p.size());
+    P.A_row[e] = (int32_t)rw;
+    P.e_h[e] = h;
+    P.e_j[e] = j;
+    P.e_kind[e] = kind;
+    P.e_var[e] = var;
+    P.pair_ptr[e + 1] = (int64_t)np;
+    e++;
     P.A_colptr[col + 1]++;
   }
   for (int64_t c = 0; c < P.dim; c++) P.A_colptr[c + 1] += P.A_colptr[c];
@@ -265,8 +314,17 @@ Graph make_graph(const Plan& P) {
   return G;
 }
 
+// Vertex -> subgraph id of the task that owns it (0: none).  Tasks own
+// disjoint vertex sets and only compare a neighbour's id with their own, so
+// concurrent tasks never observe each other's ids as their own; the atomics
+// make those reads well defined.
+using PartArray = std::vector<std::atomic<int32_t>>;
+
+inline int32_t part_of(const PartArray& part, int32_t v) { return part[v].load(std::memory_order_relaxed); }
+inline void set_part(PartArray& part, int32_t v, int32_t id) { part[v].store(id, std::memory_order_relaxed); }
+
 // minimum degree on a small dense graph (k <= 256): bitset elimination graph
-void leaf_min_degree(const Graph& G, const std::vector<int32_t>& part, int32_t id,
+void leaf_min_degree(const Graph& G, const PartArray& part, int32_t id,
                      const std::vector<int32_t>& verts, std::vector<int32_t>& local, int32_t* out) {
   const int k = (int)verts.size();
   const int W = (k + 63) / 64;
@@ -276,7 +334,7 @@ void leaf_min_degree(const Graph& G, const std::vector<int32_t>& part, int32_t i
     int32_t v = verts[a];
     for (int64_t p = G.xadj[v]; p < G.xadj[v + 1]; p++) {
       int32_t u = G.adj[p];
-      if (part[u] != id) continue;
+      if (part_of(part, u) != id) continue;
       int b = local[u];
       adj[(size_t)a * W + b / 64] |= 1ull << (b % 64);
     }
@@ -302,13 +360,10 @@ void leaf_min_degree(const Graph& G, const std::vector<int32_t>& part, int32_t i
         int b = w * 64 + __builtin_ctzll(bits);
         bits &= bits - 1;
         uint64_t* ru = &adj[(size_t)b * W];
-        int d = 0;
-        for (int x = 0; x < W; x++) {
-          ru[x] |= rb[x];
-          d += 0;
-        }
+        for (int x = 0; x < W; x++) ru[x] |= rb[x];
         ru[b / 64] &= ~(1ull << (b % 64));
         ru[best / 64] &= ~(1ull << (best % 64));
+        int d = 0;
         for (int x = 0; x < W; x++) d += __builtin_popcountll(ru[x]);
         deg[b] = d;
       }
@@ -318,38 +373,55 @@ void leaf_min_degree(const Graph& G, const std::vector<int32_t>& part, int32_t i
   for (int a = 0; a < k; a++) local[verts[a]] = -1;
 }
 
-std::vector<int32_t> nested_dissection(const Graph& G, int leaf) {
-  const int64_t n = G.n;
-  std::vector<int32_t> order(n, -1);
-  std::vector<int32_t> part(n, 0), lvl(n, -1), local(n, -1);
-  int32_t next_id = 1;
-  struct Task {
-    std::vector<int32_t> v;
-    int64_t lo;
-  };
-  std::vector<Task> stack;
-  {
-    Task t;
-    t.v.resize(n);
-    std::iota(t.v.begin(), t.v.end(), 0);
-    t.lo = 0;
-    stack.push_back(std::move(t));
+struct NdTask {
+  std::vector<int32_t> v;
+  int64_t lo;
+};
+
+// Shared state of one nested dissection; a task reads and writes only the
+// entries of its own vertices (part, lvl, local) and its own range of order.
+struct NdState {
+  const Graph& G;
+  int leaf;
+  std::vector<int32_t> order, lvl, local;
+  PartArray part;
+  std::atomic<int32_t> next_id{1};
+  NdState(const Graph& g, int lf) : G(g), leaf(lf), order(g.n, -1), lvl(g.n, -1), local(g.n, -1), part(g.n) {
+    for (auto& x : part) x.store(0, std::memory_order_relaxed);
   }
-  std::vector<int32_t> queue(n);
-  // BFS restricted to subgraph `id` from root; returns number reached; fills
-  // lvl[] and queue[0..reached); nlev = number of levels
-  auto bfs = [&](int32_t id, int32_t root, int& nlev) -> int64_t {
+};
+
+// One task: order a leaf, or split off a component, or find a level-structure
+// separator (ordered last in the task's range) and return the two parts.
+void nd_task(NdState& S, NdTask& t, std::vector<int32_t>& queue, std::vector<NdTask>& out) {
+  const Graph& G = S.G;
+  const int64_t sz = (int64_t)t.v.size();
+  if (sz == 0) return;
+  if ((int64_t)queue.size() < sz) queue.resize(sz);
+  const int32_t id = S.next_id.fetch_add(1, std::memory_order_relaxed);
+  for (int32_t v : t.v) set_part(S.part, v, id);
+  auto release = [&] {
+    for (int32_t v : t.v) set_part(S.part, v, 0);
+  };
+  if (sz <= S.leaf) {
+    leaf_min_degree(G, S.part, id, t.v, S.local, &S.order[t.lo]);
+    release();
+    return;
+  }
+  // BFS restricted to the task's subgraph from root; fills lvl[] and
+  // queue[0..reached); nlev = number of levels
+  auto bfs = [&](int32_t root, int& nlev) -> int64_t {
     int64_t head = 0, tail = 0;
     queue[tail++] = root;
-    lvl[root] = 0;
+    S.lvl[root] = 0;
     int maxl = 0;
     while (head < tail) {
       int32_t v = queue[head++];
-      int lv = lvl[v];
+      int lv = S.lvl[v];
       for (int64_t p = G.xadj[v]; p < G.xadj[v + 1]; p++) {
         int32_t u = G.adj[p];
-        if (part[u] != id || lvl[u] >= 0) continue;
-        lvl[u] = lv + 1;
+        if (part_of(S.part, u) != id || S.lvl[u] >= 0) continue;
+        S.lvl[u] = lv + 1;
         if (lv + 1 > maxl) maxl = lv + 1;
         queue[tail++] = u;
       }
@@ -358,122 +430,158 @@ std::vector<int32_t> nested_dissection(const Graph& G, int leaf) {
     return tail;
   };
   auto clear_lvl = [&](int64_t cnt) {
-    for (int64_t i = 0; i < cnt; i++) lvl[queue[i]] = -1;
+    for (int64_t i = 0; i < cnt; i++) S.lvl[queue[i]] = -1;
   };
-
-  while (!stack.empty()) {
-    Task t = std::move(stack.back());
-    stack.pop_back();
-    const int64_t sz = (int64_t)t.v.size();
-    if (sz == 0) continue;
-    int32_t id = next_id++;
-    for (int32_t v : t.v) part[v] = id;
-    if (sz <= leaf) {
-      leaf_min_degree(G, part, id, t.v, local, &order[t.lo]);
-      for (int32_t v : t.v) part[v] = 0;
-      continue;
-    }
-    // pseudo-peripheral root: two sweeps from the vertex of smallest degree
-    int32_t root = t.v[0];
-    int nlev = 0;
-    int64_t reached = bfs(id, root, nlev);
-    if (reached < sz) {
-      // disconnected: split off this component
-      std::vector<int32_t> comp(queue.begin(), queue.begin() + reached);
-      clear_lvl(reached);
-      for (int32_t v : comp) part[v] = -1;
-      std::vector<int32_t> rest;
-      rest.reserve(sz - reached);
-      for (int32_t v : t.v)
-        if (part[v] == id) rest.push_back(v);
-      for (int32_t v : t.v) part[v] = 0;
-      Task a{std::move(comp), t.lo};
-      Task b{std::move(rest), t.lo + reached};
-      stack.push_back(std::move(a));
-      stack.push_back(std::move(b));
-      continue;
-    }
-    for (int sweep = 0; sweep < 2; sweep++) {
-      // farthest vertex of smallest degree in the last level
-      int32_t best = queue[reached - 1];
-      int lastl = lvl[best];
-      int64_t bestdeg = G.xadj[best + 1] - G.xadj[best];
-      for (int64_t i = reached - 1; i >= 0 && lvl[queue[i]] == lastl; i--) {
-        int64_t d = G.xadj[queue[i] + 1] - G.xadj[queue[i]];
-        if (d < bestdeg) {
-          bestdeg = d;
-          best = queue[i];
-        }
-      }
-      clear_lvl(reached);
-      int nl2 = 0;
-      reached = bfs(id, best, nl2);
-      if (nl2 <= nlev && sweep > 0) {
-        nlev = nl2;
-        break;
-      }
-      nlev = nl2;
-    }
-    if (nlev < 3) {
-      // (nearly) complete subgraph: no useful separator
-      clear_lvl(reached);
-      if (sz <= 256) leaf_min_degree(G, part, id, t.v, local, &order[t.lo]);
-      else
-        for (int64_t i = 0; i < sz; i++) order[t.lo + i] = t.v[i];
-      for (int32_t v : t.v) part[v] = 0;
-      continue;
-    }
-    std::vector<int64_t> cnt(nlev + 1, 0);
-    for (int64_t i = 0; i < reached; i++) cnt[lvl[queue[i]] + 1]++;
-    std::vector<int64_t> levsz(nlev);
-    for (int l = 0; l < nlev; l++) levsz[l] = cnt[l + 1];
-    for (int l = 0; l < nlev; l++) cnt[l + 1] += cnt[l];
-    // choose the separator level
-    int sep = -1;
-    double bestcost = 1e300;
-    for (int l = 1; l < nlev - 1; l++) {
-      int64_t below = cnt[l], above = sz - cnt[l + 1];
-      double lo = (double)std::min(below, above), hi = (double)std::max(below, above);
-      if (lo < 0.3 * (double)sz && !(sep < 0 && l == nlev / 2)) continue;
-      double cost = (double)levsz[l] * (1.0 + 0.5 * (hi - lo) / (double)sz);
-      if (cost < bestcost) {
-        bestcost = cost;
-        sep = l;
-      }
-    }
-    if (sep < 0) sep = nlev / 2;
-    std::vector<int32_t> A, B, S;
-    A.reserve(cnt[sep]);
-    B.reserve(sz - cnt[sep + 1]);
-    for (int64_t i = 0; i < reached; i++) {
-      int32_t v = queue[i];
-      int l = lvl[v];
-      if (l < sep) A.push_back(v);
-      else if (l > sep) B.push_back(v);
-      else {
-        bool above = false;
-        for (int64_t p = G.xadj[v]; p < G.xadj[v + 1]; p++) {
-          int32_t u = G.adj[p];
-          if (part[u] == id && lvl[u] == sep + 1) {
-            above = true;
-            break;
-          }
-        }
-        if (above) S.push_back(v);
-        else A.push_back(v);
+  // pseudo-peripheral root: two sweeps from the vertex of smallest degree
+  int32_t root = t.v[0];
+  int nlev = 0;
+  int64_t reached = bfs(root, nlev);
+  if (reached < sz) {
+    // disconnected: split off this component
+    std::vector<int32_t> comp(queue.begin(), queue.begin() + reached);
+    clear_lvl(reached);
+    for (int32_t v : comp) set_part(S.part, v, -1);
+    std::vector<int32_t> rest;
+    rest.reserve(sz - reached);
+    for (int32_t v : t.v)
+      if (part_of(S.part, v) == id) rest.push_back(v);
+    release();
+    out.push_back(NdTask{std::move(comp), t.lo});
+    out.push_back(NdTask{std::move(rest), t.lo + reached});
+    return;
+  }
+  for (int sweep = 0; sweep < 2; sweep++) {
+    // farthest vertex of smallest degree in the last level
+    int32_t best = queue[reached - 1];
+    int lastl = S.lvl[best];
+    int64_t bestdeg = G.xadj[best + 1] - G.xadj[best];
+    for (int64_t i = reached - 1; i >= 0 && S.lvl[queue[i]] == lastl; i--) {
+      int64_t d = G.xadj[queue[i] + 1] - G.xadj[queue[i]];
+      if (d < bestdeg) {
+        bestdeg = d;
+        best = queue[i];
       }
     }
     clear_lvl(reached);
-    for (int32_t v : t.v) part[v] = 0;
-    int64_t hi = t.lo + sz;
-    for (size_t i = 0; i < S.size(); i++) order[hi - (int64_t)S.size() + (int64_t)i] = S[i];
-    int64_t na = (int64_t)A.size();
-    Task ta{std::move(A), t.lo};
-    Task tb{std::move(B), t.lo + na};
-    stack.push_back(std::move(ta));
-    stack.push_back(std::move(tb));
+    int nl2 = 0;
+    reached = bfs(best, nl2);
+    if (nl2 <= nlev && sweep > 0) {
+      nlev = nl2;
+      break;
+    }
+    nlev = nl2;
   }
-  return order;
+  if (nlev < 3) {
+    // (nearly) complete subgraph: no useful separator
+    clear_lvl(reached);
+    if (sz <= 256) leaf_min_degree(G, S.part, id, t.v, S.local, &S.order[t.lo]);
+    else
+      for (int64_t i = 0; i < sz; i++) S.order[t.lo + i] = t.v[i];
+    release();
+    return;
+  }
+  std::vector<int64_t> cnt(nlev + 1, 0);
+  for (int64_t i = 0; i < reached; i++) cnt[S.lvl[queue[i]] + 1]++;
+  std::vector<int64_t> levsz(nlev);
+  for (int l = 0; l < nlev; l++) levsz[l] = cnt[l + 1];
+  for (int l = 0; l < nlev; l++) cnt[l + 1] += cnt[l];
+  // choose the separator level
+  int sep = -1;
+  double bestcost = 1e300;
+  for (int l = 1; l < nlev - 1; l++) {
+    int64_t below = cnt[l], above = sz - cnt[l + 1];
+    double lo = (double)std::min(below, above), hi = (double)std::max(below, above);
+    if (lo < 0.3 * (double)sz && !(sep < 0 && l == nlev / 2)) continue;
+    double cost = (double)levsz[l] * (1.0 + 0.5 * (hi - lo) / (double)sz);
+    if (cost < bestcost) {
+      bestcost = cost;
+      sep = l;
+    }
+  }
+  if (sep < 0) sep = nlev / 2;
+  std::vector<int32_t> A, B, Sp;
+  A.reserve(cnt[sep]);
+  B.reserve(sz - cnt[sep + 1]);
+  for (int64_t i = 0; i < reached; i++) {
+    int32_t v = queue[i];
+    int l = S.lvl[v];
+    if (l < sep) A.push_back(v);
+    else if (l > sep) B.push_back(v);
+    else {
+      bool above = false;
+      for (int64_t p = G.xadj[v]; p < G.xadj[v + 1]; p++) {
+        int32_t u = G.adj[p];
+        if (part_of(S.part, u) == id && S.lvl[u] == sep + 1) {
+          above = true;
+          break;
+        }
+      }
+      if (above) Sp.push_back(v);
+      else A.push_back(v);
+    }
+  }
+  clear_lvl(reached);
+  release();
+  int64_t hi = t.lo + sz;
+  for (size_t i = 0; i < Sp.size(); i++) S.order[hi - (int64_t)Sp.size() + (int64_t)i] = Sp[i];
+  int64_t na = (int64_t)A.size();
+  out.push_back(NdTask{std::move(A), t.lo});
+  out.push_back(NdTask{std::move(B), t.lo + na});
+}
+
+// Tasks are independent (disjoint vertices and ranges of order), so they run
+// on a pool of host threads; the ordering does not depend on their timing.
+std::vector<int32_t> nested_dissection(const Graph& G, int leaf) {
+  NdState S(G, leaf);
+  std::vector<NdTask> stack;
+  {
+    NdTask t;
+    t.v.resize(G.n);
+    std::iota(t.v.begin(), t.v.end(), 0);
+    t.lo = 0;
+    stack.push_back(std::move(t));
+  }
+  const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)std::thread::hardware_concurrency()));
+  std::mutex mu;
+  std::condition_variable cv;
+  int active = 0;
+  std::exception_ptr failure;
+  auto worker = [&] {
+    std::vector<int32_t> queue;
+    std::vector<NdTask> out;
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      cv.wait(lk, [&] { return !stack.empty() || active == 0 || failure; });
+      if (failure || (stack.empty() && active == 0)) break;
+      NdTask t = std::move(stack.back());
+      stack.pop_back();
+      active++;
+      lk.unlock();
+      out.clear();
+      try {
+        nd_task(S, t, queue, out);
+      } catch (...) {
+        lk.lock();
+        if (!failure) failure = std::current_exception();
+        active--;
+        cv.notify_all();
+        break;
+      }
+      lk.lock();
+      for (auto& o : out) stack.push_back(std::move(o));
+      active--;
+      cv.notify_all();
+    }
+  };
+  if (nth <= 1 || G.n < 20000) {
+    worker();
+  } else {
+    std::vector<std::thread> th;
+    for (int i = 0; i < nth; i++) th.emplace_back(worker);
+    for (auto& x : th) x.join();
+  }
+  if (failure) std::rethrow_exception(failure);
+  return std::move(S.order);
 }
 
 // ---------------------------------------------------------------------------
@@ -624,9 +732,19 @@ void symbolic(Plan& P, const std::vector<int32_t>& perm0) {
   for (int64_t j = 0; j < N; j++)
     if (parent[j] >= 0) nchild[parent[j]]++;
 
-  // column-by-column symbolic factorisation with a stack of child structures
-  std::vector<std::vector<int32_t>> stack;
-  std::vector<int32_t> mark(N, -1);
+  // column counts and fundamental supernodes.  Column j joins the supernode
+  // t of its only child j-1 when its own lower entries all lie in the
+  // structure of j-1 (then struct(j) = struct(j-1) minus j and the counts
+  // differ by one); only the first column of each supernode gets an explicit
+  // structure: its lower entries and the structures of its children's
+  // supernodes, whose last columns are its etree children.
+  std::vector<int32_t> chead(N, -1), cnext(N, -1);
+  for (int64_t c = N - 1; c >= 0; c--)
+    if (parent[c] >= 0) {
+      cnext[c] = chead[parent[c]];
+      chead[parent[c]] = (int32_t)c;
+    }
+  std::vector<int32_t> mark(N, -1);   // supernode whose first-column structure holds the row
   std::vector<int64_t> colcount(N);
   std::vector<SNode> S;
   std::vector<int32_t> sn_of(N);
@@ -635,55 +753,62 @@ void symbolic(Plan& P, const std::vector<int32_t>& perm0) {
   P.inst_flops.assign(P.inst.size(), 0.0);
   P.inst_nnzL.assign(P.inst.size(), 0);
   for (int64_t j = 0; j < N; j++) {
-    std::vector<int32_t> st;
-    mark[j] = (int32_t)j;
-    int32_t nc = nchild[j];
-    size_t prev_size = 0;
-    bool single_chain = false;
-    if (nc == 1 && !stack.empty()) prev_size = stack.back().size();
-    for (int32_t c = 0; c < nc; c++) {
-      std::vector<int32_t>& cs = stack.back();
-      for (int32_t r : cs)
-        if (r > j && mark[r] != j) {
-          mark[r] = (int32_t)j;
+    bool join = false;
+    if (nchild[j] == 1 && j > 0 && parent[j - 1] == j) {
+      const int32_t t = sn_of[j - 1];
+      join = true;
+      for (int64_t p = lo_ptr[j]; p < lo_ptr[j + 1]; p++)
+        if (mark[lo_row[p]] != t) {
+          join = false;
+          break;
+        }
+    }
+    int64_t cj;
+    if (join) {
+      const int32_t t = sn_of[j - 1];
+      cj = colcount[j - 1] - 1;
+      S[t].cols.push_back((int32_t)j);
+      S[t].ncol++;
+      sn_of[j] = t;
+    } else {
+      const int32_t s = (int32_t)S.size();
+      std::vector<int32_t> st;
+      for (int32_t c = chead[j]; c >= 0; c = cnext[c]) {
+        // struct(c): the rows of c's supernode below its columns
+        const SNode& T = S[sn_of[c]];
+        for (size_t q = (size_t)(T.ncol - 1); q < T.below.size(); q++) {
+          const int32_t r = T.below[q];
+          if (r > j && mark[r] != s) {
+            mark[r] = s;
+            st.push_back(r);
+          }
+        }
+      }
+      for (int64_t p = lo_ptr[j]; p < lo_ptr[j + 1]; p++) {
+        const int32_t r = lo_row[p];
+        if (mark[r] != s) {
+          mark[r] = s;
           st.push_back(r);
         }
-      stack.pop_back();
-    }
-    for (int64_t p = lo_ptr[j]; p < lo_ptr[j + 1]; p++) {
-      int32_t r = lo_row[p];
-      if (mark[r] != j) {
-        mark[r] = (int32_t)j;
-        st.push_back(r);
       }
-    }
-    std::sort(st.begin(), st.end());
-    int64_t cj = (int64_t)st.size();  // strictly-lower count of column j
-    colcount[j] = cj;
-    P.nnzL += cj;
-    double fj = (double)cj * (double)cj + 3.0 * (double)cj;
-    P.flops += fj;
-    int32_t ij = P.row_inst[perm1[j]];
-    P.inst_flops[ij] += fj;
-    P.inst_nnzL[ij] += cj;
-    if (nc == 1 && j > 0 && parent[j - 1] == j && (int64_t)prev_size == cj + 1) single_chain = true;
-    if (single_chain) {
-      int32_t s = sn_of[j - 1];
-      S[s].cols.push_back((int32_t)j);
-      S[s].ncol++;
-      sn_of[j] = s;
-    } else {
+      std::sort(st.begin(), st.end());
+      cj = (int64_t)st.size();
       SNode sn;
       sn.cols.push_back((int32_t)j);
       sn.ncol = 1;
-      sn.below = st;
+      sn.below = std::move(st);
       sn.nrow = 1 + cj;
       S.push_back(std::move(sn));
-      sn_of[j] = (int32_t)S.size() - 1;
+      sn_of[j] = s;
     }
-    stack.push_back(std::move(st));
+    colcount[j] = cj;
+    P.nnzL += cj;
+    const double fj = (double)cj * (double)cj + 3.0 * (double)cj;
+    P.flops += fj;
+    const int32_t ij = P.row_inst[perm1[j]];
+    P.inst_flops[ij] += fj;
+    P.inst_nnzL[ij] += cj;
   }
-  stack.clear();
   // within a fundamental supernode, below rows = below(first) minus its own cols
   for (auto& s : S) {
     if (s.ncol > 1) {
