@@ -351,6 +351,16 @@ class Runner:
         return infos, si, adj_ms
 
 
+def reduce_max(v, dist=None, device="cpu"):
+    """The largest of a scalar over the ranks of the process group (the value
+    itself without one): whole-job times are the slowest rank's."""
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     from paper_2510_05885_gb300 import ncl_kkt as nk
@@ -371,10 +381,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, dist, dev)
 
     nk.load()
     R = Runner(args, dev, rank)

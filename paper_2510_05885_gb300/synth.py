@@ -101,8 +101,8 @@ def make_pattern(R: int, C: int, deleted: np.ndarray | None = None) -> GridPatte
     cols_o = (4 * edges[:, 0][:, None] + c4.ravel()[None, :]).ravel()
     rows = np.concatenate([rows_d, rows_o])
     cols = np.concatenate([cols_d, cols_o])
-    key = rows * n + cols
-    key = np.unique(key)
+    key = np.sort(rows * n + cols)
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])]   # sorted, unique
     rows = key // n
     cols = key % n
     H_rowptr = np.zeros(n + 1, np.int64)
