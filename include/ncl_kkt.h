@@ -166,6 +166,16 @@ ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m,
                            const ncl_kkt_options* opt, ncl_kkt_t* out);
 
 /*
+ * ncl_kkt_analyze_like -- a new handle with the options opt (e.g. another
+ * precision or pivot policy) on the analysis of an existing handle src: the
+ * pattern, ordering, supernodes and schedule are copied, not recomputed
+ * (analyse once, factor in several precisions).  opt->leaf_size is not used.
+ * src is not modified and may be destroyed afterwards.  Uses the current
+ * CUDA device.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+ncl_status ncl_kkt_analyze_like(ncl_kkt_t src, const ncl_kkt_options* opt, ncl_kkt_t* out);
+
+/*
  * ncl_kkt_factor -- numeric LDL^T of the KKT matrix for new values on the
  * analysed pattern (every Newton step).
  *   H_val   device double[nnz(H)], J_val device double[nnz(J)],

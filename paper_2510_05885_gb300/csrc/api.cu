@@ -1578,11 +1578,8 @@ ncl_status guarded(ncl_kkt_s* h, F&& f) {
   }
 }
 
-ncl_status analyze_common(const AnalyzeInput& in, const ncl_kkt_options* opt, ncl_kkt_t* out) {
-  if (!out) return fail(NCL_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (in.form != 0 && in.form != 1) return fail(NCL_ERR_INVALID_ARG, "bad form");
-  std::unique_ptr<ncl_kkt_s> h(new ncl_kkt_s());
+// options of a new handle, validated, with the precision-dependent defaults
+static ncl_status init_options(ncl_kkt_s* h, const ncl_kkt_options* opt) {
   ncl_kkt_default_options(&h->opt);
   if (opt) h->opt = *opt;
   if (h->opt.prec != NCL_PREC_FP64 && h->opt.prec != NCL_PREC_FP32_IR) return fail(NCL_ERR_INVALID_ARG, "bad prec");
@@ -1591,6 +1588,18 @@ ncl_status analyze_common(const AnalyzeInput& in, const ncl_kkt_options* opt, nc
   if (!(h->opt.pivot_eps >= 0)) return fail(NCL_ERR_INVALID_ARG, "bad pivot_eps");
   if (!(h->opt.ir_tol > 0)) h->opt.ir_tol = h->opt.prec == NCL_PREC_FP64 ? 1e-12 : 1e-10;
   if (h->opt.ir_max_iter < 0) h->opt.ir_max_iter = h->opt.prec == NCL_PREC_FP64 ? 3 : 10;
+  return NCL_OK;
+}
+
+static ncl_status finish_handle(std::unique_ptr<ncl_kkt_s>& h, ncl_kkt_t* out);
+
+ncl_status analyze_common(const AnalyzeInput& in, const ncl_kkt_options* opt, ncl_kkt_t* out) {
+  if (!out) return fail(NCL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (in.form != 0 && in.form != 1) return fail(NCL_ERR_INVALID_ARG, "bad form");
+  std::unique_ptr<ncl_kkt_s> h(new ncl_kkt_s());
+  ncl_status so = init_options(h.get(), opt);
+  if (so != NCL_OK) return so;
   AnalyzeInput a = in;
   a.leaf_size = h->opt.leaf_size;
   a.colpad = 4;
@@ -1602,6 +1611,25 @@ ncl_status analyze_common(const AnalyzeInput& in, const ncl_kkt_options* opt, nc
   }
   h->ninst = in.count;
   h->dp.ninst = in.count;
+  return finish_handle(h, out);
+}
+
+// A handle with new options on the analysis of an existing one (the plan is
+// copied; the nested-dissection leaf size of the new options is not used).
+ncl_status analyze_like(ncl_kkt_s* src, const ncl_kkt_options* opt, ncl_kkt_t* out) {
+  if (!out) return fail(NCL_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!src) return fail(NCL_ERR_INVALID_ARG, "NULL source handle");
+  std::unique_ptr<ncl_kkt_s> h(new ncl_kkt_s());
+  ncl_status so = init_options(h.get(), opt);
+  if (so != NCL_OK) return so;
+  h->plan = src->plan;
+  h->ninst = src->ninst;
+  h->dp.ninst = src->dp.ninst;
+  return finish_handle(h, out);
+}
+
+static ncl_status finish_handle(std::unique_ptr<ncl_kkt_s>& h, ncl_kkt_t* out) {
   try {
     build_schedule(h.get());
   } catch (const std::exception& e) {
@@ -1656,6 +1684,10 @@ ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m, const int32_t* H_
   in.J_rowptr = &J_rowptr;
   in.J_colind = &J_colind;
   return analyze_common(in, opt, out);
+}
+
+ncl_status ncl_kkt_analyze_like(ncl_kkt_t src, const ncl_kkt_options* opt, ncl_kkt_t* out) {
+  return analyze_like(src, opt, out);
 }
 
 ncl_status ncl_kkt_batch_analyze(int32_t count, int32_t form, const int32_t* n, const int32_t* m,

@@ -88,6 +88,7 @@ _SIGS = {
     "ncl_kkt_default_options": (None, [ctypes.POINTER(Options)]),
     "ncl_kkt_analyze": (I32, [I32, I32, I32, P, P, P, P, ctypes.POINTER(Options), ctypes.POINTER(P)]),
     "ncl_kkt_batch_analyze": (I32, [I32, I32, P, P, P, P, P, P, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+    "ncl_kkt_analyze_like": (I32, [P, ctypes.POINTER(Options), ctypes.POINTER(P)]),
     "ncl_kkt_factor": (I32, [P, P, P, P, D, D, P, ctypes.POINTER(FactorInfo)]),
     "ncl_kkt_batch_factor": (I32, [P, P, P, P, P, P, P, P]),
     "ncl_kkt_factor_regularize": (I32, [P, P, P, P, P, P, D, D, I32, P, P, P]),
@@ -203,6 +204,12 @@ def ncl_kkt_batch_analyze(form, ns, ms, H_rowptrs, H_colinds, J_rowptrs, J_colin
                                      ctypes.cast(pHi, P), ctypes.cast(pJ, P), ctypes.cast(pJi, P),
                                      ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
     return h
+
+
+def ncl_kkt_analyze_like(src, opt: Options | None = None):
+    out = P()
+    _check(load().ncl_kkt_analyze_like(src, ctypes.byref(opt or default_options()), ctypes.byref(out)))
+    return out
 
 
 def ncl_kkt_factor(h, H_val, J_val, Sigma, delta, rho, stream=None) -> FactorInfo:
@@ -419,6 +426,19 @@ class KKT:
         self.nnz_H = sum(int(np.asarray(p[2])[-1]) if p[0] > 0 else 0 for p in patterns)
         self.nnz_J = sum(int(np.asarray(p[4])[-1]) if p[1] > 0 else 0 for p in patterns)
         self.n_var = sum(int(p[0]) for p in patterns)
+        self._post()
+        return self
+
+    @classmethod
+    def like(cls, other, **opts):
+        """A handle with new options (e.g. prec="fp64") on the analysis of
+        ``other`` (copied, not recomputed)."""
+        self = cls.__new__(cls)
+        self._h = None
+        self.opt = default_options(**opts)
+        self._h = ncl_kkt_analyze_like(other._h, self.opt)
+        self.form, self.count = other.form, other.count
+        self.nnz_H, self.nnz_J, self.n_var = other.nnz_H, other.nnz_J, other.n_var
         self._post()
         return self
 

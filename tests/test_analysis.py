@@ -163,3 +163,23 @@ def test_analysis_300x300_condensed_fill():
         assert ai.nnz_L < 2.0e8 and ai.flops < 3e11
     finally:
         nk.ncl_kkt_destroy(h)
+
+
+def test_analyze_like_copies_the_analysis():
+    """A handle made from another's analysis (other options) has the same
+    ordering, supernodes and statistics; the source is not needed afterwards."""
+    pat = synth.make_pattern(13, 17)
+    src = nk.KKT(1, pat.n, pat.m, pat.H_rowptr, pat.H_colind, pat.J_rowptr, pat.J_colind, host_only=1)
+    twin = nk.KKT.like(src, host_only=1, prec="fp64", pivot_policy=1)
+    assert np.array_equal(src.permutation, twin.permutation)
+    for a, b in zip(src.supernodes(), twin.supernodes()):
+        assert np.array_equal(a, b)
+    ia, ib = src.analysis.as_dict(), twin.analysis.as_dict()
+    ia.pop("analyze_ms")
+    ib.pop("analyze_ms")
+    assert ia == ib
+    src.close()
+    assert twin.analysis.dim == pat.n
+    twin.close()
+    with pytest.raises(nk.NclError):
+        nk.ncl_kkt_analyze_like(None, nk.default_options(host_only=1))
