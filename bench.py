@@ -57,6 +57,8 @@ def parse():
                     help="also time the inertia correction (Section 3.1) from delta = 0 on the first draw")
     ap.add_argument("--k1s", action="store_true",
                     help="condensed workloads: also time the step with slacks (Eq. K1s) on the first draw")
+    ap.add_argument("--newton", action="store_true",
+                    help="also time the Newton step (right-hand side + refined solve + recovery) on the first draw")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -614,6 +616,48 @@ def run_ours(args):
         out["k1s"] = {"ms": statistics.median(times), "backward_err_max": max(etas), "rows": ncon,
                       "rows_without_slack": int(np.isinf(Ss).sum()),
                       "steps": "factor_k1s + k1s_rhs + solve + slack_step, 3 timed after 1 warm-up"}
+
+    # Newton step around the factorisation (right-hand side of Eq. K2r / K1,
+    # refined solve, recovery of Delta y, Delta r, Delta z): a seeded interior
+    # point with bounds 0.1..2 away from x (30% of them infinite), mu = 0.05;
+    # the factorisation of the first draw is reused for every repetition
+    if args.newton:
+        d = R.dev_draws[0]
+        insts = R.draws[0]
+        n_tot = sum(i.n for i in insts)
+        m_tot = sum(i.m for i in insts)
+        rng = np.random.default_rng(11)
+        x = rng.standard_normal(n_tot)
+        lo = x - rng.uniform(0.1, 2.0, n_tot)
+        up = x + rng.uniform(0.1, 2.0, n_tot)
+        lo[rng.random(n_tot) < 0.3] = -np.inf
+        up[rng.random(n_tot) < 0.3] = np.inf
+        zl = np.where(np.isinf(lo), 0.0, rng.uniform(0.01, 1.0, n_tot))
+        zu = np.where(np.isinf(up), 0.0, rng.uniform(0.01, 1.0, n_tot))
+        host_pt = {"grad_phi": rng.standard_normal(n_tot), "x": x, "lower": lo, "upper": up, "z_lower": zl,
+                   "z_upper": zu, "c": rng.standard_normal(m_tot), "y": rng.standard_normal(m_tot),
+                   "y_k": rng.standard_normal(m_tot), "r": rng.standard_normal(m_tot)}
+        pt = {k: torch.as_tensor(v, device=dev) for k, v in host_pt.items()}
+        mu = [0.05] * len(insts)
+        K.factor(d["H"], d["J"], d["S"], d["delta"] if len(insts) > 1 else d["delta"][0],
+                 d["rho"] if len(insts) > 1 else d["rho"][0])
+        times, etas = [], []
+        for rep in range(4):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b = K.newton_rhs(pt, mu)
+            X, si = K.solve(b)
+            dirn = K.newton_recover(pt, mu, X)
+            e1.record()
+            e1.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+                etas.append(si.backward_err)
+        out["newton_step"] = {"ms": statistics.median(times), "backward_err_max": max(etas),
+                              "variables": n_tot, "constraints": m_tot,
+                              "steps": "newton_rhs + refined solve + newton_recover on the same factors, "
+                                       "3 timed after 1 warm-up"}
 
     # end to end through the C ABI with host buffers
     if not args.skip_e2e:
