@@ -183,3 +183,33 @@ def test_analyze_like_copies_the_analysis():
     twin.close()
     with pytest.raises(nk.NclError):
         nk.ncl_kkt_analyze_like(None, nk.default_options(host_only=1))
+
+
+def test_next_row_entry_points_check_their_arguments_on_the_host():
+    """The entry points of the inertia correction, the slack form and the
+    Newton step reject NULL handles and host-only handles before any device
+    work (status codes, nothing thrown across the C ABI)."""
+    lib = nk.load()
+    assert lib.ncl_kkt_factor_regularize(None, None, None, None, None, None, 1e-4, 10.0, 5, None, None, None) == 1
+    assert lib.ncl_kkt_factor_k1s(None, None, None, None, None, None, None, None, None) == 1
+    assert lib.ncl_kkt_k1s_rhs(None, 1, None, 0, None, 0, None, 0, None) == 1
+    assert lib.ncl_kkt_k1s_slack_step(None, 1, None, 0, None, 0, None, 0, None) == 1
+    assert lib.ncl_kkt_newton_rhs(None, None, None, None, None) == 1
+    assert lib.ncl_kkt_newton_recover(None, None, None, None, None, None, None, None, None, None) == 1
+    pat = synth.make_pattern(2, 3)
+    for form in (0, 1):
+        h = _host(form, pat)
+        try:
+            d = np.zeros(1)
+            r = np.ones(1)
+            st = lib.ncl_kkt_factor_regularize(h, None, None, None, d.ctypes.data, r.ctypes.data, 1e-4, 10.0, 5,
+                                               None, None, None)
+            assert st == 5                                   # host-only: no numeric state
+            st = lib.ncl_kkt_factor_k1s(h, None, None, None, None, d.ctypes.data, r.ctypes.data, None, None)
+            assert st == 5
+            pt = nk.NewtonPoint()
+            mu = np.full(1, 0.1)
+            assert lib.ncl_kkt_newton_rhs(h, nk.ctypes.byref(pt), mu.ctypes.data, None, None) == 1   # NULL B
+            assert lib.ncl_kkt_k1s_slack_step(h, 1, None, 0, None, 0, None, 0, None) == 5
+        finally:
+            nk.ncl_kkt_destroy(h)
