@@ -1014,24 +1014,34 @@ void schedule(Plan& P, int colpad) {
   P.amap_ptr.assign(totrows + 1, 0);
   std::vector<int64_t> frow(P.nnzA);
   std::vector<int32_t> fcol(P.nnzA);
-  for (int64_t c = 0; c < N; c++)
-    for (int64_t p = P.A_colptr[c]; p < P.A_colptr[c + 1]; p++) {
-      int32_t a = P.iperm[P.A_row[p]], b = P.iperm[c];
-      int32_t r = std::max(a, b), cc = std::min(a, b);
-      int32_t s = sn_of_col[cc];
-      int64_t lr;
-      if (r < P.sn_col0[s] + P.sn_ncol[s]) lr = r - P.sn_col0[s];
-      else {
-        const int32_t* beg = &P.sn_rows[P.sn_rows_off[s] + P.sn_ncol[s]];
-        const int32_t* end = &P.sn_rows[P.sn_rows_off[s + 1]];
-        const int32_t* it = std::lower_bound(beg, end, r);
-        if (it == end || *it != r) throw std::runtime_error("internal: entry outside supernode rows");
-        lr = P.sn_ncol[s] + (it - beg);
+  // front row and column of every entry (columns in parallel), then the
+  // counts in entry order
+  std::atomic<bool> outside{false};
+  parallel_ranges(N, 8192, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; c++)
+      for (int64_t p = P.A_colptr[c]; p < P.A_colptr[c + 1]; p++) {
+        int32_t a = P.iperm[P.A_row[p]], b = P.iperm[c];
+        int32_t r = std::max(a, b), cc = std::min(a, b);
+        int32_t s = sn_of_col[cc];
+        int64_t lr;
+        if (r < P.sn_col0[s] + P.sn_ncol[s]) lr = r - P.sn_col0[s];
+        else {
+          const int32_t* beg = &P.sn_rows[P.sn_rows_off[s] + P.sn_ncol[s]];
+          const int32_t* end = &P.sn_rows[P.sn_rows_off[s + 1]];
+          const int32_t* it = std::lower_bound(beg, end, r);
+          if (it == end || *it != r) {
+            outside.store(true, std::memory_order_relaxed);
+            lr = 0;
+          } else {
+            lr = P.sn_ncol[s] + (it - beg);
+          }
+        }
+        frow[p] = P.sn_rows_off[s] + lr;
+        fcol[p] = cc - P.sn_col0[s];
       }
-      frow[p] = P.sn_rows_off[s] + lr;
-      fcol[p] = cc - P.sn_col0[s];
-      P.amap_ptr[frow[p] + 1]++;
-    }
+  });
+  if (outside.load()) throw std::runtime_error("internal: entry outside supernode rows");
+  for (int64_t p = 0; p < P.nnzA; p++) P.amap_ptr[frow[p] + 1]++;
   for (int64_t r = 0; r < totrows; r++) P.amap_ptr[r + 1] += P.amap_ptr[r];
   P.amap_col.resize(P.nnzA);
   P.amap_src.resize(P.nnzA);
