@@ -26,6 +26,13 @@
  * K2r, +rho multiplies J^T J in K.  (The paper writes rho-hat = rho + delta
  * there; a caller following it passes rho-hat.)
  *
+ * Around these: the condensed form with slacks (Section 3.3, Eq. K1s;
+ * ncl_kkt_factor_k1s and its right-hand side and slack step), the inertia
+ * correction of Section 3.1 (ncl_kkt_factor_regularize), the right-hand side
+ * of the Newton step and the recovery of its other components (Sections
+ * 3.1-3.3; ncl_kkt_newton_rhs / ncl_kkt_newton_recover), the adjoint, and
+ * batches of independent instances in one handle.
+ *
  * Conventions shared by every entry point
  *   - Pattern arrays (CSR row pointers and column indices) are HOST memory.
  *     Value arrays, right-hand sides and solutions are DEVICE memory, FP64.
