@@ -601,3 +601,39 @@ def test_planted_mistake_dropped_barrier_term(monkeypatch):
     monkeypatch.setattr(O, "newton_rhs", bad)
     with pytest.raises(AssertionError):
         test_newton_step_matches_the_full_newton_system("stabilized")
+
+
+# ------------------------------------------------ helpers that set the parity bar
+
+def test_backward_error_hand_computed():
+    """eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf), worked by hand:
+    A = [[2, 1], [1, 3]], x = [1, 1], b = [3, 5]: r = [0, 1], ||A||_inf = 4,
+    ||x||_inf = 1, ||b||_inf = 5, so eta = 1/9; a second column with the exact
+    solution has eta = 0 and the largest column is reported."""
+    A = sp.csr_matrix(np.array([[2.0, 1.0], [1.0, 3.0]]))
+    assert O.backward_error(A, np.array([1.0, 1.0]), np.array([3.0, 5.0])) == pytest.approx(1.0 / 9.0, rel=1e-15)
+    X = np.array([[1.0, 0.4], [1.0, 0.8]])          # column 2 solves A x = [1.6, 2.8] exactly
+    B = np.array([[3.0, 1.6], [5.0, 2.8]])
+    assert O.backward_error(A, X, B) == pytest.approx(1.0 / 9.0, rel=1e-15)
+    assert O.backward_error(A, X[:, 1], B[:, 1]) <= 1e-16
+    # invariant under a common scaling of A and b (x unchanged)
+    assert O.backward_error(7.0 * A, np.array([1.0, 1.0]), 7.0 * np.array([3.0, 5.0])) == pytest.approx(1.0 / 9.0)
+
+
+def test_cond1_estimate_against_the_exact_condition_number():
+    """kappa_1 of a small SPD and an SQD matrix against ||A||_1 ||A^-1||_1
+    from a dense inverse (the estimate is a lower bound, exact on these
+    sizes), and exactly max|d| / min|d| for a diagonal matrix."""
+    rng = np.random.default_rng(3)
+    for form in ("stabilized", "condensed"):
+        inst = _tiny(2, 2, 5, form, rho=10.0)
+        A = O.instance_matrix(inst)
+        fac = O.LDLT(A, O.block_signs(form, inst.n, inst.m))
+        Ad = A.toarray()
+        exact = np.linalg.norm(Ad, 1) * np.linalg.norm(np.linalg.inv(Ad), 1)
+        est = O.cond1_estimate(A, fac)
+        assert exact / 3.0 <= est <= exact * (1 + 1e-10)
+    d = rng.uniform(0.1, 10.0, 12) * rng.choice([-1.0, 1.0], 12)
+    D = sp.diags(d, format="csc")
+    est = O.cond1_estimate(D, O.LDLT(D, np.where(d > 0, 1, -1).astype(np.int32)))
+    assert est == pytest.approx(np.max(np.abs(d)) / np.min(np.abs(d)), rel=1e-12)
