@@ -171,8 +171,10 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
     con0 += I.m;
   }
 
-  // order by (key, type, a, b): a counting sort by column, then each
-  // column's few contributions by (row, type, a, b), columns in parallel
+  // order by (key, type, a, b): a counting sort by column (the scatter in
+  // parallel, in any order), then each column's few contributions by (row,
+  // type, a, b), a total order, so the result does not depend on the scatter
+  std::vector<int64_t> cp((size_t)P.dim + 1, 0);
   {
     auto less = [](const Contrib& x, const Contrib& y) {
       if (x.key != y.key) return x.key < y.key;
@@ -180,14 +182,18 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
       if (x.a != y.a) return x.a < y.a;
       return x.b < y.b;
     };
-    std::vector<int64_t> cp((size_t)P.dim + 1, 0);
-    for (const Contrib& c : C) cp[c.key / D + 1]++;
-    for (int64_t i = 0; i < P.dim; i++) cp[i + 1] += cp[i];
+    std::vector<std::atomic<int64_t>> cnt((size_t)P.dim);
+    for (auto& x : cnt) x.store(0, std::memory_order_relaxed);
+    const int64_t nc = (int64_t)C.size();
+    parallel_ranges(nc, 1 << 16, [&](int64_t lo, int64_t hi) {
+      for (int64_t q = lo; q < hi; q++) cnt[C[q].key / D].fetch_add(1, std::memory_order_relaxed);
+    });
+    for (int64_t i = 0; i < P.dim; i++) cp[i + 1] = cp[i] + cnt[i].load(std::memory_order_relaxed);
+    for (int64_t i = 0; i < P.dim; i++) cnt[i].store(cp[i], std::memory_order_relaxed);
     std::vector<Contrib> S(C.size());
-    {
-      std::vector<int64_t> f(cp.begin(), cp.end() - 1);
-      for (const Contrib& c : C) S[f[c.key / D]++] = c;
-    }
+    parallel_ranges(nc, 1 << 16, [&](int64_t lo, int64_t hi) {
+      for (int64_t q = lo; q < hi; q++) S[cnt[C[q].key / D].fetch_add(1, std::memory_order_relaxed)] = C[q];
+    });
     std::vector<Contrib>().swap(C);
     parallel_ranges(P.dim, 4096, [&](int64_t lo, int64_t hi) {
       for (int64_t c = lo; c < hi; c++)
@@ -196,13 +202,26 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
     C.swap(S);
   }
 
-  // group into entries (sizes counted first)
-  size_t nent = 0, npair = 0;
-  for (size_t q = 0; q < C.size(); q++) {
-    if (q == 0 || C[q].key != C[q - 1].key) nent++;
-    if (C[q].type == 4) npair++;
+  // group into entries, column by column in parallel: count the entries and
+  // products of each column, then fill at the prefix offsets
+  std::vector<int64_t> eoff((size_t)P.dim + 1, 0), poff((size_t)P.dim + 1, 0);
+  parallel_ranges(P.dim, 4096, [&](int64_t lo, int64_t hi) {
+    for (int64_t c = lo; c < hi; c++) {
+      int64_t ne = 0, np = 0;
+      for (int64_t q = cp[c]; q < cp[c + 1]; q++) {
+        if (q == cp[c] || C[q].key != C[q - 1].key) ne++;
+        if (C[q].type == 4) np++;
+      }
+      eoff[c + 1] = ne;
+      poff[c + 1] = np;
+    }
+  });
+  for (int64_t c = 0; c < P.dim; c++) {
+    eoff[c + 1] += eoff[c];
+    poff[c + 1] += poff[c];
   }
-  P.A_colptr.assign(P.dim + 1, 0);
+  const size_t nent = (size_t)eoff[P.dim], npair = (size_t)poff[P.dim];
+  P.A_colptr.assign(eoff.begin(), eoff.end());
   P.A_row.resize(nent);
   P.e_h.resize(nent);
   P.e_j.resize(nent);
@@ -212,35 +231,37 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
   P.pair_ptr[0] = 0;
   P.pair_p.resize(npair);
   P.pair_q.resize(npair);
-  size_t k = 0, e = 0, np = 0;
-  while (k < C.size()) {
-    uint64_t key = C[k].key;
-    int64_t col = (int64_t)(key / D), rw = (int64_t)(key % D);
-    int32_t h = -1, j = -1, var = -1;
-    int8_t kind = DIAG_NONE;
-    for (; k < C.size() && C[k].key == key; k++) {
-      const Contrib& c = C[k];
-      switch (c.type) {
-        case 0: h = c.a; break;
-        case 1: j = c.a; break;
-        case 2: kind = DIAG_PRIMAL; var = c.a; break;
-        case 3: kind = DIAG_DUAL; var = c.a; break;
-        case 4:
-          P.pair_p[np] = c.a;
-          P.pair_q[np++] = c.b;
-          break;
+  parallel_ranges(P.dim, 4096, [&](int64_t lo, int64_t hi) {
+    for (int64_t c = lo; c < hi; c++) {
+      int64_t e = eoff[c], np = poff[c];
+      int64_t k = cp[c];
+      while (k < cp[c + 1]) {
+        const uint64_t key = C[k].key;
+        int32_t h = -1, j = -1, var = -1;
+        int8_t kind = DIAG_NONE;
+        for (; k < cp[c + 1] && C[k].key == key; k++) {
+          const Contrib& ct = C[k];
+          switch (ct.type) {
+            case 0: h = ct.a; break;
+            case 1: j = ct.a; break;
+            case 2: kind = DIAG_PRIMAL; var = ct.a; break;
+            case 3: kind = DIAG_DUAL; var = ct.a; break;
+            case 4:
+              P.pair_p[np] = ct.a;
+              P.pair_q[np++] = ct.b;
+              break;
+          }
+        }
+        P.A_row[e] = (int32_t)(key % D);
+        P.e_h[e] = h;
+        P.e_j[e] = j;
+        P.e_kind[e] = kind;
+        P.e_var[e] = var;
+        P.pair_ptr[e + 1] = np;
+        e++;
       }
     }
-    P.A_row[e] = (int32_t)rw;
-    P.e_h[e] = h;
-    P.e_j[e] = j;
-    P.e_kind[e] = kind;
-    P.e_var[e] = var;
-    P.pair_ptr[e + 1] = (int64_t)np;
-    e++;
-    P.A_colptr[col + 1]++;
-  }
-  for (int64_t c = 0; c < P.dim; c++) P.A_colptr[c + 1] += P.A_colptr[c];
+  });
   P.nnzA = (int64_t)P.A_row.size();
   if (P.nnzA >= INT32_MAX) throw PatternError("pattern: too many KKT entries");
   std::vector<Contrib>().swap(C);
