@@ -89,19 +89,6 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
   if (hoff >= INT32_MAX || joff >= INT32_MAX) throw PatternError("pattern: too many values");
 
   const uint64_t D = (uint64_t)P.dim;
-  std::vector<Contrib> C;
-  size_t reserve = 0;
-  for (int i = 0; i < in.count; i++) {
-    const Instance& I = P.inst[i];
-    reserve += I.nnzH + I.n + I.m;
-    if (in.form == 0) reserve += I.nnzJ;
-    else
-      for (int r = 0; r < I.m; r++) {
-        int64_t k = in.J_rowptr[i][r + 1] - in.J_rowptr[i][r];
-        reserve += k * (k + 1) / 2;
-      }
-  }
-  C.reserve(reserve);
   P.row_inst.assign(P.dim, 0);
   P.row_sign.assign(P.dim, 1);
   P.H_row.resize(hoff);
@@ -113,62 +100,110 @@ void build_pattern(const AnalyzeInput& in, Plan& P) {
   P.con_row.assign(coff, -1);
   P.J_rowptr_all.assign(coff + 1, 0);
 
-  int64_t con0 = 0;
+  // validation, in the order the pattern is read
   for (int i = 0; i < in.count; i++) {
     const Instance& I = P.inst[i];
     const int32_t* Hp = in.H_rowptr[i];
     const int32_t* Hc = in.H_colind[i];
     const int32_t* Jp = in.J_rowptr[i];
     const int32_t* Jc = in.J_colind[i];
-    for (int64_t r = 0; r < I.dim; r++) {
-      P.row_inst[I.row_off + r] = i;
-      P.row_sign[I.row_off + r] = (in.form == 0 && r >= I.n) ? -1 : 1;
-    }
     for (int32_t r = 0; r < I.n; r++) {
-      P.var_row[I.S_off + r] = (int32_t)(I.row_off + r);
       if (Hp[r + 1] < Hp[r]) throw PatternError("pattern: H_rowptr decreasing");
       for (int32_t p = Hp[r]; p < Hp[r + 1]; p++) {
         int32_t c = Hc[p];
         if (c < 0 || c > r) throw PatternError("pattern: H entry outside the lower triangle");
         if (p > Hp[r] && c <= Hc[p - 1]) throw PatternError("pattern: H columns not sorted/unique");
-        uint64_t gr = I.row_off + r, gc = I.row_off + c;
-        C.push_back({gc * D + gr, (int32_t)(I.H_off + p), 0, 0});
-        P.H_row[I.H_off + p] = (int32_t)gr;
-        P.H_col[I.H_off + p] = (int32_t)gc;
       }
-      uint64_t g = I.row_off + r;
-      C.push_back({g * D + g, (int32_t)(I.S_off + r), 0, 2});
     }
     for (int32_t r = 0; r < I.m; r++) {
       if (Jp[r + 1] < Jp[r]) throw PatternError("pattern: J_rowptr decreasing");
-      int64_t con = con0 + r;
-      P.J_rowptr_all[con + 1] = P.J_rowptr_all[con] + (Jp[r + 1] - Jp[r]);
       for (int32_t p = Jp[r]; p < Jp[r + 1]; p++) {
         int32_t c = Jc[p];
         if (c < 0 || c >= I.n) throw PatternError("pattern: J column out of range");
         if (p > Jp[r] && c <= Jc[p - 1]) throw PatternError("pattern: J columns not sorted/unique");
-        P.J_col[I.J_off + p] = (int32_t)(I.row_off + c);
-        P.J_inst[I.J_off + p] = i;
-        P.J_row[I.J_off + p] = (int32_t)con;
-      }
-      if (in.form == 0) {
-        uint64_t gr = I.row_off + I.n + r;
-        P.con_row[con] = (int32_t)gr;
-        for (int32_t p = Jp[r]; p < Jp[r + 1]; p++) {
-          uint64_t gc = I.row_off + Jc[p];
-          C.push_back({gc * D + gr, (int32_t)(I.J_off + p), 0, 1});
-        }
-        C.push_back({gr * D + gr, i, 0, 3});
-      } else {
-        // rho * J^T J: every pair of entries of one constraint row
-        for (int32_t s = Jp[r]; s < Jp[r + 1]; s++)
-          for (int32_t t = Jp[r]; t <= s; t++) {
-            uint64_t gr = I.row_off + Jc[s], gc = I.row_off + Jc[t];
-            C.push_back({gc * D + gr, (int32_t)(I.J_off + s), (int32_t)(I.J_off + t), 4});
-          }
       }
     }
-    con0 += I.m;
+  }
+
+  // contributions: one work unit per H row and per J row of every instance,
+  // each writing its contributions at a prefix offset (units in parallel)
+  std::vector<int64_t> unit_off(in.count + 1, 0);   // first unit of each instance
+  for (int i = 0; i < in.count; i++) unit_off[i + 1] = unit_off[i] + P.inst[i].n + P.inst[i].m;
+  const int64_t nunits = unit_off[in.count];
+  std::vector<int64_t> coff_u((size_t)nunits + 1, 0);
+  {
+    int64_t u = 0, con = 0;
+    for (int i = 0; i < in.count; i++) {
+      const Instance& I = P.inst[i];
+      const int32_t* Hp = in.H_rowptr[i];
+      const int32_t* Jp = in.J_rowptr[i];
+      for (int32_t r = 0; r < I.n; r++, u++) coff_u[u + 1] = (Hp[r + 1] - Hp[r]) + 1;
+      for (int32_t r = 0; r < I.m; r++, u++, con++) {
+        const int64_t k = Jp[r + 1] - Jp[r];
+        coff_u[u + 1] = in.form == 0 ? k + 1 : k * (k + 1) / 2;
+        P.J_rowptr_all[con + 1] = P.J_rowptr_all[con] + k;
+      }
+    }
+    for (int64_t q = 0; q < nunits; q++) coff_u[q + 1] += coff_u[q];
+  }
+  std::vector<Contrib> C((size_t)coff_u[nunits]);
+  std::vector<int64_t> con0(in.count + 1, 0);
+  for (int i = 0; i < in.count; i++) con0[i + 1] = con0[i] + P.inst[i].m;
+  parallel_ranges(nunits, 4096, [&](int64_t u0, int64_t u1) {
+    int i = (int)(std::upper_bound(unit_off.begin(), unit_off.end(), u0) - unit_off.begin()) - 1;
+    for (int64_t u = u0; u < u1; u++) {
+      while (u >= unit_off[i + 1]) i++;
+      const Instance& I = P.inst[i];
+      const int32_t* Hp = in.H_rowptr[i];
+      const int32_t* Hc = in.H_colind[i];
+      const int32_t* Jp = in.J_rowptr[i];
+      const int32_t* Jc = in.J_colind[i];
+      int64_t q = coff_u[u];
+      const int64_t lu = u - unit_off[i];
+      if (lu < I.n) {
+        const int32_t r = (int32_t)lu;
+        P.var_row[I.S_off + r] = (int32_t)(I.row_off + r);
+        for (int32_t p = Hp[r]; p < Hp[r + 1]; p++) {
+          const uint64_t gr = I.row_off + r, gc = I.row_off + Hc[p];
+          C[q++] = {gc * D + gr, (int32_t)(I.H_off + p), 0, 0};
+          P.H_row[I.H_off + p] = (int32_t)gr;
+          P.H_col[I.H_off + p] = (int32_t)gc;
+        }
+        const uint64_t g = I.row_off + r;
+        C[q++] = {g * D + g, (int32_t)(I.S_off + r), 0, 2};
+      } else {
+        const int32_t r = (int32_t)(lu - I.n);
+        const int64_t con = con0[i] + r;
+        for (int32_t p = Jp[r]; p < Jp[r + 1]; p++) {
+          P.J_col[I.J_off + p] = (int32_t)(I.row_off + Jc[p]);
+          P.J_inst[I.J_off + p] = i;
+          P.J_row[I.J_off + p] = (int32_t)con;
+        }
+        if (in.form == 0) {
+          const uint64_t gr = I.row_off + I.n + r;
+          P.con_row[con] = (int32_t)gr;
+          for (int32_t p = Jp[r]; p < Jp[r + 1]; p++) {
+            const uint64_t gc = I.row_off + Jc[p];
+            C[q++] = {gc * D + gr, (int32_t)(I.J_off + p), 0, 1};
+          }
+          C[q++] = {gr * D + gr, i, 0, 3};
+        } else {
+          // rho * J^T J: every pair of entries of one constraint row
+          for (int32_t a = Jp[r]; a < Jp[r + 1]; a++)
+            for (int32_t b = Jp[r]; b <= a; b++) {
+              const uint64_t gr = I.row_off + Jc[a], gc = I.row_off + Jc[b];
+              C[q++] = {gc * D + gr, (int32_t)(I.J_off + a), (int32_t)(I.J_off + b), 4};
+            }
+        }
+      }
+    }
+  });
+  for (int i = 0; i < in.count; i++) {
+    const Instance& I = P.inst[i];
+    for (int64_t r = 0; r < I.dim; r++) {
+      P.row_inst[I.row_off + r] = i;
+      P.row_sign[I.row_off + r] = (in.form == 0 && r >= I.n) ? -1 : 1;
+    }
   }
 
   // order by (key, type, a, b): a counting sort by column (the scatter in
