@@ -72,7 +72,10 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
 // (lane = row, the published values by shuffles); the diagonal block-row
 // L_BB is then solved inside the CTA sub-block by sub-block with the
 // inverted 32 x 32 diagonal blocks, its strictly lower part staged in shared
-// memory while the CTA waits.
+// memory while the CTA waits (only when it has more than one sub-block).
+// Levels whose supernodes all have a single block-row launch the
+// instantiation without the cross-block-row part (MULTI = false), which
+// needs far fewer registers.
 // ---------------------------------------------------------------------------
 constexpr long long CHAIN_WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
 
