@@ -213,3 +213,46 @@ def test_next_row_entry_points_check_their_arguments_on_the_host():
             assert lib.ncl_kkt_k1s_slack_step(h, 1, None, 0, None, 0, None, 0, None) == 5
         finally:
             nk.ncl_kkt_destroy(h)
+
+
+def _csr(rows, n_cols):
+    """CSR (rowptr, colind) from a list of sorted column lists."""
+    rp = np.zeros(len(rows) + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.array([c for r in rows for c in r], np.int32)
+    return rp, ci
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_symbolic_counts_on_degenerate_patterns(form):
+    """Patterns outside the grids: empty constraint rows, rows of H without
+    a diagonal entry, no constraints at all, and two disconnected parts; the
+    library's nnz(L) under its own permutation equals the oracle's."""
+    import types
+    cases = [
+        # n = 5, m = 3 with an empty J row and H rows without diagonal
+        ([[0], [], [0, 2], [3], [1, 4]], [[0, 2], [], [3, 4]], 5),
+        # no constraints
+        ([[0], [0, 1], [2], [1, 3]], [], 4),
+        # two disconnected parts (H and J both split)
+        ([[0], [0, 1], [2], [2, 3], [4]], [[0, 1], [2, 3], [4]], 5),
+        # a single variable, a single constraint
+        ([[0]], [[0]], 1),
+    ]
+    for Hrows, Jrows, n in cases:
+        Hp, Hi = _csr(Hrows, n)
+        Jp, Ji = _csr(Jrows, n) if Jrows else (np.zeros(1, np.int32), np.zeros(0, np.int32))
+        m = len(Jrows)
+        pat = types.SimpleNamespace(n=n, m=m, H_rowptr=Hp, H_colind=Hi, J_rowptr=Jp, J_colind=Ji,
+                                    nnz_H=int(Hp[-1]), nnz_J=int(Jp[-1]))
+        inst = _structural(pat, "stabilized" if form == 0 else "condensed")
+        h = _host(form, pat)
+        try:
+            ai = nk.ncl_kkt_get_analysis_info(h)
+            perm = nk.ncl_kkt_get_permutation(h, ai.dim)
+            assert sorted(perm.tolist()) == list(range(ai.dim))
+            fac = O.LDLT(O.instance_matrix(inst), O.block_signs(inst.form, inst.n, inst.m), perm=perm)
+            assert ai.nnz_L == fac.nnz_L
+            assert ai.flops == pytest.approx(fac.flops, rel=1e-12)
+        finally:
+            nk.ncl_kkt_destroy(h)
