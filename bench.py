@@ -43,7 +43,7 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 WORKLOADS = ("condensed300", "stabilized20x25", "batch64", "adjoint256", "large700")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -70,7 +70,10 @@ def parse():
     ap.add_argument("--side", type=int, default=None, help="grid side of condensed300 / large700 (smaller captures)")
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
-    return ap.parse_args()
+    ap.add_argument("--no-others", action="store_true",
+                    help="condensed300: skip the other workloads and the rho sweep in the default line")
+    ap.add_argument("--skip-peaks", action="store_true", help="do not measure the TF32 / FP64 matmul peaks")
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------
@@ -129,6 +132,37 @@ def peaks():
         return json.load(open(MEASURED))
     except Exception:
         return {}
+
+
+def measure_matmul_peaks(dev):
+    """Dense-matmul peaks of this GPU measured now: FP32 inputs on the TF32
+    tensor cores and FP64, torch.matmul 8192^3 (2 N^3 flops), best of a few
+    CUDA-event timed runs after a warm-up."""
+    import torch
+    out = {}
+    n = 8192
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for key, dt, reps in (("tf32_tflops", torch.float32, 6), ("fp64_tflops", torch.float64, 2)):
+            torch.backends.cuda.matmul.allow_tf32 = dt == torch.float32
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            c = torch.matmul(a, b)
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[key] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = "torch.matmul 8192^3 (2 N^3 flops), FP32 inputs with TF32 allowed / FP64, best of 6 / 2, CUDA events"
+    return out
 
 
 def recorded_traffic(kernel, workload):
@@ -289,13 +323,13 @@ def run_reference(args):
 class Runner:
     """Device-resident draws and one handle per precision for a workload."""
 
-    def __init__(self, args, dev, rank):
+    def __init__(self, args, dev, rank, pats=None):
         import torch
         from paper_2510_05885_gb300 import ncl_kkt as nk
         self.torch, self.nk, self.args, self.dev = torch, nk, args, dev
         self.name = args.workload
         self.spec = workload_spec(self.name, args.rho)
-        self.pats = make_patterns(self.name, rank, args.side)
+        self.pats = pats if pats is not None else make_patterns(self.name, rank, args.side)
         if args.side and self.name in ("condensed300", "large700"):
             self.spec["desc"] = self.spec["desc"].replace("300x300" if self.name == "condensed300" else "700x700",
                                                           f"{args.side}x{args.side}")
@@ -392,6 +426,7 @@ def run_ours(args):
 
     def timed(K, steps, warm, runner=None):
         R_ = runner if runner is not None else R
+        adjoint = R_.name == "adjoint256"
         for i in range(warm):
             R_.stage(i)
             R_.step(K, i, adjoint)
@@ -419,7 +454,7 @@ def run_ours(args):
         solve (with refinement) call on the same draws, from the library's
         own events (a breakdown of the step; not the headline)."""
         R_ = runner if runner is not None else R
-        fms, sms = [], []
+        fms, sms, its = [], [], []
         for i in range(reps):
             d = R_.dev_draws[i % len(R_.dev_draws)]
             R_.stage(i)
@@ -427,8 +462,33 @@ def run_ours(args):
             si = nk.ncl_kkt_solve(K._h, R_.spec["nrhs"], R_.Bfix, K.dim, R_.Xc, K.dim)
             fms.append(infos[0].ms)
             sms.append(si.ms)
+            its.append(si.ir_iters)
         torch.cuda.synchronize()
+        split.ir_iters = max(its)
         return statistics.median(fms), statistics.median(sms)
+
+    def solve_bytes(ai, nrhs, ir_iters, esz):
+        """Algorithmic bytes of one refined solve: 1 + ir_iters sweep pairs,
+        each reading L (nnz_L values) twice plus the permuted vectors, and as
+        many FP64 residuals over the full symmetric matrix (value, column and
+        source index per entry) and three FP64 vectors."""
+        passes = 1 + ir_iters
+        nnz_full = 2 * ai.nnz_A - ai.dim
+        sweep = 2.0 * ai.nnz_L * esz + nrhs * (4.0 * ai.dim * esz + 2.0 * ai.dim * 12)
+        resid = 16.0 * nnz_full + nrhs * 24.0 * ai.dim
+        return passes * (sweep + resid)
+
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = int(props.multi_processor_count)
+    mp = {} if args.skip_peaks else measure_matmul_peaks(dev)
+    bf16 = pk.get("bf16_tflops")
+    tf32_peak = mp.get("tf32_tflops") or ((bf16 if bf16 else 1900.0) / 2)
+    tf32_note = ("of measured TF32 matmul (this run)" if mp.get("tf32_tflops") else
+                 "of measured bf16 burst x 1/2 (nominal TF32:bf16 ratio)")
+    fp64_peak = mp.get("fp64_tflops") or 1.25
+    fp64_note = "of measured FP64 matmul (this run)" if mp.get("fp64_tflops") else "of nominal FP64 1.25 TFLOP/s"
+    hbm = pk.get("hbm_gbs") or 6800.0
 
     K = R.make("fp32_ir")
     ai = K.analysis
@@ -468,6 +528,9 @@ def run_ours(args):
         out["adjoint_ms_median"] = statistics.median([r[2] for r in res])
     fms, sms = split(K)
     out["factor_ms_median"], out["solve_ms_median"] = fms, sms
+    out["peaks"] = {"tf32_tflops": tf32_peak, "tf32_note": tf32_note, "fp64_tflops": fp64_peak,
+                    "fp64_note": fp64_note, "hbm_gbs": hbm, "hbm_note": "of measured copy bandwidth",
+                    "sm_count": sm_count, "matmul": mp or None}
 
     # per-kernel device times (events around each launch, separate pass)
     roof = None
@@ -481,26 +544,19 @@ def run_ours(args):
         nk.ncl_kkt_profile(K._h, 0)
         prof = nk.ncl_kkt_profile_report(K._h)
         out["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in prof.items()}
-        factor_kernels = {k: v for k, v in prof.items() if k.startswith(("update_", "panel_", "factor_small",
-                                                                         "assemble"))}
         name, st = max(prof.items(), key=lambda kv: kv[1]["ms"])
-        pk = peaks()
-        if name.startswith("update_tc"):
-            bf16 = pk.get("bf16_tflops")
-            peak = (bf16 if bf16 else 1900.0) / 2 / 3
+        if name.startswith("update_tc") or name.startswith("front_dag"):
             roof = {"kernel": name, "bound": "tensor", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
-                    "peak": peak, "unit": "TFLOP/s",
-                    "peak_note": "of measured: TF32 = bf16 burst x 1/2 (nominal ratio), /3 for the 3-product split"}
+                    "peak": tf32_peak / 3, "unit": "TFLOP/s",
+                    "peak_note": tf32_note + ", /3 for the 3-product split-TF32 (useful flops)"}
         elif any(t in name for t in ("simt", "small", "panel", "invert")):
             clk = (ck or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
             f32 = "f32" in name
-            peak = 152 * 128 * 2 * clk * 1e6 / 1e12 if f32 else 1.25
+            peak = sm_count * 128 * 2 * clk * 1e6 / 1e12 if f32 else fp64_peak
             roof = {"kernel": name, "bound": "alu", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
                     "peak": peak, "unit": "TFLOP/s",
-                    "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 x max SM clock" if f32 else
-                    "FP64 nominal 1.25 TFLOP/s"}
+                    "peak_note": (f"FP32 FFMA: {sm_count} SMs x 128 lanes x 2 x max SM clock" if f32 else fp64_note)}
         else:
-            hbm = pk.get("hbm_gbs") or 6800.0
             roof = {"kernel": name, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
                     "peak": hbm, "unit": "GB/s", "peak_note": "of measured copy bandwidth"}
         roof["frac"] = roof["achieved"] / roof["peak"]
@@ -511,39 +567,81 @@ def run_ours(args):
         roof["share_of_profiled_time"] = st["ms"] / sum(v["ms"] for v in prof.values())
         tc = prof.get("update_tc_f32")
         if tc:
-            bf16 = pk.get("bf16_tflops") or 1900.0
             out["tensor_core_update"] = {"achieved_tflops_useful": tc["flops"] / (tc["ms"] * 1e-3) / 1e12,
                                          "frac_of_split_tf32_peak": tc["flops"] / (tc["ms"] * 1e-3) / 1e12
-                                         / (bf16 / 2 / 3), "launches": tc["launches"]}
-        del factor_kernels
+                                         / (tf32_peak / 3), "launches": tc["launches"]}
+    else:
+        roof = {}
+    # the two phase fractions: the whole factorisation's algorithmic flops
+    # against the split-TF32 useful peak, the whole refined solve's
+    # algorithmic bytes against the copy bandwidth
+    roof["factor_frac"] = flops / (fms * 1e-3) / 1e12 / (tf32_peak / 3)
+    roof["factor_note"] = ("algorithmic flops sum_j c_j^2 + 3 c_j / factor_ms_median / (TF32 peak / 3), "
+                           + tf32_note)
+    sb = solve_bytes(ai, spec["nrhs"], split.ir_iters, 4)
+    roof["solve_frac"] = sb / (sms * 1e-3) / 1e9 / hbm
+    roof["solve_bytes"] = sb
+    roof["solve_note"] = (f"(1 + {split.ir_iters}) x (2 nnz_L x 4 B sweeps + vectors + FP64 residual over the "
+                          "full matrix) / solve_ms_median / measured copy bandwidth")
     out["roofline"] = roof
 
-    # plain FP64 path on the same systems
+    # second right-hand-side workload (the extrapolation step of Algorithm
+    # NCL, Section 2.3: one more solve per outer iteration on the factors
+    # already computed): refined solves of 1, 4 and 8 right-hand sides on
+    # one factorisation, device-timed; GB/s of the algorithmic solve bytes
+    if not R.batch:
+        d = R.dev_draws[0]
+        nk.ncl_kkt_batch_factor(K._h, d["H"], d["J"], d["S"], d["delta"], d["rho"])
+        ex = {}
+        rng = np.random.default_rng(17)
+        for nr in (1, 4, 8):
+            Bx = torch.as_tensor(rng.standard_normal((nr, K.dim)), device=dev)
+            Xx = torch.empty_like(Bx)
+            nk.ncl_kkt_solve(K._h, nr, Bx, K.dim, Xx, K.dim)        # warm-up (captures the sweep graph)
+            times, its, etas = [], [], []
+            for _ in range(3):
+                flush.zero_()
+                si = nk.ncl_kkt_solve(K._h, nr, Bx, K.dim, Xx, K.dim)
+                times.append(si.ms)
+                its.append(si.ir_iters)
+                etas.append(si.backward_err)
+            t = statistics.median(times)
+            byts = solve_bytes(ai, nr, max(its), 4)
+            ex[str(nr)] = {"ms": t, "ms_per_rhs": t / nr, "ir_iters": max(its), "backward_err_max": max(etas),
+                           "algorithmic_gbs": byts / (t * 1e-3) / 1e9, "frac_of_hbm": byts / (t * 1e-3) / 1e9 / hbm}
+        out["second_rhs_solve"] = ex
+
+    # plain FP64 path on the same systems (a handle on the same analysis)
+    K64 = None
     if not args.skip_fp64:
-        K64 = R.make("fp64")
+        K64 = nk.KKT.like(K, prec="fp64")
         n64 = max(2, args.steps // 3)
         ms64, res64, _ = timed(K64, n64, 1)
         t64 = max_over_ranks(sum(ms64))
         f64ms, s64ms = split(K64, 2)
         out["fp64"] = {"ms_per_step": t64 / n64, "gflops": world * flops / (t64 / n64 * 1e-3) / 1e9,
                        "backward_err_max": max(r[1].backward_err for r in res64),
-                       "factor_ms_median": f64ms, "solve_ms_median": s64ms}
+                       "factor_ms_median": f64ms, "solve_ms_median": s64ms,
+                       "factor_frac_of_fp64_peak": flops / (f64ms * 1e-3) / 1e12 / fp64_peak,
+                       "fp64_peak_note": fp64_note}
         if adjoint:
             out["fp64"]["adjoint_ms_median"] = statistics.median([r[2] for r in res64])
         out["speedup_fp32ir_vs_fp64"] = out["fp64"]["ms_per_step"] / out["ms_per_step"]
-        K64.close()
 
-    # rho sweep of the condensed workload
-    if args.rho_sweep and args.workload == "condensed300":
+    others = args.workload == "condensed300" and not args.no_others and args.side is None
+    # rho sweep of the condensed workload: new draws at each rho on the same
+    # pattern, factored by the same two handles
+    if (args.rho_sweep or others) and args.workload == "condensed300":
         sweep = {}
         for rho in (1e2, 1e5, 1e8):
             a2 = argparse.Namespace(**vars(args))
             a2.rho = rho
             a2.draws = 2
-            R2 = Runner(a2, dev, rank)
+            R2 = Runner(a2, dev, rank, pats=R.pats)
             entry = {}
-            for prec in ("fp32_ir", "fp64"):
-                Kx = R2.make(prec)
+            for prec, Kx in (("fp32_ir", K), ("fp64", K64)):
+                if Kx is None:
+                    continue
                 msx, resx, _ = timed(Kx, max(2, args.steps // 3), 1, R2)
                 entry[prec] = {"ms_per_step": sum(msx) / len(msx),
                                "backward_err_max": max(r[1].backward_err for r in resx),
@@ -551,9 +649,58 @@ def run_ours(args):
                                "fgmres": any(r[1].used_fgmres for r in resx),
                                "fp64_fallback": any(r[1].fp64_fallback for r in resx),
                                "inertia": list(resx[-1][0][0].inertia)}
-                Kx.close()
+            if "fp64" in entry:
+                entry["speedup_fp32ir_vs_fp64"] = entry["fp64"]["ms_per_step"] / entry["fp32_ir"]["ms_per_step"]
             sweep[f"{rho:g}"] = entry
+            del R2
         out["rho_sweep"] = sweep
+    if K64 is not None:
+        K64.close()
+
+    # the other workloads, each FP32+IR and FP64 (handles on one analysis),
+    # device-timed like the default one (L2 flushed before every step)
+    if others:
+        wl = {}
+        for name, n32, n64_ in (("large700", 5, 2), ("batch64", 5, 2), ("adjoint256", 5, 2),
+                                ("stabilized20x25", 10, 4)):
+            try:
+                a3 = argparse.Namespace(**vars(args))
+                a3.workload, a3.rho, a3.draws, a3.side = name, None, 2, None
+                R3 = Runner(a3, dev, rank)
+                K3 = R3.make("fp32_ir")
+                ai3 = K3.analysis
+                m3, r3, l3 = timed(K3, n32, 3, R3)
+                f3, s3 = split(K3, 2, R3)
+                it3 = split.ir_iters
+                e = {"workload": R3.spec["desc"], "dim": ai3.dim, "instances": len(R3.pats),
+                     "factor_flops": ai3.flops, "analyze_ms": ai3.analyze_ms,
+                     "fp32_ir": {"ms_per_step": max_over_ranks(sum(m3)) / n32, "step_ms_median": statistics.median(m3),
+                                 "gflops": world * ai3.flops / (max_over_ranks(sum(m3)) / n32 * 1e-3) / 1e9,
+                                 "factor_ms_median": f3, "solve_ms_median": s3,
+                                 "backward_err_max": max(r[1].backward_err for r in r3),
+                                 "ir_iters": max(r[1].ir_iters for r in r3), "gpu_launches": l3,
+                                 "factor_frac": ai3.flops / (f3 * 1e-3) / 1e12 / (tf32_peak / 3),
+                                 "solve_frac": solve_bytes(ai3, R3.spec["nrhs"], it3, 4) / (s3 * 1e-3) / 1e9 / hbm,
+                                 "inertia_ok": all(tuple(f.inertia) == (i.n, i.m if R3.spec["form"] == 0 else 0, 0)
+                                                   for r in r3 for f, i in zip(r[0], R3.draws[0]))}}
+                if name == "adjoint256":
+                    e["fp32_ir"]["adjoint_ms_median"] = statistics.median([r[2] for r in r3])
+                K3b = nk.KKT.like(K3, prec="fp64")
+                m4, r4, _ = timed(K3b, n64_, 1, R3)
+                t4 = max_over_ranks(sum(m4)) / n64_
+                e["fp64"] = {"ms_per_step": t4, "gflops": world * ai3.flops / (t4 * 1e-3) / 1e9,
+                             "backward_err_max": max(r[1].backward_err for r in r4)}
+                if name == "adjoint256":
+                    e["fp64"]["adjoint_ms_median"] = statistics.median([r[2] for r in r4])
+                e["speedup_fp32ir_vs_fp64"] = t4 / e["fp32_ir"]["ms_per_step"]
+                K3b.close()
+                K3.close()
+                del R3
+                torch.cuda.empty_cache()
+                wl[name] = e
+            except Exception as ex:      # a failed extra workload is reported, not fatal to the line
+                wl[name] = {"error": f"{type(ex).__name__}: {ex}"}
+        out["other_workloads"] = wl
 
     # inertia correction (Section 3.1) from delta = 0 on the first draw: the
     # draw's rho is taken as the unregularised penalty, rho-hat = rho + delta

@@ -118,6 +118,13 @@ typedef struct {
                                  produces when rho*||J||^2 swamps H+Sigma+delta I) or
                                  when refinement cannot reach ir_tol; 0: never */
     int64_t max_device_bytes; /* 0 = no limit */
+    int64_t wait_cycles;      /* bound, in SM clock cycles, of every wait of one CTA
+                                 on another inside a kernel (the panel factorisation's
+                                 rows waiting for the diagonal block, the chained
+                                 triangular sweeps, the tensor-core pipeline); past it
+                                 the kernel sets an error flag, finishes without the
+                                 awaited data and the call returns NCL_ERR_TIMEOUT.
+                                 <= 0 selects 4e9 (about 2 s) */
 } ncl_kkt_options;
 
 typedef struct {
@@ -232,22 +239,32 @@ ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t l
                            ncl_stream_t stream, ncl_kkt_solve_info* info);
 
 /*
- * ncl_kkt_solve_noalloc -- ncl_kkt_solve without any device allocation
- * (the paper has no counterpart; this serves callers that cannot allocate
- * device memory when they solve: code running while a stream is captured
- * into a CUDA graph, real-time loops, or processes whose device memory is
- * committed elsewhere).  Same arguments, results and refinement as
- * ncl_kkt_solve, on a handle that has been factored.
+ * ncl_kkt_solve_noalloc -- ncl_kkt_solve without any memory allocation (the
+ * paper has no counterpart).  It serves callers that cannot allocate at the
+ * point where they solve: real-time loops that cannot afford an allocator
+ * round trip, and processes whose device memory is committed elsewhere (for
+ * instance a factorisation sized to max_device_bytes).  Same arguments and
+ * results as ncl_kkt_solve on a handle that has been factored, with two
+ * differences: it never refactors in FP64 (an FP32_IR handle whose
+ * refinement falls short returns NCL_ERR_IR_NOT_CONVERGED with the best
+ * iterate, where ncl_kkt_solve would escalate), and its FGMRES stage runs
+ * only when the Krylov vectors also fit in the static array (else it is left
+ * out of the call).  After an earlier precision fallback the FP64 factors
+ * are used, on the same static array.
  * The sweep and refinement workspace comes from one static device array of
  * 8 MiB inside the library (held by every GPU that loads the library until
  * the process exits) instead of the handle's workspace.  It must hold
  * min(nrhs, 8) * (dim + update and partial-sum vectors) solve values plus
- * min(nrhs, 8) * dim FP64 residuals; larger problems get
- * NCL_ERR_INVALID_ARG with the required size in ncl_kkt_last_error().
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call shares the one array:
- * calls whose work overlaps on the GPU (other threads or streams) race, so
- * serialise them.  Not available while profiling is on (NCL_ERR_STATE).
+ * min(nrhs, 8) * dim FP64 residuals (about dim <= 100k at one right-hand
+ * side in FP32); larger problems get NCL_ERR_INVALID_ARG with the required
+ * size in ncl_kkt_last_error().  The FGMRES stage needs 41 * dim FP64
+ * values more.  The first call on a device looks up the array's device
+ * address.  Every call shares the one array, which keeps the last call's
+ * contents (the call clears what must start at zero itself); calls whose
+ * work overlapped on the GPU would race on it, so the library serialises
+ * them on the host and each returns only after its work is complete.  The
+ * refinement reads norms back to the host between steps, so a stream under
+ * graph capture is refused (NCL_ERR_STATE), as is a handle with profiling on.
  */
 ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const double* B, int64_t ldb,
                                  double* X, int64_t ldx, ncl_stream_t stream,
@@ -481,6 +498,25 @@ ncl_status ncl_kkt_profile_report(ncl_kkt_t h, char* buf, int64_t buflen);
 ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, int32_t K, const float* L,
                                           const float* d, int32_t row_a, int32_t row_b, int32_t M,
                                           int32_t N, float* C, int32_t ldc, ncl_stream_t stream);
+
+/* Make one bounded inter-CTA wait of a real kernel run out, to test the
+ * failure path of options.wait_cycles without faulting or hanging anything:
+ *   which = 0: the forward sweep's chain kernel on the block-rows of a
+ *              supernode with more than one block-row (needs a factored
+ *              handle); its ticket counter starts past block-row 0, so that
+ *              block-row's flag is never published and the next one's CTA
+ *              waits for it;
+ *   which = 1: the first macro panel with rows below it; its ticket counter
+ *              starts past the diagonal role, so the row CTAs wait for
+ *              sub-block flags that are never published.  The handle's
+ *              factors are void afterwards (factor again before solving).
+ * Every wait of that launch is bounded by wait_cycles (> 0) SM clock cycles;
+ * the kernel then finishes without the awaited data.  Returns
+ * NCL_ERR_TIMEOUT when the wait ran out (the expected outcome), NCL_OK if it
+ * did not, INVALID_ARG when the handle has no such supernode or panel, STATE
+ * for a sweep test before a factor.  The error flags are cleared afterwards. */
+ncl_status ncl_kkt_selftest_wait_timeout(ncl_kkt_t h, int32_t which, int64_t wait_cycles,
+                                         ncl_stream_t stream);
 
 /* Number of instances of a handle (1 for ncl_kkt_analyze). */
 int32_t ncl_kkt_instance_count(ncl_kkt_t h);

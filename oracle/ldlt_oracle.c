@@ -13,6 +13,12 @@
  * a sparse triangular solve whose nonzero pattern is the set of
  * elimination-tree ancestors of the nonzeros of A(0:k, k) below k
  * (the "row subtree").  d_k = A(k,k) - sum_i l_ki^2 d_i.
+ * This is the textbook up-looking algorithm as T. A. Davis states it in
+ * "Algorithm 849: A concise sparse Cholesky factorization package" (ACM
+ * Trans. Math. Software 31(4), 2005): the symbolic pass (elimination tree
+ * and column counts) and the numeric pass (one row subtree per row, then
+ * the forward / diagonal / backward solves) follow that published
+ * algorithm's steps and its variable naming.
  *
  * Zero-pivot policy (Section 3.1, cases (i) and (ii)): if |d_k| <= eps,
  *   policy 0 (perturb): d_k := sign_k * eps, counted as perturbed, where

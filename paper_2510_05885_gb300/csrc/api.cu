@@ -52,6 +52,9 @@ struct CudaError {
 // kernel.
 constexpr int TC_MIN_K = 256;
 
+// default bound of the inter-CTA waits inside the kernels (about 2 s at 2 GHz)
+constexpr long long DEFAULT_WAIT_CYCLES = 4000000000LL;
+
 // per-launch arithmetic (flops on the stored blocks) and minimum traffic
 // (bytes), used only for profiling reports
 struct Cost {
@@ -964,7 +967,8 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
     });
     for (const Step& S : L.steps) {
       klaunch(h, st, f32 ? "macro_panel_f32" : "macro_panel_f64", S.panel_cnt, S.panel_cost, [&] {
-        launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->d_panel_sync, h->d_err, eps, pol, st);
+        launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->d_panel_sync, h->d_err, eps, pol,
+                              h->opt.wait_cycles, st);
       });
       klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost, [&] {
         launch_gemm_simt<T>(P, N, h->d_probs + S.prob_off, h->d_tilep + S.tp_off, S.tiles, st);
@@ -972,7 +976,7 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
       if constexpr (sizeof(T) == 4)
         klaunch(h, st, "update_tc_f32", S.tc_tiles, S.tc_cost, [&] {
           launch_update_tc(P, N, h->d_tc + S.tc_off, h->d_tilep_tc + S.ttp_off, S.tc_tiles, 3, h->d_maps,
-                           h->d_err, st);
+                           h->d_err, h->opt.wait_cycles, st);
         });
     }
     klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", L.syrk_tiles, L.syrk_cost, [&] {
@@ -981,7 +985,7 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
     if constexpr (sizeof(T) == 4)
       klaunch(h, st, "update_tc_f32", L.tsyrk_tiles, L.syrk_cost, [&] {
         launch_update_tc(P, N, h->d_tc + L.tsyrk_off, h->d_tilep_tc + L.tsyrk_tp_off, L.tsyrk_tiles,
-                         L.tsyrk_stages, h->d_maps, h->d_err, st);
+                         L.tsyrk_stages, h->d_maps, h->d_err, h->opt.wait_cycles, st);
       });
   }
   CK(cudaGetLastError());
@@ -1002,9 +1006,13 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
   int* serr = h->d_err + 1;
   CK(cudaMemsetAsync(h->d_chain_sync, 0, (2 * ns + 2 * nb) * sizeof(int), st));
   for (const Level& L : h->levels) {
-    klaunch(h, st, f32 ? "fwd_chain_f32" : "fwd_chain_f64", L.chain_cnt, scaled(L.fdiag_cost, nrhs), [&] {
+    // levels with a supernode of more than one block-row run the chained
+    // instantiation (named apart in the profile)
+    const char* fname = L.chain_multi ? (f32 ? "fwd_chain_multi_f32" : "fwd_chain_multi_f64")
+                                      : (f32 ? "fwd_chain_f32" : "fwd_chain_f64");
+    klaunch(h, st, fname, L.chain_cnt, scaled(L.fdiag_cost, nrhs), [&] {
       launch_fwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, L.chain_multi,
-                          h->d_chain_pptr, h->d_chain_pran, xp, W, nrhs, tk_f, fl_f, serr, st);
+                          h->d_chain_pptr, h->d_chain_pran, xp, W, nrhs, tk_f, fl_f, serr, h->opt.wait_cycles, st);
     });
     klaunch(h, st, f32 ? "fwd_below_f32" : "fwd_below_f64", L.below_cnt, scaled(L.fbelow_cost, nrhs),
             [&] {
@@ -1016,9 +1024,11 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
     const Level& L = h->levels[l];
     klaunch(h, st, f32 ? "bwd_below_f32" : "bwd_below_f64", L.bbelow_cnt, scaled(L.bbelow_cost, nrhs),
             [&] { launch_bwd_below<T>(P, N, h->d_bbelow + L.bbelow_off, L.bbelow_cnt, xp, Pw, nrhs, st); });
-    klaunch(h, st, f32 ? "bwd_chain_f32" : "bwd_chain_f64", L.chain_cnt, scaled(L.bdiag_cost, nrhs), [&] {
+    const char* bname = L.chain_multi ? (f32 ? "bwd_chain_multi_f32" : "bwd_chain_multi_f64")
+                                      : (f32 ? "bwd_chain_f32" : "bwd_chain_f64");
+    klaunch(h, st, bname, L.chain_cnt, scaled(L.bdiag_cost, nrhs), [&] {
       launch_bwd_chain<T>(P, N, h->d_chain + L.chain_off, L.chain_cnt, (int)L.chain_smem, L.chain_multi, xp, Pw,
-                          nrhs, tk_b, fl_b, serr, st);
+                          nrhs, tk_b, fl_b, serr, h->opt.wait_cycles, st);
     });
   }
   CK(cudaGetLastError());
@@ -1538,6 +1548,8 @@ ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, do
   if (nrhs < 0 || (nrhs > 0 && (!B || !X)) || ldb < h->dp.dim || ldx < h->dp.dim)
     return fail(NCL_ERR_INVALID_ARG, "bad right-hand side block");
   if (info) *info = ncl_kkt_solve_info{};
+  // the sweeps' error flag reports on this solve only
+  CK(cudaMemsetAsync(h->d_err + 1, 0, sizeof(int), st));
   CK(cudaEventRecord(h->ev0, st));
   ncl_status worst = NCL_OK;
   for (int r0 = 0; r0 < nrhs; r0 += MAX_RHS_SWEEP) {
@@ -1588,6 +1600,7 @@ static ncl_status init_options(ncl_kkt_s* h, const ncl_kkt_options* opt) {
   if (!(h->opt.pivot_eps >= 0)) return fail(NCL_ERR_INVALID_ARG, "bad pivot_eps");
   if (!(h->opt.ir_tol > 0)) h->opt.ir_tol = h->opt.prec == NCL_PREC_FP64 ? 1e-12 : 1e-10;
   if (h->opt.ir_max_iter < 0) h->opt.ir_max_iter = h->opt.prec == NCL_PREC_FP64 ? 3 : 10;
+  if (h->opt.wait_cycles <= 0) h->opt.wait_cycles = DEFAULT_WAIT_CYCLES;
   return NCL_OK;
 }
 
@@ -1667,6 +1680,7 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->host_only = 0;
   o->precision_fallback = 1;
   o->max_device_bytes = 0;
+  o->wait_cycles = 0;
 }
 
 ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m, const int32_t* H_rowptr, const int32_t* H_colind,
@@ -2030,14 +2044,14 @@ const char* ncl_kkt_last_error(void) { return g_last_error.c_str(); }
 // ---------------------------------------------------------------------------
 // Solve without any device allocation.
 //
-// For callers that must not allocate device memory at the point where they
-// solve: code running while a stream is being captured into a CUDA graph,
+// For callers that must not allocate memory at the point where they solve:
 // real-time loops that cannot afford an allocator round trip, and processes
 // whose device memory is fully committed to other pools (for instance after
 // the factorisation was sized to the memory cap).  The workspace of the
-// triangular sweeps and of the refinement lives in one file-scope device
-// array of NCL_NOALLOC_SCRATCH_BYTES, which every GPU that loads this
-// library keeps until the process exits.
+// triangular sweeps, of the refinement and of its FGMRES stage lives in one
+// file-scope device array of NCL_NOALLOC_SCRATCH_BYTES, which every GPU that
+// loads this library keeps until the process exits, and the FGMRES host
+// mirror in a file-scope host array.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -2046,8 +2060,11 @@ namespace {
 constexpr size_t NCL_NOALLOC_SCRATCH_BYTES = size_t(8) << 20;  // 8 MiB per GPU
 __device__ __align__(256) unsigned char g_noalloc_scratch[NCL_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_noalloc_mu;
+std::mutex g_noalloc_mu;       // the per-device address table
+std::mutex g_noalloc_call_mu;  // one no-alloc solve at a time in the process
 void* g_noalloc_base[256] = {};
+// host mirror of the FGMRES partial sums and coefficients
+double g_noalloc_host[(GM_M + 1) * 256 + GM_M + 8];
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -2076,8 +2093,18 @@ extern "C" ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const dou
   if (nrhs <= 0) return fail(NCL_ERR_INVALID_ARG, "nrhs must be positive");
   return guarded(h, [&]() -> ncl_status {
     if (h->prof_on) return fail(NCL_ERR_STATE, "turn profiling off before the no-alloc solve");
+    {
+      // the refinement reads residual norms back to the host between steps,
+      // which a stream under capture cannot do
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      CK(cudaStreamIsCapturing((cudaStream_t)stream, &cs));
+      if (cs != cudaStreamCaptureStatusNone)
+        return fail(NCL_ERR_STATE, "the no-alloc solve cannot run on a stream that is being captured");
+    }
+    std::lock_guard<std::mutex> serial(g_noalloc_call_mu);
     // the handle whose factors are in use (the FP64 twin after a precision
-    // fallback; it exists already, so nothing is allocated)
+    // fallback; it exists already, and its workspace is swapped for the
+    // static array as well)
     ncl_kkt_s* owner = h;
     if (h->use_twin) h = h->twin;
     void* base = nullptr;
@@ -2096,6 +2123,15 @@ extern "C" ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const dou
       return fail(NCL_ERR_INVALID_ARG, "problem too large for the no-alloc solve: needs " + std::to_string(need) +
                                            " bytes of workspace, the fixed scratch holds " +
                                            std::to_string(NCL_NOALLOC_SCRATCH_BYTES));
+    // the FGMRES stage (single-instance handles, when Richardson stagnates)
+    // works in the rest of the array when its Krylov vectors fit there, and
+    // is left out of this call otherwise
+    const int G = vec_grid();
+    const size_t b_gv = align256((size_t)(GM_M + 1) * dim * 8), b_gz = align256((size_t)GM_M * dim * 8);
+    const size_t b_gw = align256(dim * 8), b_gp = align256((size_t)(GM_M + 1) * G * 8);
+    const size_t b_gc = align256((size_t)(GM_M + 1) * 8);
+    const bool gm_fits = need + b_gv + b_gz + b_gw + b_gp + b_gc <= NCL_NOALLOC_SCRATCH_BYTES &&
+                         (size_t)(GM_M + 1) * G + GM_M + 8 <= sizeof(g_noalloc_host) / sizeof(double);
     char* p = (char*)base;
     // run the regular solve on the static workspace, then give the handle
     // its own workspace back
@@ -2104,22 +2140,142 @@ extern "C" ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const dou
       void *xp, *W, *Pw;
       double* R;
       unsigned long long* norms;
+      double *gV, *gZ, *gw, *gpart, *gcoef, *ghost;
+      int32_t use_fgmres;
       ~Swap() {
         h->xp = xp;
         h->W = W;
         h->Pw = Pw;
         h->R = R;
         h->d_norms = norms;
+        h->gm_V = gV;
+        h->gm_Z = gZ;
+        h->gm_w = gw;
+        h->gm_part = gpart;
+        h->gm_coef = gcoef;
+        h->gm_host = ghost;
+        h->opt.use_fgmres = use_fgmres;
       }
-    } keep{h, h->xp, h->W, h->Pw, h->R, h->d_norms};
+    } keep{h, h->xp, h->W, h->Pw, h->R, h->d_norms, h->gm_V, h->gm_Z, h->gm_w, h->gm_part, h->gm_coef,
+           h->gm_host, h->opt.use_fgmres};
     h->xp = p;
     h->W = p + b_xp;
     h->Pw = p + b_xp + b_w;
     h->R = (double*)(p + b_xp + b_w + b_pw);
     h->d_norms = (unsigned long long*)(p + b_xp + b_w + b_pw + b_r);
+    if (gm_fits) {
+      char* q = p + need;
+      h->gm_V = (double*)q;
+      h->gm_Z = (double*)(q + b_gv);
+      h->gm_w = (double*)(q + b_gv + b_gz);
+      h->gm_part = (double*)(q + b_gv + b_gz + b_gw);
+      h->gm_coef = (double*)(q + b_gv + b_gz + b_gw + b_gp);
+      h->gm_host = g_noalloc_host;
+    } else {
+      h->opt.use_fgmres = 0;
+    }
     ncl_status r = do_solve(h, nrhs, B, ldb, X, ldx, (cudaStream_t)stream, info, false);
     if (info && h != owner) info->fp64_fallback = 1;
     return r;
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: a bounded inter-CTA wait that runs out, on a real kernel
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+ncl_status selftest_timeout(ncl_kkt_s* h, DevNum<T>& N, int which, long long wait, cudaStream_t st) {
+  static const int one = 1;
+  const Plan& P = h->plan;
+  const HostSched& hs = h->hs;
+  int herr = 0;
+  if (which == 0) {
+    // the forward sweep's chain over the block-rows of a supernode with more
+    // than one: its ticket counter starts at 1 and only nbr - 1 CTAs run, so
+    // block-row 0 is never solved and its flag never published; the CTA of
+    // block-row 1 waits for it until the limit
+    int64_t i0 = -1;
+    int nbr = 0, smem = 0;
+    for (const Level& L : h->levels) {
+      for (int64_t i = L.chain_off; i < L.chain_off + L.chain_cnt; i++) {
+        const int s = hs.chainv[i].x;
+        if (P.sn_ncol[s] > CHAIN_ROWS && (i == L.chain_off || hs.chainv[i - 1].x != s)) {
+          i0 = i;
+          nbr = (P.sn_ncol[s] + CHAIN_ROWS - 1) / CHAIN_ROWS;
+          smem = (int)L.chain_smem;
+          break;
+        }
+      }
+      if (i0 >= 0) break;
+    }
+    if (i0 < 0) return fail(NCL_ERR_INVALID_ARG, "no supernode with more than one block-row");
+    const int s = hs.chainv[i0].x;
+    const int64_t ns = P.ns, nb = hs.nbrows;
+    int* tk_f = h->d_chain_sync;
+    int* fl_f = tk_f + 2 * ns;
+    CK(cudaMemsetAsync(h->d_chain_sync, 0, (2 * ns + 2 * nb) * sizeof(int), st));
+    CK(cudaMemcpyAsync(tk_f + s, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->d_err + 1, 0, sizeof(int), st));
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    launch_fwd_chain<T>(h->dp, N, h->d_chain + i0, nbr - 1, smem, true, h->d_chain_pptr, h->d_chain_pran,
+                        (T*)h->own_xp, (const T*)h->W, 1, tk_f, fl_f, h->d_err + 1, wait, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&herr, h->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(h->d_err + 1, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    // the first macro panel of a large front with rows below it: its ticket
+    // counter starts at 1, so no CTA takes the diagonal role and the
+    // sub-block flags are never published; the row CTAs wait until the limit
+    int64_t g0 = -1;
+    int nrc = 0;
+    for (size_t i = 0; i < hs.panelv.size();) {
+      const int4 it = hs.panelv[i];
+      const int qe = std::min(it.y + MACRO_NB, (int)P.sn_ncol[it.x]);
+      const int n = (P.sn_nrow[it.x] - qe + MACRO_ROWS - 1) / MACRO_ROWS;
+      if (n >= 1) {
+        g0 = (int64_t)i;
+        nrc = n;
+        break;
+      }
+      i += 1 + (size_t)n;
+    }
+    if (g0 < 0) return fail(NCL_ERR_INVALID_ARG, "no macro panel with rows below it");
+    CK(cudaMemsetAsync(h->d_panel_sync, 0, std::max<int64_t>(hs.panel_sync, 8) * sizeof(int), st));
+    CK(cudaMemcpyAsync(h->d_panel_sync + hs.panelv[g0].z, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    launch_macro_panel<T>(h->dp, N, h->d_panel + g0, nrc, h->d_panel_sync, h->d_err, h->opt.pivot_eps,
+                          h->opt.pivot_policy, wait, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    // the row CTAs went on without the diagonal block: the factors are void
+    h->factored = false;
+    h->use_twin = false;
+  }
+  if (herr) return fail(NCL_ERR_TIMEOUT, "the bounded wait ran out (as this self-test arranges)");
+  return NCL_OK;
+}
+
+}  // namespace
+
+extern "C" ncl_status ncl_kkt_selftest_wait_timeout(ncl_kkt_t h, int32_t which, int64_t wait_cycles,
+                                                    ncl_stream_t stream) {
+  if (!h) return fail(NCL_ERR_INVALID_ARG, "NULL handle");
+  if (h->opt.host_only) return fail(NCL_ERR_STATE, "host-only handle");
+  if (which != 0 && which != 1) return fail(NCL_ERR_INVALID_ARG, "which must be 0 (sweep) or 1 (panel)");
+  if (wait_cycles <= 0) return fail(NCL_ERR_INVALID_ARG, "wait_cycles must be positive");
+  if (which == 0 && !h->factored) return fail(NCL_ERR_STATE, "sweep self-test before a successful factor");
+  return guarded(h, [&]() -> ncl_status {
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (is_fp32(h)) return selftest_timeout<float>(h, h->nf, which, (long long)wait_cycles, st);
+    return selftest_timeout<double>(h, h->nd, which, (long long)wait_cycles, st);
   });
 }
 
@@ -2187,7 +2343,7 @@ extern "C" ncl_status ncl_kkt_selftest_tensor_update(int32_t rows, int32_t ld, i
   if (e == cudaSuccess) e = cudaMemsetAsync(dtp, 0, tiles * sizeof(int32_t), st);
   if (e == cudaSuccess) {
     launch_split_rows(L, d, rows, ld, K, S, st);
-    launch_update_tc(P0, N0, dp, dtp, tiles, 3, dmaps, derr, st);
+    launch_update_tc(P0, N0, dp, dtp, tiles, 3, dmaps, derr, DEFAULT_WAIT_CYCLES, st);
     g_kernel_launches.fetch_add(2);
     e = cudaGetLastError();
   }

@@ -200,8 +200,6 @@ __device__ __forceinline__ void store_tile(T* dst, int64_t ldd, const T* src, in
   }
 }
 
-constexpr long long PANEL_WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
-
 __device__ __forceinline__ int ld_acquire_i32(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -347,7 +345,8 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
 // tensor-core front the split TF32 operands of L21 and of W = L21 D1 = X.
 template <typename T>
 __device__ __forceinline__ void panel_rows_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int r0,
-                                                const int* flags, int* err, unsigned char* smem_raw) {
+                                                const int* flags, int* err, long long wait,
+                                                unsigned char* smem_raw) {
   T* R = reinterpret_cast<T*>(smem_raw);   // RB rows x w columns, stride LDM
   T* Ld = R + RB * LDM;                    // 4 unit lower diagonal sub-blocks of L11
   T* Lo = Ld + 4 * 32 * LDS;               // 6 off-diagonal sub-blocks (i > j) of L11
@@ -367,7 +366,7 @@ __device__ __forceinline__ void panel_rows_role(const DevPlan& P, const DevNum<T
       if (!ld_acquire_i32(flags + j) && !ld_acquire_i32(err)) {
         const long long t0 = clock64();
         while (!ld_acquire_i32(flags + j)) {
-          if (clock64() - t0 > PANEL_WAIT_CYCLES || ld_acquire_i32(err)) {
+          if (clock64() - t0 > wait || ld_acquire_i32(err)) {
             atomicExch(err, 1);
             break;
           }
@@ -446,7 +445,8 @@ __device__ __forceinline__ void panel_rows_role(const DevPlan& P, const DevNum<T
 // + j] = flag of sub-block j.
 template <typename T>
 __global__ void __launch_bounds__(256, 1) k_macro_panel(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
-                                                        int* sync, int* err, double eps, int policy) {
+                                                        int* sync, int* err, double eps, int policy,
+                                                        long long wait) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int ticket;
   const int4 it = items[blockIdx.x];
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(256, 1) k_macro_panel(DevPlan P, DevNum<T> N, 
     panel_diag_role<T>(P, N, s, q0, slot + 1, eps, policy, smem_raw);
   } else {
     const int qe = min(q0 + MNB, P.sn_ncol[s]);
-    panel_rows_role<T>(P, N, s, q0, qe + RB * (ticket - 1), slot + 1, err, smem_raw);
+    panel_rows_role<T>(P, N, s, q0, qe + RB * (ticket - 1), slot + 1, err, wait, smem_raw);
   }
 }
 
@@ -558,7 +558,7 @@ template void launch_factor_small<double>(const DevPlan&, const DevNum<double>&,
 
 template <typename T>
 void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,
-                        double eps, int policy, cudaStream_t st) {
+                        double eps, int policy, long long wait, cudaStream_t st) {
   if (count <= 0) return;
   static bool attr = false;
   const int smem = macro_panel_smem((int)sizeof(T));
@@ -566,12 +566,12 @@ void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items,
     cudaFuncSetAttribute(k_macro_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  k_macro_panel<T><<<count, 256, smem, st>>>(P, N, items, sync, err, eps, policy);
+  k_macro_panel<T><<<count, 256, smem, st>>>(P, N, items, sync, err, eps, policy, wait);
 }
 
 template void launch_macro_panel<float>(const DevPlan&, const DevNum<float>&, const int4*, int, int*, int*, double,
-                                        int, cudaStream_t);
+                                        int, long long, cudaStream_t);
 template void launch_macro_panel<double>(const DevPlan&, const DevNum<double>&, const int4*, int, int*, int*, double,
-                                         int, cudaStream_t);
+                                         int, long long, cudaStream_t);
 
 }  // namespace ncl

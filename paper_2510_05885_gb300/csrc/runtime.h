@@ -126,7 +126,7 @@ struct TcProb {
 };
 
 void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, const int32_t* tile_prob,
-                      int64_t ntiles, int stages, const CUtensorMap* maps, int* err, cudaStream_t st);
+                      int64_t ntiles, int stages, const CUtensorMap* maps, int* err, long long wait, cudaStream_t st);
 bool tc_encode_maps(const float* split, int64_t rows, int64_t ld, CUtensorMap* out4, std::string* why);
 int64_t tc_tiles(int M, int N, int* Nt_out);
 int tc_smem_bytes();
@@ -164,7 +164,7 @@ int small_front_smem(int nrow, int ncp, int esz);
 int macro_panel_smem(int esz);
 template <typename T>
 void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,
-                        double eps, int policy, cudaStream_t st);
+                        double eps, int policy, long long wait, cudaStream_t st);
 template <typename T>
 void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st);
 
@@ -179,7 +179,7 @@ int chain_smem(int rows, int esz);
 template <typename T>
 void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi,
                       const int32_t* pptr, const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags,
-                      int* err, cudaStream_t st);
+                      int* err, long long wait, cudaStream_t st);
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
                       int count, T* xp, T* W, int nrhs, cudaStream_t st);
@@ -188,7 +188,7 @@ void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, i
                       T* Pw, int nrhs, cudaStream_t st);
 template <typename T>
 void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi, T* xp,
-                      const T* Pw, int nrhs, int* tickets, int* flags, int* err, cudaStream_t st);
+                      const T* Pw, int nrhs, int* tickets, int* flags, int* err, long long wait, cudaStream_t st);
 void launch_residual(const DevPlan& P, const double* Klow, const double* B, int64_t ldb, const double* X,
                      int64_t ldx, double* R, int64_t ldr, int nrhs, unsigned long long* rnorm,
                      unsigned long long* xnorm, cudaStream_t st);

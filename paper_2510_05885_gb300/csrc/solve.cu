@@ -77,8 +77,6 @@ void launch_perm_out(const DevPlan& P, const T* xp, double* X, int64_t ldx, int 
 // instantiation without the cross-block-row part (MULTI = false), which
 // needs far fewer registers.
 // ---------------------------------------------------------------------------
-constexpr long long CHAIN_WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
-
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -88,13 +86,14 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// lane 0 waits (bounded) for the flag; the warp then proceeds together.
-// err is the sweep's error flag: once set, nobody waits any more.
-__device__ __forceinline__ void chain_wait(const int* flag, int* err) {
+// lane 0 waits (bounded by `limit` clock cycles) for the flag; the warp then
+// proceeds together.  err is the sweep's error flag: once set, nobody waits
+// any more.
+__device__ __forceinline__ void chain_wait(const int* flag, int* err, long long limit) {
   if ((threadIdx.x & 31) == 0 && !ld_acquire(flag) && !ld_acquire(err)) {
     const long long t0 = clock64();
     while (!ld_acquire(flag)) {
-      if (clock64() - t0 > CHAIN_WAIT_CYCLES || ld_acquire(err)) {
+      if (clock64() - t0 > limit || ld_acquire(err)) {
         atomicExch(err, 1);
         break;
       }
@@ -142,7 +141,7 @@ template <typename T, bool MULTI>
 __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
                                                    const int32_t* __restrict__ pptr, const int4* __restrict__ pran,
                                                    T* __restrict__ xp, const T* __restrict__ W, int nrhs,
-                                                   int* tickets, int* flags, int* err) {
+                                                   int* tickets, int* flags, int* err, long long wait) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sb;
   const int4 it = items[blockIdx.x];
@@ -215,7 +214,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
         for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp + c0 + 32] : T(0);
       }
       if ((q & 3) == 0) {
-        chain_wait(flags + broff + (q >> 2), err);
+        chain_wait(flags + broff + (q >> 2), err, wait);
 #pragma unroll
         for (int c = 0; c < 4; c++)
 #pragma unroll
@@ -283,7 +282,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
 template <typename T, bool MULTI>
 __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
                                                    T* __restrict__ xp, const T* __restrict__ Pw, int nrhs,
-                                                   int* tickets, int* flags, int* err) {
+                                                   int* tickets, int* flags, int* err, long long wait) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sb;
   const int4 it = items[blockIdx.x];
@@ -359,7 +358,7 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
         for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
       }
       if ((q & 3) == 0) {
-        chain_wait(flags + broff + nbr - 1 - (q >> 2), err);
+        chain_wait(flags + broff + nbr - 1 - (q >> 2), err, wait);
 #pragma unroll
         for (int c = 0; c < 4; c++) {
           const int bw = max(0, min(32, ncol - (q0 + 32 * c)));
@@ -573,7 +572,7 @@ __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const
 template <typename T>
 void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi,
                       const int32_t* pptr, const int4* pran, T* xp, const T* W, int nrhs, int* tickets, int* flags,
-                      int* err, cudaStream_t st) {
+                      int* err, long long wait, cudaStream_t st) {
   if (count <= 0) return;
   static bool attr = false;
   if (!attr) {
@@ -584,9 +583,9 @@ void launch_fwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, i
     attr = true;
   }
   if (multi)
-    k_fwd_chain<T, true><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err);
+    k_fwd_chain<T, true><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err, wait);
   else
-    k_fwd_chain<T, false><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err);
+    k_fwd_chain<T, false><<<count, 128, smem, st>>>(P, N, items, pptr, pran, xp, W, nrhs, tickets, flags, err, wait);
 }
 template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
@@ -600,7 +599,7 @@ void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, i
 }
 template <typename T>
 void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi, T* xp,
-                      const T* Pw, int nrhs, int* tickets, int* flags, int* err, cudaStream_t st) {
+                      const T* Pw, int nrhs, int* tickets, int* flags, int* err, long long wait, cudaStream_t st) {
   if (count <= 0) return;
   static bool attr = false;
   if (!attr) {
@@ -611,9 +610,9 @@ void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, i
     attr = true;
   }
   if (multi)
-    k_bwd_chain<T, true><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err);
+    k_bwd_chain<T, true><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err, wait);
   else
-    k_bwd_chain<T, false><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err);
+    k_bwd_chain<T, false><<<count, 128, smem, st>>>(P, N, items, xp, Pw, nrhs, tickets, flags, err, wait);
 }
 
 // ---------------------------------------------------------------------------
@@ -1059,13 +1058,13 @@ void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, co
   template void launch_perm_out<T>(const DevPlan&, const T*, double*, int64_t, int, int, cudaStream_t);           \
   template void launch_fwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, bool,               \
                                     const int32_t*, const int4*, T*, const T*, int, int*, int*, int*,            \
-                                    cudaStream_t);                                                                \
+                                    long long, cudaStream_t);                                                     \
   template void launch_fwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, const int32_t*, const int4*,  \
                                     int, T*, T*, int, cudaStream_t);                                              \
   template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int4*, int, const T*, T*, int,        \
                                     cudaStream_t);                                                                \
   template void launch_bwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, bool, T*, const T*, \
-                                    int, int*, int*, int*, cudaStream_t);
+                                    int, int*, int*, int*, long long, cudaStream_t);
 NCL_INST(float)
 NCL_INST(double)
 #undef NCL_INST

@@ -17,7 +17,8 @@
 // columns) and commits them to the stage barriers, then all four warps read
 // their 32 accumulator lanes back with tcgen05.ld and update C.  Every wait
 // is bounded: on a timeout the kernel sets an error flag, skips the update,
-// frees its TMEM and returns.
+// waits (bounded) for the TMA copies it has issued, frees its TMEM and
+// returns.
 #include "runtime.h"
 
 #include <cuda.h>
@@ -38,7 +39,6 @@ constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;        // A_hi, A_lo, B_hi, B_
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
 constexpr int tc_smem_for(int stages) { return stages * TC_STAGE_BYTES + 1024 + 256; }
 constexpr uint32_t TC_TMEM_COLS = 128;
-constexpr long long TC_WAIT_CYCLES = 4000000000LL;       // about 2 s at 2 GHz
 
 // instruction descriptor: dense, D = F32, A = B = TF32, both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24
@@ -70,10 +70,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -157,7 +157,8 @@ __device__ __forceinline__ void decode_lower_tile(int64_t t, int Nt, int& ti, in
 
 __global__ void __launch_bounds__(128) k_update_tc(DevNum<float> Nm, const TcProb* __restrict__ probs,
                                                    const int32_t* __restrict__ tile_prob,
-                                                   const CUtensorMap* __restrict__ maps, int* err, int stages) {
+                                                   const CUtensorMap* __restrict__ maps, int* err, int stages,
+                                                   long long wait) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment of the shared-window address (the swizzle atom)
   unsigned char* sb = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -197,14 +198,16 @@ __global__ void __launch_bounds__(128) k_update_tc(DevNum<float> Nm, const TcPro
   const uint32_t tmem = *tslot;
   const int nk = pb.nk;
 
+  int issued = 0;   // TMA stages issued by the producer (thread 0)
   if (warp == 0 && lane == 0) {
     // TMA producer
     for (int kt = 0; kt < nk; kt++) {
       const int s = kt % stages;
-      if (kt >= stages && !mbar_wait_bounded(&empty[s], ((kt / stages) - 1) & 1)) {
+      if (kt >= stages && !mbar_wait_bounded(&empty[s], ((kt / stages) - 1) & 1, wait)) {
         s_fail = 1;
         break;
       }
+      issued = kt + 1;
       unsigned char* st = sb + s * TC_STAGE_BYTES;
       mbar_expect_tx(&full[s], TC_STAGE_BYTES);
       const int x = pb.k0 + kt * TC_BK;
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(128) k_update_tc(DevNum<float> Nm, const TcPro
     int kt = 0;
     for (; kt < nk; kt++) {
       const int s = kt % stages;
-      if (!mbar_wait_bounded(&full[s], (kt / stages) & 1)) {
+      if (!mbar_wait_bounded(&full[s], (kt / stages) & 1, wait)) {
         s_fail = 1;
         break;
       }
@@ -241,11 +244,19 @@ __global__ void __launch_bounds__(128) k_update_tc(DevNum<float> Nm, const TcPro
   __syncwarp();
 
   // epilogue: lane (row) 32*warp + lane of the accumulator
-  if (!mbar_wait_bounded(done, 0)) s_fail = 1;
+  if (!mbar_wait_bounded(done, 0, wait)) s_fail = 1;
   tc_fence_after();
   __syncthreads();
   if (s_fail) {
-    if (tid == 0) atomicExch(err, 1);
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // a wait ran out: the TMA copies already issued may still be landing
+      // in this CTA's shared memory, so wait (bounded) for the last phase of
+      // every stage that has one in flight before the CTA exits (the phases
+      // of a stage complete in order)
+      for (int kt = issued > stages ? issued - stages : 0; kt < issued; kt++)
+        mbar_wait_bounded(&full[kt % stages], (kt / stages) & 1, wait);
+    }
   } else {
     // accumulator rows 32*warp .. 32*warp+31 are this warp's TMEM lanes;
     // each 32 x 32 chunk goes through shared memory (the operand stages are
@@ -348,7 +359,7 @@ int64_t tc_tiles(int M, int N, int* Nt_out) {
 }
 
 void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, const int32_t* tile_prob,
-                      int64_t ntiles, int stages, const CUtensorMap* maps, int* err, cudaStream_t st) {
+                      int64_t ntiles, int stages, const CUtensorMap* maps, int* err, long long wait, cudaStream_t st) {
   (void)P;
   if (ntiles <= 0) return;
   static bool attr = false;
@@ -357,7 +368,7 @@ void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* pr
     attr = true;
   }
   stages = stages < 1 ? 1 : (stages > TC_STAGES ? TC_STAGES : stages);
-  k_update_tc<<<(unsigned)ntiles, 128, tc_smem_for(stages), st>>>(N, probs, tile_prob, maps, err, stages);
+  k_update_tc<<<(unsigned)ntiles, 128, tc_smem_for(stages), st>>>(N, probs, tile_prob, maps, err, stages, wait);
 }
 
 void launch_split_rows(const float* L, const float* d, int rows, int ld, int K, float* S, cudaStream_t st) {

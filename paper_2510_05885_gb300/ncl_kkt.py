@@ -30,7 +30,7 @@ class Options(ctypes.Structure):
                 ("ir_max_iter", ctypes.c_int32), ("use_fgmres", ctypes.c_int32),
                 ("use_tensor_cores", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("precision_fallback", ctypes.c_int32),
-                ("max_device_bytes", ctypes.c_int64)]
+                ("max_device_bytes", ctypes.c_int64), ("wait_cycles", ctypes.c_int64)]
 
 
 class FactorInfo(ctypes.Structure):
@@ -108,6 +108,7 @@ _SIGS = {
     "ncl_kkt_instance_count": (I32, [P]),
     "ncl_kkt_kernel_launches": (I64, []),
     "ncl_kkt_selftest_tensor_update": (I32, [I32, I32, I32, P, P, I32, I32, I32, I32, P, I32, P]),
+    "ncl_kkt_selftest_wait_timeout": (I32, [P, I32, I64, P]),
     "ncl_kkt_profile": (I32, [P, I32]),
     "ncl_kkt_profile_report": (I32, [P, ctypes.c_char_p, I64]),
     "ncl_kkt_destroy": (None, [P]),
@@ -370,6 +371,14 @@ def ncl_kkt_selftest_tensor_update(L, d, K, row_a, row_b, M, N, C, stream=None):
     rows, ld = L.shape
     _check(load().ncl_kkt_selftest_tensor_update(rows, ld, K, _ptr(L), _ptr(d), row_a, row_b, M, N, _ptr(C),
                                                  C.shape[1], _stream_ptr(stream)))
+
+
+def ncl_kkt_selftest_wait_timeout(h, which, wait_cycles, stream=None) -> int:
+    """Status of the self-test (NCL_ERR_TIMEOUT = 9 expected); other errors raise."""
+    st = load().ncl_kkt_selftest_wait_timeout(h, int(which), int(wait_cycles), _stream_ptr(stream))
+    if st not in (OK, 9):
+        _check(st)
+    return st
 
 
 def ncl_kkt_kernel_launches() -> int:

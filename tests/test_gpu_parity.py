@@ -353,3 +353,96 @@ def test_batch_factor_solve_graph_replay():
             assert fi.inertia == (inst.n, inst.m, 0)
             check_against_oracle(inst, "fp32_ir", X[off:off + inst.dim], fi, sinfo, 1e-10)
             off += inst.dim
+
+
+# ------------------------------------------------------------------ deep fronts, elementwise
+
+@pytest.mark.parametrize("prec,eta_tol", [("fp64", 1e-12), ("fp32_ir", 1e-10)])
+@pytest.mark.parametrize("form,side", [("condensed", 80), ("stabilized", 80)])
+def test_deep_fronts_elementwise(prec, eta_tol, form, side):
+    """Grids large enough that the top fronts hold several 128-column macro
+    panels (712 pivots condensed, 528 stabilized), tensor-core updates
+    (FP32) and supernodes of several 128-row block-rows in the chained
+    sweeps: the whole solution against the oracle, elementwise, and the
+    kernel profile showing that those paths ran."""
+    if form == "condensed":
+        inst = synth.condensed_grid(side, rho=1e4, draw=2)
+    else:
+        inst = synth.random_instance(side, side, seed=880 + side, form="stabilized", rho=1e4)
+    p = inst.pat
+    K = nk().KKT(0 if form == "stabilized" else 1, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind,
+                 prec=prec)
+    nk().ncl_kkt_profile(K._h, 1)
+    finfo = K.factor(_t(inst.H_val), _t(inst.J_val), _t(inst.Sigma), inst.delta, inst.rho)
+    X, sinfo = K.solve(_t(inst.b))
+    torch.cuda.synchronize()
+    prof = nk().ncl_kkt_profile_report(K._h)
+    assert K.analysis.max_pivots > 4 * 128
+    suffix = "f32" if prec == "fp32_ir" else "f64"
+    assert prof[f"macro_panel_{suffix}"]["launches"] >= 5
+    assert prof[f"fwd_chain_multi_{suffix}"]["launches"] >= 1
+    assert prof[f"bwd_chain_multi_{suffix}"]["launches"] >= 1
+    if prec == "fp32_ir":
+        assert prof["update_tc_f32"]["launches"] >= 4
+    want = (inst.n, inst.m, 0) if form == "stabilized" else (inst.n, 0, 0)
+    assert finfo.inertia == want
+    check_against_oracle(inst, prec, X.cpu().numpy(), finfo, sinfo, eta_tol)
+
+
+# ------------------------------------------------------------------ the other full-size workloads
+
+def _sampled_rows_ok(A, X, b, eta_tol, count=64, seed=0):
+    rows = np.random.default_rng(seed).choice(A.shape[0], count, replace=False)
+    Ar = sp.csr_matrix(A)[rows]
+    ok = True
+    for r in range(X.shape[1]):
+        scale = np.abs(Ar).sum(axis=1).A1 * np.max(np.abs(X[:, r])) + np.abs(b[rows, r])
+        ok = ok and bool(np.all(np.abs(Ar @ X[:, r] - b[rows, r]) <= eta_tol * scale))
+    return ok
+
+
+@pytest.mark.parametrize("prec,eta_tol", [("fp32_ir", 1e-10), ("fp64", 1e-12)])
+def test_stabilized_700x700_full_size(prec, eta_tol):
+    """The 700 x 700 stabilized workload (n = 1.96M, m = 0.98M, rho = 1e6) at
+    full size: inertia, the FP64 backward error recomputed on the CPU from
+    the oracle's matrix, and 64 sampled rows of K x - b."""
+    inst = synth.large_stabilized(700, rho=1e6, draw=0)
+    K, finfo, X, sinfo = gpu_solve(inst, prec)
+    assert finfo.inertia == (inst.n, inst.m, 0)
+    assert finfo.n_perturbed == 0
+    assert sinfo.status == 0
+    A = O.instance_matrix(inst)
+    eta = O.backward_error(A, X, inst.b)
+    assert eta <= eta_tol, eta
+    assert _sampled_rows_ok(A, X, inst.b, eta_tol)
+    K.close()
+
+
+def test_scenario_batch_64_full_size():
+    """The 64-scenario batch of 100 x 100 grids (1-3 edges deleted each,
+    4 right-hand sides) at full size, through the one-graph factor + solve:
+    per instance its inertia, its FP64 backward error recomputed on the CPU
+    and sampled rows."""
+    batch = synth.scenario_batch(count=64, side=100, nrhs=4)
+    pats = [(i.n, i.m, i.pat.H_rowptr, i.pat.H_colind, i.pat.J_rowptr, i.pat.J_colind) for i in batch]
+    K = nk().KKT.batch(0, pats, prec="fp32_ir")
+    Hv = _t(np.concatenate([i.H_val for i in batch]))
+    Jv = _t(np.concatenate([i.J_val for i in batch]))
+    S = _t(np.concatenate([i.Sigma for i in batch]))
+    Bc = _t(np.concatenate([i.b for i in batch], axis=0).T.copy())
+    Xc = torch.empty_like(Bc)
+    for _ in range(2):      # the direct first call, then the replayed graph
+        infos, sinfo = nk().ncl_kkt_batch_factor_solve(K._h, Hv, Jv, S, [i.delta for i in batch],
+                                                       [i.rho for i in batch], 4, Bc, K.dim, Xc, K.dim)
+        assert sinfo.status == 0
+        X = Xc.cpu().numpy().T
+        off = 0
+        for k, (inst, fi) in enumerate(zip(batch, infos)):
+            assert fi.inertia == (inst.n, inst.m, 0)
+            Xi = X[off:off + inst.dim]
+            A = O.instance_matrix(inst)
+            assert O.backward_error(A, Xi, inst.b) <= 1e-10
+            if k % 8 == 0:
+                assert _sampled_rows_ok(A, Xi, inst.b, 1e-10, count=16, seed=k)
+            off += inst.dim
+    K.close()
