@@ -125,6 +125,12 @@ typedef struct {
                                  the kernel sets an error flag, finishes without the
                                  awaited data and the call returns NCL_ERR_TIMEOUT.
                                  <= 0 selects 4e9 (about 2 s) */
+    int32_t persistent_fronts; /* 1 (default): the large fronts of each level are
+                                 factored by one persistent launch whose CTAs take
+                                 panel, row and trailing-update tile tasks from a
+                                 dependency-ordered list; 0: one launch per
+                                 128-column panel step plus one per trailing
+                                 update */
 } ncl_kkt_options;
 
 typedef struct {

@@ -99,7 +99,9 @@ struct Level {
   int below_cnt = 0;
   int64_t bbelow_off = 0; // (s, a0, k0) backward solve items
   int bbelow_cnt = 0;
-  Cost asm_cost, small_cost, syrk_cost, fdiag_cost, fbelow_cost, bdiag_cost, bbelow_cost;
+  int64_t dag_off = 0;    // tasks of the persistent large-front launch
+  int dag_cnt = 0;
+  Cost asm_cost, small_cost, syrk_cost, fdiag_cost, fbelow_cost, bdiag_cost, bbelow_cost, dag_cost;
 };
 
 struct KStat {
@@ -140,6 +142,12 @@ struct HostSched {
   int64_t split_max = 0;
   std::vector<int8_t> sn_flags;
   std::vector<int64_t> sn_Ioff;
+  // persistent large-front factorisation: tasks of every level, and the
+  // counters they wait on (one queue head per level, then the fronts'
+  // tile and row-task counters)
+  bool dag = false;
+  std::vector<DagTask> dagv;
+  int64_t dag_counters = 0;
 };
 
 }  // namespace
@@ -209,6 +217,9 @@ struct ncl_kkt_s {
   CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
   TcProb* d_tc = nullptr;
   int* d_err = nullptr;                    // device error flags (bounded waits)
+  DagTask* d_dag = nullptr;                // persistent large-front tasks
+  int* d_dag_cnt = nullptr;                //   their queue heads and counters
+  int n_sm = 148;                          // multiprocessors of the device
   // CUDA graphs: the factor and the triangular sweeps are captured once (on
   // a private stream, after one direct call) and replayed
   cudaStream_t cap_stream = nullptr;
@@ -302,6 +313,9 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<int4>& panelv = hs.panelv;
   std::vector<GemmProb>& probv = hs.probv;
   hs.tc = is_fp32(h) && h->opt.use_tensor_cores;
+  hs.dag = h->opt.persistent_fronts != 0;
+  hs.dagv.clear();
+  hs.dag_counters = (int64_t)P.nlevels;   // one queue head per level first
   hs.sn_Soff.assign(P.ns, -1);
   hs.sn_flags.assign(P.ns, 0);
   hs.sn_Ioff.assign(P.ns + 1, 0);
@@ -440,7 +454,7 @@ void build_schedule(ncl_kkt_s* h) {
     if (hs.tc) {
       int64_t off = 0;
       for (int32_t s : large) {
-        if (P.sn_ncol[s] < TC_MIN_K || P.sn_nrow[s] == P.sn_ncol[s]) continue;
+        if (P.sn_ncol[s] < TC_MIN_K) continue;
         fid[s] = (int32_t)hs.tc_fronts.size();
         hs.tc_fronts.push_back(s);
         hs.sn_Soff[s] = off;
@@ -504,6 +518,78 @@ void build_schedule(ncl_kkt_s* h) {
       S.panel_cnt = (int)(panelv.size() - S.panel_off);
       S.prob_cnt = (int)(probv.size() - S.prob_off);
       S.tc_cnt = (int)(hs.tcv.size() - S.tc_off);
+    }
+    if (hs.dag && !large.empty()) {
+      // the persistent launch's tasks: per front f, panels p of 128 columns;
+      // counters cnt[i][j] (trailing updates applied to tile (i, j)) and
+      // rows[p][t] (row tasks of panel p done in row tile t).  Order: panel
+      // 0's DIAG and ROWS, then per p the tiles of panel p + 1's columns,
+      // panel p + 1's DIAG and ROWS, the rest of panel p's trailing update
+      // (every dependency of a task comes before it).
+      L.dag_off = (int64_t)hs.dagv.size();
+      struct FrontDag {
+        int32_t s, P, Rt, Ct, map;
+        int64_t cbase, rbase;
+        std::vector<int32_t> slot;
+      };
+      std::vector<FrontDag> fr;
+      for (int32_t s : large) {
+        FrontDag F;
+        F.s = s;
+        F.P = (P.sn_ncol[s] + MACRO_NB - 1) / MACRO_NB;
+        F.Ct = F.P;
+        F.Rt = (P.sn_nrow[s] + MACRO_NB - 1) / MACRO_NB;
+        F.map = fid[s];
+        F.cbase = hs.dag_counters;
+        hs.dag_counters += (int64_t)F.Rt * F.Ct;
+        F.rbase = hs.dag_counters;
+        hs.dag_counters += (int64_t)F.P * F.Rt;
+        for (int p = 0; p < F.P; p++) {
+          F.slot.push_back((int32_t)hs.panel_sync);
+          hs.panel_sync += 8;
+        }
+        fr.push_back(std::move(F));
+      }
+      auto task = [&](const FrontDag& F, int kind, int p, int x, int y) {
+        DagTask t{};
+        t.kind = kind;
+        t.s = F.s;
+        t.p = p;
+        t.x = x;
+        t.y = y;
+        t.slot = F.slot[p];
+        t.cbase = (int32_t)F.cbase;
+        t.rbase = (int32_t)F.rbase;
+        t.Ct = F.Ct;
+        t.Rt = F.Rt;
+        t.map = F.map;
+        hs.dagv.push_back(t);
+      };
+      auto diag_rows = [&](const FrontDag& F, int p) {
+        task(F, DAG_DIAG, p, 0, 0);
+        const int qe = std::min((p + 1) * MACRO_NB, (int)P.sn_ncol[F.s]);
+        const int nrc = (P.sn_nrow[F.s] - qe + MACRO_ROWS - 1) / MACRO_ROWS;
+        for (int r = 0; r < nrc; r++) task(F, DAG_ROWS, p, r, 0);
+      };
+      int maxP = 0;
+      for (const FrontDag& F : fr) maxP = std::max(maxP, F.P);
+      for (const FrontDag& F : fr) diag_rows(F, 0);
+      for (int p = 0; p + 1 < maxP; p++) {
+        for (const FrontDag& F : fr)
+          if (p + 1 < F.P)
+            for (int ti = p + 1; ti < F.Rt; ti++) task(F, DAG_UPD, p, ti, p + 1);
+        for (const FrontDag& F : fr)
+          if (p + 1 < F.P) diag_rows(F, p + 1);
+        for (const FrontDag& F : fr)
+          if (p + 1 < F.P)
+            for (int tj = p + 2; tj < F.Ct; tj++)
+              for (int ti = tj; ti < F.Rt; ti++) task(F, DAG_UPD, p, ti, tj);
+      }
+      L.dag_cnt = (int)(hs.dagv.size() - L.dag_off);
+      for (const Step& S : L.steps) {
+        L.dag_cost.flops += S.panel_cost.flops + S.gemm_cost.flops + S.tc_cost.flops;
+        L.dag_cost.bytes += S.panel_cost.bytes + S.gemm_cost.bytes + S.tc_cost.bytes;
+      }
     }
     // update blocks F22 -= L21 D1 L21^T: tensor cores for the fronts with
     // enough pivots, the SIMT kernel for the rest (small fronts included)
@@ -658,6 +744,62 @@ void build_schedule(ncl_kkt_s* h) {
         if (panelv[i + k].x != s || panelv[i + k].y != it.y || panelv[i + k].z != it.z) bad("macro panel item");
       if (i + n < panelv.size() && panelv[i + n].z == it.z) bad("macro panel item");
       i += n;
+    }
+    // persistent large-front tasks: every index against its front, its
+    // counters, its sync slot and the tensor maps
+    for (const DagTask& t : hs.dagv) {
+      if (t.s < 0 || t.s >= P.ns) bad("front task");
+      const int ncol = P.sn_ncol[t.s], nrow = P.sn_nrow[t.s];
+      const int Pf = (ncol + MACRO_NB - 1) / MACRO_NB, Rt = (nrow + MACRO_NB - 1) / MACRO_NB;
+      if (t.p < 0 || t.p >= Pf || t.Ct != Pf || t.Rt != Rt) bad("front task");
+      if (t.cbase < P.nlevels || (int64_t)t.cbase + (int64_t)Rt * Pf > hs.dag_counters ||
+          t.rbase < P.nlevels || (int64_t)t.rbase + (int64_t)Pf * Rt > hs.dag_counters)
+        bad("front task counters");
+      if (t.slot < 0 || t.slot % 8 || t.slot + 8 > hs.panel_sync) bad("front task slot");
+      if (t.map >= (int)hs.tc_fronts.size() || (t.map >= 0 && hs.tc_fronts[t.map] != t.s)) bad("front task map");
+      const int qe = std::min((t.p + 1) * MACRO_NB, ncol);
+      if (t.kind == DAG_ROWS) {
+        if (t.x < 0 || qe + MACRO_ROWS * t.x >= nrow) bad("front task rows");
+      } else if (t.kind == DAG_UPD) {
+        if (t.p + 1 >= Pf || t.y < t.p + 1 || t.y >= Pf || t.x < t.y || t.x >= Rt) bad("front task tile");
+        if (t.map >= 0 && (qe - t.p * MACRO_NB) % 32) bad("front task tile");
+      } else if (t.kind != DAG_DIAG) {
+        bad("front task kind");
+      }
+    }
+    {
+      // replay the task lists in order with the kernel's wait conditions:
+      // every task's dependencies must be met by tasks listed before it (the
+      // CTAs take tasks in list order, so this makes the waits deadlock-free)
+      std::vector<int> c((size_t)hs.dag_counters, 0);
+      for (const DagTask& t : hs.dagv) {
+        const int ncol = P.sn_ncol[t.s], nrow = P.sn_nrow[t.s];
+        const int q0 = t.p * MACRO_NB, qe = std::min(q0 + MACRO_NB, ncol);
+        int* tc = c.data() + t.cbase;
+        int* rd = c.data() + t.rbase;
+        if (t.kind == DAG_DIAG) {
+          if (tc[t.p * t.Ct + t.p] < t.p) bad("front task order");
+        } else if (t.kind == DAG_ROWS) {
+          const int r0 = qe + MACRO_ROWS * t.x, r1 = std::min(r0 + MACRO_ROWS, nrow);
+          for (int rt = r0 / MACRO_NB; rt <= (r1 - 1) / MACRO_NB; rt++)
+            if (tc[rt * t.Ct + t.p] < t.p) bad("front task order");
+          if (qe < ncol) rd[t.p * t.Rt + r0 / MACRO_NB]++;
+        } else {
+          const int ei = (MACRO_NB * t.x + MACRO_ROWS < nrow) ? 2 : 1;
+          const int ej = (MACRO_NB * t.y + MACRO_ROWS < nrow) ? 2 : 1;
+          if (rd[t.p * t.Rt + t.x] < ei || rd[t.p * t.Rt + t.y] < ej || tc[t.x * t.Ct + t.y] != t.p)
+            bad("front task order");
+          tc[t.x * t.Ct + t.y] = t.p + 1;
+        }
+      }
+      // and every trailing update of every front was applied
+      for (const DagTask& t : hs.dagv)
+        if (t.kind == DAG_DIAG) {
+          const int* tc = c.data() + t.cbase;
+          for (int tj = 0; tj < t.Ct; tj++)
+            for (int ti = tj; ti < t.Rt; ti++)
+              if (tc[ti * t.Ct + tj] != std::min(tj, ti)) bad("front task coverage");
+        }
     }
     for (const TcProb& q : hs.tcv) {
       const int64_t csz = q.c_in_u ? Usz : Lsz;
@@ -844,6 +986,14 @@ void build_device(ncl_kkt_s* h) {
     h->d_tilep_tc = h->upload(hs.tilep_tc);
   }
   h->d_err = h->alloc<int>(4);
+  if (!h->hs.dagv.empty()) h->d_dag = h->upload(h->hs.dagv);
+  h->d_dag_cnt = h->alloc<int>(std::max<int64_t>(h->hs.dag_counters, 1));
+  {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    h->n_sm = std::max(1, nsm);
+  }
   d.sn_flags = h->upload(h->hs.sn_flags);
   d.sn_Ioff = h->upload(h->hs.sn_Ioff);
   CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
@@ -965,7 +1115,18 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
     klaunch(h, st, f32 ? "factor_small_f32" : "factor_small_f64", L.small_cnt, L.small_cost, [&] {
       launch_factor_small<T>(P, N, h->d_small + L.small_off, L.small_cnt, (int)L.small_smem, eps, pol, st);
     });
+    if (L.dag_cnt > 0) {
+      // the level's large fronts in one persistent launch (panels, rows and
+      // trailing-update tiles as dependent tasks)
+      const int li = (int)(&L - h->levels.data());
+      const int grid = std::min(L.dag_cnt, h->n_sm);
+      klaunch(h, st, f32 ? "front_dag_f32" : "front_dag_f64", L.dag_cnt, L.dag_cost, [&] {
+        launch_front_dag<T>(P, N, h->d_dag + L.dag_off, L.dag_cnt, grid, h->d_dag_cnt + li, h->d_dag_cnt,
+                            h->d_panel_sync, h->d_maps, h->d_err, eps, pol, h->opt.wait_cycles, st);
+      });
+    }
     for (const Step& S : L.steps) {
+      if (L.dag_cnt > 0) break;
       klaunch(h, st, f32 ? "macro_panel_f32" : "macro_panel_f64", S.panel_cnt, S.panel_cost, [&] {
         launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->d_panel_sync, h->d_err, eps, pol,
                               h->opt.wait_cycles, st);
@@ -1322,6 +1483,7 @@ void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
   CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), s2));
   CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s2));
   CK(cudaMemsetAsync(h->d_panel_sync, 0, std::max<int64_t>(h->hs.panel_sync, 8) * sizeof(int), s2));
+  CK(cudaMemsetAsync(h->d_dag_cnt, 0, std::max<int64_t>(h->hs.dag_counters, 1) * sizeof(int), s2));
   if (is_fp32(h)) {
     run_factor<float>(h, h->nf, s2);
     klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},
@@ -1681,6 +1843,7 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->precision_fallback = 1;
   o->max_device_bytes = 0;
   o->wait_cycles = 0;
+  o->persistent_fronts = 1;
 }
 
 ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m, const int32_t* H_rowptr, const int32_t* H_colind,

@@ -1,438 +1,10 @@
-// Dense front kernels (sm_103a): macro panels of a large front, and whole
-// small fronts.
-//
-// The pivot columns of a large front are processed MACRO_NB = 128 at a time
-// (right-looking blocked LDL^T with D diagonal and static pivoting, Section
-// 3.1).  For macro panel [q0, qe) one launch (k_macro_panel) runs, for every
-// large front of the level:
-//   the diagonal role  one CTA: the w x w diagonal block (w <= 128) is
-//                      factored in shared memory by 32-column sub-blocks,
-//                      each published as soon as it is done;
-//   the row role       one CTA per 64 rows below the panel: as the
-//                      sub-blocks appear, the blocked forward substitution
-//                      L21 = F21 L11^-T D1^-1; for a tensor-core front also
-//                      the split TF32 operands of L21 and W = L21 D1.
-// Then the trailing update of the remaining pivot columns with K = w runs on
-// the SIMT or the tensor-core update kernel.
-#include "runtime.h"
-#include "pivot.cuh"
+// Dense front kernels (sm_103a): the per-step macro-panel kernel of large
+// fronts (the roles are in panel_roles.cuh), and whole small fronts.
+#include "panel_roles.cuh"
 
 #include <algorithm>
 
 namespace ncl {
-
-namespace {
-
-constexpr int MNB = MACRO_NB;
-constexpr int LDM = MNB + 1;       // shared row stride of the diagonal block
-constexpr int RB = MACRO_ROWS;     // rows per row CTA
-constexpr int LDS = 33;            // stride of the 32 x 32 shared blocks
-
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-}  // namespace
-
-// Copy a rows x cols tile from global memory (row stride lds) into shared
-// memory (row stride ldd), zero where keep(r, c) is false, with 8 loads in
-// flight per thread before the shared stores.
-template <typename T, typename Keep>
-__device__ __forceinline__ void load_tile(T* dst, int ldd, const T* src, int64_t lds, int rows, int cols, Keep keep) {
-  const int n = rows * cols;
-  for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
-    T v[8];
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const int idx = base + k * blockDim.x;
-      const int r = idx / cols, c = idx - r * cols;
-      v[k] = (idx < n && keep(r, c)) ? src[(int64_t)r * lds + c] : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const int idx = base + k * blockDim.x;
-      const int r = idx / cols, c = idx - r * cols;
-      if (idx < n) dst[r * ldd + c] = v[k];
-    }
-  }
-}
-
-static int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + MNB) * esz + 2 * MNB; }
-static int macro_rows_smem(int esz) { return (RB * LDM + 10 * 32 * LDS + MNB) * esz; }
-int macro_panel_smem(int esz) { return std::max(macro_diag_smem(esz), macro_rows_smem(esz)); }
-
-// LDL^T of a 32 x 32 diagonal sub-block in shared memory (row stride ld,
-// cw <= 32 valid rows) by one warp, lane i holding row i in registers:
-// right-looking with column broadcasts by shuffles.  Writes the unit lower
-// factor (strictly below the diagonal) and D on the diagonal back; returns
-// lane's pivot (1 on the padding) and its status in st.
-template <typename T>
-__device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, double eps, int policy, int lane,
-                                       int8_t& st) {
-  T r[32];
-#pragma unroll
-  for (int j = 0; j < 32; j++) r[j] = (j <= lane && lane < cw) ? blk[lane * ld + j] : T(0);
-  int8_t my_st = 0;
-  T my_d = T(1);
-#pragma unroll
-  for (int k = 0; k < 32; k++) {
-    if (k < cw) {
-      int8_t stt;
-      const int sg = __shfl_sync(0xffffffffu, my_sign, k);
-      const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
-      const T wk = r[k];
-      // rows above the pivot get a zero multiplier, so the update needs no
-      // per-column select or branch (a predicated branch around each shuffle
-      // costs a reconvergence per shuffle); entries above a lane's diagonal
-      // are never read
-      const T li = lane > k ? wk * (T(1) / dk) : T(0);
-#pragma unroll
-      for (int j = k + 1; j < 32; j++) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
-      r[k] = lane > k ? li : (lane == k ? dk : r[k]);
-      my_d = lane == k ? dk : my_d;
-      my_st = lane == k ? stt : my_st;
-    }
-  }
-  if (lane < cw) {
-#pragma unroll
-    for (int j = 0; j < 32; j++)
-      if (j <= lane) blk[lane * ld + j] = r[j];
-  }
-  __syncwarp();
-  st = my_st;
-  return my_d;
-}
-
-// Inverse of the unit lower 32 x 32 block blk (row stride ld, cw valid
-// rows; identity on the padding) by one warp, written row-major to out:
-// lane j forms column j by forward substitution in registers,
-// x_i = -sum_{k<i} L[i][k] x_k, x_j = 1, x_i = 0 for i < j.
-template <typename T>
-__device__ __noinline__ void invert_sub32(const T* blk, int ld, int cw, T* out, int lane) {
-  T x[32];
-#pragma unroll
-  for (int i = 0; i < 32; i++) {
-    T a0 = T(0), a1 = T(0);
-#pragma unroll
-    for (int k = 0; k + 1 < i; k += 2) {
-      a0 += blk[i * ld + k] * x[k];
-      a1 += blk[i * ld + k + 1] * x[k + 1];
-    }
-    if (i & 1) a0 += blk[i * ld + i - 1] * x[i - 1];
-    x[i] = (i == lane) ? T(1) : ((i > lane && i < cw) ? -(a0 + a1) : T(0));
-  }
-#pragma unroll
-  for (int i = 0; i < 32; i++) out[i * 32 + lane] = x[i];
-}
-
-// X = R L^-T for the rows [0, nrows) of R (shared, row stride ldr, ncols <=
-// 32 columns) and the unit lower 32 x 32 block L (shared, row stride ldl;
-// only the entries strictly below its diagonal are read, zero beyond
-// ncols): blocked forward
-// substitution with 8-column groups, four threads per row (thread g holds
-// columns 8g..8g+7).  Stage s: group s substitutes with the 8 x 8 diagonal
-// block, its 8 values go to the row's other threads by shuffles, and the
-// later groups subtract their products with the (g, s) block.  No inverse is
-// formed.  Called by all threads of the CTA (blockDim a multiple of 32).
-template <typename T>
-__device__ __forceinline__ void block_trsm32(T* R, int ldr, int nrows, int ncols, const T* L, int ldl) {
-  const int lane = threadIdx.x & 31, g = threadIdx.x & 3;
-  const int src0 = lane & ~3;
-  for (int r0 = 0; r0 < nrows; r0 += blockDim.x >> 2) {
-    const int row = r0 + (threadIdx.x >> 2);
-    const bool act = row < nrows;
-    T* rp = R + (act ? row : 0) * ldr + 8 * g;
-    T q[8];
-#pragma unroll
-    for (int t = 0; t < 8; t++) q[t] = (act && 8 * g + t < ncols) ? rp[t] : T(0);
-#pragma unroll
-    for (int st = 0; st < 4; st++) {
-      if (g == st) {
-        const T* Ld = L + (8 * st) * ldl + 8 * st;
-#pragma unroll
-        for (int u = 0; u < 7; u++)
-#pragma unroll
-          for (int t = u + 1; t < 8; t++) q[t] -= Ld[t * ldl + u] * q[u];
-      }
-      T xs[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) xs[u] = __shfl_sync(0xffffffffu, q[u], src0 | st);
-      if (g > st) {
-        const T* Lg = L + (8 * g) * ldl + 8 * st;
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-          T acc = T(0);
-#pragma unroll
-          for (int u = 0; u < 8; u++) acc += Lg[t * ldl + u] * xs[u];
-          q[t] -= acc;
-        }
-      }
-    }
-    if (act) {
-#pragma unroll
-      for (int t = 0; t < 8; t++)
-        if (8 * g + t < ncols) rp[t] = q[t];
-    }
-  }
-}
-
-// Copy a tile from shared memory back to global memory (stores where
-// keep(r, c)), 8 shared loads in flight per thread before the stores.
-template <typename T, typename Keep>
-__device__ __forceinline__ void store_tile(T* dst, int64_t ldd, const T* src, int lds, int rows, int cols, Keep keep) {
-  const int n = rows * cols;
-  for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
-    T v[8];
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const int idx = min(base + k * blockDim.x, n - 1);
-      const int r = idx / cols, c = idx - r * cols;
-      v[k] = src[r * lds + c];
-    }
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const int idx = base + k * blockDim.x;
-      const int r = idx / cols, c = idx - r * cols;
-      if (idx < n && keep(r, c)) dst[(int64_t)r * ldd + c] = v[k];
-    }
-  }
-}
-
-__device__ __forceinline__ int ld_acquire_i32(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_i32(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// barrier among warps 1..7 of a 256-thread CTA (warp 0 is busy meanwhile)
-__device__ __forceinline__ void bar_warps_1_7() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
-
-// A[r][c] -= sum_u X[r - rb][u] L21[c][u] (L21 in the columns c0..c0+31 of
-// A) for rows [r_begin, w) and columns [c_begin, c_end) (at most 64), c <= r;
-// done by the nw warps wfirst.. of the CTA, lane = column, register tiles of
-// up to 8 rows per warp and trip
-template <typename T>
-__device__ __forceinline__ void block_update(T* A, const T* Xs, int c0, int rb, int w, int r_begin, int c_begin,
-                                             int c_end, int wfirst, int nw) {
-  const int warp = (threadIdx.x >> 5) - wfirst, lane = threadIdx.x & 31;
-  if (warp < 0 || warp >= nw || c_begin >= c_end) return;
-  constexpr int MRW = 8;
-  const int ng = (c_end - c_begin + 31) / 32;   // 1 or 2
-  for (int rr0 = r_begin + warp * MRW; rr0 < w; rr0 += nw * MRW) {
-    T acc[MRW][2];
-#pragma unroll
-    for (int m = 0; m < MRW; m++) acc[m][0] = acc[m][1] = T(0);
-#pragma unroll 2
-    for (int u = 0; u < 32; u++) {
-      T bv[2];
-#pragma unroll
-      for (int g = 0; g < 2; g++) bv[g] = g < ng ? A[min(c_begin + 32 * g + lane, c_end - 1) * LDM + c0 + u] : T(0);
-#pragma unroll
-      for (int m = 0; m < MRW; m++) {
-        const T a = Xs[(min(rr0 + m, w - 1) - rb) * LDS + u];
-        acc[m][0] += a * bv[0];
-        acc[m][1] += a * bv[1];
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < MRW; m++) {
-      const int r = rr0 + m;
-#pragma unroll
-      for (int g = 0; g < 2; g++) {
-        const int c = c_begin + 32 * g + lane;
-        if (g < ng && r < w && c < c_end && c <= r) A[r * LDM + c] -= acc[m][g];
-      }
-    }
-  }
-}
-
-// Diagonal role of a macro panel (one CTA of 256 threads): factors the w x w
-// diagonal block (w <= 128) in shared memory by 32-column sub-blocks.  For
-// sub-block j: the rows below it inside the block are solved by the blocked
-// forward substitution, X = F21 L_jj^-T, and scaled, L21 = X D^-1; the next
-// sub-block's columns are updated by all warps; then warp 0 factors the
-// next sub-block (factor_sub32) while warps 1..7 publish sub-block j (its
-// columns and pivots to global memory, fence, release flag j, for the row
-// CTAs) and update the columns beyond the next sub-block.  The rows below
-// the first sub-block are loaded while warp 0 factors it.  At the end four
-// warps invert the four unit lower sub-blocks (for the triangular sweeps).
-template <typename T>
-__device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int* flags,
-                                                double eps, int policy, unsigned char* smem_raw) {
-  T* A = reinterpret_cast<T*>(smem_raw);   // w x w block, row stride LDM
-  T* Xs = A + MNB * LDM;                   // X of the rows below the sub-block
-  T* dsh = Xs + (MNB - 32) * LDS;          // pivots of the block (MNB)
-  int8_t* sg = reinterpret_cast<int8_t*>(dsh + MNB);   // block signs, then pivot status
-  int8_t* pst = sg + MNB;
-  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
-  const int w = min(MNB, ncol - q0);
-  const int nbk = (w + 31) / 32;
-  T* Lb = N.L + P.sn_Loff[s] + (int64_t)q0 * ncp + q0;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // the first sub-block's rows, then its factorisation by warp 0 while the
-  // other warps load the rest of the block
-  load_tile(A, LDM, Lb, ncp, min(32, w), MNB, [&](int r, int c) { return c <= r; });
-  for (int c = tid; c < MNB; c += blockDim.x) sg[c] = c < w ? P.col_sign[col0 + q0 + c] : 1;
-  __syncthreads();
-  auto factor = [&](int c0) {
-    int8_t st;
-    const T d = factor_sub32<T>(A + c0 * LDM + c0, LDM, min(32, w - c0), sg[c0 + lane], eps, policy, lane, st);
-    dsh[c0 + lane] = d;
-    pst[c0 + lane] = st;
-  };
-  if (warp == 0) {
-    factor(0);
-  } else if (w > 32) {
-    const int n = (w - 32) * MNB;
-    for (int idx = tid - 32; idx < n; idx += 224) {
-      const int r = 32 + idx / MNB, c = idx % MNB;
-      A[r * LDM + c] = (c <= r) ? Lb[(int64_t)r * ncp + c] : T(0);
-    }
-  }
-  __syncthreads();
-  for (int j = 0; j < nbk; j++) {
-    const int c0 = 32 * j, cw = min(32, w - c0);
-    const int rb = c0 + 32, nr = w - rb;
-    if (nr > 0) {
-      // rows below the sub-block: X = F21 L_jj^-T (kept), L21 = X D^-1
-      block_trsm32<T>(A + rb * LDM + c0, LDM, nr, 32, A + c0 * LDM + c0, LDM);
-      __syncthreads();
-      for (int idx = tid; idx < nr * 32; idx += blockDim.x) {
-        const int r = idx >> 5, c = idx & 31;
-        const T x = A[(rb + r) * LDM + c0 + c];
-        Xs[r * LDS + c] = x;
-        A[(rb + r) * LDM + c0 + c] = x / dsh[c0 + c];
-      }
-      __syncthreads();
-      // the next sub-block's columns, by all warps
-      block_update<T>(A, Xs, c0, rb, w, rb, rb, min(rb + 32, w), 0, 8);
-      __syncthreads();
-    }
-    if (warp == 0) {
-      if (j + 1 < nbk) factor(rb);
-    } else {
-      // publish sub-block j: columns [c0, c0 + cw) of rows [c0, w), pivots
-      const int n = (w - c0) * cw;
-      for (int idx = tid - 32; idx < n; idx += 224) {
-        const int r = idx / cw, c = idx - r * cw;
-        if (c <= r) Lb[(int64_t)(c0 + r) * ncp + c0 + c] = A[(c0 + r) * LDM + c0 + c];
-      }
-      if (tid - 32 < cw) N.D[col0 + q0 + c0 + tid - 32] = dsh[c0 + tid - 32];
-      __threadfence();
-      bar_warps_1_7();
-      if (tid == 32) st_release_i32(flags + j, 1);
-      // the columns beyond the next sub-block
-      if (nr > 32) block_update<T>(A, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
-    }
-    __syncthreads();
-  }
-  if (warp < nbk)
-    invert_sub32<T>(A + 32 * warp * LDM + 32 * warp, LDM, min(32, w - 32 * warp),
-                    N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + warp) * 1024, lane);
-  for (int c = tid; c < w; c += blockDim.x) N.piv[col0 + q0 + c] = pst[c];
-}
-
-// Row role of a macro panel (one CTA per RB rows below it): stages its rows
-// while the diagonal role works, then for each 32-column sub-block j, as
-// soon as it is published, X_j = R_j L_jj^-T by the blocked forward
-// substitution and R_i -= X_j L_ij^T for the later sub-blocks (lane =
-// column, the rows of a warp in registers); finally L21 = X D1^-1, and for a
-// tensor-core front the split TF32 operands of L21 and of W = L21 D1 = X.
-template <typename T>
-__device__ __forceinline__ void panel_rows_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int r0,
-                                                const int* flags, int* err, long long wait,
-                                                unsigned char* smem_raw) {
-  T* R = reinterpret_cast<T*>(smem_raw);   // RB rows x w columns, stride LDM
-  T* Ld = R + RB * LDM;                    // 4 unit lower diagonal sub-blocks of L11
-  T* Lo = Ld + 4 * 32 * LDS;               // 6 off-diagonal sub-blocks (i > j) of L11
-  T* dsh = Lo + 6 * 32 * LDS;              // D1
-  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
-  const int w = min(MNB, ncol - q0);
-  const int nbk = (w + 31) / 32;
-  const int nr = min(RB, nrow - r0);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  T* Lb = N.L + P.sn_Loff[s];
-  load_tile(R, LDM, Lb + (int64_t)r0 * ncp + q0, ncp, RB, MNB, [&](int r, int c) { return r < nr && c < w; });
-  constexpr int KR = RB / 8;   // rows per warp in the updates (lane = column)
-  T* Rw = R + warp * LDM;      // row warp + 8 k is Rw[8 k LDM + ...]
-  for (int j = 0; j < nbk; j++) {
-    // wait (bounded) for sub-block j, then fetch its published columns
-    if (tid == 0) {
-      if (!ld_acquire_i32(flags + j) && !ld_acquire_i32(err)) {
-        const long long t0 = clock64();
-        while (!ld_acquire_i32(flags + j)) {
-          if (clock64() - t0 > wait || ld_acquire_i32(err)) {
-            atomicExch(err, 1);
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-    }
-    __syncthreads();
-    for (int i = j; i < nbk; i++) {
-      T* dst = (i == j) ? Ld + i * 32 * LDS : Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
-      const int rows = min(32, w - 32 * i);
-      const T* src = Lb + (int64_t)(q0 + 32 * i) * ncp + q0 + 32 * j;
-      for (int e = tid; e < 1024; e += blockDim.x) {
-        const int rr = e >> 5, cc = e & 31;
-        dst[rr * LDS + cc] = (rr < rows && (i > j || cc < rr)) ? __ldcg(src + (int64_t)rr * ncp + cc) : T(0);
-      }
-    }
-    if (tid < 32) dsh[32 * j + tid] = 32 * j + tid < w ? __ldcg(N.D + col0 + q0 + 32 * j + tid) : T(1);
-    __syncthreads();
-    block_trsm32<T>(R + 32 * j, LDM, nr, min(32, w - 32 * j), Ld + j * 32 * LDS, LDS);
-    __syncthreads();
-    for (int i = j + 1; i < nbk; i++) {
-      const T* lij = Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
-      T x[KR];
-#pragma unroll
-      for (int k = 0; k < KR; k++) x[k] = T(0);
-#pragma unroll 4
-      for (int u = 0; u < 32; u++) {
-        const T b = lij[lane * LDS + u];
-#pragma unroll
-        for (int k = 0; k < KR; k++) x[k] += Rw[8 * k * LDM + 32 * j + u] * b;
-      }
-#pragma unroll
-      for (int k = 0; k < KR; k++) Rw[8 * k * LDM + 32 * i + lane] -= x[k];
-    }
-    __syncthreads();
-  }
-  // L21 = X D1^-1 (+ split operands of L21 and W = X for a tensor-core front)
-  int64_t so = -1;
-  if constexpr (sizeof(T) == 4) so = (N.S && P.sn_Soff) ? P.sn_Soff[s] : -1;
-  const int64_t plane = (int64_t)nrow * ncp;
-  const int cend = (q0 + w == ncol) ? ncp - q0 : w;   // the last panel also clears the padding columns
-  for (int j = 0; 32 * j < cend; j++) {
-    const int c = 32 * j + lane;
-    if (c >= cend) continue;
-    const T invd = c < w ? T(1) / dsh[c] : T(0);
-#pragma unroll
-    for (int k = 0; k < KR; k++) {
-      const int r = warp + 8 * k;
-      if (r >= nr) continue;
-      const T xv = c < w ? R[r * LDM + c] : T(0);
-      const T l = xv * invd;
-      if (c < w) Lb[(int64_t)(r0 + r) * ncp + q0 + c] = l;
-      if constexpr (sizeof(T) == 4) {
-        if (so >= 0) {
-          float* sp = N.S + so + (int64_t)(r0 + r) * ncp + q0 + c;
-          const float lh = tf32_round(l), wh = tf32_round(xv);
-          sp[0] = lh;
-          sp[plane] = tf32_round(l - lh);
-          sp[2 * plane] = wh;
-          sp[3 * plane] = tf32_round(xv - wh);
-        }
-      }
-    }
-  }
-}
 
 // One launch per macro panel step of a level: for each large front, one
 // CTA in the diagonal role and one per RB rows below the panel in the row

@@ -125,6 +125,23 @@ struct TcProb {
   int32_t ldc, c_in_u, map, row_a, row_b, k0, nk, M, N, Nt;
 };
 
+// One task of the persistent factorisation of a level's large fronts
+// (front_dag.cu): kind DAG_DIAG (diagonal block of panel p), DAG_ROWS (the
+// 64 rows qe + 64 x.. below panel p) or DAG_UPD (tile (x, y) of panel p's
+// trailing update).  cbase / rbase: the front's tile counters (Rt x Ct) and
+// row-task counters (P x Rt) in the level's counter array; slot: the sync
+// slot of (s, p) (sub-block flags at slot + 1 ..); map: the front's first
+// tensor map (4 per front) or -1 for the FMA path.
+enum : int32_t { DAG_DIAG = 0, DAG_ROWS = 1, DAG_UPD = 2 };
+struct DagTask {
+  int32_t kind, s, p, x, y, slot, cbase, rbase, Ct, Rt, map, pad;
+};
+int front_dag_smem(int esz);
+template <typename T>
+void launch_front_dag(const DevPlan& P, const DevNum<T>& N, const DagTask* tasks, int ntasks, int grid, int* head,
+                      int* cnt, int* sync, const CUtensorMap* maps, int* err, double eps, int policy, long long wait,
+                      cudaStream_t st);
+
 void launch_update_tc(const DevPlan& P, const DevNum<float>& N, const TcProb* probs, const int32_t* tile_prob,
                       int64_t ntiles, int stages, const CUtensorMap* maps, int* err, long long wait, cudaStream_t st);
 bool tc_encode_maps(const float* split, int64_t rows, int64_t ld, CUtensorMap* out4, std::string* why);

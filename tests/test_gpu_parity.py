@@ -382,7 +382,7 @@ def test_deep_fronts_elementwise(prec, eta_tol, form, side):
     assert prof[f"macro_panel_{suffix}"]["launches"] >= 5
     assert prof[f"fwd_chain_multi_{suffix}"]["launches"] >= 1
     assert prof[f"bwd_chain_multi_{suffix}"]["launches"] >= 1
-    if prec == "fp32_ir":
+    if prec == "fp32_ir" and form == "condensed":
         assert prof["update_tc_f32"]["launches"] >= 4
     want = (inst.n, inst.m, 0) if form == "stabilized" else (inst.n, 0, 0)
     assert finfo.inertia == want
