@@ -73,6 +73,8 @@ def parse(argv=None):
     ap.add_argument("--no-others", action="store_true",
                     help="condensed300: skip the other workloads and the rho sweep in the default line")
     ap.add_argument("--skip-peaks", action="store_true", help="do not measure the TF32 / FP64 matmul peaks")
+    ap.add_argument("--ir-switch", type=float, default=0.5,
+                    help="Richardson hands over to FGMRES when a step gains less than this factor")
     ap.add_argument("--persistent-fronts", type=int, default=1, choices=[0, 1],
                     help="1: one persistent launch per level for the large fronts; 0: one launch per panel step")
     return ap.parse_args(argv)
@@ -365,6 +367,7 @@ class Runner:
         nk = self.nk
         f = self.spec["form"]
         opts.setdefault("persistent_fronts", self.args.persistent_fronts)
+        opts.setdefault("ir_switch", self.args.ir_switch)
         if self.batch:
             return nk.KKT.batch(f, [(p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind) for p in self.pats],
                                 prec=prec, **opts)

@@ -131,6 +131,10 @@ typedef struct {
                                  dependency-ordered list; 0: one launch per
                                  128-column panel step plus one per trailing
                                  update */
+    double ir_switch;         /* single-instance handles with use_fgmres: Richardson
+                                 hands over to FGMRES as soon as a step reduces the
+                                 backward error by less than this factor (default
+                                 0.5; values outside (0, 1] select it) */
 } ncl_kkt_options;
 
 typedef struct {

@@ -1407,7 +1407,7 @@ ncl_status refine_block(ncl_kkt_s* h, int nrhs, const double* B, int64_t ldb, do
     it++;
     const double prev = eta;
     eta = residual_eta(h, B, ldb, X, ldx, nrhs, st);
-    if (eta > 0.5 * prev && h->opt.use_fgmres && h->dp.ninst == 1) {
+    if (eta > h->opt.ir_switch * prev && h->opt.use_fgmres && h->dp.ninst == 1) {
       stagnated = true;   // Richardson stagnates (kappa * u_factor is not small): switch to FGMRES
       break;
     }
@@ -1763,6 +1763,7 @@ static ncl_status init_options(ncl_kkt_s* h, const ncl_kkt_options* opt) {
   if (!(h->opt.ir_tol > 0)) h->opt.ir_tol = h->opt.prec == NCL_PREC_FP64 ? 1e-12 : 1e-10;
   if (h->opt.ir_max_iter < 0) h->opt.ir_max_iter = h->opt.prec == NCL_PREC_FP64 ? 3 : 10;
   if (h->opt.wait_cycles <= 0) h->opt.wait_cycles = DEFAULT_WAIT_CYCLES;
+  if (!(h->opt.ir_switch > 0.0) || !(h->opt.ir_switch <= 1.0)) h->opt.ir_switch = 0.5;
   return NCL_OK;
 }
 
@@ -1844,6 +1845,7 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->max_device_bytes = 0;
   o->wait_cycles = 0;
   o->persistent_fronts = 1;
+  o->ir_switch = 0.5;
 }
 
 ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m, const int32_t* H_rowptr, const int32_t* H_colind,

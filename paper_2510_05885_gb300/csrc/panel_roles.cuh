@@ -71,32 +71,37 @@ inline int macro_panel_smem(int esz) { return std::max(macro_diag_smem(esz), mac
 // right-looking with column broadcasts by shuffles.  Writes the unit lower
 // factor (strictly below the diagonal) and D on the diagonal back; returns
 // lane's pivot (1 on the padding) and its status in st.
+// reciprocal of a pivot: correctly rounded in FP32 without the general
+// division's slow path (pivots are normal numbers: |d| > eps or replaced)
+__device__ __forceinline__ float pivot_rcp(float d) { return __frcp_rn(d); }
+__device__ __forceinline__ double pivot_rcp(double d) { return 1.0 / d; }
+
 template <typename T>
 __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, double eps, int policy, int lane,
                                        int8_t& st) {
+  // rows and columns past cw are padded with the identity, so every column
+  // step runs unconditionally (its pivot there is 1 and nothing couples to it)
   T r[32];
 #pragma unroll
-  for (int j = 0; j < 32; j++) r[j] = (j <= lane && lane < cw) ? blk[lane * ld + j] : T(0);
+  for (int j = 0; j < 32; j++)
+    r[j] = lane < cw ? ((j <= lane) ? blk[lane * ld + j] : T(0)) : (j == lane ? T(1) : T(0));
   int8_t my_st = 0;
   T my_d = T(1);
 #pragma unroll
   for (int k = 0; k < 32; k++) {
-    if (k < cw) {
-      int8_t stt;
-      const int sg = __shfl_sync(0xffffffffu, my_sign, k);
-      const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
-      const T wk = r[k];
-      // rows above the pivot get a zero multiplier, so the update needs no
-      // per-column select or branch (a predicated branch around each shuffle
-      // costs a reconvergence per shuffle); entries above a lane's diagonal
-      // are never read
-      const T li = lane > k ? wk * (T(1) / dk) : T(0);
+    int8_t stt;
+    const int sg = __shfl_sync(0xffffffffu, my_sign, k);
+    const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
+    const T wk = r[k];
+    // rows above the pivot get a zero multiplier, so the update needs no
+    // per-column select or branch; entries above a lane's diagonal are
+    // never read
+    const T li = lane > k ? wk * pivot_rcp(dk) : T(0);
 #pragma unroll
-      for (int j = k + 1; j < 32; j++) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
-      r[k] = lane > k ? li : (lane == k ? dk : r[k]);
-      my_d = lane == k ? dk : my_d;
-      my_st = lane == k ? stt : my_st;
-    }
+    for (int j = k + 1; j < 32; j++) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
+    r[k] = lane > k ? li : (lane == k ? dk : r[k]);
+    my_d = lane == k ? dk : my_d;
+    my_st = lane == k ? stt : my_st;
   }
   if (lane < cw) {
 #pragma unroll
@@ -309,34 +314,43 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
         const int r = idx >> 5, c = idx & 31;
         const T x = A[(rb + r) * LDM + c0 + c];
         Xs[r * LDS + c] = x;
-        A[(rb + r) * LDM + c0 + c] = x / dsh[c0 + c];
+        A[(rb + r) * LDM + c0 + c] = x * pivot_rcp(dsh[c0 + c]);
       }
       __syncthreads();
-      // the next sub-block's columns, by all warps
-      block_update<T>(A, Xs, c0, rb, w, rb, rb, min(rb + 32, w), 0, 8);
+      // only the next sub-block's diagonal block waits for this update
+      block_update<T>(A, Xs, c0, rb, min(rb + 32, w), rb, rb, min(rb + 32, w), 0, 8);
       __syncthreads();
     }
     if (warp == 0) {
       if (j + 1 < nbk) factor(rb);
     } else {
-      // publish sub-block j: columns [c0, c0 + cw) of rows [c0, w), pivots
+      // publish sub-block j (columns [c0, c0 + cw) of rows [c0, w), pivots)
+      // for the row CTAs: the stores of warps 1..7, their barrier, then one
+      // fence and the release flag
       const int n = (w - c0) * cw;
       for (int idx = tid - 32; idx < n; idx += 224) {
         const int r = idx / cw, c = idx - r * cw;
         if (c <= r) Lb[(int64_t)(c0 + r) * ncp + c0 + c] = A[(c0 + r) * LDM + c0 + c];
       }
       if (tid - 32 < cw) N.D[col0 + q0 + c0 + tid - 32] = dsh[c0 + tid - 32];
-      __threadfence();
       bar_warps_1_7();
-      if (tid == 32) st_release_i32(flags + j, 1);
-      // the columns beyond the next sub-block
-      if (nr > 32) block_update<T>(A, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
+      if (tid == 32) {
+        __threadfence();
+        st_release_i32(flags + j, 1);
+      }
+      // the rest of sub-block j's update, while warp 0 factors the next one:
+      // the next sub-block's columns below its diagonal block, then the
+      // columns beyond it
+      if (nr > 32) {
+        block_update<T>(A, Xs, c0, rb, w, rb + 32, rb, rb + 32, 1, 7);
+        block_update<T>(A, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
+      }
+      // the inverse of the unit lower L_jj (for the triangular sweeps)
+      if (warp == 1)
+        invert_sub32<T>(A + c0 * LDM + c0, LDM, cw, N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + j) * 1024, lane);
     }
     __syncthreads();
   }
-  if (warp < nbk)
-    invert_sub32<T>(A + 32 * warp * LDM + 32 * warp, LDM, min(32, w - 32 * warp),
-                    N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + warp) * 1024, lane);
   for (int c = tid; c < w; c += blockDim.x) N.piv[col0 + q0 + c] = pst[c];
 }
 

@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
                 ("use_tensor_cores", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("precision_fallback", ctypes.c_int32),
                 ("max_device_bytes", ctypes.c_int64), ("wait_cycles", ctypes.c_int64),
-                ("persistent_fronts", ctypes.c_int32)]
+                ("persistent_fronts", ctypes.c_int32), ("ir_switch", ctypes.c_double)]
 
 
 class FactorInfo(ctypes.Structure):

@@ -357,21 +357,23 @@ def test_batch_factor_solve_graph_replay():
 
 # ------------------------------------------------------------------ deep fronts, elementwise
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("prec,eta_tol", [("fp64", 1e-12), ("fp32_ir", 1e-10)])
 @pytest.mark.parametrize("form,side", [("condensed", 80), ("stabilized", 80)])
-def test_deep_fronts_elementwise(prec, eta_tol, form, side):
+def test_deep_fronts_elementwise(prec, eta_tol, form, side, persistent):
     """Grids large enough that the top fronts hold several 128-column macro
     panels (712 pivots condensed, 528 stabilized), tensor-core updates
     (FP32) and supernodes of several 128-row block-rows in the chained
     sweeps: the whole solution against the oracle, elementwise, and the
-    kernel profile showing that those paths ran."""
+    kernel profile showing that those paths ran -- the persistent
+    large-front launch per level, or one launch per panel step."""
     if form == "condensed":
         inst = synth.condensed_grid(side, rho=1e4, draw=2)
     else:
         inst = synth.random_instance(side, side, seed=880 + side, form="stabilized", rho=1e4)
     p = inst.pat
     K = nk().KKT(0 if form == "stabilized" else 1, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind,
-                 prec=prec)
+                 prec=prec, persistent_fronts=persistent)
     nk().ncl_kkt_profile(K._h, 1)
     finfo = K.factor(_t(inst.H_val), _t(inst.J_val), _t(inst.Sigma), inst.delta, inst.rho)
     X, sinfo = K.solve(_t(inst.b))
@@ -379,11 +381,19 @@ def test_deep_fronts_elementwise(prec, eta_tol, form, side):
     prof = nk().ncl_kkt_profile_report(K._h)
     assert K.analysis.max_pivots > 4 * 128
     suffix = "f32" if prec == "fp32_ir" else "f64"
-    assert prof[f"macro_panel_{suffix}"]["launches"] >= 5
+    if persistent:
+        assert prof[f"front_dag_{suffix}"]["launches"] >= 1 and f"macro_panel_{suffix}" not in prof
+    else:
+        assert prof[f"macro_panel_{suffix}"]["launches"] >= 5
     assert prof[f"fwd_chain_multi_{suffix}"]["launches"] >= 1
     assert prof[f"bwd_chain_multi_{suffix}"]["launches"] >= 1
-    if prec == "fp32_ir" and form == "condensed":
+    if prec == "fp32_ir" and not persistent:
+        # the trailing updates of every many-pivot front (roots included)
         assert prof["update_tc_f32"]["launches"] >= 4
+    if prec == "fp32_ir" and persistent and form == "condensed":
+        # the update blocks of the many-pivot fronts with rows below (the
+        # trailing updates run inside the persistent launch)
+        assert prof["update_tc_f32"]["launches"] >= 1
     want = (inst.n, inst.m, 0) if form == "stabilized" else (inst.n, 0, 0)
     assert finfo.inertia == want
     check_against_oracle(inst, prec, X.cpu().numpy(), finfo, sinfo, eta_tol)
