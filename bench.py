@@ -75,6 +75,8 @@ def parse(argv=None):
     ap.add_argument("--skip-peaks", action="store_true", help="do not measure the TF32 / FP64 matmul peaks")
     ap.add_argument("--ir-switch", type=float, default=0.5,
                     help="Richardson hands over to FGMRES when a step gains less than this factor")
+    ap.add_argument("--subtree-sweeps", type=int, default=1, choices=[0, 1],
+                    help="1: the small subtrees of the sweeps one warp each; 0: per-level launches for all")
     ap.add_argument("--persistent-fronts", type=int, default=1, choices=[0, 1],
                     help="1: one persistent launch per level for the large fronts; 0: one launch per panel step")
     return ap.parse_args(argv)
@@ -368,6 +370,7 @@ class Runner:
         f = self.spec["form"]
         opts.setdefault("persistent_fronts", self.args.persistent_fronts)
         opts.setdefault("ir_switch", self.args.ir_switch)
+        opts.setdefault("subtree_sweeps", self.args.subtree_sweeps)
         if self.batch:
             return nk.KKT.batch(f, [(p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind) for p in self.pats],
                                 prec=prec, **opts)
@@ -620,7 +623,8 @@ def run_ours(args):
     # plain FP64 path on the same systems (a handle on the same analysis)
     K64 = None
     if not args.skip_fp64:
-        K64 = nk.KKT.like(K, prec="fp64", persistent_fronts=args.persistent_fronts)
+        K64 = nk.KKT.like(K, prec="fp64", persistent_fronts=args.persistent_fronts,
+                          subtree_sweeps=args.subtree_sweeps)
         n64 = max(2, args.steps // 3)
         ms64, res64, _ = timed(K64, n64, 1)
         t64 = max_over_ranks(sum(ms64))
@@ -691,7 +695,8 @@ def run_ours(args):
                                                    for r in r3 for f, i in zip(r[0], R3.draws[0]))}}
                 if name == "adjoint256":
                     e["fp32_ir"]["adjoint_ms_median"] = statistics.median([r[2] for r in r3])
-                K3b = nk.KKT.like(K3, prec="fp64", persistent_fronts=args.persistent_fronts)
+                K3b = nk.KKT.like(K3, prec="fp64", persistent_fronts=args.persistent_fronts,
+                                  subtree_sweeps=args.subtree_sweeps)
                 m4, r4, _ = timed(K3b, n64_, 1, R3)
                 t4 = max_over_ranks(sum(m4)) / n64_
                 e["fp64"] = {"ms_per_step": t4, "gflops": world * ai3.flops / (t4 * 1e-3) / 1e9,

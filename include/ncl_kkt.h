@@ -135,6 +135,11 @@ typedef struct {
                                  hands over to FGMRES as soon as a step reduces the
                                  backward error by less than this factor (default
                                  0.5; values outside (0, 1] select it) */
+    int32_t subtree_sweeps;   /* 1 (default): in the triangular sweeps, every maximal
+                                 subtree of supernodes with at most 32 pivots is
+                                 swept by one warp (one launch per sweep for all of
+                                 them); 0: those supernodes go through the
+                                 per-level launches like the others */
 } ncl_kkt_options;
 
 typedef struct {

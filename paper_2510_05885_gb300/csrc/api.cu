@@ -148,6 +148,13 @@ struct HostSched {
   bool dag = false;
   std::vector<DagTask> dagv;
   int64_t dag_counters = 0;
+  // triangular sweeps of the region of small subtrees: supernodes with at
+  // most 32 pivots all of whose descendants have at most 32 (one warp per
+  // maximal subtree); the level launches skip them
+  std::vector<int8_t> inreg;
+  std::vector<int32_t> regnodes;          // each subtree's supernodes in postorder
+  std::vector<int2> regitems;             // (first node, count) per subtree
+  Cost reg_fwd_cost, reg_bwd_cost;
 };
 
 }  // namespace
@@ -217,6 +224,8 @@ struct ncl_kkt_s {
   CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
   TcProb* d_tc = nullptr;
   int* d_err = nullptr;                    // device error flags (bounded waits)
+  int2* d_regitems = nullptr;              // small-subtree sweep items and their nodes
+  int32_t* d_regnodes = nullptr;
   DagTask* d_dag = nullptr;                // persistent large-front tasks
   int* d_dag_cnt = nullptr;                //   their queue heads and counters
   int n_sm = 148;                          // multiprocessors of the device
@@ -316,6 +325,45 @@ void build_schedule(ncl_kkt_s* h) {
   hs.dag = h->opt.persistent_fronts != 0;
   hs.dagv.clear();
   hs.dag_counters = (int64_t)P.nlevels;   // one queue head per level first
+  hs.inreg.assign(P.ns, 0);
+  hs.regnodes.clear();
+  hs.regitems.clear();
+  hs.reg_fwd_cost = hs.reg_bwd_cost = Cost{};
+  if (h->opt.subtree_sweeps) {
+    for (int32_t s = 0; s < P.ns; s++) hs.inreg[s] = P.sn_ncol[s] <= 32;
+    // children come before their parent: a supernode outside the region
+    // takes its parent out
+    for (int32_t s = 0; s < P.ns; s++)
+      if (!hs.inreg[s] && P.sn_parent[s] >= 0) hs.inreg[P.sn_parent[s]] = 0;
+    std::vector<int32_t> stack;
+    for (int32_t r = 0; r < P.ns; r++) {
+      if (!hs.inreg[r] || (P.sn_parent[r] >= 0 && hs.inreg[P.sn_parent[r]])) continue;
+      // the subtree of r in postorder (iterative: children first)
+      const int32_t first = (int32_t)hs.regnodes.size();
+      stack.assign(1, r);
+      std::vector<int32_t> pre;
+      while (!stack.empty()) {
+        const int32_t v = stack.back();
+        stack.pop_back();
+        pre.push_back(v);
+        for (int32_t k = P.child_ptr[v]; k < P.child_ptr[v + 1]; k++) stack.push_back(P.child_list[k]);
+      }
+      // reversed preorder (node after its children, children pushed in
+      // order) is a postorder
+      for (auto it = pre.rbegin(); it != pre.rend(); ++it) hs.regnodes.push_back(*it);
+      hs.regitems.push_back(make_int2(first, (int32_t)pre.size()));
+    }
+    for (int32_t s : hs.regnodes) {
+      const double nb = P.sn_nrow[s] - P.sn_ncol[s], nc = P.sn_ncol[s];
+      double child = 0;
+      for (int32_t k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++)
+        child += P.sn_nrow[P.child_list[k]] - P.sn_ncol[P.child_list[k]];
+      hs.reg_fwd_cost.bytes += esz * (1024.0 + nb * nc + 2.0 * nb + child + 2.0 * nc) + 4.0 * child;
+      hs.reg_fwd_cost.flops += 2.0 * (nc * nc + nb * nc);
+      hs.reg_bwd_cost.bytes += esz * (1024.0 + nb * nc + nb + 3.0 * nc) + 4.0 * nb;
+      hs.reg_bwd_cost.flops += 2.0 * (nc * nc + nb * nc);
+    }
+  }
   hs.sn_Soff.assign(P.ns, -1);
   hs.sn_flags.assign(P.ns, 0);
   hs.sn_Ioff.assign(P.ns + 1, 0);
@@ -384,9 +432,11 @@ void build_schedule(ncl_kkt_s* h) {
         // carries its first block-row and first 32-row block) and, per
         // 32-row block, the children's W entries that land on its rows
         const int nblk = (ncol + 31) / 32, nbr = (ncol + CHAIN_ROWS - 1) / CHAIN_ROWS;
-        for (int B = 0; B < nbr; B++) hs.chainv.push_back(make_int4(s, (int32_t)hs.nbrows, (int32_t)hs.nblocks, 0));
-        L.chain_smem = std::max<int64_t>(L.chain_smem, chain_smem(std::min(CHAIN_ROWS, ncol), (int)esz));
-        if (nbr > 1) L.chain_multi = true;
+        if (!hs.inreg[s]) {
+          for (int B = 0; B < nbr; B++) hs.chainv.push_back(make_int4(s, (int32_t)hs.nbrows, (int32_t)hs.nblocks, 0));
+          L.chain_smem = std::max<int64_t>(L.chain_smem, chain_smem(std::min(CHAIN_ROWS, ncol), (int)esz));
+          if (nbr > 1) L.chain_multi = true;
+        }
         for (int b = 0; b < nblk; b++) {
           const int lo = 32 * b, hi = std::min(32 * b + 32, ncol);
           for (int32_t k2 = P.child_ptr[s]; k2 < P.child_ptr[s + 1]; k2++) {
@@ -402,7 +452,7 @@ void build_schedule(ncl_kkt_s* h) {
         hs.nblocks += nblk;
         hs.nbrows += nbr;
       }
-      for (int a0 = 0; a0 < nrow - ncol; a0 += SOLVE_ROWS) {
+      for (int a0 = 0; a0 < nrow - ncol && !hs.inreg[s]; a0 += SOLVE_ROWS) {
         belowv.push_back(make_int2(s, a0));
         for (int k0 = 0; k0 < ncol; k0 += 256) hs.bbelowv.push_back(make_int4(s, a0, k0, 0));
         // the children's W entries that land on the rows [a0, a1) below
@@ -438,13 +488,15 @@ void build_schedule(ncl_kkt_s* h) {
         L.small_cost.flops += 2.0 * (ncol * (double)ncol * ncol / 3.0 + nb * ncol * ncol);
         L.small_cost.bytes += esz * 2.0 * nrow * ncp;
       }
-      L.fdiag_cost.bytes += esz * 0.5 * ncol * (ncol + 1.0);
-      L.fdiag_cost.flops += (double)ncol * ncol;
-      L.fbelow_cost.bytes += esz * nb * ncol;
-      L.fbelow_cost.flops += 2.0 * nb * ncol;
-      L.bdiag_cost = L.fdiag_cost;
-      L.bbelow_cost.bytes += esz * nb * ncol;
-      L.bbelow_cost.flops += 2.0 * nb * ncol;
+      if (!hs.inreg[s]) {
+        L.fdiag_cost.bytes += esz * 0.5 * ncol * (ncol + 1.0);
+        L.fdiag_cost.flops += (double)ncol * ncol;
+        L.fbelow_cost.bytes += esz * nb * ncol;
+        L.fbelow_cost.flops += 2.0 * nb * ncol;
+        L.bdiag_cost = L.fdiag_cost;
+        L.bbelow_cost.bytes += esz * nb * ncol;
+        L.bbelow_cost.flops += 2.0 * nb * ncol;
+      }
     }
     L.asm_cnt = (int)(asmv.size() - L.asm_off);
     L.small_cnt = (int)(smallv.size() - L.small_off);
@@ -664,7 +716,23 @@ void build_schedule(ncl_kkt_s* h) {
             bad("assembly map");
       }
     }
-    if (hs.chain_pptr.size() != (size_t)hs.nblocks + 1 || hs.chainv.size() != (size_t)hs.nbrows) bad("pivot blocks");
+    if (hs.chain_pptr.size() != (size_t)hs.nblocks + 1 || hs.chainv.size() > (size_t)hs.nbrows) bad("pivot blocks");
+    // the small-subtree region: every node once, in a subtree of its own
+    // region, children before parents within it, at most 32 pivots
+    {
+      std::vector<int> seen(P.ns, 0);
+      for (const int2& it : hs.regitems) {
+        if (it.x < 0 || it.y <= 0 || (size_t)(it.x + it.y) > hs.regnodes.size()) bad("subtree item");
+        for (int q = 0; q < it.y; q++) {
+          const int32_t v = hs.regnodes[it.x + q];
+          if (v < 0 || v >= P.ns || !hs.inreg[v] || P.sn_ncol[v] > 32 || seen[v]++) bad("subtree node");
+          for (int32_t k = P.child_ptr[v]; k < P.child_ptr[v + 1]; k++)
+            if (!seen[P.child_list[k]]) bad("subtree order");
+        }
+      }
+      for (int32_t v = 0; v < P.ns; v++)
+        if (hs.inreg[v] && !seen[v]) bad("subtree coverage");
+    }
     for (size_t i = 0; i < hs.chainv.size(); i++) {
       const int4 it = hs.chainv[i];
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y + (P.sn_ncol[it.x] + CHAIN_ROWS - 1) / CHAIN_ROWS > hs.nbrows ||
@@ -987,6 +1055,10 @@ void build_device(ncl_kkt_s* h) {
   }
   h->d_err = h->alloc<int>(4);
   if (!h->hs.dagv.empty()) h->d_dag = h->upload(h->hs.dagv);
+  if (!h->hs.regitems.empty()) {
+    h->d_regitems = h->upload(h->hs.regitems);
+    h->d_regnodes = h->upload(h->hs.regnodes);
+  }
   h->d_dag_cnt = h->alloc<int>(std::max<int64_t>(h->hs.dag_counters, 1));
   {
     int dev = 0, nsm = 0;
@@ -1010,7 +1082,7 @@ void build_device(ncl_kkt_s* h) {
   h->d_chain = h->upload(hs.chainv);
   h->d_chain_pptr = h->upload(hs.chain_pptr);
   h->d_chain_pran = h->upload(hs.chain_pran);
-  h->d_chain_sync = h->alloc<int>(2 * (int64_t)P.ns + 2 * hs.nbrows);
+  h->d_chain_sync = h->alloc<int>(2 * (int64_t)P.ns + 2 * hs.nbrows + 2);   // + the two subtree-sweep counters
   h->d_below = h->upload(hs.belowv);
   h->d_bbelow = h->upload(hs.bbelowv);
   h->d_below_cptr = h->upload(hs.below_cptr);
@@ -1165,7 +1237,14 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
   int* fl_f = tk_b + ns;
   int* fl_b = fl_f + nb;
   int* serr = h->d_err + 1;
-  CK(cudaMemsetAsync(h->d_chain_sync, 0, (2 * ns + 2 * nb) * sizeof(int), st));
+  int* reg_ctr = h->d_chain_sync + 2 * ns + 2 * nb;
+  const HostSched& hs = h->hs;
+  CK(cudaMemsetAsync(h->d_chain_sync, 0, (2 * ns + 2 * nb + 2) * sizeof(int), st));
+  klaunch(h, st, f32 ? "subtree_fwd_f32" : "subtree_fwd_f64", (int64_t)hs.regitems.size(),
+          scaled(hs.reg_fwd_cost, nrhs), [&] {
+            launch_region_fwd<T>(P, N, h->d_regitems, (int)hs.regitems.size(), h->d_regnodes, xp, W, nrhs, reg_ctr,
+                                 h->n_sm, st);
+          });
   for (const Level& L : h->levels) {
     // levels with a supernode of more than one block-row run the chained
     // instantiation (named apart in the profile)
@@ -1192,6 +1271,11 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
                           nrhs, tk_b, fl_b, serr, h->opt.wait_cycles, st);
     });
   }
+  klaunch(h, st, f32 ? "subtree_bwd_f32" : "subtree_bwd_f64", (int64_t)hs.regitems.size(),
+          scaled(hs.reg_bwd_cost, nrhs), [&] {
+            launch_region_bwd<T>(P, N, h->d_regitems, (int)hs.regitems.size(), h->d_regnodes, xp, nrhs, reg_ctr + 1,
+                                 h->n_sm, st);
+          });
   CK(cudaGetLastError());
 }
 
@@ -1846,6 +1930,7 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->wait_cycles = 0;
   o->persistent_fronts = 1;
   o->ir_switch = 0.5;
+  o->subtree_sweeps = 1;
 }
 
 ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m, const int32_t* H_rowptr, const int32_t* H_colind,

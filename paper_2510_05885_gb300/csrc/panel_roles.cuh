@@ -85,13 +85,21 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
 #pragma unroll
   for (int j = 0; j < 32; j++)
     r[j] = lane < cw ? ((j <= lane) ? blk[lane * ld + j] : T(0)) : (j == lane ? T(1) : T(0));
+  // the block signs of the 32 pivots as a bit mask (bit k: pivot k is dual)
+  const unsigned neg = __ballot_sync(0xffffffffu, my_sign < 0);
+  const T e = (T)eps;
+  const int8_t tiny_st = policy == 0 ? 1 : 2;
   int8_t my_st = 0;
   T my_d = T(1);
 #pragma unroll
   for (int k = 0; k < 32; k++) {
-    int8_t stt;
-    const int sg = __shfl_sync(0xffffffffu, my_sign, k);
-    const T dk = static_pivot<T>(__shfl_sync(0xffffffffu, r[k], k), sg, eps, policy, stt);
+    // static pivot (Section 3.1): |d| <= eps -> +-eps by the block sign
+    // (status 1 perturbed / 2 zero), a non-finite pivot is kept (status 3)
+    const T d0 = __shfl_sync(0xffffffffu, r[k], k);
+    const T a = d0 < T(0) ? -d0 : d0;
+    const bool fin = finite_val(d0);
+    const bool tiny = fin && a <= e;
+    const T dk = tiny ? (((neg >> k) & 1u) ? -e : e) : d0;
     const T wk = r[k];
     // rows above the pivot get a zero multiplier, so the update needs no
     // per-column select or branch; entries above a lane's diagonal are
@@ -101,7 +109,7 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
     for (int j = k + 1; j < 32; j++) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
     r[k] = lane > k ? li : (lane == k ? dk : r[k]);
     my_d = lane == k ? dk : my_d;
-    my_st = lane == k ? stt : my_st;
+    my_st = lane == k ? (int8_t)(!fin ? 3 : (tiny ? tiny_st : 0)) : my_st;
   }
   if (lane < cw) {
 #pragma unroll
@@ -145,11 +153,15 @@ __device__ __noinline__ void invert_sub32(const T* blk, int ld, int cw, T* out, 
 // later groups subtract their products with the (g, s) block.  No inverse is
 // formed.  Called by all threads of the CTA (blockDim a multiple of 32).
 template <typename T>
-__device__ __forceinline__ void block_trsm32(T* R, int ldr, int nrows, int ncols, const T* L, int ldl) {
+__device__ __forceinline__ void block_trsm32(T* R, int ldr, int nrows, int ncols, const T* L, int ldl, int t0 = 0,
+                                             int nthr = -1) {
+  // the threads [t0, t0 + nthr) of the CTA (whole warps; all of them by default)
+  if (nthr < 0) nthr = blockDim.x;
+  const int t = threadIdx.x - t0;
   const int lane = threadIdx.x & 31, g = threadIdx.x & 3;
   const int src0 = lane & ~3;
-  for (int r0 = 0; r0 < nrows; r0 += blockDim.x >> 2) {
-    const int row = r0 + (threadIdx.x >> 2);
+  for (int r0 = 0; r0 < nrows; r0 += nthr >> 2) {
+    const int row = r0 + (t >> 2);
     const bool act = row < nrows;
     T* rp = R + (act ? row : 0) * ldr + 8 * g;
     T q[8];
@@ -306,27 +318,40 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
   for (int j = 0; j < nbk; j++) {
     const int c0 = 32 * j, cw = min(32, w - c0);
     const int rb = c0 + 32, nr = w - rb;
+    const int nn = min(32, max(nr, 0));   // rows of the next sub-block
     if (nr > 0) {
-      // rows below the sub-block: X = F21 L_jj^-T (kept), L21 = X D^-1
-      block_trsm32<T>(A + rb * LDM + c0, LDM, nr, 32, A + c0 * LDM + c0, LDM);
+      // the critical path: only the next sub-block's rows are solved,
+      // X = F21 L_jj^-T (kept), L21 = X D^-1, and its diagonal block updated
+      block_trsm32<T>(A + rb * LDM + c0, LDM, nn, 32, A + c0 * LDM + c0, LDM);
       __syncthreads();
-      for (int idx = tid; idx < nr * 32; idx += blockDim.x) {
+      for (int idx = tid; idx < nn * 32; idx += blockDim.x) {
         const int r = idx >> 5, c = idx & 31;
         const T x = A[(rb + r) * LDM + c0 + c];
         Xs[r * LDS + c] = x;
         A[(rb + r) * LDM + c0 + c] = x * pivot_rcp(dsh[c0 + c]);
       }
       __syncthreads();
-      // only the next sub-block's diagonal block waits for this update
-      block_update<T>(A, Xs, c0, rb, min(rb + 32, w), rb, rb, min(rb + 32, w), 0, 8);
+      block_update<T>(A, Xs, c0, rb, rb + nn, rb, rb, rb + nn, 0, 8);
       __syncthreads();
     }
     if (warp == 0) {
       if (j + 1 < nbk) factor(rb);
     } else {
-      // publish sub-block j (columns [c0, c0 + cw) of rows [c0, w), pivots)
-      // for the row CTAs: the stores of warps 1..7, their barrier, then one
-      // fence and the release flag
+      // warps 1..7, while warp 0 factors the next sub-block: the remaining
+      // rows below it, the publication of sub-block j (columns [c0, c0 + cw)
+      // of rows [c0, w), pivots; one fence after the warps' barrier, then
+      // the release flag) and the rest of sub-block j's update
+      if (nr > 32) {
+        block_trsm32<T>(A + (rb + 32) * LDM + c0, LDM, nr - 32, 32, A + c0 * LDM + c0, LDM, 32, 224);
+        bar_warps_1_7();
+        for (int idx = tid - 32; idx < (nr - 32) * 32; idx += 224) {
+          const int r = 32 + (idx >> 5), c = idx & 31;
+          const T x = A[(rb + r) * LDM + c0 + c];
+          Xs[r * LDS + c] = x;
+          A[(rb + r) * LDM + c0 + c] = x * pivot_rcp(dsh[c0 + c]);
+        }
+        bar_warps_1_7();
+      }
       const int n = (w - c0) * cw;
       for (int idx = tid - 32; idx < n; idx += 224) {
         const int r = idx / cw, c = idx - r * cw;
@@ -338,19 +363,19 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
         __threadfence();
         st_release_i32(flags + j, 1);
       }
-      // the rest of sub-block j's update, while warp 0 factors the next one:
-      // the next sub-block's columns below its diagonal block, then the
-      // columns beyond it
       if (nr > 32) {
         block_update<T>(A, Xs, c0, rb, w, rb + 32, rb, rb + 32, 1, 7);
         block_update<T>(A, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
       }
-      // the inverse of the unit lower L_jj (for the triangular sweeps)
-      if (warp == 1)
-        invert_sub32<T>(A + c0 * LDM + c0, LDM, cw, N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + j) * 1024, lane);
     }
     __syncthreads();
   }
+  // the inverses of the unit lower diagonal sub-blocks (for the triangular
+  // sweeps), after the last publication: nothing waits for them inside the
+  // factorisation
+  if (warp < nbk)
+    invert_sub32<T>(A + 32 * warp * LDM + 32 * warp, LDM, min(32, w - 32 * warp),
+                    N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + warp) * 1024, lane);
   for (int c = tid; c < w; c += blockDim.x) N.piv[col0 + q0 + c] = pst[c];
 }
 

@@ -206,6 +206,13 @@ void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, i
 template <typename T>
 void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi, T* xp,
                       const T* Pw, int nrhs, int* tickets, int* flags, int* err, long long wait, cudaStream_t st);
+int region_smem(int esz);
+template <typename T>
+void launch_region_fwd(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes, T* xp,
+                       T* W, int nrhs, int* counter, int nsm, cudaStream_t st);
+template <typename T>
+void launch_region_bwd(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes, T* xp,
+                       int nrhs, int* counter, int nsm, cudaStream_t st);
 void launch_residual(const DevPlan& P, const double* Klow, const double* B, int64_t ldb, const double* X,
                      int64_t ldx, double* R, int64_t ldr, int nrhs, unsigned long long* rnorm,
                      unsigned long long* xnorm, cudaStream_t st);

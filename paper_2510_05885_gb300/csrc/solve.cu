@@ -11,6 +11,8 @@
 #include "runtime.h"
 #include "reduce.cuh"
 
+#include <algorithm>
+
 namespace ncl {
 
 // ---------------------------------------------------------------------------
@@ -616,6 +618,193 @@ void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, i
 }
 
 // ---------------------------------------------------------------------------
+// Sweeps over the subtrees of small supernodes.
+//
+// Near the leaves the assembly tree holds very many supernodes of a few
+// columns (at the 700 x 700 grid 170k of 184k supernodes have at most 32
+// pivots); per-level launches with one CTA per supernode or per 64 rows keep
+// most lanes idle there.  A supernode with at most 32 pivots all of whose
+// descendants have at most 32 as well belongs to a region of small
+// subtrees; each maximal subtree of it is swept by ONE warp, supernode by
+// supernode in postorder (forward) or in reverse (backward), so no flags or
+// launches separate a supernode from its children.  The region's forward
+// sweep runs before the level launches of the rest of the tree, its
+// backward sweep after them.  Lane c holds column c of the supernode; the
+// 32 x 32 inverse of its unit lower pivot block is staged in the warp's
+// shared memory (row stride 33).
+//   forward:  t = own entries + children's updates (in child order),
+//             y = L11^-1 t, W_s = children's updates below - L21 y;
+//   backward: z = D^-1 y - L21^T x_below, x = L11^-T z.
+// ---------------------------------------------------------------------------
+constexpr int REG_WARPS = 8;
+
+template <typename T>
+__device__ __forceinline__ void region_stage_inverse(const DevPlan& P, const DevNum<T>& N, int s, T* iv, int lane) {
+  const T* ip = N.Linv + P.sn_Ioff[s];
+#pragma unroll 8
+  for (int i = 0; i < 32; i++) iv[i * 33 + lane] = ip[i * 32 + lane];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_region_fwd(DevPlan P, DevNum<T> N, const int2* __restrict__ items, int count,
+                                                    const int32_t* __restrict__ nodes, T* __restrict__ xp,
+                                                    T* __restrict__ W, int nrhs, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* iv = reinterpret_cast<T*>(smem_raw) + warp * (32 * 33 + MAX_RHS_SWEEP * 33);
+  T* tb = iv + 32 * 33;                              // [MAX_RHS_SWEEP][33]
+  const int64_t dim = P.dim, Wtot = P.Wtot;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= count) break;
+    const int2 item = items[it];
+    for (int q = 0; q < item.y; q++) {
+      const int s = nodes[item.x + q];
+      const int ncol = P.sn_ncol[s], nb = P.sn_nrow[s] - ncol, ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+      T* Ws = W + P.sn_Woff[s];
+      region_stage_inverse(P, N, s, iv, lane);
+      for (int r = 0; r < nrhs; r++) tb[r * 33 + lane] = lane < ncol ? xp[r * dim + col0 + lane] : T(0);
+      for (int a = lane; a < nb; a += 32)
+        for (int r = 0; r < nrhs; r++) Ws[r * Wtot + a] = T(0);
+      __syncwarp();
+      // the children's updates, child by child (distinct rows within a child)
+      for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
+        const int c = P.child_list[k];
+        const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
+        const int32_t* rel = P.relmap + P.relmap_off[c];
+        const T* Wc = W + P.sn_Woff[c];
+        for (int a = lane; a < nbc; a += 32) {
+          const int row = rel[a];
+          for (int r = 0; r < nrhs; r++) {
+            const T v = Wc[r * Wtot + a];
+            if (row < ncol) tb[r * 33 + row] += v;
+            else Ws[r * Wtot + row - ncol] += v;
+          }
+        }
+        __syncwarp();
+      }
+      // y = L11^-1 t (unit lower inverse, lane = row)
+      for (int r = 0; r < nrhs; r++) {
+        T y = T(0);
+#pragma unroll 8
+        for (int u = 0; u < 32; u++) y += iv[lane * 33 + u] * tb[r * 33 + u];
+        __syncwarp();
+        tb[r * 33 + lane] = lane < ncol ? y : T(0);
+        if (lane < ncol) xp[r * dim + col0 + lane] = y;
+      }
+      __syncwarp();
+      // W_s -= L21 y (lane = row below, 16-byte vectors of its row)
+      using V = typename Vec16<T>::type;
+      constexpr int VW = Vec16<T>::n;
+      const int nv = (ncol + VW - 1) / VW;
+      for (int a = lane; a < nb; a += 32) {
+        const V* row = reinterpret_cast<const V*>(N.L + P.sn_Loff[s] + (int64_t)(ncol + a) * ncp);
+        T acc[MAX_RHS_SWEEP];
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
+        for (int v = 0; v < nv; v++) {
+          const V lv = __ldg(row + v);
+#pragma unroll
+          for (int e = 0; e < VW; e++) {
+            const int k = v * VW + e;
+            if (k >= ncol) break;
+            const T l = reinterpret_cast<const T*>(&lv)[e];
+#pragma unroll
+            for (int r = 0; r < MAX_RHS_SWEEP; r++)
+              if (r < nrhs) acc[r] += l * tb[r * 33 + k];
+          }
+        }
+        for (int r = 0; r < nrhs; r++) Ws[r * Wtot + a] -= acc[r];
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_region_bwd(DevPlan P, DevNum<T> N, const int2* __restrict__ items, int count,
+                                                    const int32_t* __restrict__ nodes, T* __restrict__ xp, int nrhs,
+                                                    int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* iv = reinterpret_cast<T*>(smem_raw) + warp * (32 * 33 + MAX_RHS_SWEEP * 33);
+  T* zb = iv + 32 * 33;                              // [MAX_RHS_SWEEP][33]
+  const int64_t dim = P.dim;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= count) break;
+    const int2 item = items[it];
+    for (int q = item.y - 1; q >= 0; q--) {
+      const int s = nodes[item.x + q];
+      const int ncol = P.sn_ncol[s], nb = P.sn_nrow[s] - ncol, ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+      const T* Lb = N.L + P.sn_Loff[s] + (int64_t)ncol * ncp;
+      const int32_t* rows = P.sn_rows + P.sn_rows_off[s] + ncol;
+      region_stage_inverse(P, N, s, iv, lane);
+      // z = D^-1 y - L21^T x_below (lane = column; the rows of L21 are read
+      // whole by the warp, x_below broadcast)
+      const T dk = lane < ncol ? N.D[col0 + lane] : T(1);
+      T acc[MAX_RHS_SWEEP];
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
+      const int cl = min(lane, max(ncol - 1, 0));
+#pragma unroll 4
+      for (int a = 0; a < nb; a++) {
+        const T l = Lb[(int64_t)a * ncp + cl];
+        const int row = rows[a];
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++)
+          if (r < nrhs) acc[r] += l * xp[r * dim + row];
+      }
+      for (int r = 0; r < nrhs; r++)
+        zb[r * 33 + lane] = lane < ncol ? xp[r * dim + col0 + lane] / dk - acc[r] : T(0);
+      __syncwarp();
+      // x = L11^-T z (lane = column of the inverse)
+      for (int r = 0; r < nrhs; r++) {
+        T x = T(0);
+#pragma unroll 8
+        for (int u = 0; u < 32; u++) x += iv[u * 33 + lane] * zb[r * 33 + u];
+        if (lane < ncol) xp[r * dim + col0 + lane] = x;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+int region_smem(int esz) { return REG_WARPS * (32 * 33 + MAX_RHS_SWEEP * 33) * esz; }
+
+template <typename T>
+void launch_region_fwd(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes, T* xp,
+                       T* W, int nrhs, int* counter, int nsm, cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  const int smem = region_smem((int)sizeof(T));
+  if (!attr) {
+    cudaFuncSetAttribute(k_region_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  const int grid = std::min((count + REG_WARPS - 1) / REG_WARPS, nsm * 4);
+  k_region_fwd<T><<<grid, 32 * REG_WARPS, smem, st>>>(P, N, items, count, nodes, xp, W, nrhs, counter);
+}
+
+template <typename T>
+void launch_region_bwd(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes, T* xp,
+                       int nrhs, int* counter, int nsm, cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  const int smem = region_smem((int)sizeof(T));
+  if (!attr) {
+    cudaFuncSetAttribute(k_region_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  const int grid = std::min((count + REG_WARPS - 1) / REG_WARPS, nsm * 4);
+  k_region_bwd<T><<<grid, 32 * REG_WARPS, smem, st>>>(P, N, items, count, nodes, xp, nrhs, counter);
+}
+
+// ---------------------------------------------------------------------------
 // FP64 residual R = B - K X on the FP64 KKT values (8 lanes per row), with
 // per-instance ||R||_inf and ||X||_inf (bit patterns, atomicMax).
 // ---------------------------------------------------------------------------
@@ -1064,7 +1253,11 @@ void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, co
   template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int4*, int, const T*, T*, int,        \
                                     cudaStream_t);                                                                \
   template void launch_bwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, bool, T*, const T*, \
-                                    int, int*, int*, int*, long long, cudaStream_t);
+                                    int, int*, int*, int*, long long, cudaStream_t);                            \
+  template void launch_region_fwd<T>(const DevPlan&, const DevNum<T>&, const int2*, int, const int32_t*, T*, T*, \
+                                     int, int*, int, cudaStream_t);                                              \
+  template void launch_region_bwd<T>(const DevPlan&, const DevNum<T>&, const int2*, int, const int32_t*, T*, int, \
+                                     int*, int, cudaStream_t);
 NCL_INST(float)
 NCL_INST(double)
 #undef NCL_INST

@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
                 ("use_tensor_cores", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("precision_fallback", ctypes.c_int32),
                 ("max_device_bytes", ctypes.c_int64), ("wait_cycles", ctypes.c_int64),
-                ("persistent_fronts", ctypes.c_int32), ("ir_switch", ctypes.c_double)]
+                ("persistent_fronts", ctypes.c_int32), ("ir_switch", ctypes.c_double),
+                ("subtree_sweeps", ctypes.c_int32)]
 
 
 class FactorInfo(ctypes.Structure):

@@ -366,14 +366,15 @@ def test_deep_fronts_elementwise(prec, eta_tol, form, side, persistent):
     (FP32) and supernodes of several 128-row block-rows in the chained
     sweeps: the whole solution against the oracle, elementwise, and the
     kernel profile showing that those paths ran -- the persistent
-    large-front launch per level, or one launch per panel step."""
+    large-front launch per level and the small-subtree sweeps, or one launch
+    per panel step and per-level sweeps throughout."""
     if form == "condensed":
         inst = synth.condensed_grid(side, rho=1e4, draw=2)
     else:
         inst = synth.random_instance(side, side, seed=880 + side, form="stabilized", rho=1e4)
     p = inst.pat
     K = nk().KKT(0 if form == "stabilized" else 1, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind,
-                 prec=prec, persistent_fronts=persistent)
+                 prec=prec, persistent_fronts=persistent, subtree_sweeps=persistent)
     nk().ncl_kkt_profile(K._h, 1)
     finfo = K.factor(_t(inst.H_val), _t(inst.J_val), _t(inst.Sigma), inst.delta, inst.rho)
     X, sinfo = K.solve(_t(inst.b))
@@ -383,8 +384,10 @@ def test_deep_fronts_elementwise(prec, eta_tol, form, side, persistent):
     suffix = "f32" if prec == "fp32_ir" else "f64"
     if persistent:
         assert prof[f"front_dag_{suffix}"]["launches"] >= 1 and f"macro_panel_{suffix}" not in prof
+        assert prof[f"subtree_fwd_{suffix}"]["launches"] == 1 and prof[f"subtree_bwd_{suffix}"]["launches"] == 1
     else:
         assert prof[f"macro_panel_{suffix}"]["launches"] >= 5
+        assert f"subtree_fwd_{suffix}" not in prof
     assert prof[f"fwd_chain_multi_{suffix}"]["launches"] >= 1
     assert prof[f"bwd_chain_multi_{suffix}"]["launches"] >= 1
     if prec == "fp32_ir" and not persistent:
