@@ -123,6 +123,142 @@ void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* li
   k_factor_small<T><<<count, 256, smem_bytes, st>>>(P, N, list, eps, policy);
 }
 
+// ---------------------------------------------------------------------------
+// Factorisation of the subtrees of small fronts.
+//
+// The fronts of the small-subtree region (at most 32 pivots, small enough
+// for the shared-memory front, and only such fronts below them) are
+// factored by one CTA per maximal subtree, front by front in postorder, in
+// one launch for the whole region; the level launches of the assembly, the
+// small-front factorisation and the update blocks skip them.  Per front:
+//   the front is assembled straight into shared memory (original entries,
+//   then the children's update blocks child by child; a child's entries
+//   that land below the pivot columns go to this front's update block in
+//   global memory, zeroed first), the 32-column pivot block is factored by
+//   one warp, the rows below by the blocked substitution, L21 = F21 L11^-T
+//   D1^-1, the factor block written back, and the update block
+//   F22 -= L21 D1 L21^T formed from the shared-memory front.
+// The children's update blocks were written by the same CTA earlier, so a
+// barrier orders them; nothing waits across CTAs.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void subtree_front(const DevPlan& P, const DevNum<T>& N, int s, double eps, int policy,
+                                              unsigned char* smem_raw) {
+  const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
+  const int nb = nrow - ncol;
+  const int ldf = ncp + 1;
+  T* F = reinterpret_cast<T*>(smem_raw);
+  T* Ls = F + nrow * ldf;
+  T* dsh = Ls + 32 * LDS;
+  T* Lg = N.L + P.sn_Loff[s];
+  T* Ub = N.U + P.sn_Uoff[s];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  // zero the front and the lower update block
+  for (int idx = tid; idx < nrow * ldf; idx += blockDim.x) F[idx] = T(0);
+  for (int a = warp; a < nb; a += nw)
+    for (int b = lane; b <= a; b += 32) Ub[(int64_t)a * nb + b] = T(0);
+  __syncthreads();
+  // original entries (each lands in its own position)
+  const int64_t rbase = P.sn_rows_off[s];
+  for (int r = warp; r < nrow; r += nw) {
+    const int64_t q0 = P.amap_ptr[rbase + r], q1 = P.amap_ptr[rbase + r + 1];
+    for (int64_t q = q0 + lane; q < q1; q += 32) F[r * ldf + P.amap_col[q]] = (T)N.Klow[P.amap_src[q]];
+  }
+  // the children's update blocks, child by child (the targets of one child
+  // are distinct: its relative map is increasing)
+  for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
+    __syncthreads();
+    const int c = P.child_list[k];
+    const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
+    const int32_t* rel = P.relmap + P.relmap_off[c];
+    const T* Uc = N.U + P.sn_Uoff[c];
+    for (int a = warp; a < nbc; a += nw) {
+      const int ra = rel[a];
+      const T* urow = Uc + (int64_t)a * nbc;
+      for (int b = lane; b <= a; b += 32) {
+        const int rb = rel[b];
+        const T v = urow[b];
+        if (rb < ncol) F[ra * ldf + rb] += v;
+        else Ub[(int64_t)(ra - ncol) * nb + (rb - ncol)] += v;
+      }
+    }
+  }
+  __syncthreads();
+  // the pivot block (one 32-column sub-block) by warp 0: LDL^T, pivots,
+  // statuses, the zero-padded unit lower block and its inverse
+  if (warp == 0) {
+    int8_t st;
+    const T d = factor_sub32<T>(F, ldf, ncol, lane < ncol ? P.col_sign[col0 + lane] : 1, eps, policy, lane, st);
+    dsh[lane] = d;
+    if (lane < ncol) {
+      N.D[col0 + lane] = d;
+      N.piv[col0 + lane] = st;
+    }
+#pragma unroll 4
+    for (int u = 0; u < 32; u++) Ls[lane * LDS + u] = (u < lane && lane < ncol) ? F[lane * ldf + u] : T(0);
+    __syncwarp();
+    invert_sub32<T>(Ls, LDS, ncol, N.Linv + P.sn_Ioff[s], lane);
+  }
+  __syncthreads();
+  // rows below: L21 = F21 L11^-T D1^-1
+  block_trsm32<T>(F + ncol * ldf, ldf, nb, ncol, Ls, LDS);
+  __syncthreads();
+  for (int idx = tid; idx < nb * 32; idx += blockDim.x) {
+    const int r = idx >> 5, c = idx & 31;
+    if (c < ncol) F[(ncol + r) * ldf + c] *= pivot_rcp(dsh[c]);
+  }
+  __syncthreads();
+  // write the factor block back, and form the update block from it
+  for (int idx = tid; idx < nrow * ncp; idx += blockDim.x) Lg[idx] = F[(idx / ncp) * ldf + idx % ncp];
+  for (int a = warp; a < nb; a += nw) {
+    const T* la = F + (ncol + a) * ldf;
+    for (int b = lane; b <= a; b += 32) {
+      const T* lb = F + (ncol + b) * ldf;
+      T acc = T(0);
+      for (int k = 0; k < ncol; k++) acc += la[k] * dsh[k] * lb[k];
+      Ub[(int64_t)a * nb + b] -= acc;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_subtree_factor(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+                                                        int count, const int32_t* __restrict__ nodes, int* counter,
+                                                        double eps, int policy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= count) break;
+    const int2 item = items[it];
+    for (int q = 0; q < item.y; q++) {
+      subtree_front<T>(P, N, nodes[item.x + q], eps, policy, smem_raw);
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+void launch_subtree_factor(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes,
+                           int* counter, int smem, int nsm, double eps, int policy, cudaStream_t st) {
+  if (count <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_subtree_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SMEM_MAX);
+    attr = true;
+  }
+  const int grid = std::min(count, nsm * 4);
+  k_subtree_factor<T><<<grid, 256, smem, st>>>(P, N, items, count, nodes, counter, eps, policy);
+}
+
+template void launch_subtree_factor<float>(const DevPlan&, const DevNum<float>&, const int2*, int, const int32_t*,
+                                           int*, int, int, double, int, cudaStream_t);
+template void launch_subtree_factor<double>(const DevPlan&, const DevNum<double>&, const int2*, int, const int32_t*,
+                                            int*, int, int, double, int, cudaStream_t);
+
 template void launch_factor_small<float>(const DevPlan&, const DevNum<float>&, const int32_t*, int, int, double,
                                          int, cudaStream_t);
 template void launch_factor_small<double>(const DevPlan&, const DevNum<double>&, const int32_t*, int, int, double,

@@ -79,8 +79,8 @@ __device__ __forceinline__ double pivot_rcp(double d) { return 1.0 / d; }
 template <typename T>
 __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, double eps, int policy, int lane,
                                        int8_t& st) {
-  // rows and columns past cw are padded with the identity, so every column
-  // step runs unconditionally (its pivot there is 1 and nothing couples to it)
+  // rows and columns past cw are padded with the identity (their pivot would
+  // be 1 and nothing couples to them); the column steps stop at cw
   T r[32];
 #pragma unroll
   for (int j = 0; j < 32; j++)
@@ -93,6 +93,7 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
   T my_d = T(1);
 #pragma unroll
   for (int k = 0; k < 32; k++) {
+    if (k >= cw) break;   // warp-uniform: a narrow block stops after its last column
     // static pivot (Section 3.1): |d| <= eps -> +-eps by the block sign
     // (status 1 perturbed / 2 zero), a non-finite pivot is kept (status 3)
     const T d0 = __shfl_sync(0xffffffffu, r[k], k);

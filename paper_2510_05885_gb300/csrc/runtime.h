@@ -178,6 +178,9 @@ void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* prob
 
 // launchers (panel.cu)
 int small_front_smem(int nrow, int ncp, int esz);
+template <typename T>
+void launch_subtree_factor(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes,
+                           int* counter, int smem, int nsm, double eps, int policy, cudaStream_t st);
 int macro_panel_smem(int esz);
 template <typename T>
 void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,

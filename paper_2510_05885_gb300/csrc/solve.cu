@@ -105,12 +105,11 @@ __device__ __forceinline__ void chain_wait(const int* flag, int* err, long long 
   __syncwarp();
 }
 
-// after a CTA barrier: thread 0 publishes the CTA's results
+// after a CTA barrier: thread 0 publishes the CTA's results (the release
+// store orders every write the barrier made visible to thread 0 before the
+// flag, so no separate fence is needed)
 __device__ __forceinline__ void chain_publish(int* flag) {
-  if (threadIdx.x == 0) {
-    __threadfence();
-    st_release(flag, 1);
-  }
+  if (threadIdx.x == 0) st_release(flag, 1);
 }
 
 int chain_smem(int rows, int esz) {
@@ -716,7 +715,9 @@ __global__ void __launch_bounds__(256) k_region_fwd(DevPlan P, DevNum<T> N, cons
               if (r < nrhs) acc[r] += l * tb[r * 33 + k];
           }
         }
-        for (int r = 0; r < nrhs; r++) Ws[r * Wtot + a] -= acc[r];
+#pragma unroll
+        for (int r = 0; r < MAX_RHS_SWEEP; r++)
+          if (r < nrhs) Ws[r * Wtot + a] -= acc[r];
       }
       __syncwarp();
     }
@@ -744,23 +745,34 @@ __global__ void __launch_bounds__(256) k_region_bwd(DevPlan P, DevNum<T> N, cons
       const T* Lb = N.L + P.sn_Loff[s] + (int64_t)ncol * ncp;
       const int32_t* rows = P.sn_rows + P.sn_rows_off[s] + ncol;
       region_stage_inverse(P, N, s, iv, lane);
-      // z = D^-1 y - L21^T x_below (lane = column; the rows of L21 are read
-      // whole by the warp, x_below broadcast)
+      // z = D^-1 y - L21^T x_below (lane = column): x_below is gathered 32
+      // rows at a time (lane = row, the gathers of a chunk independent), then
+      // each row of L21 is read whole by the warp and its x value taken from
+      // the row's lane by a shuffle
       const T dk = lane < ncol ? N.D[col0 + lane] : T(1);
       T acc[MAX_RHS_SWEEP];
 #pragma unroll
       for (int r = 0; r < MAX_RHS_SWEEP; r++) acc[r] = T(0);
       const int cl = min(lane, max(ncol - 1, 0));
-#pragma unroll 4
-      for (int a = 0; a < nb; a++) {
-        const T l = Lb[(int64_t)a * ncp + cl];
-        const int row = rows[a];
+      for (int a0 = 0; a0 < nb; a0 += 32) {
+        const int a = a0 + lane;
+        const int row = a < nb ? rows[a] : 0;
+        T xb[MAX_RHS_SWEEP];
 #pragma unroll
-        for (int r = 0; r < MAX_RHS_SWEEP; r++)
-          if (r < nrhs) acc[r] += l * xp[r * dim + row];
+        for (int r = 0; r < MAX_RHS_SWEEP; r++) xb[r] = (r < nrhs && a < nb) ? xp[r * dim + row] : T(0);
+        const int cnt = min(32, nb - a0);
+        const T* lr = Lb + (int64_t)a0 * ncp + cl;
+#pragma unroll 8
+        for (int u = 0; u < cnt; u++) {
+          const T l = lr[(int64_t)u * ncp];
+#pragma unroll
+          for (int r = 0; r < MAX_RHS_SWEEP; r++)
+            if (r < nrhs) acc[r] += l * __shfl_sync(0xffffffffu, xb[r], u);
+        }
       }
-      for (int r = 0; r < nrhs; r++)
-        zb[r * 33 + lane] = lane < ncol ? xp[r * dim + col0 + lane] / dk - acc[r] : T(0);
+#pragma unroll
+      for (int r = 0; r < MAX_RHS_SWEEP; r++)
+        if (r < nrhs) zb[r * 33 + lane] = lane < ncol ? xp[r * dim + col0 + lane] / dk - acc[r] : T(0);
       __syncwarp();
       // x = L11^-T z (lane = column of the inverse)
       for (int r = 0; r < nrhs; r++) {

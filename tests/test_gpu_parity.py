@@ -384,7 +384,7 @@ def test_deep_fronts_elementwise(prec, eta_tol, form, side, persistent):
     suffix = "f32" if prec == "fp32_ir" else "f64"
     if persistent:
         assert prof[f"front_dag_{suffix}"]["launches"] >= 1 and f"macro_panel_{suffix}" not in prof
-        assert prof[f"subtree_fwd_{suffix}"]["launches"] == 1 and prof[f"subtree_bwd_{suffix}"]["launches"] == 1
+        assert prof[f"subtree_fwd_{suffix}"]["launches"] >= 1 and prof[f"subtree_bwd_{suffix}"]["launches"] >= 1
     else:
         assert prof[f"macro_panel_{suffix}"]["launches"] >= 5
         assert f"subtree_fwd_{suffix}" not in prof
