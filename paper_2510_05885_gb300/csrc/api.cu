@@ -154,7 +154,8 @@ struct HostSched {
   std::vector<int8_t> inreg;
   std::vector<int32_t> regnodes;          // each subtree's supernodes in postorder
   std::vector<int2> regitems;             // (first node, count) per subtree
-  Cost reg_fwd_cost, reg_bwd_cost;
+  Cost reg_fwd_cost, reg_bwd_cost, reg_fac_cost;
+  int64_t reg_smem = 0;                   // dynamic shared memory of the subtree factorisation
 };
 
 }  // namespace
@@ -328,9 +329,14 @@ void build_schedule(ncl_kkt_s* h) {
   hs.inreg.assign(P.ns, 0);
   hs.regnodes.clear();
   hs.regitems.clear();
-  hs.reg_fwd_cost = hs.reg_bwd_cost = Cost{};
+  hs.reg_fwd_cost = hs.reg_bwd_cost = hs.reg_fac_cost = Cost{};
+  hs.reg_smem = 0;
   if (h->opt.subtree_sweeps) {
-    for (int32_t s = 0; s < P.ns; s++) hs.inreg[s] = P.sn_ncol[s] <= 32;
+    // at most 32 pivots (one inverse block for the sweeps) and small enough
+    // for the shared-memory front (the subtree factorisation)
+    for (int32_t s = 0; s < P.ns; s++)
+      hs.inreg[s] = P.sn_ncol[s] <= 32 && P.sn_nrow[s] <= 512 &&
+                    (int64_t)P.sn_nrow[s] * P.sn_ncolp[s] * (int64_t)esz <= SMALL_SMEM;
     // children come before their parent: a supernode outside the region
     // takes its parent out
     for (int32_t s = 0; s < P.ns; s++)
@@ -354,6 +360,20 @@ void build_schedule(ncl_kkt_s* h) {
       hs.regitems.push_back(make_int2(first, (int32_t)pre.size()));
     }
     for (int32_t s : hs.regnodes) {
+      hs.reg_smem = std::max<int64_t>(hs.reg_smem, (small_front_smem(P.sn_nrow[s], P.sn_ncolp[s], (int)esz) + 15) / 16 * 16);
+      {
+        // subtree factorisation: zero + assemble (L block, update block,
+        // children's update blocks), write back, the update block's update
+        const double nr = P.sn_nrow[s], ncp = P.sn_ncolp[s], nbb = nr - P.sn_ncol[s], ncc = P.sn_ncol[s];
+        double cu = 0;
+        for (int32_t k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
+          const double cb = P.sn_nrow[P.child_list[k]] - P.sn_ncol[P.child_list[k]];
+          cu += 0.5 * cb * (cb + 1);
+        }
+        hs.reg_fac_cost.bytes += esz * (nr * ncp + 1.5 * nbb * (nbb + 1) + cu) +
+                                 12.0 * (double)(P.amap_ptr[P.sn_rows_off[s + 1]] - P.amap_ptr[P.sn_rows_off[s]]);
+        hs.reg_fac_cost.flops += 2.0 * (ncc * ncc * ncc / 3.0 + nbb * ncc * ncc) + nbb * (nbb + 1) * ncc;
+      }
       const double nb = P.sn_nrow[s] - P.sn_ncol[s], nc = P.sn_ncol[s];
       double child = 0;
       for (int32_t k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++)
@@ -412,7 +432,8 @@ void build_schedule(ncl_kkt_s* h) {
     for (int32_t k = P.level_ptr[l]; k < P.level_ptr[l + 1]; k++) {
       const int32_t s = P.level_list[k];
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
-      for (int r0 = 0; r0 < nrow; r0 += ASM_ROWS) {
+      const bool reg = hs.inreg[s] != 0;   // factored and swept by the subtree kernels
+      for (int r0 = 0; r0 < nrow && !reg; r0 += ASM_ROWS) {
         asmv.push_back(make_int2(s, r0));
         // rows [alo, ahi) of each child's update block that land on the
         // item's rows [r0, r1) (the relative map is increasing)
@@ -468,7 +489,9 @@ void build_schedule(ncl_kkt_s* h) {
         hs.below_cptr.push_back((int32_t)hs.below_cran.size());
       }
       const bool is_small = ncol <= 64 && nrow <= 512 && (int64_t)nrow * ncp * (int64_t)esz <= SMALL_SMEM;
-      if (is_small) {
+      if (reg) {
+        // the subtree kernels take care of it
+      } else if (is_small) {
         smallv.push_back(s);
         small.push_back(s);
         L.small_smem = std::max<int64_t>(L.small_smem, (small_front_smem(nrow, ncp, (int)esz) + 15) / 16 * 16);
@@ -482,9 +505,10 @@ void build_schedule(ncl_kkt_s* h) {
         const double cb = P.sn_nrow[P.child_list[k2]] - P.sn_ncol[P.child_list[k2]];
         child_u += 0.5 * cb * (cb + 1);
       }
-      L.asm_cost.bytes += esz * ((double)nrow * ncp + 0.5 * nb * (nb + 1) + child_u) +
-                          12.0 * (double)(P.amap_ptr[P.sn_rows_off[s + 1]] - P.amap_ptr[P.sn_rows_off[s]]);
-      if (is_small) {
+      if (!reg)
+        L.asm_cost.bytes += esz * ((double)nrow * ncp + 0.5 * nb * (nb + 1) + child_u) +
+                            12.0 * (double)(P.amap_ptr[P.sn_rows_off[s + 1]] - P.amap_ptr[P.sn_rows_off[s]]);
+      if (is_small && !reg) {
         L.small_cost.flops += 2.0 * (ncol * (double)ncol * ncol / 3.0 + nb * ncol * ncol);
         L.small_cost.bytes += esz * 2.0 * nrow * ncp;
       }
@@ -685,7 +709,7 @@ void build_schedule(ncl_kkt_s* h) {
       push_gemm(g, L.syrk_off, L.syrk_tiles, L.syrk_cost);
     };
     for (int32_t s : large) push_syrk(s);
-    for (int32_t s : small) push_syrk(s);
+    for (int32_t s : small) push_syrk(s);   // (region fronts are in neither list)
     L.syrk_cnt = (int)(probv.size() - L.syrk_off);
     L.tsyrk_cnt = (int)(hs.tcv.size() - L.tsyrk_off);
   }
@@ -732,6 +756,11 @@ void build_schedule(ncl_kkt_s* h) {
       }
       for (int32_t v = 0; v < P.ns; v++)
         if (hs.inreg[v] && !seen[v]) bad("subtree coverage");
+      if (hs.reg_smem > SMALL_SMEM_MAX) bad("subtree shared memory");
+      for (int32_t v = 0; v < P.ns; v++)
+        if (hs.inreg[v] && (P.sn_ncol[v] > 32 || P.sn_nrow[v] > 512 ||
+                            small_front_smem(P.sn_nrow[v], P.sn_ncolp[v], (int)esz) > hs.reg_smem))
+          bad("subtree front");
     }
     for (size_t i = 0; i < hs.chainv.size(); i++) {
       const int4 it = hs.chainv[i];
@@ -1059,7 +1088,7 @@ void build_device(ncl_kkt_s* h) {
     h->d_regitems = h->upload(h->hs.regitems);
     h->d_regnodes = h->upload(h->hs.regnodes);
   }
-  h->d_dag_cnt = h->alloc<int>(std::max<int64_t>(h->hs.dag_counters, 1));
+  h->d_dag_cnt = h->alloc<int>(h->hs.dag_counters + 1);   // + the subtree factorisation's counter
   {
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
@@ -1179,6 +1208,13 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
   const bool f32 = sizeof(T) == 4;
   const double eps = h->opt.pivot_eps;
   const int pol = h->opt.pivot_policy;
+  // the region of small subtrees first (one CTA per subtree, all of it in
+  // one launch): every front below a level launch's fronts is then done
+  klaunch(h, st, f32 ? "subtree_factor_f32" : "subtree_factor_f64", (int64_t)h->hs.regitems.size(),
+          h->hs.reg_fac_cost, [&] {
+            launch_subtree_factor<T>(P, N, h->d_regitems, (int)h->hs.regitems.size(), h->d_regnodes,
+                                     h->d_dag_cnt + h->hs.dag_counters, (int)h->hs.reg_smem, h->n_sm, eps, pol, st);
+          });
   for (const Level& L : h->levels) {
     klaunch(h, st, f32 ? "assemble_f32" : "assemble_f64", L.asm_cnt, L.asm_cost,
             [&] {
@@ -1567,7 +1603,7 @@ void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
   CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), s2));
   CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s2));
   CK(cudaMemsetAsync(h->d_panel_sync, 0, std::max<int64_t>(h->hs.panel_sync, 8) * sizeof(int), s2));
-  CK(cudaMemsetAsync(h->d_dag_cnt, 0, std::max<int64_t>(h->hs.dag_counters, 1) * sizeof(int), s2));
+  CK(cudaMemsetAsync(h->d_dag_cnt, 0, (h->hs.dag_counters + 1) * sizeof(int), s2));
   if (is_fp32(h)) {
     run_factor<float>(h, h->nf, s2);
     klaunch(h, s2, "inertia", h->dp.dim, Cost{0, 5.0 * h->dp.dim},
