@@ -978,6 +978,13 @@ void build_device(ncl_kkt_s* h) {
   d.amap_ptr = h->upload(P.amap_ptr);
   d.amap_col = h->upload(P.amap_col);
   d.amap_src = h->upload(P.amap_src);
+  {
+    std::vector<int32_t> arow(P.amap_src.size() ? P.amap_src.size() : 1, 0);
+    for (int32_t s = 0; s < P.ns; s++)
+      for (int64_t i = P.sn_rows_off[s]; i < P.sn_rows_off[s + 1]; i++)
+        for (int64_t q = P.amap_ptr[i]; q < P.amap_ptr[i + 1]; q++) arow[q] = (int32_t)(i - P.sn_rows_off[s]);
+    d.amap_row = h->upload(arow);
+  }
   d.perm = h->upload(P.perm);
   d.col_inst = h->upload(P.col_inst);
   d.col_sign = h->upload(P.col_sign);

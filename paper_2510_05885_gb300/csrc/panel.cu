@@ -153,34 +153,37 @@ __device__ __forceinline__ void subtree_front(const DevPlan& P, const DevNum<T>&
   T* Lg = N.L + P.sn_Loff[s];
   T* Ub = N.U + P.sn_Uoff[s];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  // zero the front and the lower update block
+  // zero the front and the update block
   for (int idx = tid; idx < nrow * ldf; idx += blockDim.x) F[idx] = T(0);
-  for (int a = warp; a < nb; a += nw)
-    for (int b = lane; b <= a; b += 32) Ub[(int64_t)a * nb + b] = T(0);
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) Ub[idx] = T(0);
   __syncthreads();
-  // original entries (each lands in its own position)
+  // original entries (each lands in its own position): the front's entries
+  // spread over all threads, so that their loads are independent
   const int64_t rbase = P.sn_rows_off[s];
-  for (int r = warp; r < nrow; r += nw) {
-    const int64_t q0 = P.amap_ptr[rbase + r], q1 = P.amap_ptr[rbase + r + 1];
-    for (int64_t q = q0 + lane; q < q1; q += 32) F[r * ldf + P.amap_col[q]] = (T)N.Klow[P.amap_src[q]];
+  {
+    const int64_t q0 = P.amap_ptr[rbase], q1 = P.amap_ptr[rbase + nrow];
+    for (int64_t q = q0 + tid; q < q1; q += blockDim.x)
+      F[P.amap_row[q] * ldf + P.amap_col[q]] = (T)N.Klow[P.amap_src[q]];
   }
   // the children's update blocks, child by child (the targets of one child
-  // are distinct: its relative map is increasing)
+  // are distinct: its relative map is increasing); each child's lower
+  // triangle spread over all threads
   for (int k = P.child_ptr[s]; k < P.child_ptr[s + 1]; k++) {
     __syncthreads();
     const int c = P.child_list[k];
     const int nbc = P.sn_nrow[c] - P.sn_ncol[c];
     const int32_t* rel = P.relmap + P.relmap_off[c];
     const T* Uc = N.U + P.sn_Uoff[c];
-    for (int a = warp; a < nbc; a += nw) {
-      const int ra = rel[a];
-      const T* urow = Uc + (int64_t)a * nbc;
-      for (int b = lane; b <= a; b += 32) {
-        const int rb = rel[b];
-        const T v = urow[b];
-        if (rb < ncol) F[ra * ldf + rb] += v;
-        else Ub[(int64_t)(ra - ncol) * nb + (rb - ncol)] += v;
-      }
+    const int tot = nbc * (nbc + 1) / 2;
+    for (int e = tid; e < tot; e += blockDim.x) {
+      int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while (a * (a + 1) / 2 > e) a--;
+      while ((a + 1) * (a + 2) / 2 <= e) a++;
+      const int b = e - a * (a + 1) / 2;
+      const int ra = rel[a], rb = rel[b];
+      const T v = Uc[(int64_t)a * nbc + b];
+      if (rb < ncol) F[ra * ldf + rb] += v;
+      else Ub[(int64_t)(ra - ncol) * nb + (rb - ncol)] += v;
     }
   }
   __syncthreads();
@@ -210,14 +213,17 @@ __device__ __forceinline__ void subtree_front(const DevPlan& P, const DevNum<T>&
   __syncthreads();
   // write the factor block back, and form the update block from it
   for (int idx = tid; idx < nrow * ncp; idx += blockDim.x) Lg[idx] = F[(idx / ncp) * ldf + idx % ncp];
-  for (int a = warp; a < nb; a += nw) {
+  const int ut = nb * (nb + 1) / 2;
+  for (int e = tid; e < ut; e += blockDim.x) {
+    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (a * (a + 1) / 2 > e) a--;
+    while ((a + 1) * (a + 2) / 2 <= e) a++;
+    const int b = e - a * (a + 1) / 2;
     const T* la = F + (ncol + a) * ldf;
-    for (int b = lane; b <= a; b += 32) {
-      const T* lb = F + (ncol + b) * ldf;
-      T acc = T(0);
-      for (int k = 0; k < ncol; k++) acc += la[k] * dsh[k] * lb[k];
-      Ub[(int64_t)a * nb + b] -= acc;
-    }
+    const T* lb = F + (ncol + b) * ldf;
+    T acc = T(0);
+    for (int k = 0; k < ncol; k++) acc += la[k] * dsh[k] * lb[k];
+    Ub[(int64_t)a * nb + b] -= acc;
   }
 }
 

@@ -79,8 +79,8 @@ __device__ __forceinline__ double pivot_rcp(double d) { return 1.0 / d; }
 template <typename T>
 __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, double eps, int policy, int lane,
                                        int8_t& st) {
-  // rows and columns past cw are padded with the identity (their pivot would
-  // be 1 and nothing couples to them); the column steps stop at cw
+  // rows past cw are padded with the identity (nothing couples to them);
+  // the column steps stop at cw
   T r[32];
 #pragma unroll
   for (int j = 0; j < 32; j++)
@@ -88,18 +88,19 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
   // the block signs of the 32 pivots as a bit mask (bit k: pivot k is dual)
   const unsigned neg = __ballot_sync(0xffffffffu, my_sign < 0);
   const T e = (T)eps;
-  const int8_t tiny_st = policy == 0 ? 1 : 2;
-  int8_t my_st = 0;
+  unsigned tiny_mask = 0u, bad_mask = 0u;   // pivots replaced by +-eps / non-finite
   T my_d = T(1);
 #pragma unroll
   for (int k = 0; k < 32; k++) {
     if (k >= cw) break;   // warp-uniform: a narrow block stops after its last column
-    // static pivot (Section 3.1): |d| <= eps -> +-eps by the block sign
-    // (status 1 perturbed / 2 zero), a non-finite pivot is kept (status 3)
+    // static pivot (Section 3.1): |d| <= eps -> +-eps by the block sign, a
+    // non-finite pivot is kept and reported
     const T d0 = __shfl_sync(0xffffffffu, r[k], k);
     const T a = d0 < T(0) ? -d0 : d0;
     const bool fin = finite_val(d0);
     const bool tiny = fin && a <= e;
+    tiny_mask |= (unsigned)tiny << k;
+    bad_mask |= (unsigned)(!fin) << k;
     const T dk = tiny ? (((neg >> k) & 1u) ? -e : e) : d0;
     const T wk = r[k];
     // rows above the pivot get a zero multiplier, so the update needs no
@@ -110,7 +111,6 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
     for (int j = k + 1; j < 32; j++) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
     r[k] = lane > k ? li : (lane == k ? dk : r[k]);
     my_d = lane == k ? dk : my_d;
-    my_st = lane == k ? (int8_t)(!fin ? 3 : (tiny ? tiny_st : 0)) : my_st;
   }
   if (lane < cw) {
 #pragma unroll
@@ -118,7 +118,8 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
       if (j <= lane) blk[lane * ld + j] = r[j];
   }
   __syncwarp();
-  st = my_st;
+  st = ((bad_mask >> lane) & 1u) ? 3 : (((tiny_mask >> lane) & 1u) ? (policy == 0 ? 1 : 2) : 0);
+  if (lane >= cw) st = 0;
   return my_d;
 }
 
@@ -237,12 +238,11 @@ __device__ __forceinline__ void bar_warps_1_7() { asm volatile("bar.sync 1, 224;
 // A) for rows [r_begin, w) and columns [c_begin, c_end) (at most 64), c <= r;
 // done by the nw warps wfirst.. of the CTA, lane = column, register tiles of
 // up to 8 rows per warp and trip
-template <typename T>
+template <typename T, int MRW = 8>
 __device__ __forceinline__ void block_update(T* A, const T* Xs, int c0, int rb, int w, int r_begin, int c_begin,
                                              int c_end, int wfirst, int nw) {
   const int warp = (threadIdx.x >> 5) - wfirst, lane = threadIdx.x & 31;
   if (warp < 0 || warp >= nw || c_begin >= c_end) return;
-  constexpr int MRW = 8;
   const int ng = (c_end - c_begin + 31) / 32;   // 1 or 2
   for (int rr0 = r_begin + warp * MRW; rr0 < w; rr0 += nw * MRW) {
     T acc[MRW][2];
@@ -332,7 +332,7 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
         A[(rb + r) * LDM + c0 + c] = x * pivot_rcp(dsh[c0 + c]);
       }
       __syncthreads();
-      block_update<T>(A, Xs, c0, rb, rb + nn, rb, rb, rb + nn, 0, 8);
+      block_update<T, 4>(A, Xs, c0, rb, rb + nn, rb, rb, rb + nn, 0, 8);   // 32 rows: 4 per warp
       __syncthreads();
     }
     if (warp == 0) {

@@ -56,6 +56,7 @@ struct DevPlan {
   const int64_t* amap_ptr;
   const int32_t* amap_col;
   const int32_t* amap_src;
+  const int32_t* amap_row;   // front row of each assembly-map entry (within its front)
   const int32_t* perm;       // pivot k -> natural index
   const int32_t* col_inst;   // instance of pivot k
   const int8_t* col_sign;    // block sign of pivot k
