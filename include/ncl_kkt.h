@@ -140,6 +140,19 @@ typedef struct {
                                  swept by one warp (one launch per sweep for all of
                                  them); 0: those supernodes go through the
                                  per-level launches like the others */
+    int32_t tc_min_pivots;    /* FP32_IR: large fronts with at least this many pivots
+                                 get split TF32 operands and tensor-core updates
+                                 (default 256, >= 32) */
+    const char* autotune_path; /* NULL (default), or a table written by the autotuner
+                                 (paper_2510_05885_gb300/autotune.py): at analysis the
+                                 first line whose form, dimension range and
+                                 instance-count range match sets persistent_fronts,
+                                 subtree_sweeps, use_tensor_cores and tc_min_pivots
+                                 (lines "form dim_lo dim_hi count_lo count_hi
+                                 persistent subtree tensor_cores tc_min_pivots",
+                                 dim_hi exclusive, '#' comments).  Read once during
+                                 the call; an unreadable file or a bad line is
+                                 INVALID_ARG */
 } ncl_kkt_options;
 
 typedef struct {
@@ -284,6 +297,10 @@ ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t l
 ncl_status ncl_kkt_solve_noalloc(ncl_kkt_t h, int32_t nrhs, const double* B, int64_t ldb,
                                  double* X, int64_t ldx, ncl_stream_t stream,
                                  ncl_kkt_solve_info* info);
+
+/* The options in effect for a handle (after the defaults, and after a
+ * tuned table's line if one matched; autotune_path is returned NULL). */
+ncl_status ncl_kkt_get_options(ncl_kkt_t h, ncl_kkt_options* out);
 
 /* Sizes and counts of the analysis (host struct). */
 ncl_status ncl_kkt_get_analysis_info(ncl_kkt_t h, ncl_kkt_analysis_info* out);

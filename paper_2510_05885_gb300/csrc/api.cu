@@ -45,12 +45,11 @@ struct CudaError {
     if (e_ != cudaSuccess) throw CudaError{e_, #x};            \
   } while (0)
 
-// In the FP32 path the fronts with at least TC_MIN_K pivots get split TF32
-// operands: their update block F22 -= L21 D1 L21^T runs on the tensor cores,
-// and with use_tensor_cores = 2 (the default) also the K = 128 trailing
-// updates of their macro panels; shorter inner dimensions stay on the SIMT
-// kernel.
-constexpr int TC_MIN_K = 256;
+// In the FP32 path the large fronts with at least options.tc_min_pivots
+// pivots (default 256) get split TF32 operands: their update block
+// F22 -= L21 D1 L21^T runs on the tensor cores, and with use_tensor_cores =
+// 2 (the default) also the K = 128 trailing updates of their panels; shorter
+// inner dimensions stay on the FMA kernels.
 
 // default bound of the inter-CTA waits inside the kernels (about 2 s at 2 GHz)
 constexpr long long DEFAULT_WAIT_CYCLES = 4000000000LL;
@@ -530,7 +529,7 @@ void build_schedule(ncl_kkt_s* h) {
     if (hs.tc) {
       int64_t off = 0;
       for (int32_t s : large) {
-        if (P.sn_ncol[s] < TC_MIN_K) continue;
+        if (P.sn_ncol[s] < h->opt.tc_min_pivots) continue;
         fid[s] = (int32_t)hs.tc_fronts.size();
         hs.tc_fronts.push_back(s);
         hs.sn_Soff[s] = off;
@@ -676,7 +675,7 @@ void build_schedule(ncl_kkt_s* h) {
     for (int32_t s : large) {
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s];
       const int nb = nrow - ncol;
-      if (nb == 0 || !(hs.tc && ncol >= TC_MIN_K && fid[s] >= 0)) continue;
+      if (nb == 0 || !(hs.tc && fid[s] >= 0)) continue;
       TcProb q{};
       q.c_off = P.sn_Uoff[s];
       q.ldc = nb;
@@ -694,7 +693,7 @@ void build_schedule(ncl_kkt_s* h) {
     auto push_syrk = [&](int32_t s) {
       const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
       const int nb = nrow - ncol;
-      if (nb == 0 || (hs.tc && ncol >= TC_MIN_K && fid[s] >= 0)) return;
+      if (nb == 0 || (hs.tc && fid[s] >= 0)) return;
       GemmProb g{};
       g.c_off = P.sn_Uoff[s];
       g.a_off = P.sn_Loff[s] + (int64_t)ncol * ncp;
@@ -1891,7 +1890,47 @@ static ncl_status init_options(ncl_kkt_s* h, const ncl_kkt_options* opt) {
   if (h->opt.ir_max_iter < 0) h->opt.ir_max_iter = h->opt.prec == NCL_PREC_FP64 ? 3 : 10;
   if (h->opt.wait_cycles <= 0) h->opt.wait_cycles = DEFAULT_WAIT_CYCLES;
   if (!(h->opt.ir_switch > 0.0) || !(h->opt.ir_switch <= 1.0)) h->opt.ir_switch = 0.5;
+  if (h->opt.tc_min_pivots < 32) return fail(NCL_ERR_INVALID_ARG, "tc_min_pivots must be >= 32");
   return NCL_OK;
+}
+
+// The cut-overs of a tuned table (written by the autotuner): the first line
+// whose form, dimension range and instance-count range match the analysis
+// sets persistent_fronts, subtree_sweeps, use_tensor_cores and
+// tc_min_pivots.  Lines: form dim_lo dim_hi count_lo count_hi persistent
+// subtree tensor_cores tc_min_pivots [comment]; '#' starts a comment line.
+static ncl_status apply_tuned(ncl_kkt_s* h) {
+  const char* path = h->opt.autotune_path;
+  h->opt.autotune_path = nullptr;   // the caller's string is not kept
+  if (!path) return NCL_OK;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(NCL_ERR_INVALID_ARG, std::string("cannot read the tuned table ") + path);
+  char line[512];
+  ncl_status st = NCL_OK;
+  int lineno = 0;
+  while (std::fgets(line, sizeof(line), f)) {
+    lineno++;
+    const char* q = line;
+    while (*q == ' ' || *q == '\t') q++;
+    if (*q == '#' || *q == '\n' || *q == '\0') continue;
+    long long v[9];
+    if (std::sscanf(q, "%lld %lld %lld %lld %lld %lld %lld %lld %lld", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                    &v[7], &v[8]) != 9 ||
+        v[5] < 0 || v[5] > 1 || v[6] < 0 || v[6] > 1 || v[7] < 0 || v[7] > 2 || v[8] < 32) {
+      st = fail(NCL_ERR_INVALID_ARG, std::string("bad line ") + std::to_string(lineno) + " in the tuned table");
+      break;
+    }
+    const int64_t cnt = (int64_t)h->plan.inst.size();
+    if (v[0] == h->plan.form && h->plan.dim >= v[1] && h->plan.dim < v[2] && cnt >= v[3] && cnt <= v[4]) {
+      h->opt.persistent_fronts = (int32_t)v[5];
+      h->opt.subtree_sweeps = (int32_t)v[6];
+      h->opt.use_tensor_cores = (int32_t)v[7];
+      h->opt.tc_min_pivots = (int32_t)v[8];
+      break;
+    }
+  }
+  std::fclose(f);
+  return st;
 }
 
 static ncl_status finish_handle(std::unique_ptr<ncl_kkt_s>& h, ncl_kkt_t* out);
@@ -1914,6 +1953,8 @@ ncl_status analyze_common(const AnalyzeInput& in, const ncl_kkt_options* opt, nc
   }
   h->ninst = in.count;
   h->dp.ninst = in.count;
+  ncl_status sa = apply_tuned(h.get());
+  if (sa != NCL_OK) return sa;
   return finish_handle(h, out);
 }
 
@@ -1929,6 +1970,8 @@ ncl_status analyze_like(ncl_kkt_s* src, const ncl_kkt_options* opt, ncl_kkt_t* o
   h->plan = src->plan;
   h->ninst = src->ninst;
   h->dp.ninst = src->dp.ninst;
+  ncl_status sa = apply_tuned(h.get());
+  if (sa != NCL_OK) return sa;
   return finish_handle(h, out);
 }
 
@@ -1974,6 +2017,8 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->persistent_fronts = 1;
   o->ir_switch = 0.5;
   o->subtree_sweeps = 1;
+  o->tc_min_pivots = 256;
+  o->autotune_path = nullptr;
 }
 
 ncl_status ncl_kkt_analyze(int32_t form, int32_t n, int32_t m, const int32_t* H_rowptr, const int32_t* H_colind,
@@ -2241,6 +2286,12 @@ ncl_status ncl_kkt_adjoint(ncl_kkt_t h, int32_t nrhs, const double* X, int64_t l
     CK(cudaStreamSynchronize(st));
     return s;
   });
+}
+
+ncl_status ncl_kkt_get_options(ncl_kkt_t h, ncl_kkt_options* o) {
+  if (!h || !o) return fail(NCL_ERR_INVALID_ARG, "NULL argument");
+  *o = h->opt;
+  return NCL_OK;
 }
 
 ncl_status ncl_kkt_get_analysis_info(ncl_kkt_t h, ncl_kkt_analysis_info* o) {

@@ -32,7 +32,8 @@ class Options(ctypes.Structure):
                 ("host_only", ctypes.c_int32), ("precision_fallback", ctypes.c_int32),
                 ("max_device_bytes", ctypes.c_int64), ("wait_cycles", ctypes.c_int64),
                 ("persistent_fronts", ctypes.c_int32), ("ir_switch", ctypes.c_double),
-                ("subtree_sweeps", ctypes.c_int32)]
+                ("subtree_sweeps", ctypes.c_int32), ("tc_min_pivots", ctypes.c_int32),
+                ("autotune_path", ctypes.c_char_p)]
 
 
 class FactorInfo(ctypes.Structure):
@@ -105,6 +106,7 @@ _SIGS = {
                                          ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_adjoint": (I32, [P, I32, P, I64, P, I64, P, I64, P, P, P, P, P, ctypes.POINTER(SolveInfo)]),
     "ncl_kkt_get_analysis_info": (I32, [P, ctypes.POINTER(AnalysisInfo)]),
+    "ncl_kkt_get_options": (I32, [P, ctypes.POINTER(Options)]),
     "ncl_kkt_get_permutation": (I32, [P, P]),
     "ncl_kkt_get_supernodes": (I32, [P, P, P, P]),
     "ncl_kkt_instance_count": (I32, [P]),
@@ -173,7 +175,16 @@ def default_options(**kw) -> Options:
             continue
         if k == "prec" and isinstance(v, str):
             v = {"fp64": PREC_FP64, "fp32_ir": PREC_FP32_IR}[v]
+        if k == "autotune_path":
+            setattr(o, k, os.fsencode(v))
+            continue
         setattr(o, k, int(v) if isinstance(getattr(o, k), int) else float(v))
+    return o
+
+
+def ncl_kkt_get_options(h) -> Options:
+    o = Options()
+    _check(load().ncl_kkt_get_options(h, ctypes.byref(o)))
     return o
 
 
