@@ -40,6 +40,7 @@ from paper_2510_05885_gb300 import synth  # noqa: E402
 
 METRIC = "KKT factor+solve ms & GFLOP/s at rel. residual 1e-10: FP32+IR vs FP64 on 1 GB300"
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TUNED = os.path.join(ROOT, "paper_2510_05885_gb300", "tuned_gb300.txt")
 WORKLOADS = ("condensed300", "stabilized20x25", "batch64", "adjoint256", "large700")
 
 
@@ -75,10 +76,13 @@ def parse(argv=None):
     ap.add_argument("--skip-peaks", action="store_true", help="do not measure the TF32 / FP64 matmul peaks")
     ap.add_argument("--ir-switch", type=float, default=0.5,
                     help="Richardson hands over to FGMRES when a step gains less than this factor")
-    ap.add_argument("--subtree-sweeps", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--subtree-sweeps", type=int, default=None, choices=[0, 1],
                     help="1: the small subtrees of the sweeps one warp each; 0: per-level launches for all")
-    ap.add_argument("--persistent-fronts", type=int, default=1, choices=[0, 1],
-                    help="1: one persistent launch per level for the large fronts; 0: one launch per panel step")
+    ap.add_argument("--persistent-fronts", type=int, default=None, choices=[0, 1],
+                    help="1: one persistent launch per level for the large fronts; 0: one launch per panel step "
+                         "(default: the library's, or the tuned table's)")
+    ap.add_argument("--tuned", default=TUNED if os.path.exists(TUNED) else None,
+                    help="table of tuned cut-overs applied at analysis (default: the committed GB300 table)")
     return ap.parse_args(argv)
 
 
@@ -371,6 +375,7 @@ class Runner:
         opts.setdefault("persistent_fronts", self.args.persistent_fronts)
         opts.setdefault("ir_switch", self.args.ir_switch)
         opts.setdefault("subtree_sweeps", self.args.subtree_sweeps)
+        opts.setdefault("autotune_path", self.args.tuned)
         if self.batch:
             return nk.KKT.batch(f, [(p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind) for p in self.pats],
                                 prec=prec, **opts)
@@ -528,6 +533,9 @@ def run_ours(args):
                    "nnz_L": ai.nnz_L, "factor_flops": flops, "supernodes": ai.n_supernodes,
                    "levels": ai.n_levels, "analyze_ms": ai.analyze_ms, "device_bytes": ai.device_bytes},
         "step_ms_median": statistics.median(ms),
+        "options": {k: getattr(nk.ncl_kkt_get_options(K._h), k)
+                    for k in ("persistent_fronts", "subtree_sweeps", "use_tensor_cores", "tc_min_pivots")},
+        "tuned_table": os.path.relpath(args.tuned, ROOT) if args.tuned else None,
         "backward_err_max": max(etas), "ir_iters": [min(iters), max(iters)], "inertia_ok": inert_ok,
         "fgmres_used": any(r[1].used_fgmres for r in res),
         "fp64_fallback": any(r[1].fp64_fallback for r in res),
@@ -624,7 +632,7 @@ def run_ours(args):
     K64 = None
     if not args.skip_fp64:
         K64 = nk.KKT.like(K, prec="fp64", persistent_fronts=args.persistent_fronts,
-                          subtree_sweeps=args.subtree_sweeps)
+                          subtree_sweeps=args.subtree_sweeps, autotune_path=args.tuned)
         n64 = max(2, args.steps // 3)
         ms64, res64, _ = timed(K64, n64, 1)
         t64 = max_over_ranks(sum(ms64))
@@ -696,7 +704,7 @@ def run_ours(args):
                 if name == "adjoint256":
                     e["fp32_ir"]["adjoint_ms_median"] = statistics.median([r[2] for r in r3])
                 K3b = nk.KKT.like(K3, prec="fp64", persistent_fronts=args.persistent_fronts,
-                                  subtree_sweeps=args.subtree_sweeps)
+                                  subtree_sweeps=args.subtree_sweeps, autotune_path=args.tuned)
                 m4, r4, _ = timed(K3b, n64_, 1, R3)
                 t4 = max_over_ranks(sum(m4)) / n64_
                 e["fp64"] = {"ms_per_step": t4, "gflops": world * ai3.flops / (t4 * 1e-3) / 1e9,

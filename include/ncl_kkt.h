@@ -125,12 +125,13 @@ typedef struct {
                                  the kernel sets an error flag, finishes without the
                                  awaited data and the call returns NCL_ERR_TIMEOUT.
                                  <= 0 selects 4e9 (about 2 s) */
-    int32_t persistent_fronts; /* 1 (default): the large fronts of each level are
-                                 factored by one persistent launch whose CTAs take
-                                 panel, row and trailing-update tile tasks from a
-                                 dependency-ordered list; 0: one launch per
-                                 128-column panel step plus one per trailing
-                                 update */
+    int32_t persistent_fronts; /* 1: the large fronts of each level are factored by
+                                 one persistent launch whose CTAs take panel, row
+                                 and trailing-update tile tasks from a
+                                 dependency-ordered list; 0 (default): one launch
+                                 per 128-column panel step plus one per trailing
+                                 update (measured a few percent faster on every
+                                 workload of the autotuner's classes) */
     double ir_switch;         /* single-instance handles with use_fgmres: Richardson
                                  hands over to FGMRES as soon as a step reduces the
                                  backward error by less than this factor (default

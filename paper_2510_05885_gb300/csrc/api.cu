@@ -2014,7 +2014,7 @@ void ncl_kkt_default_options(ncl_kkt_options* o) {
   o->precision_fallback = 1;
   o->max_device_bytes = 0;
   o->wait_cycles = 0;
-  o->persistent_fronts = 1;
+  o->persistent_fronts = 0;
   o->ir_switch = 0.5;
   o->subtree_sweeps = 1;
   o->tc_min_pivots = 256;

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, co
     const int cw = min(32, ncol - c0);
     if (warp == 0) {
       int8_t st;
-      const T d = factor_sub32<T>(F + c0 * ldf + c0, ldf, cw, lane < cw ? P.col_sign[col0 + c0 + lane] : 1, eps,
+      const T d = factor_sub32<T, true>(F + c0 * ldf + c0, ldf, cw, lane < cw ? P.col_sign[col0 + c0 + lane] : 1, eps,
                                   policy, lane, st);
       dsh[c0 + lane] = d;
       if (lane < cw) {
@@ -191,7 +191,7 @@ __device__ __forceinline__ void subtree_front(const DevPlan& P, const DevNum<T>&
   // statuses, the zero-padded unit lower block and its inverse
   if (warp == 0) {
     int8_t st;
-    const T d = factor_sub32<T>(F, ldf, ncol, lane < ncol ? P.col_sign[col0 + lane] : 1, eps, policy, lane, st);
+    const T d = factor_sub32<T, true>(F, ldf, ncol, lane < ncol ? P.col_sign[col0 + lane] : 1, eps, policy, lane, st);
     dsh[lane] = d;
     if (lane < ncol) {
       N.D[col0 + lane] = d;

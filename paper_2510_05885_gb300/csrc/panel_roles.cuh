@@ -76,41 +76,71 @@ inline int macro_panel_smem(int esz) { return std::max(macro_diag_smem(esz), mac
 __device__ __forceinline__ float pivot_rcp(float d) { return __frcp_rn(d); }
 __device__ __forceinline__ double pivot_rcp(double d) { return 1.0 / d; }
 
+// One column step of the 32 x 32 factorisation in registers: rows above the
+// pivot get a zero multiplier, so the update needs no per-column select or
+// branch; entries above a lane's diagonal are never read.
 template <typename T>
+__device__ __forceinline__ void factor_step(T (&r)[32], int k, T dk, int lane, T& my_d) {
+  const T wk = r[k];
+  const T li = lane > k ? wk * pivot_rcp(dk) : T(0);
+#pragma unroll
+  for (int j = k + 1; j < 32; j++)
+    if (j > k) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
+  r[k] = lane > k ? li : (lane == k ? dk : r[k]);
+  my_d = lane == k ? dk : my_d;
+}
+
+// LDL^T of a 32 x 32 diagonal sub-block in shared memory (row stride ld,
+// cw <= 32 valid rows) by one warp, lane i holding row i in registers:
+// right-looking with column broadcasts by shuffles.  Writes the unit lower
+// factor (strictly below the diagonal) and D on the diagonal back; returns
+// lane's pivot (1 on the padding) and its status in st.  Static pivoting
+// (Section 3.1): a pivot with |d| <= eps becomes +-eps by the sign of its
+// block (status 1 perturbed, or 2 zero under the stop policy), a non-finite
+// pivot is kept (status 3).  The common case has no such pivot: the columns
+// run without the pivot test on the dependency chain, and only when a test
+// fired does the block run again from shared memory with the replacement.
+// EARLY: stop after column cw (narrow blocks of small fronts); otherwise
+// all 32 steps run on the identity-padded block (no branch between steps).
+template <typename T, bool EARLY>
 __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, double eps, int policy, int lane,
                                        int8_t& st) {
-  // rows past cw are padded with the identity (nothing couples to them);
-  // the column steps stop at cw
   T r[32];
+  auto load = [&] {
 #pragma unroll
-  for (int j = 0; j < 32; j++)
-    r[j] = lane < cw ? ((j <= lane) ? blk[lane * ld + j] : T(0)) : (j == lane ? T(1) : T(0));
-  // the block signs of the 32 pivots as a bit mask (bit k: pivot k is dual)
-  const unsigned neg = __ballot_sync(0xffffffffu, my_sign < 0);
+    for (int j = 0; j < 32; j++)
+      r[j] = lane < cw ? ((j <= lane) ? blk[lane * ld + j] : T(0)) : (j == lane ? T(1) : T(0));
+  };
+  load();
   const T e = (T)eps;
-  unsigned tiny_mask = 0u, bad_mask = 0u;   // pivots replaced by +-eps / non-finite
+  unsigned tiny_mask = 0u, bad_mask = 0u;
   T my_d = T(1);
 #pragma unroll
   for (int k = 0; k < 32; k++) {
-    if (k >= cw) break;   // warp-uniform: a narrow block stops after its last column
-    // static pivot (Section 3.1): |d| <= eps -> +-eps by the block sign, a
-    // non-finite pivot is kept and reported
+    if (EARLY && k >= cw) break;
     const T d0 = __shfl_sync(0xffffffffu, r[k], k);
     const T a = d0 < T(0) ? -d0 : d0;
-    const bool fin = finite_val(d0);
-    const bool tiny = fin && a <= e;
-    tiny_mask |= (unsigned)tiny << k;
-    bad_mask |= (unsigned)(!fin) << k;
-    const T dk = tiny ? (((neg >> k) & 1u) ? -e : e) : d0;
-    const T wk = r[k];
-    // rows above the pivot get a zero multiplier, so the update needs no
-    // per-column select or branch; entries above a lane's diagonal are
-    // never read
-    const T li = lane > k ? wk * pivot_rcp(dk) : T(0);
+    tiny_mask |= (unsigned)(a <= e) << k;             // NaN compares false
+    bad_mask |= (unsigned)(!finite_val(d0)) << k;
+    factor_step(r, k, d0, lane, my_d);
+  }
+  if (tiny_mask | bad_mask) {
+    // again, with the static pivot applied at each step
+    const unsigned neg = __ballot_sync(0xffffffffu, my_sign < 0);
+    load();
+    tiny_mask = bad_mask = 0u;
+    my_d = T(1);
 #pragma unroll
-    for (int j = k + 1; j < 32; j++) r[j] -= li * __shfl_sync(0xffffffffu, wk, j);
-    r[k] = lane > k ? li : (lane == k ? dk : r[k]);
-    my_d = lane == k ? dk : my_d;
+    for (int k = 0; k < 32; k++) {
+      if (EARLY && k >= cw) break;
+      const T d0 = __shfl_sync(0xffffffffu, r[k], k);
+      const T a = d0 < T(0) ? -d0 : d0;
+      const bool fin = finite_val(d0);
+      const bool tiny = fin && a <= e;
+      tiny_mask |= (unsigned)tiny << k;
+      bad_mask |= (unsigned)(!fin) << k;
+      factor_step(r, k, tiny ? (((neg >> k) & 1u) ? -e : e) : d0, lane, my_d);
+    }
   }
   if (lane < cw) {
 #pragma unroll
@@ -118,8 +148,7 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
       if (j <= lane) blk[lane * ld + j] = r[j];
   }
   __syncwarp();
-  st = ((bad_mask >> lane) & 1u) ? 3 : (((tiny_mask >> lane) & 1u) ? (policy == 0 ? 1 : 2) : 0);
-  if (lane >= cw) st = 0;
+  st = (lane >= cw) ? 0 : (((bad_mask >> lane) & 1u) ? 3 : (((tiny_mask >> lane) & 1u) ? (policy == 0 ? 1 : 2) : 0));
   return my_d;
 }
 
@@ -302,7 +331,7 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
   __syncthreads();
   auto factor = [&](int c0) {
     int8_t st;
-    const T d = factor_sub32<T>(A + c0 * LDM + c0, LDM, min(32, w - c0), sg[c0 + lane], eps, policy, lane, st);
+    const T d = factor_sub32<T, false>(A + c0 * LDM + c0, LDM, min(32, w - c0), sg[c0 + lane], eps, policy, lane, st);
     dsh[c0 + lane] = d;
     pst[c0 + lane] = st;
   };
