@@ -154,6 +154,7 @@ struct HostSched {
   std::vector<int32_t> regnodes;          // each subtree's supernodes in postorder
   std::vector<int2> regitems;             // (first node, count) per subtree
   Cost reg_fwd_cost, reg_bwd_cost, reg_fac_cost;
+  std::vector<int2> invv;                 // (large front, 32-column sub-block): inverses after the factorisation
   int64_t reg_smem = 0;                   // dynamic shared memory of the subtree factorisation
 };
 
@@ -224,11 +225,13 @@ struct ncl_kkt_s {
   CUtensorMap* d_maps = nullptr;           // 4 tensor maps per tensor-core front
   TcProb* d_tc = nullptr;
   int* d_err = nullptr;                    // device error flags (bounded waits)
+  int2* d_invv = nullptr;                  // sub-blocks whose inverses follow the factorisation
   int2* d_regitems = nullptr;              // small-subtree sweep items and their nodes
   int32_t* d_regnodes = nullptr;
   DagTask* d_dag = nullptr;                // persistent large-front tasks
   int* d_dag_cnt = nullptr;                //   their queue heads and counters
   int n_sm = 148;                          // multiprocessors of the device
+  int panel_nb = MACRO_NB;                 // pivot columns per panel step of the schedule
   // CUDA graphs: the factor and the triangular sweeps are captured once (on
   // a private stream, after one direct call) and replayed
   cudaStream_t cap_stream = nullptr;
@@ -323,8 +326,14 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<GemmProb>& probv = hs.probv;
   hs.tc = is_fp32(h) && h->opt.use_tensor_cores;
   hs.dag = h->opt.persistent_fronts != 0;
+  // panel width of the per-step path: 192 columns for FP32 (fewer, longer
+  // panel steps; the FP64 diagonal block of that width would not fit the
+  // shared memory), 128 otherwise and for the persistent path's tiles
+  h->panel_nb = (is_fp32(h) && !hs.dag) ? MACRO_NB_WIDE : MACRO_NB;
+  const int PNB = h->panel_nb;
   hs.dagv.clear();
   hs.dag_counters = (int64_t)P.nlevels;   // one queue head per level first
+  hs.invv.clear();
   hs.inreg.assign(P.ns, 0);
   hs.regnodes.clear();
   hs.regitems.clear();
@@ -537,9 +546,12 @@ void build_schedule(ncl_kkt_s* h) {
       }
       hs.split_max = std::max(hs.split_max, off);
     }
-    for (int32_t s : large) hs.sn_flags[s] = 1;
+    for (int32_t s : large) {
+      hs.sn_flags[s] = 1;
+      for (int b = 0; b < (P.sn_ncol[s] + 31) / 32; b++) hs.invv.push_back(make_int2(s, b));
+    }
     int maxm = 0;
-    for (int32_t s : large) maxm = std::max(maxm, (P.sn_ncol[s] + MACRO_NB - 1) / MACRO_NB);
+    for (int32_t s : large) maxm = std::max(maxm, (P.sn_ncol[s] + PNB - 1) / PNB);
     L.steps.resize(maxm);
     for (int m = 0; m < maxm; m++) {
       Step& S = L.steps[m];
@@ -550,9 +562,9 @@ void build_schedule(ncl_kkt_s* h) {
       S.ttp_off = (int64_t)hs.tilep_tc.size();
       for (int32_t s : large) {
         const int nrow = P.sn_nrow[s], ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
-        const int q0 = m * MACRO_NB;
+        const int q0 = m * PNB;
         if (q0 >= ncol) continue;
-        const int qe = std::min(q0 + MACRO_NB, ncol), w = qe - q0;
+        const int qe = std::min(q0 + PNB, ncol), w = qe - q0;
         // one diagonal CTA and one CTA per MACRO_ROWS rows below, sharing a
         // sync slot (ticket counter, four sub-block flags)
         const int nrc = (nrow - qe + MACRO_ROWS - 1) / MACRO_ROWS;
@@ -830,10 +842,10 @@ void build_schedule(ncl_kkt_s* h) {
     for (size_t i = 0; i < panelv.size();) {
       const int4 it = panelv[i];
       const int s = it.x;
-      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.y % MACRO_NB || it.z < 0 ||
+      if (s < 0 || s >= P.ns || it.y < 0 || it.y >= P.sn_ncol[s] || it.y % PNB || it.z < 0 ||
           it.z + 8 > hs.panel_sync || it.z % 8)
         bad("macro panel item");
-      const int qe = std::min(it.y + MACRO_NB, P.sn_ncol[s]);
+      const int qe = std::min(it.y + PNB, P.sn_ncol[s]);
       const size_t n = 1 + (size_t)((P.sn_nrow[s] - qe + MACRO_ROWS - 1) / MACRO_ROWS);
       if (i + n > panelv.size()) bad("macro panel item");
       for (size_t k = 0; k < n; k++)
@@ -897,6 +909,10 @@ void build_schedule(ncl_kkt_s* h) {
               if (tc[ti * t.Ct + tj] != std::min(tj, ti)) bad("front task coverage");
         }
     }
+    for (const int2& it : hs.invv)
+      if (it.x < 0 || it.x >= P.ns || it.y < 0 || 32 * it.y >= P.sn_ncol[it.x] || !hs.sn_flags[it.x] ||
+          hs.sn_Ioff[it.x] + (int64_t)(it.y + 1) * 1024 > hs.sn_Ioff[it.x + 1])
+        bad("inverse item");
     for (const TcProb& q : hs.tcv) {
       const int64_t csz = q.c_in_u ? Usz : Lsz;
       if (q.map < 0 || q.map >= (int)hs.tc_fronts.size()) bad("tc map");
@@ -1090,6 +1106,7 @@ void build_device(ncl_kkt_s* h) {
   }
   h->d_err = h->alloc<int>(4);
   if (!h->hs.dagv.empty()) h->d_dag = h->upload(h->hs.dagv);
+  if (!h->hs.invv.empty()) h->d_invv = h->upload(h->hs.invv);
   if (!h->hs.regitems.empty()) {
     h->d_regitems = h->upload(h->hs.regitems);
     h->d_regnodes = h->upload(h->hs.regnodes);
@@ -1242,8 +1259,8 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
     for (const Step& S : L.steps) {
       if (L.dag_cnt > 0) break;
       klaunch(h, st, f32 ? "macro_panel_f32" : "macro_panel_f64", S.panel_cnt, S.panel_cost, [&] {
-        launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->d_panel_sync, h->d_err, eps, pol,
-                              h->opt.wait_cycles, st);
+        launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->panel_nb, h->d_panel_sync, h->d_err,
+                              eps, pol, h->opt.wait_cycles, st);
       });
       klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost, [&] {
         launch_gemm_simt<T>(P, N, h->d_probs + S.prob_off, h->d_tilep + S.tp_off, S.tiles, st);
@@ -1263,6 +1280,10 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
                          L.tsyrk_stages, h->d_maps, h->d_err, h->opt.wait_cycles, st);
       });
   }
+  const int ninv = (int)h->hs.invv.size();
+  klaunch(h, st, f32 ? "invert_blocks_f32" : "invert_blocks_f64", ninv,
+          Cost{ninv * 32.0 * 32 * 32 / 3.0, ninv * 2.0 * 1024 * sizeof(T)},
+          [&] { launch_invert_blocks<T>(P, N, h->d_invv, ninv, st); });
   CK(cudaGetLastError());
 }
 
@@ -2578,7 +2599,7 @@ ncl_status selftest_timeout(ncl_kkt_s* h, DevNum<T>& N, int which, long long wai
     int nrc = 0;
     for (size_t i = 0; i < hs.panelv.size();) {
       const int4 it = hs.panelv[i];
-      const int qe = std::min(it.y + MACRO_NB, (int)P.sn_ncol[it.x]);
+      const int qe = std::min(it.y + h->panel_nb, (int)P.sn_ncol[it.x]);
       const int n = (P.sn_nrow[it.x] - qe + MACRO_ROWS - 1) / MACRO_ROWS;
       if (n >= 1) {
         g0 = (int64_t)i;
@@ -2592,8 +2613,8 @@ ncl_status selftest_timeout(ncl_kkt_s* h, DevNum<T>& N, int which, long long wai
     CK(cudaMemcpyAsync(h->d_panel_sync + hs.panelv[g0].z, &one, sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-    launch_macro_panel<T>(h->dp, N, h->d_panel + g0, nrc, h->d_panel_sync, h->d_err, h->opt.pivot_eps,
-                          h->opt.pivot_policy, wait, st);
+    launch_macro_panel<T>(h->dp, N, h->d_panel + g0, nrc, h->panel_nb, h->d_panel_sync, h->d_err,
+                          h->opt.pivot_eps, h->opt.pivot_policy, wait, st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -131,7 +131,7 @@ __device__ __forceinline__ void simt_block64(T* C, int64_t ldc, const T* A, cons
 }  // namespace
 
 int front_dag_smem(int esz) {
-  const int roles = macro_panel_smem(esz);
+  const int roles = macro_panel_smem(esz, DAG_TILE);
   const int simt = 2 * 16 * 65 * esz;
   const int tc = esz == 4 ? DAG_STAGES * TC_STAGE_BYTES : 0;
   return std::max(std::max(roles, simt), tc) + 1024;   // + alignment of the swizzled stages
@@ -204,9 +204,9 @@ __global__ void __launch_bounds__(DAG_THREADS, 1)
     __syncthreads();
     if (!s_ok) continue;   // after an error every later task is skipped
     if (tk.kind == DAG_DIAG) {
-      panel_diag_role<T>(P, N, s, q0, sync + tk.slot + 1, eps, policy, sb);
+      panel_diag_role<T, DAG_TILE>(P, N, s, q0, sync + tk.slot + 1, eps, policy, sb);
     } else if (tk.kind == DAG_ROWS) {
-      panel_rows_role<T>(P, N, s, q0, qe + MACRO_ROWS * tk.x, sync + tk.slot + 1, err, wait, sb);
+      panel_rows_role<T, DAG_TILE>(P, N, s, q0, qe + MACRO_ROWS * tk.x, sync + tk.slot + 1, err, wait, sb);
       // the split operands just stored are read by other CTAs' TMA
       asm volatile("fence.proxy.async.global;" ::: "memory");
     } else {

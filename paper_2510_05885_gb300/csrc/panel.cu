@@ -15,7 +15,7 @@ namespace ncl {
 // is set past the limit).
 // items: (front, q0, sync slot); sync[slot] = ticket counter, sync[slot + 1
 // + j] = flag of sub-block j.
-template <typename T>
+template <typename T, int NB>
 __global__ void __launch_bounds__(256, 1) k_macro_panel(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
                                                         int* sync, int* err, double eps, int policy,
                                                         long long wait) {
@@ -27,10 +27,10 @@ __global__ void __launch_bounds__(256, 1) k_macro_panel(DevPlan P, DevNum<T> N, 
   if (threadIdx.x == 0) ticket = atomicAdd(slot, 1);
   __syncthreads();
   if (ticket == 0) {
-    panel_diag_role<T>(P, N, s, q0, slot + 1, eps, policy, smem_raw);
+    panel_diag_role<T, NB>(P, N, s, q0, slot + 1, eps, policy, smem_raw);
   } else {
-    const int qe = min(q0 + MNB, P.sn_ncol[s]);
-    panel_rows_role<T>(P, N, s, q0, qe + RB * (ticket - 1), slot + 1, err, wait, smem_raw);
+    const int qe = min(q0 + NB, P.sn_ncol[s]);
+    panel_rows_role<T, NB>(P, N, s, q0, qe + RB * (ticket - 1), slot + 1, err, wait, smem_raw);
   }
 }
 
@@ -265,27 +265,66 @@ template void launch_subtree_factor<float>(const DevPlan&, const DevNum<float>&,
 template void launch_subtree_factor<double>(const DevPlan&, const DevNum<double>&, const int2*, int, const int32_t*,
                                             int*, int, int, double, int, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Inverses of the unit lower 32 x 32 diagonal sub-blocks of the large
+// fronts' pivot blocks (used by the triangular sweeps), one warp per
+// sub-block, after the factorisation: items (supernode, sub-block).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_invert_blocks(DevPlan P, DevNum<T> N, const int2* __restrict__ items,
+                                                       int count) {
+  const int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (it >= count) return;
+  const int s = items[it].x, b = items[it].y;
+  const int ncol = P.sn_ncol[s], ncp = P.sn_ncolp[s];
+  const T* blk = N.L + P.sn_Loff[s] + (int64_t)(32 * b) * ncp + 32 * b;
+  invert_sub32<T>(blk, ncp, min(32, ncol - 32 * b), N.Linv + P.sn_Ioff[s] + (int64_t)b * 1024, lane);
+}
+
+template <typename T>
+void launch_invert_blocks(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, cudaStream_t st) {
+  if (count <= 0) return;
+  k_invert_blocks<T><<<(count + 7) / 8, 256, 0, st>>>(P, N, items, count);
+}
+
+template void launch_invert_blocks<float>(const DevPlan&, const DevNum<float>&, const int2*, int, cudaStream_t);
+template void launch_invert_blocks<double>(const DevPlan&, const DevNum<double>&, const int2*, int, cudaStream_t);
+
 template void launch_factor_small<float>(const DevPlan&, const DevNum<float>&, const int32_t*, int, int, double,
                                          int, cudaStream_t);
 template void launch_factor_small<double>(const DevPlan&, const DevNum<double>&, const int32_t*, int, int, double,
                                           int, cudaStream_t);
 
-template <typename T>
-void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,
-                        double eps, int policy, long long wait, cudaStream_t st) {
-  if (count <= 0) return;
+template <typename T, int NB>
+static void launch_macro_panel_nb(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync,
+                                  int* err, double eps, int policy, long long wait, cudaStream_t st) {
   static bool attr = false;
-  const int smem = macro_panel_smem((int)sizeof(T));
+  const int smem = macro_panel_smem((int)sizeof(T), NB);
   if (!attr) {
-    cudaFuncSetAttribute(k_macro_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_macro_panel<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  k_macro_panel<T><<<count, 256, smem, st>>>(P, N, items, sync, err, eps, policy, wait);
+  k_macro_panel<T, NB><<<count, 256, smem, st>>>(P, N, items, sync, err, eps, policy, wait);
 }
 
-template void launch_macro_panel<float>(const DevPlan&, const DevNum<float>&, const int4*, int, int*, int*, double,
-                                        int, long long, cudaStream_t);
-template void launch_macro_panel<double>(const DevPlan&, const DevNum<double>&, const int4*, int, int*, int*, double,
-                                         int, long long, cudaStream_t);
+// nb: the panel width of the handle's schedule (192 only for FP32: the FP64
+// diagonal block would not fit the shared memory)
+template <typename T>
+void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int nb, int* sync,
+                        int* err, double eps, int policy, long long wait, cudaStream_t st) {
+  if (count <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    if (nb == MACRO_NB_WIDE) {
+      launch_macro_panel_nb<T, MACRO_NB_WIDE>(P, N, items, count, sync, err, eps, policy, wait, st);
+      return;
+    }
+  }
+  launch_macro_panel_nb<T, MACRO_NB>(P, N, items, count, sync, err, eps, policy, wait, st);
+}
+
+template void launch_macro_panel<float>(const DevPlan&, const DevNum<float>&, const int4*, int, int, int*, int*,
+                                        double, int, long long, cudaStream_t);
+template void launch_macro_panel<double>(const DevPlan&, const DevNum<double>&, const int4*, int, int, int*, int*,
+                                         double, int, long long, cudaStream_t);
 
 }  // namespace ncl

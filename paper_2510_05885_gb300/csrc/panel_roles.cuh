@@ -3,7 +3,7 @@
 // (front_dag.cu): the 32-column sub-block LDL^T, the blocked substitution,
 // the diagonal role and the row role of a 128-column macro panel.
 //
-// The pivot columns of a large front are processed MACRO_NB = 128 at a time
+// The pivot columns of a large front are processed NB = 128 or 192 at a time
 // (right-looking blocked LDL^T with D diagonal and static pivoting, Section
 // 3.1).  For macro panel [q0, qe) one launch (k_macro_panel) runs, for every
 // large front of the level:
@@ -26,8 +26,6 @@ namespace ncl {
 
 namespace {
 
-constexpr int MNB = MACRO_NB;
-constexpr int LDM = MNB + 1;       // shared row stride of the diagonal block
 constexpr int RB = MACRO_ROWS;     // rows per row CTA
 constexpr int LDS = 33;            // stride of the 32 x 32 shared blocks
 
@@ -62,9 +60,13 @@ __device__ __forceinline__ void load_tile(T* dst, int ldd, const T* src, int64_t
   }
 }
 
-static int macro_diag_smem(int esz) { return (MNB * LDM + (MNB - 32) * LDS + MNB) * esz + 2 * MNB; }
-static int macro_rows_smem(int esz) { return (RB * LDM + 10 * 32 * LDS + MNB) * esz; }
-inline int macro_panel_smem(int esz) { return std::max(macro_diag_smem(esz), macro_rows_smem(esz)); }
+// shared memory of the two roles of a panel nb columns wide (row stride nb + 1)
+inline int macro_diag_smem(int esz, int nb) { return (nb * (nb + 1) + (nb - 32) * LDS + nb) * esz + 2 * nb; }
+inline int macro_rows_smem(int esz, int nb) {
+  const int k = nb / 32;   // the diagonal sub-blocks of L11 and those below them
+  return (RB * (nb + 1) + (k + k * (k - 1) / 2) * 32 * LDS + nb) * esz;
+}
+inline int macro_panel_smem(int esz, int nb) { return std::max(macro_diag_smem(esz, nb), macro_rows_smem(esz, nb)); }
 
 // LDL^T of a 32 x 32 diagonal sub-block in shared memory (row stride ld,
 // cw <= 32 valid rows) by one warp, lane i holding row i in registers:
@@ -268,8 +270,8 @@ __device__ __forceinline__ void bar_warps_1_7() { asm volatile("bar.sync 1, 224;
 // done by the nw warps wfirst.. of the CTA, lane = column, register tiles of
 // up to 8 rows per warp and trip
 template <typename T, int MRW = 8>
-__device__ __forceinline__ void block_update(T* A, const T* Xs, int c0, int rb, int w, int r_begin, int c_begin,
-                                             int c_end, int wfirst, int nw) {
+__device__ __forceinline__ void block_update(T* A, int LDM, const T* Xs, int c0, int rb, int w, int r_begin,
+                                             int c_begin, int c_end, int wfirst, int nw) {
   const int warp = (threadIdx.x >> 5) - wfirst, lane = threadIdx.x & 31;
   if (warp < 0 || warp >= nw || c_begin >= c_end) return;
   const int ng = (c_end - c_begin + 31) / 32;   // 1 or 2
@@ -311,9 +313,10 @@ __device__ __forceinline__ void block_update(T* A, const T* Xs, int c0, int rb, 
 // CTAs) and update the columns beyond the next sub-block.  The rows below
 // the first sub-block are loaded while warp 0 factors it.  At the end four
 // warps invert the four unit lower sub-blocks (for the triangular sweeps).
-template <typename T>
+template <typename T, int MNB>
 __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int* flags,
                                                 double eps, int policy, unsigned char* smem_raw) {
+  constexpr int LDM = MNB + 1;   // shared row stride of the diagonal block
   T* A = reinterpret_cast<T*>(smem_raw);   // w x w block, row stride LDM
   T* Xs = A + MNB * LDM;                   // X of the rows below the sub-block
   T* dsh = Xs + (MNB - 32) * LDS;          // pivots of the block (MNB)
@@ -361,7 +364,7 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
         A[(rb + r) * LDM + c0 + c] = x * pivot_rcp(dsh[c0 + c]);
       }
       __syncthreads();
-      block_update<T, 4>(A, Xs, c0, rb, rb + nn, rb, rb, rb + nn, 0, 8);   // 32 rows: 4 per warp
+      block_update<T, 4>(A, LDM, Xs, c0, rb, rb + nn, rb, rb, rb + nn, 0, 8);   // 32 rows: 4 per warp
       __syncthreads();
     }
     if (warp == 0) {
@@ -394,18 +397,14 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
         st_release_i32(flags + j, 1);
       }
       if (nr > 32) {
-        block_update<T>(A, Xs, c0, rb, w, rb + 32, rb, rb + 32, 1, 7);
-        block_update<T>(A, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
+        block_update<T>(A, LDM, Xs, c0, rb, w, rb + 32, rb, rb + 32, 1, 7);
+        block_update<T>(A, LDM, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
       }
     }
     __syncthreads();
   }
-  // the inverses of the unit lower diagonal sub-blocks (for the triangular
-  // sweeps), after the last publication: nothing waits for them inside the
-  // factorisation
-  if (warp < nbk)
-    invert_sub32<T>(A + 32 * warp * LDM + 32 * warp, LDM, min(32, w - 32 * warp),
-                    N.Linv + P.sn_Ioff[s] + (int64_t)((q0 >> 5) + warp) * 1024, lane);
+  // (the inverses of the unit lower diagonal sub-blocks, which only the
+  // triangular sweeps use, are formed by one launch after the factorisation)
   for (int c = tid; c < w; c += blockDim.x) N.piv[col0 + q0 + c] = pst[c];
 }
 
@@ -415,14 +414,16 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
 // substitution and R_i -= X_j L_ij^T for the later sub-blocks (lane =
 // column, the rows of a warp in registers); finally L21 = X D1^-1, and for a
 // tensor-core front the split TF32 operands of L21 and of W = L21 D1 = X.
-template <typename T>
+template <typename T, int MNB>
 __device__ __forceinline__ void panel_rows_role(const DevPlan& P, const DevNum<T>& N, int s, int q0, int r0,
                                                 const int* flags, int* err, long long wait,
                                                 unsigned char* smem_raw) {
+  constexpr int LDM = MNB + 1;
+  constexpr int KB = MNB / 32;             // sub-blocks of the panel
   T* R = reinterpret_cast<T*>(smem_raw);   // RB rows x w columns, stride LDM
-  T* Ld = R + RB * LDM;                    // 4 unit lower diagonal sub-blocks of L11
-  T* Lo = Ld + 4 * 32 * LDS;               // 6 off-diagonal sub-blocks (i > j) of L11
-  T* dsh = Lo + 6 * 32 * LDS;              // D1
+  T* Ld = R + RB * LDM;                    // the KB unit lower diagonal sub-blocks of L11
+  T* Lo = Ld + KB * 32 * LDS;              // the KB (KB - 1) / 2 off-diagonal sub-blocks (i > j) of L11
+  T* dsh = Lo + (KB * (KB - 1) / 2) * 32 * LDS;   // D1
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
   const int w = min(MNB, ncol - q0);
   const int nbk = (w + 31) / 32;
