@@ -397,8 +397,8 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
         st_release_i32(flags + j, 1);
       }
       if (nr > 32) {
-        block_update<T>(A, LDM, Xs, c0, rb, w, rb + 32, rb, rb + 32, 1, 7);
-        block_update<T>(A, LDM, Xs, c0, rb, w, rb + 32, rb + 32, w, 1, 7);
+        // (block_update covers at most 64 columns per call)
+        for (int cb = rb; cb < w; cb += 64) block_update<T>(A, LDM, Xs, c0, rb, w, rb + 32, cb, min(cb + 64, w), 1, 7);
       }
     }
     __syncthreads();

@@ -392,13 +392,16 @@ def test_deep_fronts_elementwise(prec, eta_tol, form, side, persistent):
     assert prof[f"bwd_chain_multi_{suffix}"]["launches"] >= 1
     if prec == "fp32_ir" and not persistent:
         # the trailing updates of every many-pivot front (roots included)
-        assert prof["update_tc_f32"]["launches"] >= 4
+        assert prof["update_tc_f32"]["launches"] >= 2
     if prec == "fp32_ir" and persistent and form == "condensed":
         # the update blocks of the many-pivot fronts with rows below (the
         # trailing updates run inside the persistent launch)
         assert prof["update_tc_f32"]["launches"] >= 1
     want = (inst.n, inst.m, 0) if form == "stabilized" else (inst.n, 0, 0)
     assert finfo.inertia == want
+    # the quality of the factors, not only the refined answer: at rho = 1e4
+    # (kappa ~ 4e5) a sound FP32 factorisation needs at most 3 Richardson steps
+    assert sinfo.used_fgmres == 0 and sinfo.ir_iters <= 3, sinfo.ir_iters
     check_against_oracle(inst, prec, X.cpu().numpy(), finfo, sinfo, eta_tol)
 
 
