@@ -657,16 +657,27 @@ def run_ours(args):
             a2.draws = 2
             R2 = Runner(a2, dev, rank, pats=R.pats)
             entry = {}
-            for prec, Kx in (("fp32_ir", K), ("fp64", K64)):
-                if Kx is None:
-                    continue
+
+            def leg(Kx):
                 msx, resx, _ = timed(Kx, max(2, args.steps // 3), 1, R2)
-                entry[prec] = {"ms_per_step": sum(msx) / len(msx),
-                               "backward_err_max": max(r[1].backward_err for r in resx),
-                               "ir_iters": max(r[1].ir_iters for r in resx),
-                               "fgmres": any(r[1].used_fgmres for r in resx),
-                               "fp64_fallback": any(r[1].fp64_fallback for r in resx),
-                               "inertia": list(resx[-1][0][0].inertia)}
+                return {"ms_per_step": sum(msx) / len(msx),
+                        "backward_err_max": max(r[1].backward_err for r in resx),
+                        "ir_iters": max(r[1].ir_iters for r in resx),
+                        "fgmres": any(r[1].used_fgmres for r in resx),
+                        "fp64_fallback": any(r[1].fp64_fallback for r in resx),
+                        # 2: started in FP64 directly (an earlier FP32 factor
+                        # at this penalty was not trusted)
+                        "fallback_modes": sorted({int(r[0][0].fp64_fallback) for r in resx}),
+                        "inertia": list(resx[-1][0][0].inertia)}
+            entry["fp32_ir"] = leg(K)
+            if entry["fp32_ir"]["fp64_fallback"]:
+                # what a step costs when the FP32 try is made every time
+                # (precision_fallback = 2), as at the first step at a new penalty
+                Ke = R.make("fp32_ir", precision_fallback=2)
+                entry["fp32_ir_tries_fp32_every_step"] = leg(Ke)
+                Ke.close()
+            if K64 is not None:
+                entry["fp64"] = leg(K64)
             if "fp64" in entry:
                 entry["speedup_fp32ir_vs_fp64"] = entry["fp64"]["ms_per_step"] / entry["fp32_ir"]["ms_per_step"]
             sweep[f"{rho:g}"] = entry

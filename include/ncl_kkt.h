@@ -116,7 +116,15 @@ typedef struct {
                                  FP64 when the FP32 factor cannot be trusted (an
                                  inertia other than (n,m,0) / (n,0,0), which FP32
                                  produces when rho*||J||^2 swamps H+Sigma+delta I) or
-                                 when refinement cannot reach ir_tol; 0: never */
+                                 when refinement cannot reach ir_tol, and remember,
+                                 per instance, the penalty rho of such a fallback
+                                 whose FP64 factors were regular: a later
+                                 factorisation in which some instance's rho is at
+                                 least its remembered one starts in FP64 directly
+                                 (fp64_fallback = 2; the penalty of the NCL outer
+                                 loop only grows, Algorithm 1); 2: fall back the
+                                 same way but remember nothing (every factorisation
+                                 tries FP32 first); 0: never */
     int64_t max_device_bytes; /* 0 = no limit */
     int64_t wait_cycles;      /* bound, in SM clock cycles, of every wait of one CTA
                                  on another inside a kernel (the panel factorisation's
@@ -163,7 +171,10 @@ typedef struct {
     double flops;                  /* sum_j (c_j^2 + 3 c_j), c_j = nnz of column j of L
                                       below the diagonal */
     float ms;                      /* device time of the call */
-    int32_t fp64_fallback;         /* 1 if the factors in use are the FP64 refactorisation */
+    int32_t fp64_fallback;         /* 0: FP32 factors (or an FP64 handle); 1: the FP64
+                                      refactorisation after an untrusted FP32 one;
+                                      2: FP64 factors started directly (the penalty
+                                      is at least one where FP32 failed before) */
 } ncl_kkt_factor_info;
 
 typedef struct {

@@ -231,7 +231,6 @@ struct ncl_kkt_s {
   DagTask* d_dag = nullptr;                // persistent large-front tasks
   int* d_dag_cnt = nullptr;                //   their queue heads and counters
   int n_sm = 148;                          // multiprocessors of the device
-  int panel_nb = MACRO_NB;                 // pivot columns per panel step of the schedule
   // CUDA graphs: the factor and the triangular sweeps are captured once (on
   // a private stream, after one direct call) and replayed
   cudaStream_t cap_stream = nullptr;
@@ -244,6 +243,11 @@ struct ncl_kkt_s {
   ncl_kkt_s* twin = nullptr;
   bool use_twin = false;
   bool skip_values = false;     // a twin factors the FP64 values copied from its parent
+  // per instance, the smallest penalty rho at which an FP32 factorisation had
+  // to be replaced by the FP64 one although the FP64 factors were regular
+  // (+inf: none yet); precision_fallback = 1 starts later factorisations
+  // with rho_i >= fp32_fail_rho[i] for some instance i directly in FP64
+  std::vector<double> fp32_fail_rho;
   // one graph for factor + solve + refinement (batch_factor_solve)
   cudaGraphExec_t fsgraph = nullptr;
   int64_t fsgraph_nodes = 0;
@@ -326,11 +330,7 @@ void build_schedule(ncl_kkt_s* h) {
   std::vector<GemmProb>& probv = hs.probv;
   hs.tc = is_fp32(h) && h->opt.use_tensor_cores;
   hs.dag = h->opt.persistent_fronts != 0;
-  // panel width of the per-step path: 192 columns for FP32 (fewer, longer
-  // panel steps; the FP64 diagonal block of that width would not fit the
-  // shared memory), 128 otherwise and for the persistent path's tiles
-  h->panel_nb = (is_fp32(h) && !hs.dag) ? MACRO_NB_WIDE : MACRO_NB;
-  const int PNB = h->panel_nb;
+  const int PNB = MACRO_NB;   // pivot columns per panel step
   hs.dagv.clear();
   hs.dag_counters = (int64_t)P.nlevels;   // one queue head per level first
   hs.invv.clear();
@@ -1259,7 +1259,7 @@ void run_factor(ncl_kkt_s* h, DevNum<T>& N, cudaStream_t st) {
     for (const Step& S : L.steps) {
       if (L.dag_cnt > 0) break;
       klaunch(h, st, f32 ? "macro_panel_f32" : "macro_panel_f64", S.panel_cnt, S.panel_cost, [&] {
-        launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->panel_nb, h->d_panel_sync, h->d_err,
+        launch_macro_panel<T>(P, N, h->d_panel + S.panel_off, S.panel_cnt, h->d_panel_sync, h->d_err,
                               eps, pol, h->opt.wait_cycles, st);
       });
       klaunch(h, st, f32 ? "update_simt_f32" : "update_simt_f64", S.tiles, S.gemm_cost, [&] {
@@ -1612,9 +1612,9 @@ ncl_status prepare_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, cons
   return NCL_OK;
 }
 
-// all device work of a factorisation, on stream s2 (capturable)
-void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
-  const int ni = h->dp.ninst;
+// the FP64 values of the matrix (K2r blocks or H + Sigma + delta I +
+// rho J^T W J) from the user's arrays, on stream s2
+void enqueue_values(ncl_kkt_s* h, cudaStream_t s2) {
   if (!h->skip_values) {
     const double np = (double)h->plan.pair_p.size();
     if (h->dp.form == 1 && h->dp.ncon > 0)
@@ -1624,6 +1624,12 @@ void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
             Cost{2.0 * np, 33.0 * h->dp.nnzA + 24.0 * np + 8.0 * (h->dp.nnzH + h->dp.nnzJ + h->dp.nvar)},
             [&] { launch_kkt_values(h->dp, h->d_valptr, h->d_delta, h->d_rho, h->d_w, h->Klow, s2); });
   }
+}
+
+// all device work of a factorisation, on stream s2 (capturable)
+void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
+  const int ni = h->dp.ninst;
+  enqueue_values(h, s2);
   CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), s2));
   klaunch(h, s2, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
           [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, s2); });
@@ -1700,6 +1706,19 @@ bool inertia_regular(ncl_kkt_s* h) {
   return true;
 }
 
+// which instances' inertia is not the regular one (after finish_factor)
+std::vector<char> irregular_instances(ncl_kkt_s* h) {
+  const int ni = h->dp.ninst;
+  const long long* hc = reinterpret_cast<const long long*>(h->h_pinned + 2 * ni);
+  std::vector<char> out(ni, 0);
+  for (int i = 0; i < ni; i++) {
+    const Instance& I = h->plan.inst[i];
+    const long long want_neg = h->plan.form == 0 ? I.m : 0;
+    out[i] = !(hc[4 * i] == I.n && hc[4 * i + 1] == want_neg && hc[4 * i + 2] == 0);
+  }
+  return out;
+}
+
 // refactor the parent's FP64 values in FP64 on the twin handle
 ncl_status escalate(ncl_kkt_s* h, cudaStream_t st, ncl_kkt_factor_info* infos) {
   if (!h->twin) {
@@ -1736,18 +1755,54 @@ ncl_status escalate(ncl_kkt_s* h, cudaStream_t st, ncl_kkt_factor_info* infos) {
   return s;
 }
 
+// the FP32 factors of the values just factored were not trusted (irregular
+// inertia, or refinement short of ir_tol) while the FP64 ones are regular:
+// remember the penalty of every instance (of the irregular ones only, when
+// the inertia told which)
+void note_fp32_failure(ncl_kkt_s* h, const std::vector<char>* which) {
+  if (h->opt.precision_fallback != 1 || !h->twin || !h->use_twin || !inertia_regular(h->twin)) return;
+  const int ni = h->dp.ninst;
+  if ((int)h->fp32_fail_rho.size() != ni) h->fp32_fail_rho.assign(ni, HUGE_VAL);
+  for (int i = 0; i < ni; i++)
+    if (!which || (*which)[i]) h->fp32_fail_rho[i] = std::min(h->fp32_fail_rho[i], h->h_rho[i]);
+}
+
+// start this factorisation directly in FP64? (an instance's penalty is at
+// least one at which its FP32 factors were already replaced)
+bool skip_fp32(const ncl_kkt_s* h, const double* rho) {
+  if (!is_fp32(h) || h->opt.precision_fallback != 1 || (int)h->fp32_fail_rho.size() != h->dp.ninst) return false;
+  for (int i = 0; i < h->dp.ninst; i++)
+    if (rho[i] >= h->fp32_fail_rho[i]) return true;
+  return false;
+}
+
+// the FP64 factorisation straight away: values on this handle, factors on
+// the twin; the infos say fp64_fallback = 2
+ncl_status factor_fp64_direct(ncl_kkt_s* h, cudaStream_t st, ncl_kkt_factor_info* infos) {
+  enqueue_values(h, st);
+  const ncl_status s = escalate(h, st, infos);
+  if (infos)
+    for (int i = 0; i < h->dp.ninst; i++) infos[i].fp64_fallback = 2;
+  return s;
+}
+
 ncl_status do_factor(ncl_kkt_s* h, const double* Hv, const double* Jv, const double* S, const double* delta,
                      const double* rho, cudaStream_t st, ncl_kkt_factor_info* infos, const double* Ss = nullptr) {
   h->use_twin = false;
   ncl_status s0 = prepare_factor(h, Hv, Jv, S, delta, rho, st, Ss);
   if (s0 != NCL_OK) return s0;
+  if (skip_fp32(h, rho)) return factor_fp64_direct(h, st, infos);
   run_graphed(h, &h->fgraph, &h->fgraph_nodes, &h->factor_calls, true, st,
               [&](cudaStream_t s2) { enqueue_factor(h, s2); });
   ncl_status s1 = finish_factor(h, st, infos);
   if (infos)
     for (int i = 0; i < h->dp.ninst; i++) infos[i].fp64_fallback = 0;
-  if (is_fp32(h) && h->opt.precision_fallback && (s1 == NCL_OK || s1 == NCL_ERR_NUMERIC) && !inertia_regular(h))
-    return escalate(h, st, infos);
+  if (is_fp32(h) && h->opt.precision_fallback && (s1 == NCL_OK || s1 == NCL_ERR_NUMERIC) && !inertia_regular(h)) {
+    const std::vector<char> irr = irregular_instances(h);
+    const ncl_status se = escalate(h, st, infos);
+    note_fp32_failure(h, &irr);
+    return se;
+  }
   return s1;
 }
 
@@ -1779,12 +1834,14 @@ ncl_status do_factor_solve(ncl_kkt_s* h, const double* Hv, const double* Jv, con
   h->fs_keyi[0] = ldb;
   h->fs_keyi[1] = ldx;
   h->fs_keyi[2] = nrhs;
-  if (h->fs_calls == 0 || h->prof_on) {
+  const bool direct64 = skip_fp32(h, rho);
+  if (h->fs_calls == 0 || h->prof_on || direct64) {
     // direct: the regular calls, which also tell how many steps are needed
+    // (not those of an FP64 factorisation started directly)
     ncl_status s1 = do_factor(h, Hv, Jv, S, delta, rho, st, infos);
     if (s1 != NCL_OK && s1 != NCL_ERR_ZERO_PIVOT) return s1;
     ncl_status s2 = do_solve(h, nrhs, B, ldb, X, ldx, st, sinfo);
-    if (!h->prof_on) {
+    if (!h->prof_on && !direct64 && !(sinfo && sinfo->fp64_fallback)) {
       h->fs_calls = 1;
       h->fs_nir = sinfo ? sinfo->ir_iters : h->opt.ir_max_iter;
       if (sinfo && sinfo->used_fgmres) h->fs_nir = 0;
@@ -1820,7 +1877,9 @@ ncl_status do_factor_solve(ncl_kkt_s* h, const double* Hv, const double* Jv, con
   if (infos)
     for (int i = 0; i < ni; i++) infos[i].fp64_fallback = 0;
   if (is_fp32(h) && h->opt.precision_fallback && (sf == NCL_OK || sf == NCL_ERR_NUMERIC) && !inertia_regular(h)) {
+    const std::vector<char> irr = irregular_instances(h);
     ncl_status se = escalate(h, st, infos);
+    note_fp32_failure(h, &irr);
     if (se != NCL_OK && se != NCL_ERR_ZERO_PIVOT) return se;
     ncl_status s2 = do_solve(h, nrhs, B, ldb, X, ldx, st, sinfo);
     return s2 != NCL_OK ? s2 : se;
@@ -1835,6 +1894,7 @@ ncl_status do_factor_solve(ncl_kkt_s* h, const double* Hv, const double* Jv, con
   }
   if (sr == NCL_ERR_IR_NOT_CONVERGED && is_fp32(h) && h->opt.precision_fallback) {
     ncl_status se = escalate(h, st, nullptr);
+    note_fp32_failure(h, nullptr);
     if (se != NCL_OK && se != NCL_ERR_ZERO_PIVOT) return se;
     return do_solve(h, nrhs, B, ldb, X, ldx, st, sinfo);
   }
@@ -1874,6 +1934,7 @@ ncl_status do_solve(ncl_kkt_s* h, int32_t nrhs, const double* B, int64_t ldb, do
   if (worst == NCL_ERR_IR_NOT_CONVERGED && allow_escalate && is_fp32(h) && h->opt.precision_fallback) {
     // the FP32 factors cannot reach the tolerance: refactor in FP64, solve again
     ncl_status se = escalate(h, st, nullptr);
+    note_fp32_failure(h, nullptr);
     if (se != NCL_OK && se != NCL_ERR_ZERO_PIVOT) return se;
     return do_solve(h, nrhs, B, ldb, X, ldx, st, info, false);
   }
@@ -1912,6 +1973,8 @@ static ncl_status init_options(ncl_kkt_s* h, const ncl_kkt_options* opt) {
   if (h->opt.wait_cycles <= 0) h->opt.wait_cycles = DEFAULT_WAIT_CYCLES;
   if (!(h->opt.ir_switch > 0.0) || !(h->opt.ir_switch <= 1.0)) h->opt.ir_switch = 0.5;
   if (h->opt.tc_min_pivots < 32) return fail(NCL_ERR_INVALID_ARG, "tc_min_pivots must be >= 32");
+  if (h->opt.precision_fallback < 0 || h->opt.precision_fallback > 2)
+    return fail(NCL_ERR_INVALID_ARG, "precision_fallback must be 0, 1 or 2");
   return NCL_OK;
 }
 
@@ -2599,7 +2662,7 @@ ncl_status selftest_timeout(ncl_kkt_s* h, DevNum<T>& N, int which, long long wai
     int nrc = 0;
     for (size_t i = 0; i < hs.panelv.size();) {
       const int4 it = hs.panelv[i];
-      const int qe = std::min(it.y + h->panel_nb, (int)P.sn_ncol[it.x]);
+      const int qe = std::min(it.y + MACRO_NB, (int)P.sn_ncol[it.x]);
       const int n = (P.sn_nrow[it.x] - qe + MACRO_ROWS - 1) / MACRO_ROWS;
       if (n >= 1) {
         g0 = (int64_t)i;
@@ -2613,7 +2676,7 @@ ncl_status selftest_timeout(ncl_kkt_s* h, DevNum<T>& N, int which, long long wai
     CK(cudaMemcpyAsync(h->d_panel_sync + hs.panelv[g0].z, &one, sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-    launch_macro_panel<T>(h->dp, N, h->d_panel + g0, nrc, h->panel_nb, h->d_panel_sync, h->d_err,
+    launch_macro_panel<T>(h->dp, N, h->d_panel + g0, nrc, h->d_panel_sync, h->d_err,
                           h->opt.pivot_eps, h->opt.pivot_policy, wait, st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));

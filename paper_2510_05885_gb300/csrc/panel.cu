@@ -307,24 +307,19 @@ static void launch_macro_panel_nb(const DevPlan& P, const DevNum<T>& N, const in
   k_macro_panel<T, NB><<<count, 256, smem, st>>>(P, N, items, sync, err, eps, policy, wait);
 }
 
-// nb: the panel width of the handle's schedule (192 only for FP32: the FP64
-// diagonal block would not fit the shared memory)
+// (a 192-column FP32 panel was measured slower than 128 columns on the
+// condensed 300 x 300 and stabilized 700 x 700 grids: the diagonal role's
+// serial chain of 32-column factorisations grows with the width)
 template <typename T>
-void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int nb, int* sync,
-                        int* err, double eps, int policy, long long wait, cudaStream_t st) {
+void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,
+                        double eps, int policy, long long wait, cudaStream_t st) {
   if (count <= 0) return;
-  if constexpr (sizeof(T) == 4) {
-    if (nb == MACRO_NB_WIDE) {
-      launch_macro_panel_nb<T, MACRO_NB_WIDE>(P, N, items, count, sync, err, eps, policy, wait, st);
-      return;
-    }
-  }
   launch_macro_panel_nb<T, MACRO_NB>(P, N, items, count, sync, err, eps, policy, wait, st);
 }
 
-template void launch_macro_panel<float>(const DevPlan&, const DevNum<float>&, const int4*, int, int, int*, int*,
+template void launch_macro_panel<float>(const DevPlan&, const DevNum<float>&, const int4*, int, int*, int*,
                                         double, int, long long, cudaStream_t);
-template void launch_macro_panel<double>(const DevPlan&, const DevNum<double>&, const int4*, int, int, int*, int*,
+template void launch_macro_panel<double>(const DevPlan&, const DevNum<double>&, const int4*, int, int*, int*,
                                          double, int, long long, cudaStream_t);
 
 }  // namespace ncl

@@ -3,7 +3,7 @@
 // (front_dag.cu): the 32-column sub-block LDL^T, the blocked substitution,
 // the diagonal role and the row role of a 128-column macro panel.
 //
-// The pivot columns of a large front are processed NB = 128 or 192 at a time
+// The pivot columns of a large front are processed NB = 128 at a time
 // (right-looking blocked LDL^T with D diagonal and static pivoting, Section
 // 3.1).  For macro panel [q0, qe) one launch (k_macro_panel) runs, for every
 // large front of the level:

@@ -10,8 +10,7 @@ namespace ncl {
 // Tile/chunk constants shared by the launch planner and the kernels.
 constexpr int ASM_ROWS = 32;      // front rows per assembly CTA
 constexpr int PANEL_NB = 32;      // pivot columns of a diagonal sub-block
-constexpr int MACRO_NB = 128;     // pivot columns per panel of a large front (persistent path, FP64)
-constexpr int MACRO_NB_WIDE = 192; // pivot columns per panel of the FP32 per-step path
+constexpr int MACRO_NB = 128;     // pivot columns per panel of a large front
 constexpr int MACRO_ROWS = 64;    // rows below the macro panel per CTA
 constexpr int GEMM_TILE = 64;     // SIMT update tile (rows x cols)
 constexpr int SOLVE_ROWS = 64;     // below rows per solve CTA
@@ -186,8 +185,8 @@ template <typename T>
 void launch_subtree_factor(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes,
                            int* counter, int smem, int nsm, double eps, int policy, cudaStream_t st);
 template <typename T>
-void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int nb, int* sync,
-                        int* err, double eps, int policy, long long wait, cudaStream_t st);
+void launch_macro_panel(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int* sync, int* err,
+                        double eps, int policy, long long wait, cudaStream_t st);
 template <typename T>
 void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cudaStream_t st);
 

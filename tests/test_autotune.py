@@ -79,3 +79,16 @@ def test_committed_table_parses():
     K = _handle(1, 20, autotune_path=path)
     assert nk.ncl_kkt_get_options(K._h).tc_min_pivots >= 32
     K.close()
+
+
+@pytest.mark.parametrize("mode", [-1, 3])
+def test_precision_fallback_mode_is_validated(mode):
+    with pytest.raises(nk.NclError):
+        _handle(0, 6, precision_fallback=mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_precision_fallback_modes_accepted(mode):
+    K = _handle(1, 6, precision_fallback=mode)
+    assert nk.ncl_kkt_get_options(K._h).precision_fallback == mode
+    K.close()

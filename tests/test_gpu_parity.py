@@ -324,6 +324,32 @@ def test_rho_1e8_fp32_falls_back_to_fp64(form):
     assert O.backward_error(A, X64, inst.b) <= 1e-12
 
 
+def test_fp32_failure_penalty_is_remembered():
+    """After an untrusted FP32 factor at rho = 1e8 (with regular FP64
+    factors), the handle starts later factorisations at rho >= 1e8 in FP64
+    directly (fp64_fallback = 2), with the same results; a smaller penalty
+    tries FP32 again, and precision_fallback = 2 remembers nothing."""
+    hi = synth.condensed_grid(24, rho=1e8, draw=0)
+    lo = synth.condensed_grid(24, rho=1e5, draw=1)
+    p = hi.pat
+    want = (hi.n, 0, 0)
+    for mode, second in ((1, 2), (2, 1)):
+        K = nk().KKT(1, p.n, p.m, p.H_rowptr, p.H_colind, p.J_rowptr, p.J_colind, prec="fp32_ir",
+                     precision_fallback=mode)
+        seen = []
+        for inst, rho in ((hi, hi.rho), (hi, 2 * hi.rho), (lo, lo.rho), (hi, hi.rho)):
+            A = O.instance_matrix(inst) if rho == inst.rho else None
+            f = K.factor(_t(inst.H_val), _t(inst.J_val), _t(inst.Sigma), inst.delta, rho)
+            X, si = K.solve(_t(inst.b))
+            torch.cuda.synchronize()
+            assert f.inertia == want and si.status == 0
+            if A is not None:
+                assert O.backward_error(A, X.cpu().numpy(), inst.b) <= 1e-10
+            seen.append((f.fp64_fallback, si.fp64_fallback))
+        assert seen == [(1, 1), (second, 1), (0, 0), (second, 1)], (mode, seen)
+        K.close()
+
+
 def test_batch_factor_solve_graph_replay():
     """The one-graph factor + solve of a batch, replayed with new values on
     the same patterns and buffers, against the oracle every time."""
