@@ -100,8 +100,9 @@ __device__ __forceinline__ void factor_step(T (&r)[32], int k, T dk, int lane, T
 // (Section 3.1): a pivot with |d| <= eps becomes +-eps by the sign of its
 // block (status 1 perturbed, or 2 zero under the stop policy), a non-finite
 // pivot is kept (status 3).  The common case has no such pivot: the columns
-// run without the pivot test on the dependency chain, and only when a test
-// fired does the block run again from shared memory with the replacement.
+// run without any pivot test, the tests run once afterwards on the pivots
+// the lanes kept, and only when one fired does the block run again from
+// shared memory with the replacement at each step.
 // EARLY: stop after column cw (narrow blocks of small fronts); otherwise
 // all 32 steps run on the identity-padded block (no branch between steps).
 template <typename T, bool EARLY>
@@ -115,17 +116,17 @@ __device__ __noinline__ T factor_sub32(T* blk, int ld, int cw, int my_sign, doub
   };
   load();
   const T e = (T)eps;
-  unsigned tiny_mask = 0u, bad_mask = 0u;
   T my_d = T(1);
 #pragma unroll
   for (int k = 0; k < 32; k++) {
     if (EARLY && k >= cw) break;
-    const T d0 = __shfl_sync(0xffffffffu, r[k], k);
-    const T a = d0 < T(0) ? -d0 : d0;
-    tiny_mask |= (unsigned)(a <= e) << k;             // NaN compares false
-    bad_mask |= (unsigned)(!finite_val(d0)) << k;
-    factor_step(r, k, d0, lane, my_d);
+    factor_step(r, k, __shfl_sync(0xffffffffu, r[k], k), lane, my_d);
   }
+  // the pivot tests, once at the end: lane k's my_d is the pivot of step k
+  // (1 on the padding and beyond cw)
+  const T ad = my_d < T(0) ? -my_d : my_d;
+  unsigned tiny_mask = __ballot_sync(0xffffffffu, ad <= e);   // NaN compares false
+  unsigned bad_mask = __ballot_sync(0xffffffffu, !finite_val(my_d));
   if (tiny_mask | bad_mask) {
     // again, with the static pivot applied at each step
     const unsigned neg = __ballot_sync(0xffffffffu, my_sign < 0);
@@ -341,10 +342,21 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
   if (warp == 0) {
     factor(0);
   } else if (w > 32) {
+    // (eight loads in flight per thread before the shared stores)
     const int n = (w - 32) * MNB;
-    for (int idx = tid - 32; idx < n; idx += 224) {
-      const int r = 32 + idx / MNB, c = idx % MNB;
-      A[r * LDM + c] = (c <= r) ? Lb[(int64_t)r * ncp + c] : T(0);
+    for (int base = tid - 32; base < n; base += 8 * 224) {
+      T v[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int idx = base + k * 224;
+        const int r = 32 + idx / MNB, c = idx % MNB;
+        v[k] = (idx < n && c <= r) ? Lb[(int64_t)r * ncp + c] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int idx = base + k * 224;
+        if (idx < n) A[(32 + idx / MNB) * LDM + idx % MNB] = v[k];
+      }
     }
   }
   __syncthreads();
@@ -408,7 +420,7 @@ __device__ __forceinline__ void panel_diag_role(const DevPlan& P, const DevNum<T
   for (int c = tid; c < w; c += blockDim.x) N.piv[col0 + q0 + c] = pst[c];
 }
 
-// Row role of a macro panel (one CTA per RB rows below it): stages its rows
+// Row role of a macro panel (one CTA of 256 threads per RB rows below it): stages its rows
 // while the diagonal role works, then for each 32-column sub-block j, as
 // soon as it is published, X_j = R_j L_jj^-T by the blocked forward
 // substitution and R_i -= X_j L_ij^T for the later sub-blocks (lane =
@@ -448,16 +460,35 @@ __device__ __forceinline__ void panel_rows_role(const DevPlan& P, const DevNum<T
       }
     }
     __syncthreads();
-    for (int i = j; i < nbk; i++) {
-      T* dst = (i == j) ? Ld + i * 32 * LDS : Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
-      const int rows = min(32, w - 32 * i);
-      const T* src = Lb + (int64_t)(q0 + 32 * i) * ncp + q0 + 32 * j;
-      for (int e = tid; e < 1024; e += blockDim.x) {
-        const int rr = e >> 5, cc = e & 31;
-        dst[rr * LDS + cc] = (rr < rows && (i > j || cc < rr)) ? __ldcg(src + (int64_t)rr * ncp + cc) : T(0);
+    {
+      // the published blocks (i, j), i >= j, and D_j: every load in flight
+      // before the shared stores (256 threads, four entries of each block)
+      T v[KB][4];
+#pragma unroll
+      for (int q = 0; q < KB; q++) {
+        const int i = j + q;
+        const int rows = min(32, w - 32 * i);
+        const T* src = Lb + (int64_t)(q0 + 32 * i) * ncp + q0 + 32 * j;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          const int e = tid + 256 * t, rr = e >> 5, cc = e & 31;
+          v[q][t] = (i < nbk && rr < rows && (i > j || cc < rr)) ? __ldcg(src + (int64_t)rr * ncp + cc) : T(0);
+        }
       }
+      const T dv = (tid < 32 && 32 * j + tid < w) ? __ldcg(N.D + col0 + q0 + 32 * j + tid) : T(1);
+#pragma unroll
+      for (int q = 0; q < KB; q++) {
+        const int i = j + q;
+        if (i >= nbk) break;
+        T* dst = (i == j) ? Ld + i * 32 * LDS : Lo + (i * (i - 1) / 2 + j) * 32 * LDS;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          const int e = tid + 256 * t;
+          dst[(e >> 5) * LDS + (e & 31)] = v[q][t];
+        }
+      }
+      if (tid < 32) dsh[32 * j + tid] = dv;
     }
-    if (tid < 32) dsh[32 * j + tid] = 32 * j + tid < w ? __ldcg(N.D + col0 + q0 + 32 * j + tid) : T(1);
     __syncthreads();
     block_trsm32<T>(R + 32 * j, LDM, nr, min(32, w - 32 * j), Ld + j * 32 * LDS, LDS);
     __syncthreads();
