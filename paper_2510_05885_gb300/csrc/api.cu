@@ -172,6 +172,7 @@ struct ncl_kkt_s {
   DevNum<float> nf{};
   DevNum<double> nd{};
   double* Klow = nullptr;
+  double* Kf = nullptr;        // FP64 values of the full pattern (F) in its row order, for the residual
   double* d_delta = nullptr;
   double* d_rho = nullptr;
   unsigned long long* d_knorm = nullptr;
@@ -1055,6 +1056,7 @@ void build_device(ncl_kkt_s* h) {
   // numeric storage
   const int ni = d.ninst;
   h->Klow = h->alloc<double>(P.nnzA);
+  h->Kf = h->alloc<double>((int64_t)P.F_col.size());
   h->d_delta = h->alloc<double>(ni);
   h->d_rho = h->alloc<double>(ni);
   h->d_knorm = h->alloc<unsigned long long>(ni);
@@ -1404,7 +1406,7 @@ double residual_eta(ncl_kkt_s* h, const double* B, int64_t ldb, const double* X,
   CK(cudaMemsetAsync(h->d_norms, 0, 2 * (size_t)ni * MAX_RHS_SWEEP * sizeof(unsigned long long), st));
   const double nnzF = (double)h->plan.F_col.size();
   klaunch(h, st, "residual_f64", h->dp.dim, Cost{2.0 * nnzF * nrhs, nnzF * 16.0 + 8.0 * h->dp.dim * (1 + 3.0 * nrhs)}, [&] {
-    launch_residual(h->dp, h->Klow, B, ldb, X, ldx, h->R, h->dp.dim, nrhs, h->d_norms,
+    launch_residual(h->dp, h->Kf, B, ldb, X, ldx, h->R, h->dp.dim, nrhs, h->d_norms,
                     h->d_norms + ni * MAX_RHS_SWEEP, st);
   });
   CK(cudaGetLastError());
@@ -1631,8 +1633,11 @@ void enqueue_factor(ncl_kkt_s* h, cudaStream_t s2) {
   const int ni = h->dp.ninst;
   enqueue_values(h, s2);
   CK(cudaMemsetAsync(h->d_knorm, 0, ni * sizeof(unsigned long long), s2));
-  klaunch(h, s2, "knorm_f64", h->dp.dim, Cost{0, 12.0 * (double)h->plan.F_col.size()},
-          [&] { launch_knorm(h->dp, h->Klow, h->d_knorm, s2); });
+  const int64_t nnzF = (int64_t)h->plan.F_col.size();
+  klaunch(h, s2, "full_values_f64", nnzF, Cost{0, 20.0 * (double)nnzF},
+          [&] { launch_full_values(h->dp, h->Klow, h->Kf, nnzF, s2); });
+  klaunch(h, s2, "knorm_f64", h->dp.dim, Cost{0, 8.0 * (double)nnzF + 8.0 * h->dp.dim},
+          [&] { launch_knorm(h->dp, h->Kf, h->d_knorm, s2); });
   CK(cudaMemsetAsync(h->d_counts, 0, (4 * ni + 1) * sizeof(long long), s2));
   CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s2));
   CK(cudaMemsetAsync(h->d_panel_sync, 0, std::max<int64_t>(h->hs.panel_sync, 8) * sizeof(int), s2));
@@ -1863,7 +1868,7 @@ ncl_status do_factor_solve(ncl_kkt_s* h, const double* Hv, const double* Jv, con
       CK(cudaMemsetAsync(h->d_norms, 0, 2 * (size_t)ni * MAX_RHS_SWEEP * sizeof(unsigned long long), s2));
       const double nnzF = (double)h->plan.F_col.size();
       klaunch(h, s2, "residual_f64", h->dp.dim, Cost{2.0 * nnzF * nrhs, nnzF * 16.0}, [&] {
-        launch_residual(h->dp, h->Klow, B, ldb, X, ldx, h->R, h->dp.dim, nrhs, h->d_norms,
+        launch_residual(h->dp, h->Kf, B, ldb, X, ldx, h->R, h->dp.dim, nrhs, h->d_norms,
                         h->d_norms + ni * MAX_RHS_SWEEP, s2);
       });
       if (k < nir) apply_inverse(h, h->R, h->dp.dim, X, ldx, nrhs, 1, s2);

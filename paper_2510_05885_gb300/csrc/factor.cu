@@ -105,15 +105,26 @@ void launch_kkt_values(const DevPlan& P, const double* const* vals, const double
   k_kkt_values<<<(unsigned)blocks, 256, 0, st>>>(P, vals, delta, rho, w, Klow);
 }
 
+// The values of the full (both triangles) pattern in its row order, Kf[q] =
+// Klow[F_src[q]], which the residual reads contiguously.
+__global__ void k_full_values(DevPlan P, const double* __restrict__ Klow, double* __restrict__ Kf, int64_t nnzF) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnzF; q += (int64_t)gridDim.x * blockDim.x)
+    Kf[q] = Klow[P.F_src[q]];
+}
+
 // ||K||_inf per instance (max absolute row sum), as the bit pattern of a
-// non-negative double so that atomicMax on the integer orders it.
-__global__ void k_knorm(DevPlan P, const double* __restrict__ Klow, unsigned long long* knorm) {
+// non-negative double so that atomicMax on the integer orders it.  Each CTA
+// takes a contiguous run of rows (its threads stride through it), so that a
+// thread's running maximum changes instance (and goes to an atomic) only at
+// an instance boundary: batches of many instances would otherwise contend
+// on a few addresses.
+__global__ void k_knorm(DevPlan P, const double* __restrict__ Kf, unsigned long long* knorm, int64_t rows_per_cta) {
   int cur = -1;
   unsigned long long mx = 0ull;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P.dim;
-       r += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t r_begin = blockIdx.x * rows_per_cta, r_end = min(P.dim, r_begin + rows_per_cta);
+  for (int64_t r = r_begin + threadIdx.x; r < r_end; r += blockDim.x) {
     double s = 0.0;
-    for (int64_t q = P.F_rowptr[r]; q < P.F_rowptr[r + 1]; q++) s += fabs(Klow[P.F_src[q]]);
+    for (int64_t q = P.F_rowptr[r]; q < P.F_rowptr[r + 1]; q++) s += fabs(Kf[q]);
     const int inst = P.row_inst[r];
     if (inst != cur) {
       if (cur >= 0) atomicMax(&knorm[cur], mx);
@@ -126,11 +137,19 @@ __global__ void k_knorm(DevPlan P, const double* __restrict__ Klow, unsigned lon
   warp_flush_max(knorm, cur, mx);
 }
 
-void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st) {
+void launch_full_values(const DevPlan& P, const double* Klow, double* Kf, int64_t nnzF, cudaStream_t st) {
+  if (nnzF <= 0) return;
+  int64_t qb = (nnzF + 255) / 256;
+  if (qb > 152 * 16) qb = 152 * 16;
+  k_full_values<<<(unsigned)qb, 256, 0, st>>>(P, Klow, Kf, nnzF);
+}
+
+void launch_knorm(const DevPlan& P, const double* Kf, unsigned long long* knorm, cudaStream_t st) {
   if (P.dim == 0) return;
   int64_t blocks = (P.dim + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_knorm<<<(unsigned)blocks, 256, 0, st>>>(P, Klow, knorm);
+  const int64_t rpc = (P.dim + blocks - 1) / blocks;
+  k_knorm<<<(unsigned)blocks, 256, 0, st>>>(P, Kf, knorm, rpc);
 }
 
 // ---------------------------------------------------------------------------
@@ -213,8 +232,20 @@ void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, co
 
 // ---------------------------------------------------------------------------
 // SIMT update C -= A diag(d) B^T (lower part), 64 x 64 tiles, 256 threads,
-// 4 x 4 outputs per thread.  FP64 uses DFMA, FP32 FFMA.
+// 4 x 4 outputs per thread: rows 4 ty .. 4 ty + 3 (one 16-byte shared load
+// of A per k) and columns tx + 16 b (four conflict-free loads of B, and
+// coalesced row segments of C).  FP64 uses DFMA, FP32 FFMA.
 // ---------------------------------------------------------------------------
+// four consecutive entries of a 16-byte aligned shared array
+__device__ __forceinline__ void ld4_shared(const float* p, float (&v)[4]) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void ld4_shared(const double* p, double (&v)[4]) {
+  const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
 __device__ __forceinline__ void decode_tile(int64_t t, int Nt, int& ti, int& tj) {
   const int64_t tri = (int64_t)Nt * (Nt + 1) / 2;
   if (t < tri) {
@@ -234,7 +265,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const GemmProb* __restrict__ probs,
                                                    const int32_t* __restrict__ tile_prob) {
   constexpr int TB = GEMM_TILE, KC = 16;
-  __shared__ T As[KC][TB + 1];
+  __shared__ __align__(16) T As[KC][TB + 4];   // rows 16-byte aligned
   __shared__ T Bs[KC][TB + 1];
   const int64_t gt = blockIdx.x;
   const GemmProb pb = probs[tile_prob[gt]];
@@ -278,8 +309,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const
 #pragma unroll
     for (int k2 = 0; k2 < KC; k2++) {
       T av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; a++) av[a] = As[k2][ty + 16 * a];
+      ld4_shared(&As[k2][4 * ty], av);
 #pragma unroll
       for (int b = 0; b < 4; b++) bv[b] = Bs[k2][tx + 16 * b];
 #pragma unroll
@@ -293,7 +323,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const
   T cv[4][4];
 #pragma unroll
   for (int a = 0; a < 4; a++) {
-    const int i = i0 + ty + 16 * a;
+    const int i = i0 + 4 * ty + a;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
       const int j = j0 + tx + 16 * b;
@@ -302,7 +332,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevPlan P, DevNum<T> N, const
   }
 #pragma unroll
   for (int a = 0; a < 4; a++) {
-    const int i = i0 + ty + 16 * a;
+    const int i = i0 + 4 * ty + a;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
       const int j = j0 + tx + 16 * b;
@@ -323,12 +353,13 @@ void launch_gemm_simt(const DevPlan& P, const DevNum<T>& N, const GemmProb* prob
 // counts[4*inst + {0,1,2,3}] = (n_pos, n_neg, n_zero, n_perturbed), plus
 // counts[4*ninst] = number of non-finite pivots.
 // ---------------------------------------------------------------------------
+// (each CTA takes a contiguous run of columns, see k_knorm)
 template <typename T>
-__global__ void k_inertia(DevPlan P, DevNum<T> N, unsigned long long* counts) {
+__global__ void k_inertia(DevPlan P, DevNum<T> N, unsigned long long* counts, int64_t cols_per_cta) {
   int cur = -1;
   unsigned c[4] = {0u, 0u, 0u, 0u}, nonfin = 0u;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P.dim;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t k_begin = blockIdx.x * cols_per_cta, k_end = min(P.dim, k_begin + cols_per_cta);
+  for (int64_t k = k_begin + threadIdx.x; k < k_end; k += blockDim.x) {
     const int inst = P.col_inst[k];
     if (inst != cur) {
       if (cur >= 0)
@@ -360,7 +391,8 @@ void launch_inertia(const DevPlan& P, const DevNum<T>& N, long long* counts, cud
   if (P.dim == 0) return;
   int64_t blocks = (P.dim + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_inertia<T><<<(unsigned)blocks, 256, 0, st>>>(P, N, reinterpret_cast<unsigned long long*>(counts));
+  k_inertia<T><<<(unsigned)blocks, 256, 0, st>>>(P, N, reinterpret_cast<unsigned long long*>(counts),
+                                                 (P.dim + blocks - 1) / blocks);
 }
 
 #define NCL_INST(T)                                                                                     \

@@ -44,9 +44,15 @@ __global__ void __launch_bounds__(256, 1) k_macro_panel(DevPlan P, DevNum<T> N, 
 // it over many CTAs.
 int small_front_smem(int nrow, int ncp, int esz) { return (nrow * (ncp + 1) + 32 * LDS + 64) * esz; }
 
+// 128 threads per CTA: the front's serial steps (the warp that factors a
+// sub-block) leave fewer warps idle, and twice as many fronts share an SM
+// as with 256 (registers and shared memory allow six to seven)
+constexpr int SMALL_THREADS = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, const int32_t* __restrict__ list,
-                                                      double eps, int policy) {
+__global__ void __launch_bounds__(SMALL_THREADS) k_factor_small(DevPlan P, DevNum<T> N,
+                                                                const int32_t* __restrict__ list, double eps,
+                                                                int policy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = list[blockIdx.x];
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s], col0 = P.sn_col0[s];
@@ -91,7 +97,7 @@ __global__ void __launch_bounds__(256) k_factor_small(DevPlan P, DevNum<T> N, co
     if (c0 + 32 < ncol) {
       const int c = c0 + 32 + lane;
       const bool cok = c < ncol;
-      for (int r0 = c0 + 32 + warp * RW; r0 < nrow; r0 += 8 * RW) {
+      for (int r0 = c0 + 32 + warp * RW; r0 < nrow; r0 += (SMALL_THREADS / 32) * RW) {
         T acc[RW];
 #pragma unroll
         for (int m = 0; m < RW; m++) acc[m] = T(0);
@@ -120,7 +126,7 @@ void launch_factor_small(const DevPlan& P, const DevNum<T>& N, const int32_t* li
     cudaFuncSetAttribute(k_factor_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SMEM_MAX);
     attr = true;
   }
-  k_factor_small<T><<<count, 256, smem_bytes, st>>>(P, N, list, eps, policy);
+  k_factor_small<T><<<count, SMALL_THREADS, smem_bytes, st>>>(P, N, list, eps, policy);
 }
 
 // ---------------------------------------------------------------------------

@@ -166,7 +166,9 @@ void launch_newton_recover(const DevPlan& P, const double* Jv, const double* rho
 void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, const double* ss, int nrhs,
                        const double* DT, int64_t ldt, const double* RS, int64_t ldr, double* DS, int64_t lds,
                        cudaStream_t st);
-void launch_knorm(const DevPlan& P, const double* Klow, unsigned long long* knorm, cudaStream_t st);
+// Kf: the values of the full pattern (nnzF entries) in its row order
+void launch_full_values(const DevPlan& P, const double* Klow, double* Kf, int64_t nnzF, cudaStream_t st);
+void launch_knorm(const DevPlan& P, const double* Kf, unsigned long long* knorm, cudaStream_t st);
 template <typename T>
 void launch_assemble(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
                      int count, cudaStream_t st);
@@ -218,7 +220,7 @@ void launch_region_fwd(const DevPlan& P, const DevNum<T>& N, const int2* items, 
 template <typename T>
 void launch_region_bwd(const DevPlan& P, const DevNum<T>& N, const int2* items, int count, const int32_t* nodes, T* xp,
                        int nrhs, int* counter, int nsm, cudaStream_t st);
-void launch_residual(const DevPlan& P, const double* Klow, const double* B, int64_t ldb, const double* X,
+void launch_residual(const DevPlan& P, const double* Kf, const double* B, int64_t ldb, const double* X,
                      int64_t ldx, double* R, int64_t ldr, int nrhs, unsigned long long* rnorm,
                      unsigned long long* xnorm, cudaStream_t st);
 void launch_vec_norm(const DevPlan& P, const double* B, int64_t ldb, int nrhs, unsigned long long* out,

@@ -817,75 +817,124 @@ void launch_region_bwd(const DevPlan& P, const DevNum<T>& N, const int2* items, 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 residual R = B - K X on the FP64 KKT values (8 lanes per row), with
-// per-instance ||R||_inf and ||X||_inf (bit patterns, atomicMax).
+// FP64 residual R = B - K X on the FP64 KKT values (4 lanes per row, 8 rows
+// per warp trip), with per-instance ||R||_inf and ||X||_inf (bit patterns,
+// atomicMax).  Kf holds the values of the full pattern in its row order
+// (written before ||K||), so the entries and column indices are read
+// contiguously and only X is gathered; an entry is read once for all NR
+// right-hand sides, and every load of a trip that does not depend on
+// another (row bounds, B, the row's own X) is issued before the products.
+// Each warp takes a contiguous run of rows, so that its running maxima
+// change instance (and go to the atomics) only at an instance boundary.
 // ---------------------------------------------------------------------------
-__global__ void k_residual(DevPlan P, const double* __restrict__ Klow, const double* __restrict__ B, int64_t ldb,
-                           const double* __restrict__ X, int64_t ldx, double* __restrict__ R, int64_t ldr, int nrhs,
-                           unsigned long long* rnorm, unsigned long long* xnorm) {
-  const int lane = threadIdx.x & 31, sub = lane & 7;
+template <int NR>
+__global__ void __launch_bounds__(256) k_residual(DevPlan P, const double* __restrict__ Kf,
+                                                  const double* __restrict__ B, int64_t ldb,
+                                                  const double* __restrict__ X, int64_t ldx, double* __restrict__ R,
+                                                  int64_t ldr, int nrhs, unsigned long long* rnorm,
+                                                  unsigned long long* xnorm, int64_t rows_per_warp) {
+  constexpr int LPR = 4;   // lanes per row
+  const int lane = threadIdx.x & 31, sub = lane & (LPR - 1);
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t r_begin = gwarp * rows_per_warp;
+  const int64_t r_end = min(P.dim, r_begin + rows_per_warp);
   // running maxima of |r| and |x| for the instance of this lane's rows
   int cur = -1;
-  unsigned long long rmx[MAX_RHS_SWEEP], xmx[MAX_RHS_SWEEP];
+  unsigned long long rmx[NR], xmx[NR];
 #pragma unroll
-  for (int r = 0; r < MAX_RHS_SWEEP; r++) rmx[r] = xmx[r] = 0ull;
-  // each warp takes 4 rows per trip (8 lanes per row); the trip count is
-  // uniform across the warp so that the full-mask shuffles are safe
-  for (int64_t rb = gwarp * 4; rb < P.dim; rb += nwarp * 4) {
-    const int64_t row = rb + (lane >> 3);
-    const bool valid = row < P.dim;
+  for (int r = 0; r < NR; r++) rmx[r] = xmx[r] = 0ull;
+  // the trip count is uniform across the warp so that the full-mask
+  // shuffles are safe
+  for (int64_t rb = r_begin; rb < r_end; rb += 32 / LPR) {
+    const int64_t row = rb + lane / LPR;
+    const bool valid = row < r_end;
     const int64_t q0 = valid ? P.F_rowptr[row] : 0, q1 = valid ? P.F_rowptr[row + 1] : 0;
     const int inst = valid ? P.row_inst[row] : -1;
+    double bv[NR], xv[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      const bool use = valid && sub == 0 && r < nrhs;
+      bv[r] = use ? B[r * ldb + row] : 0.0;
+      xv[r] = use ? X[r * ldx + row] : 0.0;
+    }
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) acc[r] = 0.0;
+    int64_t q = q0 + sub;
+    for (; q + LPR < q1; q += 2 * LPR) {
+      const double k0 = Kf[q], k1 = Kf[q + LPR];
+      const int64_t c0 = P.F_col[q], c1 = P.F_col[q + LPR];
+#pragma unroll
+      for (int r = 0; r < NR; r++)
+        if (r < nrhs) acc[r] = fma(k1, X[r * ldx + c1], fma(k0, X[r * ldx + c0], acc[r]));
+    }
+    if (q < q1) {
+      const double k0 = Kf[q];
+      const int64_t c0 = P.F_col[q];
+#pragma unroll
+      for (int r = 0; r < NR; r++)
+        if (r < nrhs) acc[r] = fma(k0, X[r * ldx + c0], acc[r]);
+    }
     if (valid && sub == 0 && inst != cur) {
       if (cur >= 0)
 #pragma unroll
-        for (int r = 0; r < MAX_RHS_SWEEP; r++)
+        for (int r = 0; r < NR; r++)
           if (r < nrhs) {
             atomicMax(&rnorm[cur * nrhs + r], rmx[r]);
             atomicMax(&xnorm[cur * nrhs + r], xmx[r]);
           }
 #pragma unroll
-      for (int r = 0; r < MAX_RHS_SWEEP; r++) rmx[r] = xmx[r] = 0ull;
+      for (int r = 0; r < NR; r++) rmx[r] = xmx[r] = 0ull;
       cur = inst;
     }
 #pragma unroll
-    for (int r = 0; r < MAX_RHS_SWEEP; r++) {
+    for (int r = 0; r < NR; r++) {
       if (r >= nrhs) break;
-      const double* x = X + r * ldx;
-      double acc = 0.0;
-      for (int64_t q = q0 + sub; q < q1; q += 8) acc = fma(Klow[P.F_src[q]], x[P.F_col[q]], acc);
-      acc += __shfl_xor_sync(FULL_MASK, acc, 4);
-      acc += __shfl_xor_sync(FULL_MASK, acc, 2);
-      acc += __shfl_xor_sync(FULL_MASK, acc, 1);
+      double a = acc[r];
+      a += __shfl_xor_sync(FULL_MASK, a, 2);
+      a += __shfl_xor_sync(FULL_MASK, a, 1);
       if (valid && sub == 0) {
-        const double res = B[r * ldb + row] - acc;
+        const double res = bv[r] - a;
         R[r * ldr + row] = res;
-        const unsigned long long a = dbits(fabs(res)), b = dbits(fabs(x[row]));
-        rmx[r] = a > rmx[r] ? a : rmx[r];
-        xmx[r] = b > xmx[r] ? b : xmx[r];
+        const unsigned long long u = dbits(fabs(res)), v = dbits(fabs(xv[r]));
+        rmx[r] = u > rmx[r] ? u : rmx[r];
+        xmx[r] = v > xmx[r] ? v : xmx[r];
       }
     }
   }
-  for (int r = 0; r < nrhs; r++) {
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    if (r >= nrhs) break;
     warp_flush_max(rnorm + r, cur < 0 ? -1 : cur * nrhs, rmx[r]);
     warp_flush_max(xnorm + r, cur < 0 ? -1 : cur * nrhs, xmx[r]);
   }
 }
 
-void launch_residual(const DevPlan& P, const double* Klow, const double* B, int64_t ldb, const double* X,
+void launch_residual(const DevPlan& P, const double* Kf, const double* B, int64_t ldb, const double* X,
                      int64_t ldx, double* R, int64_t ldr, int nrhs, unsigned long long* rnorm,
                      unsigned long long* xnorm, cudaStream_t st) {
   if (P.dim == 0) return;
-  k_residual<<<grid_for(P.dim * 8), 256, 0, st>>>(P, Klow, B, ldb, X, ldx, R, ldr, nrhs, rnorm, xnorm);
+  const unsigned grid = grid_for(P.dim * 8);
+  const int64_t nwarp = (int64_t)grid * 8;
+  const int64_t rpw = ((P.dim + nwarp - 1) / nwarp + 7) / 8 * 8;
+  if (nrhs <= 1)
+    k_residual<1><<<grid, 256, 0, st>>>(P, Kf, B, ldb, X, ldx, R, ldr, nrhs, rnorm, xnorm, rpw);
+  else if (nrhs <= 2)
+    k_residual<2><<<grid, 256, 0, st>>>(P, Kf, B, ldb, X, ldx, R, ldr, nrhs, rnorm, xnorm, rpw);
+  else if (nrhs <= 4)
+    k_residual<4><<<grid, 256, 0, st>>>(P, Kf, B, ldb, X, ldx, R, ldr, nrhs, rnorm, xnorm, rpw);
+  else
+    k_residual<MAX_RHS_SWEEP><<<grid, 256, 0, st>>>(P, Kf, B, ldb, X, ldx, R, ldr, nrhs, rnorm, xnorm, rpw);
 }
 
-__global__ void k_vec_norm(DevPlan P, const double* __restrict__ B, int64_t ldb, int nrhs, unsigned long long* out) {
+// per-instance ||B||_inf; each CTA takes a contiguous run of rows (see k_knorm)
+__global__ void k_vec_norm(DevPlan P, const double* __restrict__ B, int64_t ldb, int nrhs, unsigned long long* out,
+                           int64_t rows_per_cta) {
+  const int64_t i_begin = blockIdx.x * rows_per_cta, i_end = min(P.dim, i_begin + rows_per_cta);
   for (int r = 0; r < nrhs; r++) {
     int cur = -1;
     unsigned long long mx = 0ull;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.dim; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = i_begin + threadIdx.x; i < i_end; i += blockDim.x) {
       const int inst = P.row_inst[i];
       const unsigned long long v = dbits(fabs(B[r * ldb + i]));
       if (inst != cur) {
@@ -901,7 +950,9 @@ __global__ void k_vec_norm(DevPlan P, const double* __restrict__ B, int64_t ldb,
 
 void launch_vec_norm(const DevPlan& P, const double* B, int64_t ldb, int nrhs, unsigned long long* out,
                      cudaStream_t st) {
-  if (P.dim) k_vec_norm<<<grid_for(P.dim), 256, 0, st>>>(P, B, ldb, nrhs, out);
+  if (P.dim == 0) return;
+  const unsigned grid = grid_for(P.dim);
+  k_vec_norm<<<grid, 256, 0, st>>>(P, B, ldb, nrhs, out, (P.dim + grid - 1) / grid);
 }
 
 __global__ void k_axpy(double* X, int64_t ldx, const double* Y, int64_t ldy, double a, int64_t dim, int nrhs) {
