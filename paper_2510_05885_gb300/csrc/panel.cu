@@ -217,19 +217,45 @@ __device__ __forceinline__ void subtree_front(const DevPlan& P, const DevNum<T>&
     if (c < ncol) F[(ncol + r) * ldf + c] *= pivot_rcp(dsh[c]);
   }
   __syncthreads();
-  // write the factor block back, and form the update block from it
+  // write the factor block back, and form the update block from it:
+  // 4 x 4 register tiles of its lower triangle spread over all threads
+  // (9 shared loads per 16 products), F22[a][b] -= sum_k (L[a][k] d_k) L[b][k]
   for (int idx = tid; idx < nrow * ncp; idx += blockDim.x) Lg[idx] = F[(idx / ncp) * ldf + idx % ncp];
-  const int ut = nb * (nb + 1) / 2;
-  for (int e = tid; e < ut; e += blockDim.x) {
-    int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    while (a * (a + 1) / 2 > e) a--;
-    while ((a + 1) * (a + 2) / 2 <= e) a++;
-    const int b = e - a * (a + 1) / 2;
-    const T* la = F + (ncol + a) * ldf;
-    const T* lb = F + (ncol + b) * ldf;
-    T acc = T(0);
-    for (int k = 0; k < ncol; k++) acc += la[k] * dsh[k] * lb[k];
-    Ub[(int64_t)a * nb + b] -= acc;
+  const int T4 = (nb + 3) / 4;
+  const int ntl = T4 * (T4 + 1) / 2;
+  for (int e = tid; e < ntl; e += blockDim.x) {
+    int ti = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (ti * (ti + 1) / 2 > e) ti--;
+    while ((ti + 1) * (ti + 2) / 2 <= e) ti++;
+    const int tj = e - ti * (ti + 1) / 2;
+    const int a0 = 4 * ti, b0 = 4 * tj;
+    const T* fa = F + (ncol + a0) * ldf;
+    const T* fb = F + (ncol + b0) * ldf;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) acc[i][j] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < ncol; k++) {
+      const T dk = dsh[k];
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) av[i] = a0 + i < nb ? fa[i * ldf + k] * dk : T(0);
+#pragma unroll
+      for (int j = 0; j < 4; j++) bv[j] = b0 + j < nb ? fb[j * ldf + k] : T(0);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] += av[i] * bv[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int a = a0 + i, b = b0 + j;
+        if (a < nb && b <= a) Ub[(int64_t)a * nb + b] -= acc[i][j];
+      }
   }
 }
 
