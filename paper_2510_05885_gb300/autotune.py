@@ -156,7 +156,9 @@ def tune_class(name, dev="cuda:0", grid=None, log=print):
     if not results:
         raise RuntimeError(f"no candidate setting of {name} met the target")
     ms, best = min(results, key=lambda t: t[0])
-    default = next((m for m, s in results if s == dict(persistent_fronts=1, subtree_sweeps=1, tc_min_pivots=256)), None)
+    d = nk.default_options()
+    dflt = dict(persistent_fronts=d.persistent_fronts, subtree_sweeps=d.subtree_sweeps, tc_min_pivots=d.tc_min_pivots)
+    default = next((m for m, s in results if s == dflt), None)
     line = (f"{form} {dlo} {dhi} {clo} {chi} {best['persistent_fronts']} {best['subtree_sweeps']} 2 "
             f"{best['tc_min_pivots']}  # {name}: dim {dim}, {ms:.3f} ms"
             + (f" (defaults {default:.3f} ms)" if default is not None else ""))
