@@ -82,8 +82,13 @@ def parse(argv=None):
                     help="1: one persistent launch per level for the large fronts; 0: one launch per panel step "
                          "(default: the library's, or the tuned table's)")
     ap.add_argument("--tuned", default=TUNED if os.path.exists(TUNED) else None,
-                    help="table of tuned cut-overs applied at analysis (default: the committed GB300 table)")
-    return ap.parse_args(argv)
+                    help="table of tuned cut-overs applied at analysis (default: the committed GB300 table; "
+                         "'none': the library's defaults; an explicit --persistent-fronts or --subtree-sweeps "
+                         "also turns it off, since the table would override it)")
+    args = ap.parse_args(argv)
+    if args.tuned in ("", "none") or args.persistent_fronts is not None or args.subtree_sweeps is not None:
+        args.tuned = None
+    return args
 
 
 # ---------------------------------------------------------------------------
