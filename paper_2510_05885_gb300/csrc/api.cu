@@ -368,6 +368,22 @@ void build_schedule(ncl_kkt_s* h) {
       for (auto it = pre.rbegin(); it != pre.rend(); ++it) hs.regnodes.push_back(*it);
       hs.regitems.push_back(make_int2(first, (int32_t)pre.size()));
     }
+    // largest subtrees first: the kernels hand subtrees out in item order
+    // (a work counter), so the longest ones start early and the tail is short
+    {
+      std::vector<double> wgt(hs.regitems.size(), 0.0);
+      for (size_t i = 0; i < hs.regitems.size(); i++)
+        for (int q = 0; q < hs.regitems[i].y; q++) {
+          const int32_t v = hs.regnodes[hs.regitems[i].x + q];
+          wgt[i] += (double)P.sn_nrow[v] * (P.sn_ncol[v] + 1);
+        }
+      std::vector<size_t> ord(hs.regitems.size());
+      for (size_t i = 0; i < ord.size(); i++) ord[i] = i;
+      std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return wgt[a] > wgt[b]; });
+      std::vector<int2> sorted(ord.size());
+      for (size_t i = 0; i < ord.size(); i++) sorted[i] = hs.regitems[ord[i]];
+      hs.regitems.swap(sorted);
+    }
     for (int32_t s : hs.regnodes) {
       hs.reg_smem = std::max<int64_t>(hs.reg_smem, (small_front_smem(P.sn_nrow[s], P.sn_ncolp[s], (int)esz) + 15) / 16 * 16);
       {

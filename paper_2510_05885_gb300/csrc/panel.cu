@@ -288,7 +288,11 @@ void launch_subtree_factor(const DevPlan& P, const DevNum<T>& N, const int2* ite
     cudaFuncSetAttribute(k_subtree_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMALL_SMEM_MAX);
     attr = true;
   }
-  const int grid = std::min(count, nsm * 4);
+  // as many CTAs as fit on the device at once (they take subtrees from a counter)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_subtree_factor<T>, 256, smem) != cudaSuccess)
+    per_sm = 4;
+  const int grid = std::min(count, nsm * std::max(per_sm, 1));
   k_subtree_factor<T><<<grid, 256, smem, st>>>(P, N, items, count, nodes, counter, eps, policy);
 }
 

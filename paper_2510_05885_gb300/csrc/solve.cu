@@ -798,7 +798,11 @@ void launch_region_fwd(const DevPlan& P, const DevNum<T>& N, const int2* items, 
     cudaFuncSetAttribute(k_region_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  const int grid = std::min((count + REG_WARPS - 1) / REG_WARPS, nsm * 4);
+  // as many CTAs as fit on the device at once (the warps take subtrees from a counter)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_region_fwd<T>, 32 * REG_WARPS, smem) != cudaSuccess)
+    per_sm = 4;
+  const int grid = std::min((count + REG_WARPS - 1) / REG_WARPS, nsm * std::max(per_sm, 1));
   k_region_fwd<T><<<grid, 32 * REG_WARPS, smem, st>>>(P, N, items, count, nodes, xp, W, nrhs, counter);
 }
 
@@ -812,7 +816,10 @@ void launch_region_bwd(const DevPlan& P, const DevNum<T>& N, const int2* items, 
     cudaFuncSetAttribute(k_region_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  const int grid = std::min((count + REG_WARPS - 1) / REG_WARPS, nsm * 4);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_region_bwd<T>, 32 * REG_WARPS, smem) != cudaSuccess)
+    per_sm = 4;
+  const int grid = std::min((count + REG_WARPS - 1) / REG_WARPS, nsm * std::max(per_sm, 1));
   k_region_bwd<T><<<grid, 32 * REG_WARPS, smem, st>>>(P, N, items, count, nodes, xp, nrhs, counter);
 }
 
