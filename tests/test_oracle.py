@@ -637,3 +637,37 @@ def test_cond1_estimate_against_the_exact_condition_number():
     D = sp.diags(d, format="csc")
     est = O.cond1_estimate(D, O.LDLT(D, np.where(d > 0, 1, -1).astype(np.int32)))
     assert est == pytest.approx(np.max(np.abs(d)) / np.min(np.abs(d)), rel=1e-12)
+
+
+def _true_min_power(Hs_at):
+    """Smallest delta in {0} U {10^k} with H + Sigma + delta I positive definite,
+    from the eigenvalues (Hs_at(delta) gives the dense matrix)."""
+    lam = np.linalg.eigvalsh(Hs_at(0.0)).min()
+    if lam > 0:
+        return 0.0
+    k = int(np.floor(np.log10(-lam)))
+    while np.linalg.eigvalsh(Hs_at(10.0 ** k)).min() <= 0:
+        k += 1
+    return 10.0 ** k
+
+
+def test_certified_delta_against_true_smallest_power():
+    """The generator's delta (a sufficient certificate, no factorisation)
+    against the true smallest power of ten from the eigenvalues, on 40 small
+    grids: never below it, at most one power above it.  The count of
+    instances where it is one power above is printed (-s)."""
+    rng = np.random.default_rng(11)
+    above = 0
+    for t in range(40):
+        R, C = int(rng.integers(5, 11)), int(rng.integers(5, 11))
+        inst = synth.random_instance(R, C, seed=1000 + t, form="condensed", rho=1.0)
+        p = inst.pat
+
+        def Hs_at(d):
+            return O.kkt_condensed(p.n, 0, p.H_rowptr, p.H_colind, inst.H_val, np.zeros(1, np.int32),
+                                   np.zeros(0, np.int32), np.zeros(0), inst.Sigma, d, 1.0).toarray()
+        true = _true_min_power(Hs_at)
+        assert inst.delta >= true
+        assert true == 0.0 or inst.delta <= 10.0 * true
+        above += inst.delta > true
+    print(f"certified delta above the true smallest power of ten in {above} of 40 instances")
