@@ -98,6 +98,7 @@ struct Level {
   int below_cnt = 0;
   int64_t bbelow_off = 0; // (s, a0, k0) backward solve items
   int bbelow_cnt = 0;
+  int bbelow_narrow = 0;  //   the first ones: supernodes of at most 32 columns (one warp each)
   int64_t dag_off = 0;    // tasks of the persistent large-front launch
   int dag_cnt = 0;
   Cost asm_cost, small_cost, syrk_cost, fdiag_cost, fbelow_cost, bdiag_cost, bbelow_cost, dag_cost;
@@ -552,6 +553,13 @@ void build_schedule(ncl_kkt_s* h) {
     L.chain_cnt = (int)(hs.chainv.size() - L.chain_off);
     L.below_cnt = (int)(belowv.size() - L.below_off);
     L.bbelow_cnt = (int)(hs.bbelowv.size() - L.bbelow_off);
+    {
+      // the items of supernodes with at most 32 columns first (a warp each),
+      // then the others (a CTA each), each group in supernode order
+      auto b0 = hs.bbelowv.begin() + L.bbelow_off;
+      auto mid = std::stable_partition(b0, hs.bbelowv.end(), [&](const int4& it) { return P.sn_ncol[it.x] <= 32; });
+      L.bbelow_narrow = (int)(mid - b0);
+    }
     if (hs.tc) {
       int64_t off = 0;
       for (int32_t s : large) {
@@ -832,6 +840,9 @@ void build_schedule(ncl_kkt_s* h) {
       if (it.x < 0 || it.x >= P.ns || it.y < 0 || it.y >= P.sn_nrow[it.x] - P.sn_ncol[it.x] || it.y % SOLVE_ROWS ||
           it.z < 0 || it.z >= P.sn_ncol[it.x] || it.z % 256)
         bad("solve item");
+    for (const Level& L : h->levels)
+      for (int i = 0; i < L.bbelow_cnt; i++)
+        if ((i < L.bbelow_narrow) != (P.sn_ncol[hs.bbelowv[L.bbelow_off + i].x] <= 32)) bad("narrow solve items");
     if (hs.below_cptr.size() != belowv.size() + 1) bad("solve child ranges");
     for (size_t i = 0; i < belowv.size(); i++) {
       const int2 it = belowv[i];
@@ -1344,7 +1355,9 @@ void run_sweeps(ncl_kkt_s* h, DevNum<T>& N, int nrhs, cudaStream_t st) {
   for (int l = (int)h->levels.size() - 1; l >= 0; l--) {
     const Level& L = h->levels[l];
     klaunch(h, st, f32 ? "bwd_below_f32" : "bwd_below_f64", L.bbelow_cnt, scaled(L.bbelow_cost, nrhs),
-            [&] { launch_bwd_below<T>(P, N, h->d_bbelow + L.bbelow_off, L.bbelow_cnt, xp, Pw, nrhs, st); });
+            [&] {
+              launch_bwd_below<T>(P, N, h->d_bbelow + L.bbelow_off, L.bbelow_cnt, L.bbelow_narrow, xp, Pw, nrhs, st);
+            });
     const char* bname = L.chain_multi ? (f32 ? "bwd_chain_multi_f32" : "bwd_chain_multi_f64")
                                       : (f32 ? "bwd_chain_f32" : "bwd_chain_f64");
     klaunch(h, st, bname, L.chain_cnt, scaled(L.bdiag_cost, nrhs), [&] {

@@ -208,7 +208,7 @@ template <typename T>
 void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, const int32_t* cptr, const int4* cran,
                       int count, T* xp, T* W, int nrhs, cudaStream_t st);
 template <typename T>
-void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, const T* xp,
+void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int narrow, const T* xp,
                       T* Pw, int nrhs, cudaStream_t st);
 template <typename T>
 void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi, T* xp,

@@ -517,16 +517,49 @@ __global__ void __launch_bounds__(256) k_fwd_below(DevPlan P, DevNum<T> N, const
 }
 
 // backward: partial sums of L21^T x_below over a run of SOLVE_ROWS rows and
-// a run of up to 256 columns (item (s, a0, k0)); for 33..128 columns,
-// G = 256 / (columns rounded up to 32) groups of threads split the rows and
-// their sums are added in shared memory (a single group for the narrowest
-// supernodes, whose CTAs are many and short)
+// a run of up to 256 columns (item (s, a0, k0)).  The level's first `narrow`
+// items (supernodes of at most 32 columns) take one warp each, eight to a
+// CTA (lane = column, the rows in order); the others one CTA each, where
+// for 33..128 columns G = 256 / (columns rounded up to 32) groups of threads
+// split the rows and their sums are added in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_below(DevPlan P, DevNum<T> N, const int4* __restrict__ items,
-                                                   const T* __restrict__ xp, T* __restrict__ Pw, int nrhs) {
+                                                   int narrow, const T* __restrict__ xp, T* __restrict__ Pw,
+                                                   int nrhs) {
   __shared__ T xb[SOLVE_ROWS * MAX_RHS_SWEEP];
   __shared__ T red[256];
-  const int4 it = items[blockIdx.x];
+  const int nnc = (narrow + 7) / 8;   // CTAs of the narrow items
+  if ((int)blockIdx.x < nnc) {
+    __shared__ T xw[8][SOLVE_ROWS * MAX_RHS_SWEEP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + w;
+    if (i >= narrow) return;   // the whole warp; no CTA barrier in this branch
+    const int4 it = items[i];
+    const int s = it.x, a0 = it.y;
+    const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
+    const int nb = nrow - ncol;
+    const int a1 = min(a0 + SOLVE_ROWS, nb), na = a1 - a0;
+    const int chunk = a0 / SOLVE_ROWS;
+    const int32_t* rows = P.sn_rows + P.sn_rows_off[s] + ncol;
+    T* x = xw[w];
+    for (int idx = lane; idx < na * nrhs; idx += 32) {
+      const int r = idx / na, a = idx - r * na;
+      x[r * SOLVE_ROWS + a] = xp[r * P.dim + rows[a0 + a]];
+    }
+    __syncwarp();
+    const T* col = N.L + P.sn_Loff[s] + (int64_t)ncol * ncp + min(lane, ncol - 1);
+    for (int r = 0; r < nrhs; r++) {
+      const T* xr = x + r * SOLVE_ROWS - a0;
+      T acc = T(0);
+      if (lane < ncol) {
+#pragma unroll 16
+        for (int a = a0; a < a1; a++) acc += col[(int64_t)a * ncp] * xr[a];
+        Pw[r * P.Ptot + P.sn_Poff[s] + (int64_t)chunk * ncol + lane] = acc;
+      }
+    }
+    return;
+  }
+  const int4 it = items[narrow + (blockIdx.x - nnc)];
   const int s = it.x, a0 = it.y, k0 = it.z;
   const int ncol = P.sn_ncol[s], nrow = P.sn_nrow[s], ncp = P.sn_ncolp[s];
   const int nb = nrow - ncol;
@@ -594,9 +627,11 @@ void launch_fwd_below(const DevPlan& P, const DevNum<T>& N, const int2* items, c
   if (count > 0) k_fwd_below<T><<<count, 256, 0, st>>>(P, N, items, cptr, cran, xp, W, nrhs);
 }
 template <typename T>
-void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, const T* xp, T* Pw,
-                      int nrhs, cudaStream_t st) {
-  if (count > 0) k_bwd_below<T><<<count, 256, 0, st>>>(P, N, items, xp, Pw, nrhs);
+void launch_bwd_below(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int narrow, const T* xp,
+                      T* Pw, int nrhs, cudaStream_t st) {
+  if (count <= 0) return;
+  const int grid = (narrow + 7) / 8 + (count - narrow);
+  k_bwd_below<T><<<grid, 256, 0, st>>>(P, N, items, narrow, xp, Pw, nrhs);
 }
 template <typename T>
 void launch_bwd_chain(const DevPlan& P, const DevNum<T>& N, const int4* items, int count, int smem, bool multi, T* xp,
@@ -1320,7 +1355,7 @@ void launch_slack_step(const DevPlan& P, const double* Jv, const double* rho, co
                                     long long, cudaStream_t);                                                     \
   template void launch_fwd_below<T>(const DevPlan&, const DevNum<T>&, const int2*, const int32_t*, const int4*,  \
                                     int, T*, T*, int, cudaStream_t);                                              \
-  template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int4*, int, const T*, T*, int,        \
+  template void launch_bwd_below<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, const T*, T*, int,   \
                                     cudaStream_t);                                                                \
   template void launch_bwd_chain<T>(const DevPlan&, const DevNum<T>&, const int4*, int, int, bool, T*, const T*, \
                                     int, int*, int*, int*, long long, cudaStream_t);                            \
