@@ -84,7 +84,8 @@ CLASSES = {
     "condensed-300": (1, 100_000, 1_000_000, 1, 1, _single(1, 300, 1e5)),
     "condensed-small": (1, 0, 100_000, 1, 1, _single(1, 96, 1e5)),
     "stabilized-700": (0, 1_000_000, 1 << 40, 1, 1, _single(0, 700, 1e6)),
-    "stabilized-small": (0, 0, 1_000_000, 1, 1, _single(0, 150, 1e4)),
+    "stabilized-tiny": (0, 0, 20_000, 1, 1, _single(0, 22, 1e4)),
+    "stabilized-small": (0, 20_000, 1_000_000, 1, 1, _single(0, 150, 1e4)),
     "batch-64x100": (0, 0, 1 << 40, 2, 128, _batch(64, 100, 4)),
     "batch-256-mixed": (0, 0, 1 << 40, 129, 1 << 20, _mixed(256, 10, 70)),
 }
