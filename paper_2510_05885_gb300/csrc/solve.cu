@@ -197,10 +197,18 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
   if (MULTI && mine && B > 0) {
     const T* wrow = Lb + (int64_t)(R0 + 32 * warp) * ncp + lane;
     const int nrw = min(32, nr - 32 * warp);
-    T lv[32], ln[32];
+    // FP32: two chunks in flight ahead of the one in use, so that after the
+    // wait for a block-row its first two chunks are already in registers
+    // (FP64: one, for registers)
+    constexpr bool PF2 = sizeof(T) == 4;
+    T lv[32], ln[32], ln2[32];
+    const int nchunk = 4 * B;
 #pragma unroll
     for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp] : T(0);
-    const int nchunk = 4 * B;
+    if (PF2) {
+#pragma unroll
+      for (int rr = 0; rr < 32; rr++) ln2[rr] = rr < nrw ? wrow[(int64_t)rr * ncp + 32] : T(0);
+    }
     // the right-hand sides of the four chunks of a block-row, loaded
     // together once it is published and rotated chunk by chunk (FP64: the
     // first right-hand side only, for registers)
@@ -208,11 +216,23 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan P, DevNum<T> N, const
     T yq[4][YQ];
     for (int q = 0; q < nchunk; q++) {
       const int c0 = 32 * q;
+      if (PF2) {
 #pragma unroll
-      for (int rr = 0; rr < 32; rr++) lv[rr] = ln[rr];
-      if (q + 1 < nchunk) {
+        for (int rr = 0; rr < 32; rr++) {
+          lv[rr] = ln[rr];
+          ln[rr] = ln2[rr];
+        }
+        if (q + 2 < nchunk) {
 #pragma unroll
-        for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp + c0 + 32] : T(0);
+          for (int rr = 0; rr < 32; rr++) ln2[rr] = rr < nrw ? wrow[(int64_t)rr * ncp + c0 + 64] : T(0);
+        }
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < 32; rr++) lv[rr] = ln[rr];
+        if (q + 1 < nchunk) {
+#pragma unroll
+          for (int rr = 0; rr < 32; rr++) ln[rr] = rr < nrw ? wrow[(int64_t)rr * ncp + c0 + 32] : T(0);
+        }
       }
       if ((q & 3) == 0) {
         chain_wait(flags + broff + (q >> 2), err, wait);
