@@ -359,11 +359,18 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
       q0 = CHAIN_ROWS * I + 32 * (q & 3);
       bwi = max(0, min(32, ncol - q0));
     };
-    T lv[32], ln[32];
-    int nq0, nbw;
+    // FP32: two chunks in flight ahead of the one in use (FP64: one, for registers)
+    constexpr bool PF2 = sizeof(T) == 4;
+    T lv[32], ln[32], ln2[32];
+    int nq0, nbw, nq2 = 0, nbw2 = 0;
     rows_of(0, nq0, nbw);
 #pragma unroll
     for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
+    if (PF2 && nchunk > 1) {
+      rows_of(1, nq2, nbw2);
+#pragma unroll
+      for (int v = 0; v < 32; v++) ln2[v] = v < nbw2 ? lcol[(int64_t)(nq2 + v) * ncp] : T(0);
+    }
     // the values of the four chunks of a block-row, loaded together once it
     // is published and rotated chunk by chunk (FP64: the first right-hand
     // side only, for registers)
@@ -371,12 +378,27 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan P, DevNum<T> N, const
     T xq[4][XQ];
     for (int q = 0; q < nchunk; q++) {
       const int q0 = nq0, bwi = nbw;
+      if (PF2) {
 #pragma unroll
-      for (int v = 0; v < 32; v++) lv[v] = ln[v];
-      if (q + 1 < nchunk) {
-        rows_of(q + 1, nq0, nbw);
+        for (int v = 0; v < 32; v++) {
+          lv[v] = ln[v];
+          ln[v] = ln2[v];
+        }
+        nq0 = nq2;
+        nbw = nbw2;
+        if (q + 2 < nchunk) {
+          rows_of(q + 2, nq2, nbw2);
 #pragma unroll
-        for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
+          for (int v = 0; v < 32; v++) ln2[v] = v < nbw2 ? lcol[(int64_t)(nq2 + v) * ncp] : T(0);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < 32; v++) lv[v] = ln[v];
+        if (q + 1 < nchunk) {
+          rows_of(q + 1, nq0, nbw);
+#pragma unroll
+          for (int v = 0; v < 32; v++) ln[v] = v < nbw ? lcol[(int64_t)(nq0 + v) * ncp] : T(0);
+        }
       }
       if ((q & 3) == 0) {
         chain_wait(flags + broff + nbr - 1 - (q >> 2), err, wait);
