@@ -44,10 +44,9 @@ __global__ void __launch_bounds__(256, 1) k_macro_panel(DevPlan P, DevNum<T> N, 
 // it over many CTAs.
 int small_front_smem(int nrow, int ncp, int esz) { return (nrow * (ncp + 1) + 32 * LDS + 64) * esz; }
 
-// 128 threads per CTA: the front's serial steps (the warp that factors a
-// sub-block) leave fewer warps idle, and twice as many fronts share an SM
-// as with 256 (registers and shared memory allow six to seven)
-constexpr int SMALL_THREADS = 128;
+// 256 threads per CTA (128 was measured slower on the 20 x 25, 300 x 300 and
+// 700 x 700 systems: the rows below the sub-block take twice the passes)
+constexpr int SMALL_THREADS = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(SMALL_THREADS) k_factor_small(DevPlan P, DevNum<T> N,
