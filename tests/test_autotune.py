@@ -92,3 +92,43 @@ def test_precision_fallback_modes_accepted(mode):
     K = _handle(1, 6, precision_fallback=mode)
     assert nk.ncl_kkt_get_options(K._h).precision_fallback == mode
     K.close()
+
+
+def _table_lines(path):
+    out = []
+    for ln in open(path):
+        body = ln.split("#", 1)[0].split()
+        if body:
+            out.append([int(v) for v in body])
+    return out
+
+
+def test_committed_table_classes_are_disjoint():
+    """No two lines of the committed table can match the same analysis, so
+    the first-match rule never hides a line."""
+    from paper_2510_05885_gb300 import autotune
+    path = os.path.join(os.path.dirname(autotune.__file__), "tuned_gb300.txt")
+    lines = _table_lines(path)
+    assert len(lines) >= 6
+    for i, a in enumerate(lines):
+        assert len(a) == 9 and a[1] < a[2] and a[3] <= a[4]
+        for b in lines[i + 1:]:
+            same_form = a[0] == b[0]
+            dims = a[1] < b[2] and b[1] < a[2]
+            counts = a[3] <= b[4] and b[3] <= a[4]
+            assert not (same_form and dims and counts), (a, b)
+
+
+@pytest.mark.parametrize("form,R,C,want", [
+    (0, 20, 25, (0, 0, 128)),     # the 20 x 25 workload: the tiny stabilized class
+    (1, 300, 300, (0, 0, 128)),   # the default workload: the condensed 300 x 300 class
+])
+def test_benchmark_workloads_get_their_class(form, R, C, want):
+    from paper_2510_05885_gb300 import autotune
+    path = os.path.join(os.path.dirname(autotune.__file__), "tuned_gb300.txt")
+    pat = synth.make_pattern(R, C)
+    K = nk.KKT(form, pat.n, pat.m, pat.H_rowptr, pat.H_colind, pat.J_rowptr, pat.J_colind, host_only=1,
+               autotune_path=path)
+    o = nk.ncl_kkt_get_options(K._h)
+    assert (o.persistent_fronts, o.subtree_sweeps, o.tc_min_pivots) == want
+    K.close()
