@@ -106,9 +106,10 @@ typedef struct {
                                  <= 0 selects 1e-10 (FP32_IR) or 1e-12 (FP64) */
     int32_t ir_max_iter;      /* refinement steps; < 0 selects 10 (FP32_IR) or 3 (FP64) */
     int32_t use_fgmres;       /* 1: FGMRES-IR when Richardson stagnates (default 1) */
-    int32_t use_tensor_cores; /* FP32_IR, fronts with >= 256 pivots: 2 (default) tcgen05
-                                 split-TF32 update blocks and panel trailing updates;
-                                 1: update blocks only; 0: SIMT FP32 everywhere */
+    int32_t use_tensor_cores; /* FP32_IR, fronts with >= tc_min_pivots pivots: 2
+                                 (default) tcgen05 split-TF32 update blocks and panel
+                                 trailing updates; 1: update blocks only; 0: SIMT
+                                 FP32 everywhere */
     int32_t leaf_size;        /* nested-dissection leaf size (default 96) */
     int32_t host_only;        /* 1: symbolic analysis only, no device memory; the
                                  handle then answers only the get_* queries */
@@ -144,11 +145,13 @@ typedef struct {
                                  hands over to FGMRES as soon as a step reduces the
                                  backward error by less than this factor (default
                                  0.5; values outside (0, 1] select it) */
-    int32_t subtree_sweeps;   /* 1 (default): in the triangular sweeps, every maximal
-                                 subtree of supernodes with at most 32 pivots is
-                                 swept by one warp (one launch per sweep for all of
-                                 them); 0: those supernodes go through the
-                                 per-level launches like the others */
+    int32_t subtree_sweeps;   /* 1 (default): every maximal subtree of supernodes with
+                                 at most 32 pivots (and a front that fits the
+                                 shared-memory front) is factored by one CTA and, in
+                                 the triangular sweeps, swept by one warp (one launch
+                                 each for all of them, largest subtrees first); 0:
+                                 those supernodes go through the per-level launches
+                                 like the others */
     int32_t tc_min_pivots;    /* FP32_IR: large fronts with at least this many pivots
                                  get split TF32 operands and tensor-core updates
                                  (default 256, >= 32) */
