@@ -54,3 +54,14 @@ def test_recorded_traffic_only_for_its_workload_and_source():
         got = bench.recorded_traffic(kernel, r["workload"])
         assert got == (r["traffic_bytes_per_launch"] if fresh else None), kernel
     assert bench.recorded_traffic("no_such_kernel", "condensed300") is None
+
+
+def test_tuned_table_default_and_overrides():
+    """The committed table is applied by default; 'none' or an explicit
+    cut-over setting turns it off (the table would override the setting)."""
+    assert bench.parse([]).tuned == bench.TUNED
+    assert bench.parse(["--tuned", "none"]).tuned is None
+    assert bench.parse(["--subtree-sweeps", "1"]).tuned is None
+    assert bench.parse(["--persistent-fronts", "0"]).tuned is None
+    assert bench.parse(["--tuned", "x.txt"]).tuned == "x.txt"
+
